@@ -1,0 +1,515 @@
+/*
+ * Plain FP64 CPU oracle for total variation on chains and for 2D TV-l2 (ROF)
+ * denoising by Lagrangian decomposition.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, obviously correct reference
+ * that the CUDA path is checked against. Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load it. It shares no code, headers, tables or
+ * constants with the CUDA library.
+ *
+ * Problem (eq. 1D-ROF, Sec. 6.1; Sec. 4.1 with a_i = 1, b_i = c_i):
+ *     x* = argmin_x  sum_i 1/2 (x_i - c_i)^2 + sum_{i<n} w_i |x_{i+1} - x_i|
+ * Edge i joins nodes i and i+1 (0-based here); w has one entry per edge.
+ *
+ * Algorithm: Algorithm 2 (convex DP with subgradient messages), specialised as
+ * in Sec. 4.1: messages are piecewise-linear, stored as a sequence of
+ * breakpoints lambda_p with an implicit slope s_p (true slope s_p + abar_i,
+ * abar_i = sum_{k<=i} a_k = i for a_k = 1) in a two-ended array started in its
+ * middle; the forward pass records lambda^-_i and lambda^+_i, the backward pass
+ * clips x_i = clip(x_{i+1}, lambda^-_i, lambda^+_i).
+ *
+ * Readings of the paper taken here (each is also listed in the design notes):
+ *  - After the left scan the segment to the right of the new breakpoint
+ *    lambda^- lies inside old segment ell, so it keeps slope s_ell (the printed
+ *    "s_{ell+1}" is read as an off-by-one).
+ *  - In the right-scan recursion the printed "alpha_t" is read as lambda_t.
+ *  - Node 1 has no incoming message: lambda^-_1 = c_1 - w_1, lambda^+_1 = c_1 + w_1.
+ *  - The virtual root edge has w = 0 (Algorithm 2, first step); x_n is the
+ *    midpoint of the (degenerate) interval [lambda^-_n, lambda^+_n].
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TVO_OK 0
+#define TVO_ERR_INVALID 1
+#define TVO_ERR_NOMEM 5
+#define TVO_NOT_CONVERGED 3
+
+/* One breakpoint of the current message: X-coordinate lambda_p and the stored
+ * slope s_p of the segment to its right (Sec. 4.1, "2 floating points per
+ * breakpoint"). */
+typedef struct {
+    double lam;
+    double s;
+} tvo_bp;
+
+static double edge_w(const double *w, double lam, int64_t i) { return w ? w[i] : lam; }
+
+/*
+ * Forward and backward pass on one chain of length n.
+ * c: n unary targets; w: n-1 edge weights or NULL (then every edge has weight lam).
+ * x: n outputs. lo, hi: optional n-entry records of lambda^-_i, lambda^+_i.
+ * D: scratch of at least 2n+2 breakpoints. Returns the largest sequence length seen.
+ */
+static int64_t chain_solve_core(int64_t n, const double *c, const double *w, double lam,
+                                double *x, double *lo, double *hi, tvo_bp *D)
+{
+    if (n <= 0) return 0;
+    if (n == 1) {
+        x[0] = c[0];
+        if (lo) lo[0] = c[0];
+        if (hi) hi[0] = c[0];
+        return 0;
+    }
+    /* The record of lambda^- lives in x (Sec. 4.1, last paragraph); lambda^+ in hi_rec. */
+    double *lam_minus = x;
+    double *lam_plus = hi ? hi : (double *)malloc(sizeof(double) * (size_t)n);
+    if (!lam_plus) return -1;
+
+    /* Node 1 (index 0): m^_1(z) = z - c_1 has slope a_1 = 1 everywhere. */
+    double w0 = edge_w(w, lam, 0);
+    int64_t front = n, back = n + 1; /* the sequence occupies D[front..back] */
+    D[front].lam = c[0] - w0;
+    D[front].s = 0.0;           /* true slope 1 = s + abar_1 between the two breakpoints */
+    D[back].lam = c[0] + w0;
+    D[back].s = -1.0;           /* right end: -abar_1, true slope 0 in m_{12} */
+    lam_minus[0] = D[front].lam;
+    lam_plus[0] = D[back].lam;
+    int64_t max_len = 2;
+    double w_prev = w0;
+
+    for (int64_t i = 1; i < n; ++i) {
+        const double abar = (double)(i + 1);                 /* abar_i = abar_{i-1} + a_i */
+        const double wi = (i < n - 1) ? edge_w(w, lam, i) : 0.0; /* root edge: w = 0 */
+        const double ci = c[i];
+
+        /* Left scan: largest ell with m^_i(lambda_ell) < -w_i. Values of m^_i at the
+         * breakpoints follow the forward recursion from the first one, whose incoming
+         * message value is -w_{i-1}. */
+        int64_t p = front;
+        double v = -w_prev + D[p].lam - ci;
+        int64_t last_popped;       /* entries D[front..last_popped] are removed */
+        double lm, lm_s;
+        if (v >= -wi) {
+            /* ell = 0: lambda^- lies on the left end segment, true slope a_i = 1. */
+            last_popped = front - 1;
+            lm = D[p].lam - (v + wi);
+            lm_s = 1.0 - abar;
+        } else {
+            while (p < back) {
+                double vq = v + (D[p].s + abar) * (D[p + 1].lam - D[p].lam);
+                if (vq < -wi) {
+                    ++p;
+                    v = vq;
+                } else {
+                    break;
+                }
+            }
+            /* m^_i(lambda_ell) = v < -w_i; lambda^- lies in segment ell, slope s_ell + abar. */
+            last_popped = p;
+            lm = D[p].lam + (-wi - v) / (D[p].s + abar);
+            lm_s = D[p].s;
+        }
+
+        /* Right scan over the original breakpoints with index > ell: smallest r with
+         * m^_i(lambda_r) > w_i, using the backward recursion from the last breakpoint,
+         * whose incoming message value is +w_{i-1}. */
+        double hp;
+        int64_t new_back_last; /* last original entry that is kept */
+        if (back > last_popped) {
+            int64_t q = back;
+            double vr = w_prev + D[q].lam - ci;
+            if (vr <= wi) {
+                /* r = t+1: lambda^+ lies on the right end segment, true slope 1. */
+                hp = D[q].lam + (wi - vr);
+                new_back_last = back;
+            } else {
+                for (;;) {
+                    if (q - 1 > last_popped) {
+                        double slope = D[q - 1].s + abar;
+                        double vprev = vr - slope * (D[q].lam - D[q - 1].lam);
+                        if (vprev > wi) {
+                            --q;
+                            vr = vprev;
+                            continue;
+                        }
+                        hp = D[q].lam - (vr - wi) / slope;
+                    } else {
+                        /* The segment to the left of lambda_r starts at the new lambda^-. */
+                        hp = D[q].lam - (vr - wi) / (lm_s + abar);
+                    }
+                    break;
+                }
+                new_back_last = q - 1;
+            }
+        } else {
+            /* Every original breakpoint lies left of lambda^-: m^_i is linear to its right. */
+            hp = lm + (wi + wi) / (lm_s + abar);
+            new_back_last = last_popped;
+        }
+
+        /* New sequence (-abar_i, lambda^-, s_ell, lambda_{ell+1}, ..., s_{r-1}, lambda^+, -abar_i). */
+        front = last_popped;
+        D[front].lam = lm;
+        D[front].s = lm_s;
+        back = (new_back_last > front ? new_back_last : front) + 1;
+        D[back].lam = hp;
+        D[back].s = -abar;
+        if (back - front + 1 > max_len) max_len = back - front + 1;
+
+        lam_minus[i] = lm;
+        lam_plus[i] = hp;
+        w_prev = wi;
+    }
+
+    if (lo) memcpy(lo, lam_minus, sizeof(double) * (size_t)n);
+    /* Backward pass (Algorithm 2, last loop): root value, then clip toward the leaves. */
+    x[n - 1] = 0.5 * (lam_minus[n - 1] + lam_plus[n - 1]);
+    for (int64_t i = n - 2; i >= 0; --i) {
+        double v = x[i + 1];
+        if (v < lam_minus[i]) v = lam_minus[i];
+        if (v > lam_plus[i]) v = lam_plus[i];
+        x[i] = v;
+    }
+    if (!hi) free(lam_plus);
+    return max_len;
+}
+
+/* Single chain, optional lambda^+- records (lo, hi may be NULL) and the largest
+ * message length. Returns TVO_OK or an error code. */
+int tvo_chain_solve(int64_t n, const double *c, const double *w, double lam, double *x,
+                    double *lo, double *hi, int64_t *max_len)
+{
+    if (n < 0 || !c || !x) return TVO_ERR_INVALID;
+    tvo_bp *D = (tvo_bp *)malloc(sizeof(tvo_bp) * (size_t)(2 * n + 2));
+    if (!D) return TVO_ERR_NOMEM;
+    int64_t m = chain_solve_core(n, c, w, lam, x, lo, hi, D);
+    free(D);
+    if (m < 0) return TVO_ERR_NOMEM;
+    if (max_len) *max_len = m;
+    return TVO_OK;
+}
+
+/* ---------------- batches of contiguous chains (CSR offsets), threaded ---------------- */
+
+typedef struct {
+    const double *c, *w;
+    double lam;
+    const int64_t *offsets;
+    int64_t begin, end;
+    double *x;
+    int64_t max_len;
+    int status;
+} batch_job;
+
+static void *batch_worker(void *arg)
+{
+    batch_job *j = (batch_job *)arg;
+    int64_t maxn = 0;
+    for (int64_t k = j->begin; k < j->end; ++k) {
+        int64_t n = j->offsets[k + 1] - j->offsets[k];
+        if (n > maxn) maxn = n;
+    }
+    tvo_bp *D = (tvo_bp *)malloc(sizeof(tvo_bp) * (size_t)(2 * maxn + 2));
+    if (!D) {
+        j->status = TVO_ERR_NOMEM;
+        return NULL;
+    }
+    j->max_len = 0;
+    for (int64_t k = j->begin; k < j->end; ++k) {
+        int64_t o = j->offsets[k], n = j->offsets[k + 1] - o;
+        /* w is indexed per node like c; the entry at a chain's last node is unused. */
+        int64_t m = chain_solve_core(n, j->c + o, j->w ? j->w + o : NULL, j->lam, j->x + o, NULL,
+                                     NULL, D);
+        if (m < 0) {
+            j->status = TVO_ERR_NOMEM;
+            break;
+        }
+        if (m > j->max_len) j->max_len = m;
+    }
+    free(D);
+    return NULL;
+}
+
+int tvo_chain_solve_batch(const double *c, const double *w, double lam, const int64_t *offsets,
+                          int64_t num_chains, double *x, int nthreads, int64_t *max_len)
+{
+    if (num_chains < 0 || !offsets) return TVO_ERR_INVALID;
+    for (int64_t k = 0; k < num_chains; ++k)
+        if (offsets[k + 1] < offsets[k]) return TVO_ERR_INVALID;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > num_chains) nthreads = num_chains > 0 ? (int)num_chains : 1;
+    batch_job *jobs = (batch_job *)calloc((size_t)nthreads, sizeof(batch_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) {
+        free(jobs);
+        free(th);
+        return TVO_ERR_NOMEM;
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = (batch_job){c, w, lam, offsets, num_chains * t / nthreads,
+                              num_chains * (t + 1) / nthreads, x, 0, TVO_OK};
+    }
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, batch_worker, &jobs[t]);
+    batch_worker(&jobs[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    int st = TVO_OK;
+    int64_t m = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        if (jobs[t].status != TVO_OK) st = jobs[t].status;
+        if (jobs[t].max_len > m) m = jobs[t].max_len;
+    }
+    if (max_len) *max_len = m;
+    free(jobs);
+    free(th);
+    return st;
+}
+
+/* ---------------- vector-Jacobian product of the chain prox ---------------- */
+
+/*
+ * Gradient of L(x*(c, w)) given g = dL/dx*, on one chain.
+ * Away from degenerate points the optimality conditions of eq. 1D-ROF give, on
+ * every maximal run S = [l..r] of equal values ("segment"),
+ *     x_S = mean(c_S) + (u_r - u_{l-1}) / |S|,   u_e = w_e * sign(x_{e+1} - x_e)
+ * at the jump edges bounding S (u = 0 past the chain ends). Hence
+ *     dL/dc_j = mean_{i in S(j)} g_i,
+ *     dL/dw_e = sign_e * (mean_{S left of e} g - mean_{S right of e} g) at a jump
+ *               edge e, and 0 on edges inside a segment.
+ * Two neighbours belong to one segment when |x_{e+1} - x_e| <= fuse_tol.
+ * grad_w (n-1 entries) may be NULL.
+ */
+int tvo_chain_vjp(int64_t n, const double *x, const double *g, double fuse_tol, double *grad_c,
+                  double *grad_w)
+{
+    if (n < 0 || (n > 0 && (!x || !g || !grad_c))) return TVO_ERR_INVALID;
+    int64_t l = 0;
+    double prev_mean = 0.0;
+    int64_t prev_edge = -1; /* jump edge that closes the previous segment */
+    while (l < n) {
+        int64_t r = l;
+        while (r + 1 < n && fabs(x[r + 1] - x[r]) <= fuse_tol) ++r;
+        double sum = 0.0;
+        for (int64_t i = l; i <= r; ++i) sum += g[i];
+        double mean = sum / (double)(r - l + 1);
+        for (int64_t i = l; i <= r; ++i) grad_c[i] = mean;
+        if (grad_w) {
+            for (int64_t e = l; e < r; ++e) grad_w[e] = 0.0;
+            if (prev_edge >= 0) {
+                double sgn = x[prev_edge + 1] > x[prev_edge] ? 1.0 : -1.0;
+                grad_w[prev_edge] = sgn * (prev_mean - mean);
+            }
+        }
+        prev_mean = mean;
+        prev_edge = r;
+        l = r + 1;
+    }
+    return TVO_OK;
+}
+
+/* ---------------- 2D TV-l2 by Lagrangian decomposition (eq. pd) ---------------- */
+
+typedef struct {
+    int64_t count, len;     /* number of chains and their length */
+    int64_t stride_chain;   /* distance between the first nodes of consecutive chains */
+    int64_t stride_node;    /* distance between consecutive nodes of one chain */
+    const double *c;        /* unary targets, image layout */
+    const double *w;        /* edge weights: chain k edge e at w[k*w_chain + e*w_node] */
+    int64_t w_chain, w_node;
+    double w_scale;         /* every weight is multiplied by this */
+    double lam;             /* used when w == NULL */
+    double *x;              /* solution, image layout */
+    int64_t begin, end;
+    int status;
+} phase_job;
+
+static void *phase_worker(void *arg)
+{
+    phase_job *j = (phase_job *)arg;
+    int64_t n = j->len;
+    double *cb = (double *)malloc(sizeof(double) * (size_t)n);
+    double *wb = (double *)malloc(sizeof(double) * (size_t)(n > 1 ? n - 1 : 1));
+    double *xb = (double *)malloc(sizeof(double) * (size_t)n);
+    tvo_bp *D = (tvo_bp *)malloc(sizeof(tvo_bp) * (size_t)(2 * n + 2));
+    if (!cb || !wb || !xb || !D) {
+        j->status = TVO_ERR_NOMEM;
+    } else {
+        for (int64_t k = j->begin; k < j->end; ++k) {
+            for (int64_t i = 0; i < n; ++i) cb[i] = j->c[k * j->stride_chain + i * j->stride_node];
+            for (int64_t e = 0; e + 1 < n; ++e)
+                wb[e] = j->w_scale * (j->w ? j->w[k * j->w_chain + e * j->w_node] : j->lam);
+            if (chain_solve_core(n, cb, wb, 0.0, xb, NULL, NULL, D) < 0) {
+                j->status = TVO_ERR_NOMEM;
+                break;
+            }
+            for (int64_t i = 0; i < n; ++i) j->x[k * j->stride_chain + i * j->stride_node] = xb[i];
+        }
+    }
+    free(cb);
+    free(wb);
+    free(xb);
+    free(D);
+    return NULL;
+}
+
+/* Solve every chain of one phase (all rows or all columns) on nthreads threads. */
+static int run_phase(phase_job proto, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > proto.count) nthreads = (int)proto.count;
+    phase_job jobs[256];
+    pthread_t th[256];
+    if (nthreads > 256) nthreads = 256;
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = proto;
+        jobs[t].begin = proto.count * t / nthreads;
+        jobs[t].end = proto.count * (t + 1) / nthreads;
+        jobs[t].status = TVO_OK;
+    }
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, phase_worker, &jobs[t]);
+    phase_worker(&jobs[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    for (int t = 0; t < nthreads; ++t)
+        if (jobs[t].status != TVO_OK) return jobs[t].status;
+    return TVO_OK;
+}
+
+/* Row phase: x = argmin TV_h(x) + k/2 ||x - c||^2 solved as chains with c and
+ * weights w_h / k (eq. 1D-ROF after dividing by k). */
+static int row_prox(int H, int W, const double *c, const double *wh, double lam, double k,
+                    double *x, int nthreads)
+{
+    phase_job p = {H, W, W, 1, c, wh, W - 1, 1, 1.0 / k, lam, x, 0, 0, TVO_OK};
+    return run_phase(p, nthreads);
+}
+
+/* Column phase: the same along columns with weights w_v / k. */
+static int col_prox(int H, int W, const double *c, const double *wv, double lam, double k,
+                    double *x, int nthreads)
+{
+    phase_job p = {W, H, 1, W, c, wv, 1, W, 1.0 / k, lam, x, 0, 0, TVO_OK};
+    return run_phase(p, nthreads);
+}
+
+/*
+ * Primal objective P(x) = 1/2 ||x - f||^2 + TV_h(x) + TV_v(x) of the ROF model
+ * (Sec. 6.1). wh: H*(W-1) (edge (r,c)-(r,c+1) at r*(W-1)+c); wv: (H-1)*W (edge
+ * (r,c)-(r+1,c) at r*W+c); NULL means the uniform weight lam.
+ */
+double tvo_rof_primal(int H, int W, const double *f, const double *wh, const double *wv,
+                      double lam, const double *x)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < (int64_t)H * W; ++i) s += 0.5 * (x[i] - f[i]) * (x[i] - f[i]);
+    for (int r = 0; r < H; ++r)
+        for (int c = 0; c + 1 < W; ++c)
+            s += (wh ? wh[(int64_t)r * (W - 1) + c] : lam) *
+                 fabs(x[(int64_t)r * W + c + 1] - x[(int64_t)r * W + c]);
+    for (int r = 0; r + 1 < H; ++r)
+        for (int c = 0; c < W; ++c)
+            s += (wv ? wv[(int64_t)r * W + c] : lam) *
+                 fabs(x[(int64_t)(r + 1) * W + c] - x[(int64_t)r * W + c]);
+    return s;
+}
+
+/*
+ * Accelerated primal-dual iteration (eq. pd) on the saddle-point problem
+ * eq. rof-saddle, with the two proximal maps of Sec. 6.1:
+ *   eta     = y^k + sigma_k (x^k + theta_{k-1} (x^k - x^{k-1}))
+ *   xhat    = argmin TV_v(x) + sigma_k/2 ||x - eta/sigma_k||^2   (column chains)
+ *   y^{k+1} = eta - sigma_k xhat                                  (eq. prox-tv-conj)
+ *   xi      = x^k - tau_k y^{k+1}
+ *   x^{k+1} = argmin TV_h(x) + (1+1/tau_k)/2 ||x - (f + xi/tau_k)/(1+1/tau_k)||^2  (row chains)
+ *   theta_k = 1/sqrt(1 + 2 gamma tau_k), tau_{k+1} = theta_k tau_k,
+ *   sigma_{k+1} = sigma_k / theta_k, with gamma = 1 and tau_0 sigma_0 = 1.
+ * Start: y^0 = y0 (or 0) and x^0 = x^{-1} = argmin TV_h(x) + 1/2 ||x - (f - y^0)||^2.
+ * Gap after step k (a reading: the paper plots convergence but defines no gap):
+ *   G_k = P(x^{k+1}) - D(p_h, p_v), with the dual-feasible edge fields that the two
+ *   chain solves certify, for which f - D_h^T p_h - D_v^T p_v = x^{k+1} + (x^{k+1}-x^k)/tau_k:
+ *   G_k = 1/2||x^{k+1}-f||^2 + TV(x^{k+1}) - 1/2||f||^2 + 1/2||x^{k+1} + (x^{k+1}-x^k)/tau_k||^2.
+ * Stops at the first k with G_k / (H W) <= tol; returns x^{k+1} and k+1 iterations.
+ * gap_trace (max_iters entries, optional) receives G_k / (H W).
+ */
+int tvo_tv2d_pd(int H, int W, const double *f, const double *wh, const double *wv, double lam,
+                const double *y0, int max_iters, double tol, double tau0, int nthreads,
+                double *x_out, int *iters_out, double *gap_trace, double *y_out)
+{
+    if (H < 1 || W < 1 || !f || !x_out || max_iters < 0 || !(tau0 > 0.0)) return TVO_ERR_INVALID;
+    int64_t N = (int64_t)H * W;
+    double *x = (double *)calloc((size_t)N, sizeof(double));
+    double *xp = (double *)calloc((size_t)N, sizeof(double));
+    double *y = (double *)calloc((size_t)N, sizeof(double));
+    double *c = (double *)calloc((size_t)N, sizeof(double));
+    double *xh = (double *)calloc((size_t)N, sizeof(double));
+    int st = TVO_OK;
+    if (!x || !xp || !y || !c || !xh) {
+        st = TVO_ERR_NOMEM;
+        goto done;
+    }
+    if (y0) memcpy(y, y0, sizeof(double) * (size_t)N);
+    for (int64_t i = 0; i < N; ++i) c[i] = f[i] - y[i];
+    if ((st = row_prox(H, W, c, wh, lam, 1.0, x, nthreads)) != TVO_OK) goto done;
+    memcpy(xp, x, sizeof(double) * (size_t)N);
+
+    double tau = tau0, sigma = 1.0 / tau0, theta_prev = 1.0;
+    double half_f2 = 0.0;
+    for (int64_t i = 0; i < N; ++i) half_f2 += 0.5 * f[i] * f[i];
+    int k;
+    st = TVO_NOT_CONVERGED;
+    for (k = 0; k < max_iters; ++k) {
+        /* dual step: column chains via the Moreau identity */
+        for (int64_t i = 0; i < N; ++i) {
+            double eta = y[i] + sigma * (x[i] + theta_prev * (x[i] - xp[i]));
+            y[i] = eta; /* eta kept in y until the chain solve returns */
+            c[i] = eta / sigma;
+        }
+        int s2 = col_prox(H, W, c, wv, lam, sigma, xh, nthreads);
+        if (s2 != TVO_OK) {
+            st = s2;
+            goto done;
+        }
+        for (int64_t i = 0; i < N; ++i) y[i] = y[i] - sigma * xh[i];
+        /* primal step: row chains */
+        double kk = 1.0 + 1.0 / tau;
+        for (int64_t i = 0; i < N; ++i) {
+            double xi = x[i] - tau * y[i];
+            c[i] = (f[i] + xi / tau) / kk;
+        }
+        memcpy(xp, x, sizeof(double) * (size_t)N);
+        s2 = row_prox(H, W, c, wh, lam, kk, x, nthreads);
+        if (s2 != TVO_OK) {
+            st = s2;
+            goto done;
+        }
+        /* gap of (x^{k+1}, certified duals) */
+        double g = tvo_rof_primal(H, W, f, wh, wv, lam, x) - half_f2;
+        for (int64_t i = 0; i < N; ++i) {
+            double z = x[i] + (x[i] - xp[i]) / tau;
+            g += 0.5 * z * z;
+        }
+        if (gap_trace) gap_trace[k] = g / (double)N;
+        /* step sizes of the accelerated variant */
+        double theta = 1.0 / sqrt(1.0 + 2.0 * tau);
+        tau = theta * tau;
+        sigma = sigma / theta;
+        theta_prev = theta;
+        if (g / (double)N <= tol) {
+            st = TVO_OK;
+            ++k;
+            break;
+        }
+    }
+    if (iters_out) *iters_out = k;
+    memcpy(x_out, x, sizeof(double) * (size_t)N);
+    if (y_out) memcpy(y_out, y, sizeof(double) * (size_t)N);
+done:
+    free(x);
+    free(xp);
+    free(y);
+    free(c);
+    free(xh);
+    return st;
+}

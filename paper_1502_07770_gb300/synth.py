@@ -1,0 +1,122 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module draws random numbers and builds arrays; it contains none of the
+total-variation arithmetic (no message passing, no proximal steps, no gap).
+Every generator draws in float64 from numpy's PCG64 and returns float32 arrays,
+so both sides of a parity test consume bit-identical inputs.
+
+Workload shapes follow the experiments of Sec. 6 of the paper (noisy piecewise-
+constant 1D signals as in the step-function experiment of Sec. 6.1, and noisy
+piecewise-constant 2D images as in the ROF experiment of Sec. 6.1); the paper's
+own test image and signal lengths are not available, so these stand in for them.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def piecewise_constant_chain(n: int, seed: int, seg_lo: int = 8, seg_hi: int = 64,
+                             noise: float = 0.1) -> np.ndarray:
+    """One noisy step signal of length ``n``.
+
+    Segment lengths are drawn uniformly from the integers ``seg_lo..seg_hi``,
+    segment levels uniformly from [0, 1], and i.i.d. Gaussian noise of standard
+    deviation ``noise`` is added (the step-function workload of Sec. 6.1).
+    """
+    rng = _rng(seed)
+    out = np.empty(n, dtype=np.float64)
+    pos = 0
+    while pos < n:
+        length = int(rng.integers(seg_lo, seg_hi + 1))
+        out[pos:pos + length] = rng.uniform(0.0, 1.0)
+        pos += length
+    out += rng.normal(0.0, noise, size=n)
+    return out.astype(np.float32)
+
+
+def chain_batch(num_chains: int, n: int, seed0: int = 0, **kw) -> np.ndarray:
+    """``num_chains`` independent step signals of length ``n``, chain ``k`` seeded
+    with ``seed0 + k``; returned as a C-contiguous (num_chains, n) float32 array."""
+    out = np.empty((num_chains, n), dtype=np.float32)
+    for k in range(num_chains):
+        out[k] = piecewise_constant_chain(n, seed0 + k, **kw)
+    return out
+
+
+def ragged_chain_batch(lengths, seed0: int = 0, **kw):
+    """Chains of the given lengths concatenated into one float32 vector, plus the
+    int64 CSR offsets (length ``len(lengths) + 1``)."""
+    lengths = [int(v) for v in lengths]
+    offsets = np.zeros(len(lengths) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(lengths)
+    y = np.empty(int(offsets[-1]), dtype=np.float32)
+    for k, n in enumerate(lengths):
+        if n:
+            y[offsets[k]:offsets[k + 1]] = piecewise_constant_chain(n, seed0 + k, **kw)
+    return y, offsets
+
+
+def shapes_image(H: int, W: int, seed: int, n_shapes: int = 200, noise: float = 0.1,
+                 background: float = 0.5) -> tuple[np.ndarray, np.ndarray]:
+    """A noisy image of random axis-aligned rectangles and disks.
+
+    Background ``background``; ``n_shapes`` shapes painted in order, each a
+    rectangle (sides uniform in [W/32, W/4] and [H/32, H/4]) or a disk (radius
+    uniform in [W/64, W/8]) with a uniform centre and a level uniform in [0, 1].
+    Returns ``(clean, noisy)`` as float32 (H, W) arrays; the noisy one adds
+    i.i.d. Gaussian noise of standard deviation ``noise`` and is not clipped.
+    """
+    rng = _rng(seed)
+    img = np.full((H, W), background, dtype=np.float64)
+    rr = np.arange(H, dtype=np.float64)[:, None]
+    cc = np.arange(W, dtype=np.float64)[None, :]
+    for _ in range(n_shapes):
+        level = rng.uniform(0.0, 1.0)
+        cy = rng.uniform(0.0, H)
+        cx = rng.uniform(0.0, W)
+        if rng.uniform() < 0.5:
+            hh = 0.5 * rng.uniform(H / 32.0, H / 4.0)
+            hw = 0.5 * rng.uniform(W / 32.0, W / 4.0)
+            y0, y1 = int(max(0, np.floor(cy - hh))), int(min(H, np.ceil(cy + hh)))
+            x0, x1 = int(max(0, np.floor(cx - hw))), int(min(W, np.ceil(cx + hw)))
+            img[y0:y1, x0:x1] = level
+        else:
+            rad = rng.uniform(W / 64.0, W / 8.0)
+            y0, y1 = int(max(0, np.floor(cy - rad))), int(min(H, np.ceil(cy + rad + 1)))
+            x0, x1 = int(max(0, np.floor(cx - rad))), int(min(W, np.ceil(cx + rad + 1)))
+            sub = (rr[y0:y1] - cy) ** 2 + (cc[:, x0:x1] - cx) ** 2 <= rad * rad
+            img[y0:y1, x0:x1][sub] = level
+    noisy = img + rng.normal(0.0, noise, size=(H, W))
+    return img.astype(np.float32), noisy.astype(np.float32)
+
+
+def edge_aware_weights(f: np.ndarray, lam: float, scale: float = 0.2):
+    """Per-edge weights ``lam * exp(-|f_i - f_j| / scale)`` of a float32 image.
+
+    Returns ``(w_h, w_v)``: ``w_h`` of shape (H, W-1) for the edge between
+    pixels (r, c) and (r, c+1), ``w_v`` of shape (H-1, W) for the edge between
+    (r, c) and (r+1, c); both float32, computed in float64 from ``f``.
+    """
+    f64 = f.astype(np.float64)
+    w_h = lam * np.exp(-np.abs(np.diff(f64, axis=1)) / scale)
+    w_v = lam * np.exp(-np.abs(np.diff(f64, axis=0)) / scale)
+    return w_h.astype(np.float32), w_v.astype(np.float32)
+
+
+def uneven_image_sizes(count: int, seed: int, w_range=(128, 2048), h_range=(96, 1536)):
+    """``count`` image sizes (H, W) with W and H drawn independently and uniformly
+    from the given integer ranges, plus per-image lambda uniform in [0.05, 0.3]."""
+    rng = _rng(seed)
+    Ws = rng.integers(w_range[0], w_range[1] + 1, size=count)
+    Hs = rng.integers(h_range[0], h_range[1] + 1, size=count)
+    lams = rng.uniform(0.05, 0.3, size=count)
+    return [(int(h), int(w)) for h, w in zip(Hs, Ws)], [float(v) for v in lams]
+
+
+def gaussian_vector(n: int, seed: int) -> np.ndarray:
+    """i.i.d. N(0, 1) float32 vector (the loss weights of the differentiable-prox workload)."""
+    return _rng(seed).normal(0.0, 1.0, size=n).astype(np.float32)
