@@ -1,0 +1,142 @@
+/*
+ * tv.h -- C ABI of the GB300 (sm_103a) total-variation library.
+ *
+ * The library solves, in batches on one GPU,
+ *   (1) TV-l2 problems on chains (eq. 1D-ROF, Sec. 6.1)
+ *           x* = argmin_x  sum_i 1/2 (x_i - y_i)^2 + sum_{i<n} w_i |x_{i+1} - x_i|
+ *       by the dynamic program of Algorithm 2 specialised to quadratic unaries
+ *       as in Sec. 4.1 (forward messages stored as breakpoint sequences with an
+ *       implicit slope, backward clip x_i = clip(x_{i+1}, lambda^-_i, lambda^+_i));
+ *   (2) the 2D ROF model of Sec. 6.1 (TV-l2 denoising on a 4-connected grid) by the
+ *       Lagrangian decomposition eq. rof-saddle solved with the accelerated
+ *       primal-dual iteration eq. pd, whose two proximal steps are the row chains
+ *       (TV_h) and the column chains (TV_v, via the Moreau identity eq. prox-tv-conj).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named d_* are DEVICE pointers; the caller owns every buffer and the
+ *    library never frees caller memory nor allocates device memory: all scratch
+ *    comes from the caller's workspace, sized by the *_workspace_size queries.
+ *  - Arrays are float32, C-contiguous. An edge weight w_i belongs to the edge
+ *    between node i and node i+1 of a chain.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Chain calls are
+ *    asynchronous and stream-ordered; tv2d_denoise returns after the solve has
+ *    finished (it reads back the iteration count and the gap).
+ *  - Argument errors are reported before any launch with TV_ERR_INVALID and leave
+ *    every output untouched. Errors found on the device (malformed offsets) are
+ *    recorded in the workspace and read back with tv_workspace_status.
+ *  - A CUDA error (including a sticky one from earlier work) returns TV_ERR_CUDA.
+ *  - tv_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef TV_GB300_TV_H
+#define TV_GB300_TV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TV_OK = 0,
+    TV_ERR_INVALID = 1,        /* bad argument, or malformed offsets found on the device */
+    TV_ERR_CUDA = 2,           /* a CUDA runtime call or launch failed */
+    TV_ERR_NOT_CONVERGED = 3,  /* tv2d_denoise stopped at max_iters above gap_tol */
+    TV_ERR_TIMEOUT = 4,        /* reserved: a bounded device wait gave up */
+    TV_ERR_NOMEM = 5           /* the workspace is smaller than the size query asked for */
+} tv_status;
+
+typedef void *tv_stream_t; /* cudaStream_t */
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *tv_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int tv_version(void);
+
+/* ---------------------------------------------------------------- chains ---- */
+
+/*
+ * Bytes of workspace tv_chain_solve needs for `num_chains` chains of at most
+ * `max_len` nodes (about 24 bytes per node of num_chains * max_len). The workspace
+ * holds the per-node records lambda^-_i, lambda^+_i of the forward pass (Sec. 4.1,
+ * "Backward pass", 8 bytes per node) and a reserve for message sequences that
+ * outgrow on-chip storage (at most 2n+2 breakpoints of 8 bytes per chain, the
+ * bound of Sec. 4.1); the reserve is touched only by chains that need it.
+ */
+size_t tv_chain_workspace_size(int64_t num_chains, int64_t max_len);
+
+/*
+ * Solve eq. 1D-ROF on every chain of a batch of contiguous chains.
+ *   d_y        node values, chain k at d_y[off_k .. off_{k+1}-1]
+ *   d_w        per-node edge weights laid out like d_y (the entry at a chain's last
+ *              node is not read), or NULL: every edge then has weight `lambda`
+ *   lambda     uniform edge weight (used iff d_w == NULL); must be >= 0 and finite
+ *   d_offsets  num_chains+1 monotone int64 offsets on the DEVICE, or NULL: chain k
+ *              then spans [k*max_len, (k+1)*max_len) (a uniform batch)
+ *   max_len    upper bound on every chain length (the uniform length if d_offsets
+ *              is NULL); a chain longer than this is skipped and flagged
+ *   d_x        output, same layout as d_y; must not overlap d_y or d_w
+ * Empty chains and chains of one node (x = y) are allowed. Weights must be >= 0.
+ */
+tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
+                         const int64_t *d_offsets, int64_t num_chains, int64_t max_len,
+                         float *d_x, void *d_workspace, size_t workspace_bytes,
+                         tv_stream_t stream);
+
+/* Bytes of workspace tv_chain_solve_columns needs for an H x W array. */
+size_t tv_columns_workspace_size(int64_t H, int64_t W);
+
+/*
+ * Solve eq. 1D-ROF on the W column chains of an H x W row-major array with
+ * leading dimension ld >= W (node i of column c at d_y[i*ld + c]). These are the
+ * chains of the TV_v proximal step of Sec. 6.1.
+ *   d_w   per-node edge weights in the same layout (row H-1 is not read), or NULL
+ *   d_x   output in the same layout; must not overlap d_y or d_w
+ */
+tv_status tv_chain_solve_columns(const float *d_y, const float *d_w, float lambda, int64_t H,
+                                 int64_t W, int64_t ld, float *d_x, void *d_workspace,
+                                 size_t workspace_bytes, tv_stream_t stream);
+
+/*
+ * Read back and clear the device-side error word of a workspace used by the chain
+ * calls above (synchronises `stream`). *d_status_out receives TV_OK or
+ * TV_ERR_INVALID (a chain longer than max_len, or decreasing offsets). When
+ * overflowed != NULL it receives how many chains outgrew on-chip message storage
+ * and were finished from the workspace reserve (a performance counter).
+ */
+tv_status tv_workspace_status(void *d_workspace, tv_stream_t stream, int *status_out,
+                              int64_t *overflowed);
+
+/* ------------------------------------------------------------------- 2D ---- */
+
+/* Bytes of workspace tv2d_denoise needs for an H x W image and max_iters iterations. */
+size_t tv2d_workspace_size(int64_t H, int64_t W, int max_iters);
+
+/*
+ * 2D TV-l2 (ROF) denoising, Sec. 6.1:
+ *     x* = argmin_x 1/2 ||x - img||^2 + TV_h(x) + TV_v(x)
+ * solved by the accelerated primal-dual iteration eq. pd with tau_0 = sigma_0 = 1,
+ * gamma = 1, x^0 the row-chain solution at img - y^0, and the stopping rule
+ * G_k / (H W) <= gap_tol on the primal-dual gap G_k of (x^{k+1}, the dual fields
+ * certified by the two chain steps).
+ *   d_img     H x W row-major image
+ *   d_wh      H x (W-1) horizontal edge weights (edge (r,c)-(r,c+1) at r*(W-1)+c), or NULL
+ *   d_wv      (H-1) x W vertical edge weights (edge (r,c)-(r+1,c) at r*W+c), or NULL
+ *   lambda    uniform weight for whichever of d_wh / d_wv is NULL (>= 0)
+ *   d_y0      optional H x W initial dual y^0 (a warm start), or NULL for y^0 = 0
+ *   max_iters iteration limit (>= 0)
+ *   gap_tol   per-pixel gap tolerance (> 0, or 0 to run exactly max_iters iterations)
+ *   d_x       output H x W (must not overlap the inputs)
+ *   iters_out, gap_out  optional HOST pointers: iterations run, final per-pixel gap
+ * Returns TV_OK when converged, TV_ERR_NOT_CONVERGED (x still written) otherwise.
+ */
+tv_status tv2d_denoise(const float *d_img, int64_t H, int64_t W, const float *d_wh,
+                       const float *d_wv, float lambda, const float *d_y0, int max_iters,
+                       double gap_tol, float *d_x, int *iters_out, double *gap_out,
+                       void *d_workspace, size_t workspace_bytes, tv_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,19 @@
+"""GB300-native total variation on chains and 2D TV-l2 denoising.
+
+Implements the O(n) chain dynamic program of "Total variation on a tree"
+(Algorithm 2 with the quadratic-unary specialisation of Sec. 4.1) as batched
+sm_103a CUDA kernels behind a C ABI (``include/tv.h``), and the paper's 2D
+Lagrangian-decomposition primal-dual ROF solver (Sec. 6.1) built on it.
+
+The CUDA binding is imported lazily so that ``synth`` (input generators) can
+be used without a GPU.
+"""
+__all__ = ["chain_prox", "chain_prox_columns", "tv2d_denoise", "workspace_status", "synth"]
+
+
+def __getattr__(name):
+    if name in ("chain_prox", "chain_prox_columns", "tv2d_denoise", "workspace_status", "load",
+                "TVError"):
+        from . import _lib
+        return getattr(_lib, name)
+    raise AttributeError(name)

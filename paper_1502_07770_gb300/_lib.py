@@ -1,0 +1,184 @@
+"""ctypes binding of ``libtv.so`` (the C ABI declared in ``include/tv.h``).
+
+Argument marshalling only: every step of every solve runs in the library's
+CUDA kernels. Tensors are torch CUDA tensors; their device pointers and the
+current torch stream are handed to the C entry points. Workspaces are
+allocated here with torch and reused across calls of the same size.
+
+There is no CPU fallback: if the library cannot be built or loaded, or no CUDA
+device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+TV_OK, TV_ERR_INVALID, TV_ERR_CUDA, TV_ERR_NOT_CONVERGED, TV_ERR_TIMEOUT, TV_ERR_NOMEM = range(6)
+
+_lock = threading.Lock()
+_lib = None
+
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_sz = ctypes.c_size_t
+
+# name -> (restype, argtypes), mirroring include/tv.h
+SIGNATURES = {
+    "tv_last_error": (ctypes.c_char_p, []),
+    "tv_version": (ctypes.c_int, []),
+    "tv_chain_workspace_size": (_sz, [_i64, _i64]),
+    "tv_chain_solve": (ctypes.c_int, [_p, _p, ctypes.c_float, _p, _i64, _i64, _p, _p, _sz, _p]),
+    "tv_columns_workspace_size": (_sz, [_i64, _i64]),
+    "tv_chain_solve_columns": (ctypes.c_int,
+                               [_p, _p, ctypes.c_float, _i64, _i64, _i64, _p, _p, _sz, _p]),
+    "tv_workspace_status": (ctypes.c_int, [_p, _p, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(_i64)]),
+    "tv2d_workspace_size": (_sz, [_i64, _i64, ctypes.c_int]),
+    "tv2d_denoise": (ctypes.c_int, [_p, _i64, _i64, _p, _p, ctypes.c_float, _p, ctypes.c_int,
+                                    ctypes.c_double, _p, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_double), _p, _sz, _p]),
+}
+
+
+class TVError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"tv status {status}: {msg}")
+        self.status = status
+
+
+def load(build_if_needed: bool = True):
+    """Load ``libtv.so`` (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_needed and (not os.path.exists(path) or _build.stale()):
+                _build.build()
+            if not os.path.exists(path):
+                raise ImportError(f"libtv.so is not built ({path})")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != TV_OK:
+        raise TVError(status, load().tv_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _require_cuda(*tensors):
+    if not torch.cuda.is_available():
+        raise RuntimeError("the TV library needs a CUDA device; there is no CPU fallback")
+    for t in tensors:
+        if t is None:
+            continue
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError("inputs must be contiguous float32 CUDA tensors")
+
+
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device, key: str = "default") -> torch.Tensor:
+    """A cached uint8 device buffer of at least ``nbytes`` bytes."""
+    dev = torch.device(device)
+    k = (key, dev.index)
+    buf = _ws_cache.get(k)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+        _ws_cache[k] = buf
+    return buf
+
+
+def chain_prox(y, w=None, lam: float = 0.0, offsets=None, max_len: int | None = None,
+               out=None, ws=None):
+    """Solve eq. 1D-ROF on a batch of contiguous chains.
+
+    ``y``: (B, n) tensor of B chains of length n, or a flat tensor with int64
+    ``offsets`` (B+1, on the same device) and ``max_len``. ``w``: per-node edge
+    weights laid out like ``y`` (last node of each chain unused), or None for
+    the uniform weight ``lam``.
+    """
+    lib = load()
+    _require_cuda(y, w)
+    if offsets is None:
+        if y.dim() != 2:
+            raise ValueError("y must be (num_chains, n) without offsets")
+        num_chains, n = y.shape
+        max_len = n
+        offp = None
+    else:
+        if offsets.dtype != torch.int64 or not offsets.is_cuda:
+            raise ValueError("offsets must be an int64 CUDA tensor")
+        num_chains = offsets.numel() - 1
+        if max_len is None:
+            raise ValueError("max_len is required with offsets")
+        offp = _ptr(offsets)
+    x = torch.empty_like(y) if out is None else out
+    nbytes = lib.tv_chain_workspace_size(num_chains, max_len)
+    wsb = ws if ws is not None else workspace(nbytes, y.device, "chain")
+    _check(lib.tv_chain_solve(_ptr(y), _ptr(w), float(lam), offp, num_chains, max_len, _ptr(x),
+                              _ptr(wsb), wsb.numel(), _stream(y.device)))
+    return x
+
+
+def chain_prox_columns(y, w=None, lam: float = 0.0, out=None, ws=None):
+    """Solve eq. 1D-ROF on the columns of a row-major (H, W) tensor."""
+    lib = load()
+    _require_cuda(y, w)
+    H, W = y.shape
+    x = torch.empty_like(y) if out is None else out
+    nbytes = lib.tv_columns_workspace_size(H, W)
+    wsb = ws if ws is not None else workspace(nbytes, y.device, "cols")
+    _check(lib.tv_chain_solve_columns(_ptr(y), _ptr(w), float(lam), H, W, W, _ptr(x), _ptr(wsb),
+                                      wsb.numel(), _stream(y.device)))
+    return x
+
+
+def workspace_status(ws, device=None):
+    """(status, overflowed chains) of a chain workspace; clears the device word."""
+    lib = load()
+    st = ctypes.c_int(0)
+    ov = ctypes.c_int64(0)
+    _check(lib.tv_workspace_status(_ptr(ws), _stream(ws.device), ctypes.byref(st),
+                                   ctypes.byref(ov)))
+    return st.value, ov.value
+
+
+def tv2d_denoise(img, lam: float = 0.1, w_h=None, w_v=None, y0=None, max_iters: int = 200,
+                 tol: float = 1e-4, out=None, ws=None):
+    """2D TV-l2 (ROF) denoising by the primal-dual Lagrangian decomposition.
+
+    Returns ``(x, iterations, per-pixel gap, converged)``.
+    """
+    lib = load()
+    _require_cuda(img, w_h, w_v, y0)
+    H, W = img.shape
+    x = torch.empty_like(img) if out is None else out
+    nbytes = lib.tv2d_workspace_size(H, W, int(max_iters))
+    wsb = ws if ws is not None else workspace(nbytes, img.device, "tv2d")
+    it = ctypes.c_int(0)
+    gap = ctypes.c_double(0.0)
+    st = lib.tv2d_denoise(_ptr(img), H, W, _ptr(w_h), _ptr(w_v), float(lam), _ptr(y0),
+                          int(max_iters), float(tol), _ptr(x), ctypes.byref(it),
+                          ctypes.byref(gap), _ptr(wsb), wsb.numel(), _stream(img.device))
+    if st not in (TV_OK, TV_ERR_NOT_CONVERGED):
+        _check(st)
+    return x, it.value, gap.value, st == TV_OK

@@ -1,0 +1,587 @@
+// 2D TV-l2 (ROF) denoising by Lagrangian decomposition (Sec. 6.1): the
+// accelerated primal-dual iteration eq. pd on the saddle-point problem
+// eq. rof-saddle, where both proximal maps are batches of chain problems.
+//
+// Per iteration k, two fused kernels run the chain dynamic program of
+// Algorithm 2 / Sec. 4.1 with the proximal arithmetic folded into their loads
+// and stores:
+//   column (dual) phase, one thread per image column:
+//       eta = y + sigma_k (x^k + theta_{k-1} (x^k - x^{k-1}))
+//       xhat = argmin TV_v(x) + sigma_k/2 ||x - eta/sigma_k||^2  (chains: c = eta/sigma_k,
+//              w' = w_v/sigma_k)
+//       y <- eta - sigma_k xhat                                   (eq. prox-tv-conj)
+//     and, from the same loads, the terms of the primal-dual gap G_{k-1};
+//   row (primal) phase, one thread per image row:
+//       x^{k+1} = argmin TV_h(x) + (1+1/tau_k)/2 ||x - (f + (x^k - tau_k y)/tau_k)/(1+1/tau_k)||^2
+//              (chains: c = (tau f + x^k - tau y)/(tau+1), w' = w_h tau/(tau+1)).
+// Step sizes follow the accelerated variant: theta_k = 1/sqrt(1+2 tau_k),
+// tau_{k+1} = theta_k tau_k, sigma_{k+1} = sigma_k/theta_k, tau_0 = sigma_0 = 1.
+//
+// Gap (the paper plots convergence but does not define its gap): with the edge
+// fields p_h, p_v that the two chain solves certify (|p| <= w, D_v^T p_v = y^{k+1},
+// f - D_h^T p_h - D_v^T p_v = x^{k+1} + (x^{k+1} - x^k)/tau_k),
+//   G_k = P(x^{k+1}) - D(p) = 1/2||x^{k+1} - f||^2 + TV(x^{k+1}) - 1/2||f||^2
+//         + 1/2||x^{k+1} + (x^{k+1} - x^k)/tau_k||^2 >= 0.
+// The column phase of iteration k+1 reads exactly x^{k+1}, x^k and f, and has
+// vertical neighbours along its chains and horizontal ones across its lanes, so
+// it accumulates G_k per pixel; the last warp to finish reduces the partials in
+// FP64 (fixed order) and raises the stop flag. Later kernels see the flag and
+// return at once, so a batch of launched iterations costs nothing after it.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "tv_dp.cuh"
+#include "tv_host.h"
+
+using namespace tvk;
+using namespace tvh;
+
+namespace {
+
+constexpr int kRing = 32;
+
+struct Tv2dState {
+    int k;                // completed primal (row) steps
+    int done;             // per-pixel gap reached the tolerance
+    unsigned ticket_col;  // warps finished in the running column phase
+    unsigned ticket_row;  // warps finished in the running row phase
+    int max_iters;
+    int gap_k;            // index of the last gap written (-1: none yet)
+    double tol;           // per-pixel tolerance; 0 never stops early
+    double inv_N;         // 1 / (H W)
+    double gap;           // last per-pixel gap G_{gap_k} / (H W)
+};
+
+struct Tv2dParams {
+    double tau, sigma, theta_prev, tau_prev;  // tau_k, sigma_k, theta_{k-1}, tau_{k-1}
+};
+
+__global__ void tv2d_init_state(Tv2dState *st, Tv2dParams *prm, int max_iters, double tol,
+                                double inv_N)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    st->k = 0;
+    st->done = 0;
+    st->ticket_col = 0;
+    st->ticket_row = 0;
+    st->max_iters = max_iters;
+    st->gap_k = -1;
+    st->tol = tol;
+    st->inv_N = inv_N;
+    st->gap = nan("");
+    double tau = 1.0, sigma = 1.0, theta_prev = 0.0, tau_prev = 1.0;
+    for (int k = 0; k <= max_iters; ++k) {
+        prm[k] = Tv2dParams{tau, sigma, theta_prev, tau_prev};
+        const double theta = 1.0 / sqrt(1.0 + 2.0 * tau);
+        tau_prev = tau;
+        tau *= theta;
+        sigma /= theta;
+        theta_prev = theta;
+    }
+}
+
+// Warp-level completion counter: returns true in lane 0 of the last warp of the grid.
+__device__ __forceinline__ bool last_warp_done(unsigned *ticket, int lane)
+{
+    bool last = false;
+    if (lane == 0) {
+        __threadfence();
+        const unsigned total = gridDim.x * (blockDim.x / WARP);
+        last = atomicAdd(ticket, 1u) == total - 1;
+        if (last) {
+            __threadfence();
+            *ticket = 0;
+        }
+    }
+    return last;
+}
+
+// ---------------------------------------------------------------- x^0 --------
+// x^0 = argmin TV_h(x) + 1/2 ||x - (f - y^0)||^2: row chains with c = f - y, w = w_h.
+template <bool HAS_WH>
+struct InitRowsP {
+    static constexpr bool COLS = false;
+    static constexpr int NIN = HAS_WH ? 3 : 2;
+    static constexpr bool NEIGH = false;
+    static constexpr bool CREC = false;
+    static constexpr int NOUT = 2;
+    struct Acc {};
+
+    const float *f, *y, *wh;
+    float lam;
+    long long H, W;
+    float *x0, *x1;
+
+    __device__ bool resolve() { return true; }
+    __device__ long long num_chains() const { return H; }
+    __device__ int max_len() const { return (int)W; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        start = k * W;
+        n = (int)W;
+        return true;
+    }
+    __device__ const float *in_ptr(int a) const { return a == 0 ? f : (a == 1 ? y : wh); }
+    __device__ long long in_off(int a, long long k, long long start) const
+    {
+        return a == 2 ? k * (W - 1) : start;
+    }
+    __device__ int in_lim(int a, int n) const { return a == 2 ? n - 1 : n; }
+    __device__ long long in_ld(int) const { return 1; }
+    __device__ long long in_kmax(int) const { return H; }
+    template <class IN>
+    __device__ void unary(const IN &in, int b, int j, int lane, int i, int n, long long, float &c,
+                          float &w, Acc &) const
+    {
+        c = in[0][b][lane][j] - in[1][b][lane][j];
+        if constexpr (HAS_WH) w = (i < n - 1) ? in[2][b][lane][j] : 0.f;
+        else w = (i < n - 1) ? lam : 0.f;
+    }
+    __device__ void unary_direct(int i, int n, long long k, long long start, float &c,
+                                 float &w) const
+    {
+        c = f[start + i] - y[start + i];
+        if constexpr (HAS_WH) w = (i < n - 1) ? wh[k * (W - 1) + i] : 0.f;
+        else w = (i < n - 1) ? lam : 0.f;
+    }
+    __device__ float *out_ptr(int o) const { return o == 0 ? x0 : x1; }
+    __device__ long long out_off(int, long long, long long start) const { return start; }
+    __device__ void emit_cols(int, long long, float, float) const {}
+    __device__ void emit_direct(int i, long long, long long start, float xv, float) const
+    {
+        x0[start + i] = xv;
+        x1[start + i] = xv;
+    }
+    __device__ long long spill_off(long long k, long long) const { return k * (2 * W + 2); }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &) const {}
+    __device__ void finish_empty() const {}
+};
+
+// ---------------------------------------------------------- primal step ------
+template <bool HAS_WH>
+struct RowPhaseP {
+    static constexpr bool COLS = false;
+    static constexpr int NIN = HAS_WH ? 4 : 3;
+    static constexpr bool NEIGH = false;
+    static constexpr bool CREC = false;
+    static constexpr int NOUT = 1;
+    struct Acc {};
+
+    const float *f, *y, *wh;
+    float lam;
+    long long H, W;
+    float *buf0, *buf1;
+    Tv2dState *st;
+    const Tv2dParams *prm;
+    // resolved per launch from the device state
+    const float *xin;
+    float *xout;
+    float ca, cb;  // c = ca (f - y) + cb x^k, w' = ca w
+
+    __device__ bool resolve()
+    {
+        const int k = st->k;
+        if (st->done || k >= st->max_iters) return false;
+        xin = (k & 1) ? buf1 : buf0;
+        xout = (k & 1) ? buf0 : buf1;
+        const double tau = prm[k].tau;
+        ca = (float)(tau / (tau + 1.0));
+        cb = (float)(1.0 / (tau + 1.0));
+        return true;
+    }
+    __device__ long long num_chains() const { return H; }
+    __device__ int max_len() const { return (int)W; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        start = k * W;
+        n = (int)W;
+        return true;
+    }
+    __device__ const float *in_ptr(int a) const
+    {
+        return a == 0 ? f : (a == 1 ? xin : (a == 2 ? y : wh));
+    }
+    __device__ long long in_off(int a, long long k, long long start) const
+    {
+        return a == 3 ? k * (W - 1) : start;
+    }
+    __device__ int in_lim(int a, int n) const { return a == 3 ? n - 1 : n; }
+    __device__ long long in_ld(int) const { return 1; }
+    __device__ long long in_kmax(int) const { return H; }
+    __device__ __forceinline__ void unary_vals(float fv, float xv, float yv, float wv, int i, int n,
+                                               float &c, float &w) const
+    {
+        c = ca * (fv - yv) + cb * xv;
+        w = (i < n - 1) ? ca * wv : 0.f;
+    }
+    template <class IN>
+    __device__ void unary(const IN &in, int b, int j, int lane, int i, int n, long long, float &c,
+                          float &w, Acc &) const
+    {
+        float wv = lam;
+        if constexpr (HAS_WH) wv = in[3][b][lane][j];
+        unary_vals(in[0][b][lane][j], in[1][b][lane][j], in[2][b][lane][j], wv, i, n, c, w);
+    }
+    __device__ void unary_direct(int i, int n, long long k, long long start, float &c,
+                                 float &w) const
+    {
+        float wv = lam;
+        if constexpr (HAS_WH) wv = (i < n - 1) ? wh[k * (W - 1) + i] : 0.f;
+        unary_vals(f[start + i], xin[start + i], y[start + i], wv, i, n, c, w);
+    }
+    __device__ float *out_ptr(int) const { return xout; }
+    __device__ long long out_off(int, long long, long long start) const { return start; }
+    __device__ void emit_cols(int, long long, float, float) const {}
+    __device__ void emit_direct(int i, long long, long long start, float xv, float) const
+    {
+        xout[start + i] = xv;
+    }
+    __device__ long long spill_off(long long k, long long) const { return k * (2 * W + 2); }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void count_done() const
+    {
+        const int lane = threadIdx.x & (WARP - 1);
+        if (last_warp_done(&st->ticket_row, lane)) st->k = st->k + 1;
+    }
+    __device__ void finish(Acc &) const { count_done(); }
+    __device__ void finish_empty() const { count_done(); }
+};
+
+// ------------------------------------------------------------ dual step ------
+template <bool HAS_WV, bool HAS_WH>
+struct ColPhaseP {
+    static constexpr bool COLS = true;
+    static constexpr int IWV = 4;
+    static constexpr int IWH = HAS_WV ? 5 : 4;
+    static constexpr int NIN = 4 + (HAS_WV ? 1 : 0) + (HAS_WH ? 1 : 0);
+    static constexpr bool NEIGH = true;
+    static constexpr bool CREC = true;
+    static constexpr int NOUT = 0;
+    struct Acc {
+        double total;
+        float chunk;
+        float x_prev, wv_prev;
+    };
+
+    const float *f, *wv, *wh;
+    float lam;
+    long long H, W;
+    float *buf0, *buf1, *y;
+    Tv2dState *st;
+    const Tv2dParams *prm;
+    double *partials, *gaps;
+    // resolved per launch
+    const float *xk, *xkm1;
+    float sigma, inv_sigma, theta, inv_tau_prev;
+    int k_iter;
+    bool gap_on;
+
+    __device__ bool resolve()
+    {
+        if (st->done) return false;
+        const int k = st->k;
+        k_iter = k;
+        xk = (k & 1) ? buf1 : buf0;
+        xkm1 = (k & 1) ? buf0 : buf1;
+        sigma = (float)prm[k].sigma;
+        inv_sigma = (float)(1.0 / prm[k].sigma);
+        theta = (float)prm[k].theta_prev;
+        inv_tau_prev = (float)(1.0 / prm[k].tau_prev);
+        gap_on = k >= 1;
+        return true;
+    }
+    __device__ long long num_chains() const { return W; }
+    __device__ int max_len() const { return (int)H; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        start = k;
+        n = (int)H;
+        return true;
+    }
+    __device__ const float *in_ptr(int a) const
+    {
+        switch (a) {
+        case 0: return xk;
+        case 1: return xkm1;
+        case 2: return y;
+        case 3: return f;
+        default: return (HAS_WV && a == IWV) ? wv : wh;
+        }
+    }
+    __device__ long long in_off(int, long long, long long start) const { return start; }
+    __device__ int in_lim(int a, int n) const { return (HAS_WV && a == IWV) ? n - 1 : n; }
+    __device__ long long in_ld(int a) const { return (HAS_WH && a == IWH) ? W - 1 : W; }
+    __device__ long long in_kmax(int a) const { return (HAS_WH && a == IWH) ? W - 1 : W; }
+    template <class IN>
+    __device__ void unary(const IN &in, int b, int j, int lane, int i, int n, long long col,
+                          float &c, float &w, Acc &acc) const
+    {
+        const float xv = in[0][b][lane][j];
+        const float sh = __shfl_down_sync(0xffffffffu, xv, 1);
+        const float xr = (lane == WARP - 1) ? in[0][b][WARP][j] : sh;
+        const float xp = in[1][b][lane][j];
+        const float yv = in[2][b][lane][j];
+        const float fv = in[3][b][lane][j];
+        float wvv = lam, whv = lam;
+        if constexpr (HAS_WV) wvv = in[IWV][b][lane][j];
+        if constexpr (HAS_WH) whv = in[IWH][b][lane][j];
+        const float xbar = xv + theta * (xv - xp);
+        c = yv * inv_sigma + xbar;  // eta / sigma
+        w = (i < n - 1) ? wvv * inv_sigma : 0.f;
+        if (gap_on && i < n && col < W) {
+            const float z = xv + (xv - xp) * inv_tau_prev;
+            float t = 0.5f * (xv - fv) * (xv - fv) + 0.5f * (z - fv) * (z + fv);
+            if (i > 0) t += acc.wv_prev * fabsf(xv - acc.x_prev);
+            if (col < W - 1) t += whv * fabsf(xr - xv);
+            acc.chunk += t;
+        }
+        acc.x_prev = xv;
+        acc.wv_prev = wvv;
+        if (j == CH - 1 || i == n - 1) {
+            acc.total += (double)acc.chunk;
+            acc.chunk = 0.f;
+        }
+    }
+    __device__ void unary_direct(int i, int n, long long col, long long, float &c, float &w) const
+    {
+        (void)c;  // c comes from the forward-pass record (CREC)
+        float wvv = lam;
+        if constexpr (HAS_WV) wvv = (i < n - 1) ? wv[(long long)i * W + col] : 0.f;
+        w = (i < n - 1) ? wvv * inv_sigma : 0.f;
+    }
+    __device__ float *out_ptr(int) const { return nullptr; }
+    __device__ long long out_off(int, long long, long long) const { return 0; }
+    __device__ void emit_cols(int i, long long col, float xhat, float c) const
+    {
+        if (col < W) y[(long long)i * W + col] = sigma * (c - xhat);
+    }
+    __device__ void emit_direct(int i, long long col, long long, float xhat, float c) const
+    {
+        y[(long long)i * W + col] = sigma * (c - xhat);
+    }
+    __device__ long long spill_off(long long col, long long) const { return col * (2 * H + 2); }
+    __device__ void acc_init(Acc &a) const
+    {
+        a.total = 0.0;
+        a.chunk = 0.f;
+        a.x_prev = 0.f;
+        a.wv_prev = 0.f;
+    }
+    __device__ void reduce_gap(double v) const
+    {
+        if (!gap_on) return;
+        const int lane = threadIdx.x & (WARP - 1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        const long long wg = (long long)blockIdx.x * (blockDim.x / WARP) + threadIdx.x / WARP;
+        if (lane == 0) partials[wg] = v;
+        if (last_warp_done(&st->ticket_col, lane)) {
+            const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
+            double G = 0.0;
+            for (long long q = 0; q < nw; ++q) G += partials[q];
+            const double g = G * st->inv_N;
+            st->gap = g;
+            st->gap_k = k_iter - 1;
+            gaps[k_iter - 1] = g;
+            if (st->tol > 0.0 && g <= st->tol) st->done = 1;
+        }
+    }
+    __device__ void finish(Acc &a) const { reduce_gap(a.total); }
+    __device__ void finish_empty() const { reduce_gap(0.0); }
+};
+
+// The column kernel needs c_i in the overflow path: it comes from the record.
+template <class P>
+tv_status launch(const P &p, long long nchains, float2 *rec, float *crec, float2 *spill,
+                 WsHeader *hdr, cudaStream_t s)
+{
+    const long long warps = (nchains + WARP - 1) / WARP;
+    if (warps == 0) return TV_OK;
+    const Shape sh = batch_shape(warps, sm_count_current());
+    const size_t per_warp = sizeof(WarpSmem<P, kRing>);
+    auto kern = chain_batch_kernel<P, kRing>;
+    tv_status st = check_cuda(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * per_warp)),
+        "cudaFuncSetAttribute");
+    if (st != TV_OK) return st;
+    kern<<<(unsigned)sh.blocks, sh.wpb * WARP, sh.wpb * per_warp, s>>>(p, rec, crec, spill, hdr);
+    return check_cuda(cudaGetLastError(), "tv2d kernel launch");
+}
+
+struct Tv2dWs {
+    Tv2dState *st;
+    Tv2dParams *prm;
+    double *gaps, *partials;
+    WsHeader *hdr;
+    float *y, *buf1;
+    float2 *rec;
+    float *crec;
+    float2 *spill;
+    size_t bytes;
+};
+
+Tv2dWs carve_tv2d(void *base, long long H, long long W, int max_iters)
+{
+    Carver cv(base);
+    Tv2dWs o;
+    const long long wr = (H + WARP - 1) / WARP, wc = (W + WARP - 1) / WARP;
+    o.st = cv.take<Tv2dState>(1);
+    o.prm = cv.take<Tv2dParams>((size_t)max_iters + 2);
+    o.gaps = cv.take<double>((size_t)max_iters + 2);
+    o.partials = cv.take<double>((size_t)(wc + 8));
+    o.hdr = cv.take<WsHeader>(1);
+    o.y = cv.take<float>((size_t)(H * W));
+    o.buf1 = cv.take<float>((size_t)(H * W));
+    const long long rec_rows = wr * W, rec_cols = wc * H;
+    o.rec = cv.take<float2>((size_t)((rec_rows > rec_cols ? rec_rows : rec_cols) * WARP));
+    o.crec = cv.take<float>((size_t)(rec_cols * WARP));
+    const long long sp_rows = H * (2 * W + 2), sp_cols = W * (2 * H + 2);
+    o.spill = cv.take<float2>((size_t)(sp_rows > sp_cols ? sp_rows : sp_cols));
+    o.bytes = align_up(cv.used, 256);
+    return o;
+}
+
+template <bool HAS_WH>
+tv_status launch_init(const float *img, const float *wh, float lam, long long H, long long W,
+                      float *x0, const Tv2dWs &ws, cudaStream_t s)
+{
+    InitRowsP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1};
+    return launch(p, H, ws.rec, nullptr, ws.spill, ws.hdr, s);
+}
+
+template <bool HAS_WH>
+tv_status launch_row(const float *img, const float *wh, float lam, long long H, long long W,
+                     float *x0, const Tv2dWs &ws, cudaStream_t s)
+{
+    RowPhaseP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1, ws.st, ws.prm,
+                        nullptr, nullptr, 0.f, 0.f};
+    return launch(p, H, ws.rec, nullptr, ws.spill, ws.hdr, s);
+}
+
+template <bool HAS_WV, bool HAS_WH>
+tv_status launch_col(const float *img, const float *wv, const float *wh, float lam, long long H,
+                     long long W, float *x0, const Tv2dWs &ws, cudaStream_t s)
+{
+    ColPhaseP<HAS_WV, HAS_WH> p{img, wv, wh, lam, H, W, x0, ws.buf1, ws.y, ws.st, ws.prm,
+                                ws.partials, ws.gaps, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f,
+                                0, false};
+    return launch(p, W, ws.rec, ws.crec, ws.spill, ws.hdr, s);
+}
+
+tv_status launch_col_any(const float *img, const float *wv, const float *wh, float lam,
+                         long long H, long long W, float *x0, const Tv2dWs &ws, cudaStream_t s)
+{
+    if (wv && wh) return launch_col<true, true>(img, wv, wh, lam, H, W, x0, ws, s);
+    if (wv) return launch_col<true, false>(img, wv, wh, lam, H, W, x0, ws, s);
+    if (wh) return launch_col<false, true>(img, wv, wh, lam, H, W, x0, ws, s);
+    return launch_col<false, false>(img, wv, wh, lam, H, W, x0, ws, s);
+}
+
+tv_status read_state(const Tv2dWs &ws, cudaStream_t s, Tv2dState &out)
+{
+    tv_status st = check_cuda(cudaMemcpyAsync(&out, ws.st, sizeof(out), cudaMemcpyDeviceToHost, s),
+                              "read state");
+    if (st != TV_OK) return st;
+    return check_cuda(cudaStreamSynchronize(s), "synchronize");
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tv2d_workspace_size(int64_t H, int64_t W, int max_iters)
+{
+    if (H < 1 || W < 1 || max_iters < 0) return 0;
+    return carve_tv2d(nullptr, H, W, max_iters).bytes;
+}
+
+tv_status tv2d_denoise(const float *d_img, int64_t H, int64_t W, const float *d_wh,
+                       const float *d_wv, float lambda, const float *d_y0, int max_iters,
+                       double gap_tol, float *d_x, int *iters_out, double *gap_out,
+                       void *d_workspace, size_t workspace_bytes, tv_stream_t stream)
+{
+    clear_error();
+    if (H < 1 || W < 1 || H > (1LL << 30) || W > (1LL << 30) || max_iters < 0 ||
+        max_iters > (1 << 24)) {
+        set_error("tv2d_denoise: need H, W >= 1 and 0 <= max_iters <= 2^24");
+        return TV_ERR_INVALID;
+    }
+    if (!d_img || !d_x || !d_workspace) {
+        set_error("tv2d_denoise: img, x and workspace must not be NULL");
+        return TV_ERR_INVALID;
+    }
+    if (!(gap_tol >= 0.0 && gap_tol < INFINITY)) {
+        set_error("tv2d_denoise: gap_tol must be finite and >= 0");
+        return TV_ERR_INVALID;
+    }
+    if ((!d_wh || !d_wv) && !(lambda >= 0.f && lambda < INFINITY)) {
+        set_error("tv2d_denoise: lambda must be finite and >= 0");
+        return TV_ERR_INVALID;
+    }
+    const size_t npx = (size_t)(H * W) * sizeof(float);
+    const void *ins[4] = {d_img, d_wh, d_wv, d_y0};
+    const size_t insz[4] = {npx, (size_t)(H * (W - 1)) * sizeof(float),
+                            (size_t)((H - 1) * W) * sizeof(float), npx};
+    for (int q = 0; q < 4; ++q) {
+        const char *a = (const char *)d_x, *b = (const char *)ins[q];
+        if (b && insz[q] && a < b + insz[q] && b < a + npx) {
+            set_error("tv2d_denoise: x must not overlap the inputs");
+            return TV_ERR_INVALID;
+        }
+    }
+    Tv2dWs ws = carve_tv2d(d_workspace, H, W, max_iters);
+    if (workspace_bytes < ws.bytes) {
+        set_error("tv2d_denoise: workspace of %zu bytes, %zu needed", workspace_bytes, ws.bytes);
+        return TV_ERR_NOMEM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    tv_status st;
+    tv2d_init_state<<<1, 1, 0, s>>>(ws.st, ws.prm, max_iters, gap_tol, 1.0 / ((double)H * W));
+    if ((st = check_cuda(cudaGetLastError(), "init state")) != TV_OK) return st;
+    if ((st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset")) != TV_OK)
+        return st;
+    st = d_y0 ? check_cuda(cudaMemcpyAsync(ws.y, d_y0, npx, cudaMemcpyDeviceToDevice, s), "copy y0")
+              : check_cuda(cudaMemsetAsync(ws.y, 0, npx, s), "zero y");
+    if (st != TV_OK) return st;
+    st = d_wh ? launch_init<true>(d_img, d_wh, lambda, H, W, d_x, ws, s)
+              : launch_init<false>(d_img, d_wh, lambda, H, W, d_x, ws, s);
+    if (st != TV_OK) return st;
+
+    // Launch iterations in small batches; the device stop flag turns the rest of a
+    // batch into immediate returns, and the host checks it once per batch.
+    const int batch = 2;
+    Tv2dState hs;
+    int launched = 0;
+    bool done = false;
+    while (launched < max_iters && !done) {
+        const int u = (max_iters - launched) < batch ? (max_iters - launched) : batch;
+        for (int t = 0; t < u; ++t) {
+            if ((st = launch_col_any(d_img, d_wv, d_wh, lambda, H, W, d_x, ws, s)) != TV_OK)
+                return st;
+            st = d_wh ? launch_row<true>(d_img, d_wh, lambda, H, W, d_x, ws, s)
+                      : launch_row<false>(d_img, d_wh, lambda, H, W, d_x, ws, s);
+            if (st != TV_OK) return st;
+        }
+        launched += u;
+        if ((st = read_state(ws, s, hs)) != TV_OK) return st;
+        done = hs.done != 0;
+    }
+    if (!done && max_iters > 0) {
+        // One more dual step computes the gap of the last primal iterate.
+        if ((st = launch_col_any(d_img, d_wv, d_wh, lambda, H, W, d_x, ws, s)) != TV_OK) return st;
+        if ((st = read_state(ws, s, hs)) != TV_OK) return st;
+        done = hs.done != 0;
+    }
+    if (max_iters == 0 && (st = read_state(ws, s, hs)) != TV_OK) return st;
+    if (hs.k & 1) {
+        st = check_cuda(cudaMemcpyAsync(d_x, ws.buf1, npx, cudaMemcpyDeviceToDevice, s), "copy x");
+        if (st == TV_OK) st = check_cuda(cudaStreamSynchronize(s), "synchronize");
+        if (st != TV_OK) return st;
+    }
+    if (iters_out) *iters_out = hs.k;
+    if (gap_out) *gap_out = hs.gap;
+    return done ? TV_OK : TV_ERR_NOT_CONVERGED;
+}
+
+}  // extern "C"

@@ -1,0 +1,367 @@
+// Batched chain TV-l2 solves (eq. 1D-ROF) behind the C ABI: contiguous chains
+// given by CSR offsets (or a uniform length), and the column chains of a
+// row-major array. One thread per chain runs the dynamic program of Algorithm 2
+// / Sec. 4.1 (tv_dp.cuh).
+#include <cuda_runtime.h>
+
+#include "tv_dp.cuh"
+#include "tv_host.h"
+
+namespace tvh {
+
+static thread_local char g_err[512];
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+tv_status check_cuda(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return TV_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return TV_ERR_CUDA;
+}
+
+int sm_count_current()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    return sms > 0 ? sms : 148;
+}
+
+Shape batch_shape(long long warps, int sm_count)
+{
+    // Spread small batches over many SMs (the DP is latency-bound); group large
+    // batches four warps per block so that two blocks share an SM.
+    int wpb = (int)(warps / (2LL * sm_count));
+    if (wpb < 1) wpb = 1;
+    if (wpb > 4) wpb = 4;
+    return Shape{wpb, (warps + wpb - 1) / wpb};
+}
+
+}  // namespace tvh
+
+using namespace tvk;
+using namespace tvh;
+
+namespace {
+
+constexpr int kRing = 32;
+
+// Contiguous chains: chain k at [off_k, off_{k+1}) (or [k*len, (k+1)*len)).
+template <bool HAS_W>
+struct ChainRowsP {
+    static constexpr bool COLS = false;
+    static constexpr int NIN = HAS_W ? 2 : 1;
+    static constexpr bool NEIGH = false;
+    static constexpr bool CREC = false;
+    static constexpr int NOUT = 1;
+    struct Acc {};
+
+    const float *y, *w;
+    float lam;
+    const int64_t *offsets;
+    long long nchains;
+    int maxlen;
+    float *x;
+    long long off0;  // offsets[0], so that reserve slices start at zero
+
+    __device__ bool resolve()
+    {
+        off0 = offsets ? (long long)offsets[0] : 0;
+        return true;
+    }
+    __device__ long long num_chains() const { return nchains; }
+    __device__ int max_len() const { return maxlen; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        if (offsets) {
+            const long long a = offsets[k], b = offsets[k + 1];
+            // monotone offsets keep every chain inside the first (k+1)*max_len nodes
+            // after offsets[0]; that also bounds its slice of the reserve
+            if (a < off0 || b < a || b - a > maxlen || b - off0 > (k + 1) * (long long)maxlen)
+                return false;
+            start = a;
+            n = (int)(b - a);
+        } else {
+            start = k * (long long)maxlen;
+            n = maxlen;
+        }
+        return true;
+    }
+    __device__ const float *in_ptr(int a) const { return a == 0 ? y : w; }
+    __device__ long long in_off(int, long long, long long start) const { return start; }
+    __device__ int in_lim(int a, int n) const { return a == 0 ? n : n - 1; }
+    __device__ long long in_ld(int) const { return 1; }
+    __device__ long long in_kmax(int) const { return nchains; }
+    template <class IN>
+    __device__ void unary(const IN &in, int b, int j, int lane, int i, int n, long long, float &c,
+                          float &wi, Acc &) const
+    {
+        c = in[0][b][lane][j];
+        if constexpr (HAS_W) wi = (i < n - 1) ? in[NIN - 1][b][lane][j] : 0.f;
+        else wi = (i < n - 1) ? lam : 0.f;
+    }
+    __device__ void unary_direct(int i, int n, long long, long long start, float &c,
+                                 float &wi) const
+    {
+        c = y[start + i];
+        if constexpr (HAS_W) wi = (i < n - 1) ? w[start + i] : 0.f;
+        else wi = (i < n - 1) ? lam : 0.f;
+    }
+    __device__ float *out_ptr(int) const { return x; }
+    __device__ long long out_off(int, long long, long long start) const { return start; }
+    __device__ void emit_cols(int, long long, float, float) const {}
+    __device__ void emit_direct(int i, long long, long long start, float xv, float) const
+    {
+        x[start + i] = xv;
+    }
+    __device__ long long spill_off(long long k, long long start) const
+    {
+        return 2 * (start - off0) + 2 * k;  // 2n+2 entries per chain
+    }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &) const {}
+    __device__ void finish_empty() const {}
+};
+
+// Column chains of an H x W array with leading dimension ld.
+template <bool HAS_W>
+struct ChainColsP {
+    static constexpr bool COLS = true;
+    static constexpr int NIN = HAS_W ? 2 : 1;
+    static constexpr bool NEIGH = false;
+    static constexpr bool CREC = false;
+    static constexpr int NOUT = 0;
+    struct Acc {};
+
+    const float *y, *w;
+    float lam;
+    long long H, W, ld;
+    float *x;
+
+    __device__ bool resolve() { return true; }
+    __device__ long long num_chains() const { return W; }
+    __device__ int max_len() const { return (int)H; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        start = k;
+        n = (int)H;
+        return true;
+    }
+    __device__ const float *in_ptr(int a) const { return a == 0 ? y : w; }
+    __device__ long long in_off(int, long long, long long start) const { return start; }
+    __device__ int in_lim(int a, int n) const { return a == 0 ? n : n - 1; }
+    __device__ long long in_ld(int) const { return ld; }
+    __device__ long long in_kmax(int) const { return W; }
+    template <class IN>
+    __device__ void unary(const IN &in, int b, int j, int lane, int i, int n, long long, float &c,
+                          float &wi, Acc &) const
+    {
+        c = in[0][b][lane][j];
+        if constexpr (HAS_W) wi = (i < n - 1) ? in[NIN - 1][b][lane][j] : 0.f;
+        else wi = (i < n - 1) ? lam : 0.f;
+    }
+    __device__ void unary_direct(int i, int n, long long k, long long, float &c, float &wi) const
+    {
+        c = y[(long long)i * ld + k];
+        if constexpr (HAS_W) wi = (i < n - 1) ? w[(long long)i * ld + k] : 0.f;
+        else wi = (i < n - 1) ? lam : 0.f;
+    }
+    __device__ float *out_ptr(int) const { return x; }
+    __device__ long long out_off(int, long long, long long) const { return 0; }
+    __device__ void emit_cols(int i, long long k, float xv, float) const
+    {
+        if (k < W) x[(long long)i * ld + k] = xv;
+    }
+    __device__ void emit_direct(int i, long long k, long long, float xv, float) const
+    {
+        x[(long long)i * ld + k] = xv;
+    }
+    __device__ long long spill_off(long long k, long long) const { return k * (2 * H + 2); }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &) const {}
+    __device__ void finish_empty() const {}
+};
+
+template <class P>
+tv_status launch_batch(const P &p, long long nchains, float2 *rec, float *crec, float2 *spill,
+                       WsHeader *hdr, cudaStream_t s)
+{
+    const long long warps = (nchains + WARP - 1) / WARP;
+    if (warps == 0) return TV_OK;
+    const Shape sh = batch_shape(warps, sm_count_current());
+    const size_t per_warp = sizeof(WarpSmem<P, kRing>);
+    auto kern = chain_batch_kernel<P, kRing>;
+    tv_status st = check_cuda(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * per_warp)),
+        "cudaFuncSetAttribute");
+    if (st != TV_OK) return st;
+    kern<<<(unsigned)sh.blocks, sh.wpb * WARP, sh.wpb * per_warp, s>>>(p, rec, crec, spill, hdr);
+    return check_cuda(cudaGetLastError(), "chain kernel launch");
+}
+
+struct ChainWs {
+    WsHeader *hdr;
+    float2 *rec;
+    float2 *spill;
+    size_t bytes;
+};
+
+ChainWs carve_chain_ws(void *ws, long long warps, long long max_len, long long spill_entries)
+{
+    Carver cv(ws);
+    ChainWs o;
+    o.hdr = cv.take<WsHeader>(1);
+    o.rec = cv.take<float2>((size_t)(warps * max_len * WARP));
+    o.spill = cv.take<float2>((size_t)spill_entries);
+    o.bytes = align_up(cv.used, 256);
+    return o;
+}
+
+bool overlaps(const void *a, size_t an, const void *b, size_t bn)
+{
+    if (!a || !b || an == 0 || bn == 0) return false;
+    const char *pa = (const char *)a, *pb = (const char *)b;
+    return pa < pb + bn && pb < pa + an;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tv_last_error(void) { return tvh::g_err; }
+
+int tv_version(void) { return 100; }
+
+size_t tv_chain_workspace_size(int64_t num_chains, int64_t max_len)
+{
+    if (num_chains < 0 || max_len < 0) return 0;
+    const long long warps = (num_chains + WARP - 1) / WARP;
+    return carve_chain_ws(nullptr, warps, max_len, 2 * num_chains * max_len + 2 * num_chains).bytes;
+}
+
+tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
+                         const int64_t *d_offsets, int64_t num_chains, int64_t max_len,
+                         float *d_x, void *d_workspace, size_t workspace_bytes,
+                         tv_stream_t stream)
+{
+    clear_error();
+    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 30)) {
+        set_error("tv_chain_solve: num_chains and max_len must be >= 0 (max_len <= 2^30)");
+        return TV_ERR_INVALID;
+    }
+    if (num_chains == 0) return TV_OK;
+    if (!d_y || !d_x || !d_workspace) {
+        set_error("tv_chain_solve: y, x and workspace must not be NULL");
+        return TV_ERR_INVALID;
+    }
+    if (!d_w && !(lambda >= 0.f && lambda < INFINITY)) {
+        set_error("tv_chain_solve: lambda must be finite and >= 0");
+        return TV_ERR_INVALID;
+    }
+    // Without offsets the node count is known on the host: check overlap of x with the inputs.
+    if (!d_offsets) {
+        const size_t bytes = (size_t)num_chains * (size_t)max_len * sizeof(float);
+        if (overlaps(d_x, bytes, d_y, bytes) || overlaps(d_x, bytes, d_w, bytes)) {
+            set_error("tv_chain_solve: x must not overlap y or w");
+            return TV_ERR_INVALID;
+        }
+    } else if (d_x == d_y || (d_w && d_x == d_w)) {
+        set_error("tv_chain_solve: x must not alias y or w");
+        return TV_ERR_INVALID;
+    }
+    const long long warps = (num_chains + WARP - 1) / WARP;
+    // The total node count may live on the device only; num_chains * max_len bounds it.
+    const long long total = (long long)num_chains * max_len;
+    ChainWs ws = carve_chain_ws(d_workspace, warps, max_len, 2 * total + 2 * num_chains);
+    if (workspace_bytes < ws.bytes) {
+        set_error("tv_chain_solve: workspace of %zu bytes, %zu needed", workspace_bytes, ws.bytes);
+        return TV_ERR_NOMEM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
+    if (st != TV_OK) return st;
+    if (d_w) {
+        ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x, 0};
+        return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
+    }
+    ChainRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x, 0};
+    return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
+}
+
+size_t tv_columns_workspace_size(int64_t H, int64_t W)
+{
+    if (H < 0 || W < 0) return 0;
+    const long long warps = (W + WARP - 1) / WARP;
+    return carve_chain_ws(nullptr, warps, H, W * (2 * H + 2)).bytes;
+}
+
+tv_status tv_chain_solve_columns(const float *d_y, const float *d_w, float lambda, int64_t H,
+                                 int64_t W, int64_t ld, float *d_x, void *d_workspace,
+                                 size_t workspace_bytes, tv_stream_t stream)
+{
+    clear_error();
+    if (H < 0 || W < 0 || ld < W || H > (1LL << 30)) {
+        set_error("tv_chain_solve_columns: need H, W >= 0 and ld >= W");
+        return TV_ERR_INVALID;
+    }
+    if (H == 0 || W == 0) return TV_OK;
+    if (!d_y || !d_x || !d_workspace) {
+        set_error("tv_chain_solve_columns: y, x and workspace must not be NULL");
+        return TV_ERR_INVALID;
+    }
+    if (!d_w && !(lambda >= 0.f && lambda < INFINITY)) {
+        set_error("tv_chain_solve_columns: lambda must be finite and >= 0");
+        return TV_ERR_INVALID;
+    }
+    const size_t bytes = (size_t)((H - 1) * ld + W) * sizeof(float);
+    if (overlaps(d_x, bytes, d_y, bytes) || overlaps(d_x, bytes, d_w, bytes)) {
+        set_error("tv_chain_solve_columns: x must not overlap y or w");
+        return TV_ERR_INVALID;
+    }
+    const long long warps = (W + WARP - 1) / WARP;
+    ChainWs ws = carve_chain_ws(d_workspace, warps, H, W * (2 * H + 2));
+    if (workspace_bytes < ws.bytes) {
+        set_error("tv_chain_solve_columns: workspace of %zu bytes, %zu needed", workspace_bytes,
+                  ws.bytes);
+        return TV_ERR_NOMEM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
+    if (st != TV_OK) return st;
+    if (d_w) {
+        ChainColsP<true> p{d_y, d_w, 0.f, H, W, ld, d_x};
+        return launch_batch(p, W, ws.rec, nullptr, ws.spill, ws.hdr, s);
+    }
+    ChainColsP<false> p{d_y, nullptr, lambda, H, W, ld, d_x};
+    return launch_batch(p, W, ws.rec, nullptr, ws.spill, ws.hdr, s);
+}
+
+tv_status tv_workspace_status(void *d_workspace, tv_stream_t stream, int *status_out,
+                              int64_t *overflowed)
+{
+    clear_error();
+    if (!d_workspace || !status_out) {
+        set_error("tv_workspace_status: workspace and status_out must not be NULL");
+        return TV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    WsHeader h;
+    tv_status st = check_cuda(cudaMemcpyAsync(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost, s),
+                              "read header");
+    if (st == TV_OK) st = check_cuda(cudaStreamSynchronize(s), "synchronize");
+    if (st != TV_OK) return st;
+    *status_out = (h.status & ERR_BAD_CHAIN) ? TV_ERR_INVALID : TV_OK;
+    if (overflowed) *overflowed = (int64_t)h.overflowed;
+    return check_cuda(cudaMemsetAsync(d_workspace, 0, sizeof(WsHeader), s), "clear header");
+}
+
+}  // extern "C"

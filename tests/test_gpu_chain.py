@@ -1,0 +1,140 @@
+"""GPU parity of the batched chain solver against the FP64 oracle (eq. 1D-ROF).
+
+Bar: max |x_gpu - x_oracle| <= 2e-5 on [0, 1]-range data, the FP32 tolerance
+the workload targets (the oracle is exact up to FP64 rounding; the kernel runs
+the same dynamic program in FP32).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1502_07770_gb300 import _lib, synth
+from tests import pins
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-5
+DEV = "cuda:0"
+
+
+def _gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _rows(y, lam=0.0, w=None):
+    return _lib.chain_prox(_gpu(y), None if w is None else _gpu(w), lam=lam).cpu().numpy()
+
+
+def test_config0_rows_uniform():
+    """512 independent chains of length 256 (a 256x256 image's rows and columns), lambda = 0.2."""
+    y = synth.chain_batch(512, 256, seed0=0)
+    x = _rows(y, lam=0.2)
+    xr = oracle.chain_solve_batch(y.ravel(), np.arange(513) * 256, lam=0.2).reshape(y.shape)
+    assert np.abs(x - xr).max() <= TOL
+
+
+def test_config0_as_columns():
+    y = synth.chain_batch(512, 256, seed0=0)
+    cols = np.ascontiguousarray(y.T)  # (256, 512): chain k is column k
+    x = _lib.chain_prox_columns(_gpu(cols), lam=0.2).cpu().numpy()
+    xr = oracle.chain_solve_batch(y.ravel(), np.arange(513) * 256, lam=0.2).reshape(y.shape)
+    assert np.abs(x.T - xr).max() <= TOL
+
+
+@pytest.mark.parametrize("layout", ["rows", "cols"])
+def test_per_edge_weights(layout):
+    rng = np.random.default_rng(3)
+    y = synth.chain_batch(96, 203, seed0=40)
+    w = rng.uniform(0.0, 0.4, size=y.shape).astype(np.float32)
+    w[:, ::17] = 0.0  # decoupled edges
+    if layout == "rows":
+        x = _rows(y, w=w)
+    else:
+        x = _lib.chain_prox_columns(_gpu(y.T.copy()), _gpu(w.T.copy())).cpu().numpy().T
+    xr = oracle.chain_solve_batch(y.ravel(), np.arange(97) * 203, w=w.ravel()).reshape(y.shape)
+    assert np.abs(x - xr).max() <= TOL
+
+
+def test_ragged_offsets_and_edge_lengths():
+    lengths = [0, 1, 2, 3, 15, 16, 17, 31, 32, 33, 1000, 0, 5, 257, 1, 64] * 5 + [1023, 7]
+    y, off = synth.ragged_chain_batch(lengths, seed0=11)
+    w = np.random.default_rng(4).uniform(0, 0.3, size=y.shape).astype(np.float32)
+    for weights in (None, w):
+        x = _lib.chain_prox(_gpu(y), None if weights is None else _gpu(weights), lam=0.15,
+                            offsets=_gpu(off), max_len=max(lengths)).cpu().numpy()
+        xr = oracle.chain_solve_batch(y, off, w=weights, lam=0.15)
+        assert np.abs(x - xr).max() <= TOL
+    # one-node chains return y exactly
+    ones = off[:-1][np.diff(off) == 1]
+    np.testing.assert_array_equal(x[ones], y[ones])
+
+
+def test_overflow_reserve_path():
+    """A steep ramp with a weight just under the all-fused threshold keeps about n/2
+    breakpoints, more than fit on chip; mixed into warps with ordinary chains."""
+    n = 512
+    ramp = (-np.arange(n) / n).astype(np.float32)
+    y = synth.chain_batch(64, n, seed0=5)
+    y[::3] = ramp
+    w = np.full(y.shape, 0.05, dtype=np.float32)
+    w[::3] = n / 16.0 / n  # threshold of the ramp is about n/8 * (1/n)
+    ws = _lib.workspace(_lib.load().tv_chain_workspace_size(64, n), DEV, "overflow-test")
+    x = _lib.chain_prox(_gpu(y), _gpu(w), ws=ws).cpu().numpy()
+    status, overflowed = _lib.workspace_status(ws)
+    assert status == _lib.TV_OK
+    assert overflowed >= 20
+    xr = oracle.chain_solve_batch(y.ravel(), np.arange(65) * n, w=w.ravel()).reshape(y.shape)
+    assert np.abs(x - xr).max() <= TOL
+
+
+def test_malformed_offsets_are_flagged_not_faulted():
+    y = np.zeros(100, np.float32)
+    off = np.array([0, 10, 5, 100], np.int64)  # decreasing
+    ws = _lib.workspace(_lib.load().tv_chain_workspace_size(3, 100), DEV, "bad-offsets")
+    _lib.chain_prox(_gpu(y), lam=0.1, offsets=_gpu(off), max_len=100, ws=ws)
+    status, _ = _lib.workspace_status(ws)
+    assert status == _lib.TV_ERR_INVALID
+    off = np.array([0, 50, 100], np.int64)  # longer than max_len
+    _lib.chain_prox(_gpu(y), lam=0.1, offsets=_gpu(off), max_len=20, ws=ws)
+    assert _lib.workspace_status(ws)[0] == _lib.TV_ERR_INVALID
+    _lib.chain_prox(_gpu(y), lam=0.1, offsets=_gpu(off), max_len=50, ws=ws)
+    assert _lib.workspace_status(ws)[0] == _lib.TV_OK
+
+
+def test_closed_forms_on_gpu():
+    y = synth.chain_batch(64, 300, seed0=9)
+    np.testing.assert_allclose(_rows(y, lam=0.0), y, atol=1e-6)          # w = 0: x = y
+    big = _rows(y, lam=1e4)                                              # all fused: mean
+    np.testing.assert_allclose(big, np.repeat(y.mean(axis=1, dtype=np.float64)[:, None], 300, 1),
+                               atol=TOL)
+    const = np.full((32, 100), 0.25, np.float32)
+    np.testing.assert_allclose(_rows(const, lam=0.3), const, atol=1e-7)
+
+
+def test_kkt_certificate_of_gpu_output():
+    y = synth.chain_batch(32, 1024, seed0=21)
+    x = _rows(y, lam=0.15).astype(np.float64)
+    for k in range(32):
+        assert pins.kkt_residual(y[k], 0.15, x[k]) < 2e-3  # FP32 rounding of u sums over 1024 nodes
+
+
+def test_bench_size_sampled():
+    """The benchmark's chain workload (65536 chains x 1024, lambda 0.15): sampled chains
+    against the oracle, and invariants on every chain."""
+    B, n = 65536, 1024
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(B, size=96, replace=False))
+    y = np.empty((B, n), np.float32)
+    base = synth.chain_batch(256, n, seed0=1000)
+    y[:] = np.tile(base, (B // 256, 1))  # 256 distinct chains, repeated
+    yg = _gpu(y)
+    x = _lib.chain_prox(yg, lam=0.15)
+    xs = x[torch.from_numpy(sample).to(DEV)].cpu().numpy()
+    xr = oracle.chain_solve_batch(y[sample].ravel(), np.arange(len(sample) + 1) * n, lam=0.15)
+    assert np.abs(xs.ravel() - xr).max() <= TOL
+    # mean preservation (sum_i x_i = sum_i y_i) on every chain
+    d = (x.double().sum(1) - yg.double().sum(1)).abs().max().item()
+    assert d < 5e-3
+    # identical inputs give identical outputs wherever they sit in the batch
+    xv = x.view(B // 256, 256, n)
+    assert torch.equal(xv[0], xv[-1])
