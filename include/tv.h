@@ -54,6 +54,23 @@ const char *tv_last_error(void);
 /* Library version, major*10000 + minor*100 + patch. */
 int tv_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (benchmark
+ * accounting; the paper has no counterpart). */
+int64_t tv_launch_count(void);
+
+/*
+ * Optional per-launch timing for benchmarks (the paper has no counterpart).
+ * While enabled, every solver kernel launch is bracketed by two CUDA events
+ * recorded on the launch's own stream. tv_profile_read(kind, ...) waits for the
+ * recorded events of one kind, returns their summed duration in milliseconds and
+ * the number of launches since the previous read, and resets both. Kinds:
+ * 0 chain batches (tv_chain_solve, tv_chain_solve_columns), 1 the 2D column
+ * (dual) phase, 2 the 2D row (primal) phase, 3 the 2D initial row solve.
+ * Events are created on first use and reused; TV_ERR_INVALID for a bad kind.
+ */
+tv_status tv_profile_enable(int on);
+tv_status tv_profile_read(int kind, double *total_ms, int64_t *launches);
+
 /* ---------------------------------------------------------------- chains ---- */
 
 /*

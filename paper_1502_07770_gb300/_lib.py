@@ -31,6 +31,10 @@ _sz = ctypes.c_size_t
 SIGNATURES = {
     "tv_last_error": (ctypes.c_char_p, []),
     "tv_version": (ctypes.c_int, []),
+    "tv_launch_count": (_i64, []),
+    "tv_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "tv_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(_i64)]),
     "tv_chain_workspace_size": (_sz, [_i64, _i64]),
     "tv_chain_solve": (ctypes.c_int, [_p, _p, ctypes.c_float, _p, _i64, _i64, _p, _p, _sz, _p]),
     "tv_columns_workspace_size": (_sz, [_i64, _i64]),
@@ -160,6 +164,26 @@ def workspace_status(ws, device=None):
     _check(lib.tv_workspace_status(_ptr(ws), _stream(ws.device), ctypes.byref(st),
                                    ctypes.byref(ov)))
     return st.value, ov.value
+
+
+PROFILE_KINDS = {"chain": 0, "col": 1, "row": 2, "init": 3}
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().tv_launch_count())
+
+
+def profile_enable(on: bool = True):
+    _check(load().tv_profile_enable(1 if on else 0))
+
+
+def profile_read(kind: str):
+    """(total ms, launches) of one kernel kind since the last read (CUDA events)."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(load().tv_profile_read(PROFILE_KINDS[kind], ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def tv2d_denoise(img, lam: float = 0.1, w_h=None, w_v=None, y0=None, max_iters: int = 200,

@@ -30,8 +30,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
-#include "tv_dp.cuh"
-#include "tv_host.h"
+#include "tv_launch.cuh"
 
 using namespace tvk;
 using namespace tvh;
@@ -111,6 +110,7 @@ struct InitRowsP {
     float lam;
     long long H, W;
     float *x0, *x1;
+    bool vec;
 
     __device__ bool resolve() { return true; }
     __device__ long long num_chains() const { return H; }
@@ -129,12 +129,13 @@ struct InitRowsP {
     __device__ int in_lim(int a, int n) const { return a == 2 ? n - 1 : n; }
     __device__ long long in_ld(int) const { return 1; }
     __device__ long long in_kmax(int) const { return H; }
-    template <class IN>
-    __device__ void unary(const IN &in, int b, int j, int lane, int i, int n, long long, float &c,
+    __device__ bool in_vec(int a) const { return vec && a < 2; }
+    __device__ bool out_vec() const { return vec; }
+    __device__ void unary(const float (&v)[NIN], float, int, int i, int n, long long, float &c,
                           float &w, Acc &) const
     {
-        c = in[0][b][lane][j] - in[1][b][lane][j];
-        if constexpr (HAS_WH) w = (i < n - 1) ? in[2][b][lane][j] : 0.f;
+        c = v[0] - v[1];
+        if constexpr (HAS_WH) w = (i < n - 1) ? v[2] : 0.f;
         else w = (i < n - 1) ? lam : 0.f;
     }
     __device__ void unary_direct(int i, int n, long long k, long long start, float &c,
@@ -174,6 +175,7 @@ struct RowPhaseP {
     float *buf0, *buf1;
     Tv2dState *st;
     const Tv2dParams *prm;
+    bool vec;
     // resolved per launch from the device state
     const float *xin;
     float *xout;
@@ -215,13 +217,14 @@ struct RowPhaseP {
         c = ca * (fv - yv) + cb * xv;
         w = (i < n - 1) ? ca * wv : 0.f;
     }
-    template <class IN>
-    __device__ void unary(const IN &in, int b, int j, int lane, int i, int n, long long, float &c,
+    __device__ bool in_vec(int a) const { return vec && a < 3; }
+    __device__ bool out_vec() const { return vec; }
+    __device__ void unary(const float (&v)[NIN], float, int, int i, int n, long long, float &c,
                           float &w, Acc &) const
     {
         float wv = lam;
-        if constexpr (HAS_WH) wv = in[3][b][lane][j];
-        unary_vals(in[0][b][lane][j], in[1][b][lane][j], in[2][b][lane][j], wv, i, n, c, w);
+        if constexpr (HAS_WH) wv = v[3];
+        unary_vals(v[0], v[1], v[2], wv, i, n, c, w);
     }
     __device__ void unary_direct(int i, int n, long long k, long long start, float &c,
                                  float &w) const
@@ -271,6 +274,7 @@ struct ColPhaseP {
     Tv2dState *st;
     const Tv2dParams *prm;
     double *partials, *gaps;
+    bool vec;
     // resolved per launch
     const float *xk, *xkm1;
     float sigma, inv_sigma, theta, inv_tau_prev;
@@ -313,19 +317,15 @@ struct ColPhaseP {
     __device__ int in_lim(int a, int n) const { return (HAS_WV && a == IWV) ? n - 1 : n; }
     __device__ long long in_ld(int a) const { return (HAS_WH && a == IWH) ? W - 1 : W; }
     __device__ long long in_kmax(int a) const { return (HAS_WH && a == IWH) ? W - 1 : W; }
-    template <class IN>
-    __device__ void unary(const IN &in, int b, int j, int lane, int i, int n, long long col,
+    __device__ bool in_vec(int a) const { return vec && !(HAS_WH && a == IWH); }
+    __device__ bool out_vec() const { return false; }
+    __device__ void unary(const float (&v)[NIN], float xr, int j, int i, int n, long long col,
                           float &c, float &w, Acc &acc) const
     {
-        const float xv = in[0][b][lane][j];
-        const float sh = __shfl_down_sync(0xffffffffu, xv, 1);
-        const float xr = (lane == WARP - 1) ? in[0][b][WARP][j] : sh;
-        const float xp = in[1][b][lane][j];
-        const float yv = in[2][b][lane][j];
-        const float fv = in[3][b][lane][j];
+        const float xv = v[0], xp = v[1], yv = v[2], fv = v[3];
         float wvv = lam, whv = lam;
-        if constexpr (HAS_WV) wvv = in[IWV][b][lane][j];
-        if constexpr (HAS_WH) whv = in[IWH][b][lane][j];
+        if constexpr (HAS_WV) wvv = v[IWV];
+        if constexpr (HAS_WH) whv = v[IWH];
         const float xbar = xv + theta * (xv - xp);
         c = yv * inv_sigma + xbar;  // eta / sigma
         w = (i < n - 1) ? wvv * inv_sigma : 0.f;
@@ -391,22 +391,11 @@ struct ColPhaseP {
     __device__ void finish_empty() const { reduce_gap(0.0); }
 };
 
-// The column kernel needs c_i in the overflow path: it comes from the record.
 template <class P>
 tv_status launch(const P &p, long long nchains, float2 *rec, float *crec, float2 *spill,
-                 WsHeader *hdr, cudaStream_t s)
+                 WsHeader *hdr, cudaStream_t s, int kind)
 {
-    const long long warps = (nchains + WARP - 1) / WARP;
-    if (warps == 0) return TV_OK;
-    const Shape sh = batch_shape(warps, sm_count_current());
-    const size_t per_warp = sizeof(WarpSmem<P, kRing>);
-    auto kern = chain_batch_kernel<P, kRing>;
-    tv_status st = check_cuda(
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * per_warp)),
-        "cudaFuncSetAttribute");
-    if (st != TV_OK) return st;
-    kern<<<(unsigned)sh.blocks, sh.wpb * WARP, sh.wpb * per_warp, s>>>(p, rec, crec, spill, hdr);
-    return check_cuda(cudaGetLastError(), "tv2d kernel launch");
+    return launch_chains<P, kRing>(p, nchains, rec, crec, spill, hdr, s, kind);
 }
 
 struct Tv2dWs {
@@ -419,7 +408,10 @@ struct Tv2dWs {
     float *crec;
     float2 *spill;
     size_t bytes;
+    bool vec_rows, vec_cols;  // 16-byte copies: W % 4 == 0 and aligned image buffers
 };
+
+bool aligned16(const void *q) { return q == nullptr || ((uintptr_t)q & 15) == 0; }
 
 Tv2dWs carve_tv2d(void *base, long long H, long long W, int max_iters)
 {
@@ -439,6 +431,7 @@ Tv2dWs carve_tv2d(void *base, long long H, long long W, int max_iters)
     const long long sp_rows = H * (2 * W + 2), sp_cols = W * (2 * H + 2);
     o.spill = cv.take<float2>((size_t)(sp_rows > sp_cols ? sp_rows : sp_cols));
     o.bytes = align_up(cv.used, 256);
+    o.vec_rows = o.vec_cols = false;
     return o;
 }
 
@@ -446,17 +439,17 @@ template <bool HAS_WH>
 tv_status launch_init(const float *img, const float *wh, float lam, long long H, long long W,
                       float *x0, const Tv2dWs &ws, cudaStream_t s)
 {
-    InitRowsP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1};
-    return launch(p, H, ws.rec, nullptr, ws.spill, ws.hdr, s);
+    InitRowsP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1, ws.vec_rows};
+    return launch(p, H, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_INIT);
 }
 
 template <bool HAS_WH>
 tv_status launch_row(const float *img, const float *wh, float lam, long long H, long long W,
                      float *x0, const Tv2dWs &ws, cudaStream_t s)
 {
-    RowPhaseP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1, ws.st, ws.prm,
+    RowPhaseP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1, ws.st, ws.prm, ws.vec_rows,
                         nullptr, nullptr, 0.f, 0.f};
-    return launch(p, H, ws.rec, nullptr, ws.spill, ws.hdr, s);
+    return launch(p, H, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_ROW);
 }
 
 template <bool HAS_WV, bool HAS_WH>
@@ -464,9 +457,9 @@ tv_status launch_col(const float *img, const float *wv, const float *wh, float l
                      long long W, float *x0, const Tv2dWs &ws, cudaStream_t s)
 {
     ColPhaseP<HAS_WV, HAS_WH> p{img, wv, wh, lam, H, W, x0, ws.buf1, ws.y, ws.st, ws.prm,
-                                ws.partials, ws.gaps, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f,
-                                0, false};
-    return launch(p, W, ws.rec, ws.crec, ws.spill, ws.hdr, s);
+                                ws.partials, ws.gaps, ws.vec_cols && aligned16(wv),
+                                nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 0, false};
+    return launch(p, W, ws.rec, ws.crec, ws.spill, ws.hdr, s, PK_COL);
 }
 
 tv_status launch_col_any(const float *img, const float *wv, const float *wh, float lam,
@@ -535,10 +528,12 @@ tv_status tv2d_denoise(const float *d_img, int64_t H, int64_t W, const float *d_
         set_error("tv2d_denoise: workspace of %zu bytes, %zu needed", workspace_bytes, ws.bytes);
         return TV_ERR_NOMEM;
     }
+    ws.vec_rows = ws.vec_cols = (W % 4 == 0) && aligned16(d_img) && aligned16(d_x);
     cudaStream_t s = (cudaStream_t)stream;
     tv_status st;
     tv2d_init_state<<<1, 1, 0, s>>>(ws.st, ws.prm, max_iters, gap_tol, 1.0 / ((double)H * W));
     if ((st = check_cuda(cudaGetLastError(), "init state")) != TV_OK) return st;
+    note_launch();
     if ((st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset")) != TV_OK)
         return st;
     st = d_y0 ? check_cuda(cudaMemcpyAsync(ws.y, d_y0, npx, cudaMemcpyDeviceToDevice, s), "copy y0")

@@ -4,8 +4,11 @@
 // / Sec. 4.1 (tv_dp.cuh).
 #include <cuda_runtime.h>
 
-#include "tv_dp.cuh"
-#include "tv_host.h"
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "tv_launch.cuh"
 
 namespace tvh {
 
@@ -34,6 +37,56 @@ int sm_count_current()
     if (cudaGetDevice(&dev) != cudaSuccess) return 148;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
     return sms > 0 ? sms : 148;
+}
+
+// ---------------------------------------------------------- launch accounting --
+static std::atomic<long long> g_launches{0};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+struct ProfPair {
+    cudaEvent_t a, b;
+};
+static std::vector<ProfPair> g_prof_pending[PK_N];
+static std::vector<ProfPair> g_prof_free;
+static cudaEvent_t g_prof_open[PK_N];
+static double g_prof_ms[PK_N];
+static long long g_prof_n[PK_N];
+
+void note_launch() { g_launches.fetch_add(1); }
+bool prof_on() { return g_prof_on; }
+
+void prof_mark(int kind, cudaStream_t s, bool start)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (start) {
+        ProfPair pr;
+        if (!g_prof_free.empty()) {
+            pr = g_prof_free.back();
+            g_prof_free.pop_back();
+        } else {
+            cudaEventCreate(&pr.a);
+            cudaEventCreate(&pr.b);
+        }
+        cudaEventRecord(pr.a, s);
+        g_prof_open[kind] = pr.b;
+        g_prof_pending[kind].push_back(pr);
+    } else if (!g_prof_pending[kind].empty()) {
+        cudaEventRecord(g_prof_pending[kind].back().b, s);
+    }
+}
+
+static void prof_collect(int kind)
+{
+    for (ProfPair &pr : g_prof_pending[kind]) {
+        float ms = 0.f;
+        cudaEventSynchronize(pr.b);
+        if (cudaEventElapsedTime(&ms, pr.a, pr.b) == cudaSuccess) {
+            g_prof_ms[kind] += ms;
+            g_prof_n[kind] += 1;
+        }
+        g_prof_free.push_back(pr);
+    }
+    g_prof_pending[kind].clear();
 }
 
 Shape batch_shape(long long warps, int sm_count)
@@ -71,6 +124,7 @@ struct ChainRowsP {
     long long nchains;
     int maxlen;
     float *x;
+    bool vec;        // uniform chains, length % 4 == 0, 16-byte aligned arrays
     long long off0;  // offsets[0], so that reserve slices start at zero
 
     __device__ bool resolve()
@@ -101,12 +155,13 @@ struct ChainRowsP {
     __device__ int in_lim(int a, int n) const { return a == 0 ? n : n - 1; }
     __device__ long long in_ld(int) const { return 1; }
     __device__ long long in_kmax(int) const { return nchains; }
-    template <class IN>
-    __device__ void unary(const IN &in, int b, int j, int lane, int i, int n, long long, float &c,
+    __device__ bool in_vec(int) const { return vec; }
+    __device__ bool out_vec() const { return vec; }
+    __device__ void unary(const float (&v)[NIN], float, int, int i, int n, long long, float &c,
                           float &wi, Acc &) const
     {
-        c = in[0][b][lane][j];
-        if constexpr (HAS_W) wi = (i < n - 1) ? in[NIN - 1][b][lane][j] : 0.f;
+        c = v[0];
+        if constexpr (HAS_W) wi = (i < n - 1) ? v[NIN - 1] : 0.f;
         else wi = (i < n - 1) ? lam : 0.f;
     }
     __device__ void unary_direct(int i, int n, long long, long long start, float &c,
@@ -146,6 +201,7 @@ struct ChainColsP {
     float lam;
     long long H, W, ld;
     float *x;
+    bool vec;  // ld % 4 == 0 and 16-byte aligned arrays
 
     __device__ bool resolve() { return true; }
     __device__ long long num_chains() const { return W; }
@@ -161,12 +217,13 @@ struct ChainColsP {
     __device__ int in_lim(int a, int n) const { return a == 0 ? n : n - 1; }
     __device__ long long in_ld(int) const { return ld; }
     __device__ long long in_kmax(int) const { return W; }
-    template <class IN>
-    __device__ void unary(const IN &in, int b, int j, int lane, int i, int n, long long, float &c,
+    __device__ bool in_vec(int) const { return vec; }
+    __device__ bool out_vec() const { return vec; }
+    __device__ void unary(const float (&v)[NIN], float, int, int i, int n, long long, float &c,
                           float &wi, Acc &) const
     {
-        c = in[0][b][lane][j];
-        if constexpr (HAS_W) wi = (i < n - 1) ? in[NIN - 1][b][lane][j] : 0.f;
+        c = v[0];
+        if constexpr (HAS_W) wi = (i < n - 1) ? v[NIN - 1] : 0.f;
         else wi = (i < n - 1) ? lam : 0.f;
     }
     __device__ void unary_direct(int i, int n, long long k, long long, float &c, float &wi) const
@@ -195,17 +252,7 @@ template <class P>
 tv_status launch_batch(const P &p, long long nchains, float2 *rec, float *crec, float2 *spill,
                        WsHeader *hdr, cudaStream_t s)
 {
-    const long long warps = (nchains + WARP - 1) / WARP;
-    if (warps == 0) return TV_OK;
-    const Shape sh = batch_shape(warps, sm_count_current());
-    const size_t per_warp = sizeof(WarpSmem<P, kRing>);
-    auto kern = chain_batch_kernel<P, kRing>;
-    tv_status st = check_cuda(
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * per_warp)),
-        "cudaFuncSetAttribute");
-    if (st != TV_OK) return st;
-    kern<<<(unsigned)sh.blocks, sh.wpb * WARP, sh.wpb * per_warp, s>>>(p, rec, crec, spill, hdr);
-    return check_cuda(cudaGetLastError(), "chain kernel launch");
+    return launch_chains<P, kRing>(p, nchains, rec, crec, spill, hdr, s, PK_CHAIN);
 }
 
 struct ChainWs {
@@ -226,6 +273,13 @@ ChainWs carve_chain_ws(void *ws, long long warps, long long max_len, long long s
     return o;
 }
 
+// 16-byte copies need every array 16-byte aligned and rows of a multiple of 4 floats.
+bool vec_ok(const int64_t *offsets, long long row, const void *a, const void *b, const void *c)
+{
+    auto al = [](const void *q) { return q == nullptr || ((uintptr_t)q & 15) == 0; };
+    return offsets == nullptr && row % 4 == 0 && al(a) && al(b) && al(c);
+}
+
 bool overlaps(const void *a, size_t an, const void *b, size_t bn)
 {
     if (!a || !b || an == 0 || bn == 0) return false;
@@ -240,6 +294,31 @@ extern "C" {
 const char *tv_last_error(void) { return tvh::g_err; }
 
 int tv_version(void) { return 100; }
+
+int64_t tv_launch_count(void) { return (int64_t)tvh::g_launches.load(); }
+
+tv_status tv_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(tvh::g_prof_mu);
+    tvh::g_prof_on = on != 0;
+    return TV_OK;
+}
+
+tv_status tv_profile_read(int kind, double *total_ms, int64_t *launches)
+{
+    clear_error();
+    if (kind < 0 || kind >= PK_N || !total_ms || !launches) {
+        set_error("tv_profile_read: kind must be 0..3 and the outputs non-NULL");
+        return TV_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(tvh::g_prof_mu);
+    tvh::prof_collect(kind);
+    *total_ms = tvh::g_prof_ms[kind];
+    *launches = (int64_t)tvh::g_prof_n[kind];
+    tvh::g_prof_ms[kind] = 0.0;
+    tvh::g_prof_n[kind] = 0;
+    return TV_OK;
+}
 
 size_t tv_chain_workspace_size(int64_t num_chains, int64_t max_len)
 {
@@ -290,10 +369,12 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
     if (st != TV_OK) return st;
     if (d_w) {
-        ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x, 0};
+        ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,
+                           vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0};
         return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
     }
-    ChainRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x, 0};
+    ChainRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x,
+                        vec_ok(d_offsets, max_len, d_y, nullptr, d_x), 0};
     return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
 }
 
@@ -338,10 +419,10 @@ tv_status tv_chain_solve_columns(const float *d_y, const float *d_w, float lambd
     tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
     if (st != TV_OK) return st;
     if (d_w) {
-        ChainColsP<true> p{d_y, d_w, 0.f, H, W, ld, d_x};
+        ChainColsP<true> p{d_y, d_w, 0.f, H, W, ld, d_x, vec_ok(nullptr, ld, d_y, d_w, d_x)};
         return launch_batch(p, W, ws.rec, nullptr, ws.spill, ws.hdr, s);
     }
-    ChainColsP<false> p{d_y, nullptr, lambda, H, W, ld, d_x};
+    ChainColsP<false> p{d_y, nullptr, lambda, H, W, ld, d_x, vec_ok(nullptr, ld, d_y, nullptr, d_x)};
     return launch_batch(p, W, ws.rec, nullptr, ws.spill, ws.hdr, s);
 }
 

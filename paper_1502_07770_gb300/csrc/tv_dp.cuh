@@ -39,28 +39,56 @@ static_assert(sizeof(WsHeader) == 64, "header size");
 
 struct DPState {
     int F, B;           // logical indices of the first and last breakpoint
-    float fl, fs;       // cached first entry (lambda, stored slope)
-    float bl, bs;       // cached last entry
+    float fl, fs;       // entry F (lambda, stored slope)
+    float f1l, f1s;     // entry F+1 (equals entry B when the sequence has two entries)
+    float bl, bs;       // entry B
+    float b1l, b1s;     // entry B-1 (equals entry F when the sequence has two entries)
     float w_prev;       // weight of the edge into the current node
 };
 
+// Message sequence of one chain in a ring of RING entries in shared memory:
+// entry j of this lane at byte offset ((j mod RING) * 32 + lane) * 8 of the ring.
 template <int RING>
 struct RingStore {
-    float2 *col;  // &ring[0][lane]
+    unsigned base;  // shared-window address of ring[0][lane]
     static constexpr int cap = RING;
-    __device__ __forceinline__ float2 ld(int j) const { return col[(j & (RING - 1)) * WARP]; }
-    __device__ __forceinline__ void st(int j, float2 e) const { col[(j & (RING - 1)) * WARP] = e; }
+    __device__ __forceinline__ unsigned addr(int j) const
+    {
+        return base + ((unsigned)(j & (RING - 1)) << 8);  // 32 lanes * 8 bytes per slot row
+    }
+    __device__ __forceinline__ float2 ld(int j) const
+    {
+        float2 e;
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(e.x), "=f"(e.y) : "r"(addr(j)));
+        return e;
+    }
+    __device__ __forceinline__ void st(int j, float2 e) const
+    {
+        asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(addr(j)), "f"(e.x), "f"(e.y)
+                     : "memory");
+    }
 };
 
 struct LinearStore {
     float2 *base;  // 2n+2 entries; logical index j at base[j]
-    __device__ __forceinline__ float2 ld(int j) const { return base[j]; }
-    __device__ __forceinline__ void st(int j, float2 e) const { base[j] = e; }
+    static constexpr int cap = 0x7fffffff;
+    __host__ __device__ __forceinline__ float2 ld(int j) const { return base[j]; }
+    __host__ __device__ __forceinline__ void st(int j, float2 e) const { base[j] = e; }
 };
 
 // Node 0: m^_0(z) = z - c_0 has slope 1, so lambda^-_0 = c_0 - w_0, lambda^+_0 = c_0 + w_0.
+// Quotient by a small positive integer slope: fast reciprocal on the device.
+__host__ __device__ __forceinline__ float slope_div(float num, float slope)
+{
+#ifdef __CUDA_ARCH__
+    return __fdividef(num, slope);
+#else
+    return num / slope;
+#endif
+}
+
 template <class S>
-__device__ __forceinline__ void dp_first(DPState &d, const S &s, int F0, float c0, float w0,
+__host__ __device__ __forceinline__ void dp_first(DPState &d, const S &s, int F0, float c0, float w0,
                                          float &lm, float &hp)
 {
     lm = c0 - w0;
@@ -71,6 +99,10 @@ __device__ __forceinline__ void dp_first(DPState &d, const S &s, int F0, float c
     d.fs = 0.f;   // true slope 1 between the two breakpoints
     d.bl = hp;
     d.bs = -1.f;  // -abar_0: the clipped flat right end
+    d.f1l = d.bl;
+    d.f1s = d.bs;
+    d.b1l = d.fl;
+    d.b1s = d.fs;
     d.w_prev = w0;
     s.st(d.F, make_float2(d.fl, d.fs));
     s.st(d.B, make_float2(d.bl, d.bs));
@@ -81,113 +113,164 @@ __device__ __forceinline__ void dp_first(DPState &d, const S &s, int F0, float c
 // lambda^-; the right scan removes breakpoints with m^_i > w_i (only among those
 // the left scan kept) and places lambda^+. Returns false, leaving the store and
 // state untouched, if the new sequence would exceed `cap` entries.
+//
+// The two entries nearest each end are kept in registers, so that removing at
+// most one breakpoint per side (the common case: one removal per side per node
+// on average, Sec. 4.1's amortised bound) needs no load from the store; longer
+// scans continue from the store. Each placement is lambda = base + num / slope
+// with an integer slope; the quotient uses the fast reciprocal (2 ulp), far
+// inside the FP32 error budget of the recursions.
 template <class S>
-__device__ __forceinline__ bool dp_step(DPState &d, const S &s, int cap, float ci, float wi,
+__host__ __device__ __forceinline__ bool dp_step(DPState &d, const S &s, int cap, float ci, float wi,
                                         float abar, float &lm, float &hp)
 {
-    // Left scan: value at the first breakpoint, then the forward recursion.
-    float v = d.fl - ci - d.w_prev;
+    const float nwi = -wi;
+    const int F = d.F, B = d.B;
+
+    // ---------------- left scan ----------------
+    // Values at the first two breakpoints (forward recursion of Sec. 4.1).
+    const float vF = d.fl - ci - d.w_prev;
+    const float sF = d.fs + abar;                       // slope of segment F
+    const float vF1 = fmaf(sF, d.f1l - d.fl, vF);
     int last_popped;
-    float lm_s;
-    if (v >= -wi) {
-        last_popped = d.F - 1;  // nothing removed; lambda^- on the left end segment (slope 1)
-        lm = d.fl - (v + wi);
+    float lm_s, lbase, lnum, lslope;
+    float nf1l, nf1s;  // entry after the new first breakpoint (if it is kept)
+    if (vF >= nwi) {
+        // nothing removed: lambda^- on the left end segment (slope 1)
+        last_popped = F - 1;
+        lbase = d.fl; lnum = nwi - vF; lslope = 1.f;
         lm_s = 1.f - abar;
+        nf1l = d.fl; nf1s = d.fs;
+    } else if (vF1 >= nwi) {
+        // exactly one removed: lambda^- on segment F
+        last_popped = F;
+        lbase = d.fl; lnum = nwi - vF; lslope = sF;
+        lm_s = d.fs;
+        nf1l = d.f1l; nf1s = d.f1s;
     } else {
-        int p = d.F;
-        float pl = d.fl, ps = d.fs;
-        while (p < d.B) {
-            float2 q = (p + 1 == d.B) ? make_float2(d.bl, d.bs) : s.ld(p + 1);
-            float vq = v + (ps + abar) * (q.x - pl);
-            if (vq < -wi) {
-                ++p;
-                pl = q.x;
-                ps = q.y;
-                v = vq;
-            } else {
+        // two or more removed: continue from the store
+        int p = F + 1;
+        float pl = d.f1l, ps = d.f1s, v = vF1;
+        float ql = 0.f, qs = 0.f;
+        while (p < B) {
+            const float2 q = (p + 1 == B) ? make_float2(d.bl, d.bs) : s.ld(p + 1);
+            const float vq = fmaf(ps + abar, q.x - pl, v);
+            if (vq >= nwi) {
+                ql = q.x;
+                qs = q.y;
                 break;
             }
+            ++p;
+            pl = q.x;
+            ps = q.y;
+            v = vq;
         }
-        // Both end values of m^_i are known exactly (-w_{i-1} + lambda_F - c_i at the
-        // first breakpoint, w_{i-1} + lambda_B - c_i at the last one). When the scan
+        // Both end values of m^_i are known exactly (-w_{i-1} + lambda_F - c_i at
+        // the first breakpoint, w_{i-1} + lambda_B - c_i at the last). When the scan
         // stopped nearer the last breakpoint, re-evaluate m^_i(lambda_p) by the
         // backward recursion from there: the same value in exact arithmetic, but
         // FP32 rounding of the breakpoints is no longer multiplied by the large
         // slopes of the segments crossed. The walk is shorter than the one just
         // made, so the update stays O(d_i + 1).
-        if (d.B - p < p - d.F) {
+        if (B - p < p - F) {
             float vb = d.bl - ci + d.w_prev;
-            float ql = d.bl;
-            for (int q = d.B - 1; q >= p; --q) {
-                const float2 e = (q == d.F) ? make_float2(d.fl, d.fs) : s.ld(q);
-                vb -= (e.y + abar) * (ql - e.x);
-                ql = e.x;
+            float el = d.bl;
+            for (int q = B - 1; q >= p; --q) {
+                const float2 e = (q == F + 1) ? make_float2(d.f1l, d.f1s) : s.ld(q);
+                vb = fmaf(-(e.y + abar), el - e.x, vb);
+                el = e.x;
             }
             v = vb;
         }
         last_popped = p;
-        lm = pl + (-wi - v) / (ps + abar);
-        lm_s = ps;  // lambda^- splits old segment p, whose slope it keeps
+        lbase = pl; lnum = nwi - v; lslope = ps + abar;
+        lm_s = ps;
+        nf1l = ql; nf1s = qs;  // meaningful only if p < B
     }
-    // Right scan over the kept breakpoints (index > last_popped).
-    int new_last;
-    if (d.B > last_popped) {
-        float vr = d.bl - ci + d.w_prev;
-        if (vr <= wi) {
-            hp = d.bl + (wi - vr);  // lambda^+ on the right end segment (slope 1)
-            new_last = d.B;
-        } else {
-            int q = d.B;
-            float ql = d.bl;
-            for (;;) {
-                if (q - 1 > last_popped) {
-                    float2 e = (q - 1 == d.F) ? make_float2(d.fl, d.fs) : s.ld(q - 1);
-                    float slope = e.y + abar;
-                    float vp = vr - slope * (ql - e.x);
-                    if (vp > wi) {
-                        --q;
-                        ql = e.x;
-                        vr = vp;
-                        continue;
-                    }
-                    if (q - d.F < d.B - q) {
-                        // nearer the first breakpoint: forward recursion from there
-                        // (the mirror image of the re-evaluation in the left scan)
-                        float vf = d.fl - ci - d.w_prev;
-                        float pl = d.fl, ps = d.fs;
-                        for (int t = d.F + 1; t <= q; ++t) {
-                            const float2 e2 = (t == d.B) ? make_float2(d.bl, d.bs) : s.ld(t);
-                            vf += (ps + abar) * (e2.x - pl);
-                            pl = e2.x;
-                            ps = e2.y;
+    lm = lbase + slope_div(lnum, lslope);
+
+    // ---------------- right scan over the kept breakpoints ----------------
+    int new_last = last_popped;
+    bool from_lm = true;  // lambda^+ on the segment that starts at lambda^-
+    float rbase = 0.f, rnum = 0.f, rslope = 1.f;
+    float nb1l = 0.f, nb1s = 0.f;  // entry before the new last breakpoint (if kept)
+    if (B > last_popped) {
+        const float vB = d.bl - ci + d.w_prev;
+        if (vB <= wi) {
+            // nothing removed: lambda^+ on the right end segment (slope 1)
+            from_lm = false;
+            rbase = d.bl; rnum = wi - vB; rslope = 1.f;
+            new_last = B;
+            nb1l = d.bl; nb1s = d.bs;
+        } else if (B - 1 > last_popped) {
+            const float sB1 = d.b1s + abar;  // slope of segment B-1
+            const float vB1 = fmaf(-sB1, d.bl - d.b1l, vB);
+            if (vB1 <= wi) {
+                // exactly one removed: lambda^+ on segment B-1
+                from_lm = false;
+                rbase = d.bl; rnum = wi - vB; rslope = sB1;
+                new_last = B - 1;
+                nb1l = d.b1l; nb1s = d.b1s;
+            } else {
+                int q = B - 1;
+                float ql = d.b1l, vr = vB1;
+                for (;;) {
+                    if (q - 1 > last_popped) {
+                        const float2 e = (q - 1 == F) ? make_float2(d.fl, d.fs) : s.ld(q - 1);
+                        const float sl = e.y + abar;
+                        const float vp = fmaf(-sl, ql - e.x, vr);
+                        if (vp > wi) {
+                            --q;
+                            ql = e.x;
+                            vr = vp;
+                            continue;
                         }
-                        vr = vf;
+                        if (q - F < B - q) {
+                            // nearer the first breakpoint: forward recursion from there
+                            // (the mirror image of the re-evaluation in the left scan)
+                            float vf = vF;
+                            float el = d.fl, es = d.fs;
+                            for (int t = F + 1; t <= q; ++t) {
+                                const float2 e2 = (t == F + 1) ? make_float2(d.f1l, d.f1s) : s.ld(t);
+                                vf = fmaf(es + abar, e2.x - el, vf);
+                                el = e2.x;
+                                es = e2.y;
+                            }
+                            vr = vf;
+                        }
+                        from_lm = false;
+                        rbase = ql; rnum = wi - vr; rslope = sl;
+                        nb1l = e.x; nb1s = e.y;
                     }
-                    hp = ql - (vr - wi) / slope;
-                } else {
-                    // lambda^+ on the segment that starts at the new lambda^-, where
-                    // m^_i = -w_i exactly
-                    hp = lm + (wi + wi) / (lm_s + abar);
+                    break;
                 }
-                break;
+                new_last = q - 1;
             }
-            new_last = q - 1;
+        } else {
+            new_last = B - 1;  // == last_popped: every other breakpoint was removed
         }
-    } else {
-        hp = lm + (wi + wi) / (lm_s + abar);  // every old breakpoint removed on the left
-        new_last = last_popped;
     }
+    if (from_lm) {
+        rbase = lm; rnum = wi + wi; rslope = lm_s + abar;
+    }
+    hp = rbase + slope_div(rnum, rslope);
+
     const int nF = last_popped;
     const int nB = (new_last > nF ? new_last : nF) + 1;
     if (nB - nF + 1 > cap) return false;
     s.st(nF, make_float2(lm, lm_s));
     s.st(nB, make_float2(hp, -abar));
+    const bool ntwo = (nB == nF + 1);
     d.F = nF;
     d.B = nB;
     d.fl = lm;
     d.fs = lm_s;
     d.bl = hp;
     d.bs = -abar;
+    d.f1l = ntwo ? hp : nf1l;
+    d.f1s = ntwo ? -abar : nf1s;
+    d.b1l = ntwo ? lm : nb1l;
+    d.b1s = ntwo ? lm_s : nb1s;
     d.w_prev = wi;
     return true;
 }
@@ -208,6 +291,11 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait()
@@ -217,28 +305,38 @@ __device__ __forceinline__ void cp_async_wait()
 
 // ------------------------------------------------------------ warp machinery --
 //
+// One warp owns 32 chains, one per lane; all lanes walk their chains node by node
+// in step, so the warp stages the next CH nodes of every chain in shared memory
+// with asynchronous copies while it works on the current ones.
+//
+// Tiles. Rows (contiguous chains): chain-major, lane l's nodes at [l*RP + j] with
+// RP = CH + 4 so rows stay 16-byte aligned; a lane reads four nodes at once
+// (128-bit loads by the 32 lanes hit distinct bank groups). Columns (node i of
+// chain k at i*ld + k): node-major, [j*CP + l] with CP = 32 + 4, so that one
+// 16-byte copy brings four neighbouring columns and every lane reads its own bank;
+// slot 32 of a node row holds the first column of the next warp (horizontal
+// neighbour of lane 31).
+//
 // A phase policy P describes one batch of chains and what surrounds the DP:
-//   static constexpr bool COLS   chains are columns of a row-major array
-//                                (node i of chain k at i*ld + k), else contiguous rows
-//   static constexpr int  NIN    number of staged per-node input arrays
-//   static constexpr bool NEIGH  also stage input 0 of the column to the right (COLS only)
-//   static constexpr bool CREC   record c_i for the epilogue
-//   static constexpr int  NOUT   number of row-layout outputs (rows only)
-//   active(), num_chains(), max_len()
-//   chain(k, &start, &n)         node-0 element offset and length; false => malformed
-//   in_ptr(a), in_off(a, k, start), in_lim(a, n), in_ld(a)
-//   unary(in[], nb, i, n, k, &c, &w, acc)   c_i and w_i (edge i -> i+1) from staged values
-//   unary_direct(i, n, k, start, &c, &w)    the same from global memory (overflow path)
-//   emit_cols(i, k, xhat, c)                column-layout output of node i
-//   out_ptr(o), out_off(o, k, start), out_val(o, xhat, c)   row-layout outputs
-//   finish(acc)                  end-of-thread hook (gap partials)
+//   COLS, NIN, NEIGH (stage input 0 of the column to the right), CREC (record c_i
+//   for the epilogue), NOUT (row-layout outputs); resolve(), num_chains(),
+//   max_len(), chain(k, &start, &n); in_ptr(a), in_off(a, k, start) (rows),
+//   in_ld(a), in_kmax(a) (cols), in_lim(a, n), in_vec(a) (16-byte copies allowed);
+//   unary(v[], xr, j, i, n, k, &c, &w, acc): c_i and the weight w_i of edge
+//   i -> i+1 from the staged values of node i; unary_direct(...) the same from
+//   global memory (overflow path); emit_cols / emit_direct, out_ptr(o),
+//   out_off(o, k, start), out_vec(); spill_off(k, start); acc_init / finish /
+//   finish_empty (end-of-warp hooks, e.g. gap partials).
+
+constexpr int RP = CH + 4;
+constexpr int CP = WARP + 4;
 
 template <class P, int RING>
-struct WarpSmem {
-    float in[P::NIN][2][WARP + (P::NEIGH ? 1 : 0)][CH + 1];
+struct alignas(16) WarpSmem {
+    float in[P::NIN][2][P::COLS ? CH * CP : WARP * RP];
     float2 rec[2][CH][WARP];
     float crec[P::CREC ? 2 : 1][P::CREC ? CH : 1][WARP];
-    float out[P::COLS ? 1 : WARP][P::COLS ? 1 : CH + 1];
+    float out[P::COLS ? 4 : WARP * RP];
     float2 ring[RING][WARP];
     long long start[WARP];
     int len[WARP];
@@ -251,33 +349,67 @@ __device__ __forceinline__ void fill_inputs(const P &p, WarpSmem<P, RING> *sm, i
 #pragma unroll
     for (int a = 0; a < P::NIN; ++a) {
         const float *src = p.in_ptr(a);
+        float *tile = sm->in[a][b];
         if constexpr (P::COLS) {
-            const long long k = warp_chain0 + lane;
             const long long ld = p.in_ld(a);
+            const long long kmax = p.in_kmax(a);
             const int lim = p.in_lim(a, p.max_len());
-            if (k < p.in_kmax(a)) {
+            if (p.in_vec(a)) {
+                // 4 node rows of 32 columns per instruction, 16 bytes per lane
+#pragma unroll
+                for (int u = 0; u < CH / 4; ++u) {
+                    const int jn = 4 * u + (lane >> 3);
+                    const int i = chunk * CH + jn;
+                    const int c4 = (lane & 7) * 4;
+                    const long long k = warp_chain0 + c4;
+                    if (i < lim) {
+                        if (k + 3 < kmax) {
+                            cp_async16(&tile[jn * CP + c4], src + (long long)i * ld + k);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (k + e < kmax)
+                                    cp_async4(&tile[jn * CP + c4 + e], src + (long long)i * ld + k + e);
+                        }
+                    }
+                }
+            } else {
+                const long long k = warp_chain0 + lane;
+                if (k < kmax) {
 #pragma unroll 4
-                for (int u = 0; u < CH; ++u) {
-                    const int i = chunk * CH + u;
-                    if (i < lim) cp_async4(&sm->in[a][b][lane][u], src + (long long)i * ld + k);
+                    for (int u = 0; u < CH; ++u) {
+                        const int i = chunk * CH + u;
+                        if (i < lim) cp_async4(&tile[u * CP + lane], src + (long long)i * ld + k);
+                    }
                 }
             }
             if (P::NEIGH && a == 0 && lane < CH) {
                 const long long kn = warp_chain0 + WARP;
                 const int i = chunk * CH + lane;
-                if (kn < p.in_kmax(a) && i < lim)
-                    cp_async4(&sm->in[a][b][WARP][lane], src + (long long)i * ld + kn);
+                if (kn < kmax && i < lim) cp_async4(&tile[lane * CP + WARP], src + (long long)i * ld + kn);
             }
         } else {
+            if (p.in_vec(a)) {
+                // 8 chains x 16 nodes per instruction, 16 bytes per lane
+#pragma unroll
+                for (int u = 0; u < CH / 4; ++u) {
+                    const int t = u * WARP + lane;
+                    const int jj = t >> 2, q = (t & 3) * 4;
+                    const int i = chunk * CH + q;
+                    if (i < p.in_lim(a, sm->len[jj]))
+                        cp_async16(&tile[jj * RP + q],
+                                   src + p.in_off(a, warp_chain0 + jj, sm->start[jj]) + i);
+                }
+            } else {
 #pragma unroll 4
-            for (int u = 0; u < CH; ++u) {
-                const int t = u * WARP + lane;
-                const int jj = t / CH, node = t % CH;
-                const int i = chunk * CH + node;
-                const int n = sm->len[jj];
-                if (i < p.in_lim(a, n))
-                    cp_async4(&sm->in[a][b][jj][node],
-                              src + p.in_off(a, warp_chain0 + jj, sm->start[jj]) + i);
+                for (int u = 0; u < CH; ++u) {
+                    const int t = u * WARP + lane;
+                    const int jj = t / CH, node = t % CH;
+                    const int i = chunk * CH + node;
+                    if (i < p.in_lim(a, sm->len[jj]))
+                        cp_async4(&tile[jj * RP + node],
+                                  src + p.in_off(a, warp_chain0 + jj, sm->start[jj]) + i);
+                }
             }
         }
     }
@@ -303,13 +435,25 @@ __device__ __forceinline__ void flush_outputs(const P &p, WarpSmem<P, RING> *sm,
                                               int lane, long long warp_chain0, int o)
 {
     float *dst = p.out_ptr(o);
+    if (p.out_vec()) {
+#pragma unroll
+        for (int u = 0; u < CH / 4; ++u) {
+            const int t = u * WARP + lane;
+            const int jj = t >> 2, q = (t & 3) * 4;
+            const int i = chunk * CH + q;
+            if (i < sm->len[jj])
+                *reinterpret_cast<float4 *>(dst + p.out_off(o, warp_chain0 + jj, sm->start[jj]) + i) =
+                    *reinterpret_cast<const float4 *>(&sm->out[jj * RP + q]);
+        }
+    } else {
 #pragma unroll 4
-    for (int u = 0; u < CH; ++u) {
-        const int t = u * WARP + lane;
-        const int jj = t / CH, node = t % CH;
-        const int i = chunk * CH + node;
-        if (i < sm->len[jj])
-            dst[p.out_off(o, warp_chain0 + jj, sm->start[jj]) + i] = sm->out[jj][node];
+        for (int u = 0; u < CH; ++u) {
+            const int t = u * WARP + lane;
+            const int jj = t / CH, node = t % CH;
+            const int i = chunk * CH + node;
+            if (i < sm->len[jj])
+                dst[p.out_off(o, warp_chain0 + jj, sm->start[jj]) + i] = sm->out[jj * RP + node];
+        }
     }
 }
 
@@ -343,11 +487,16 @@ __device__ void solve_chain_global(const P &p, long long k, long long start, int
         float cc = 0.f;
         if constexpr (P::CREC) cc = crec_w[(long long)i * WARP + lane];
         if (i < n - 1) {
-            float2 r = rec_w[(long long)i * WARP + lane];
+            const float2 r = rec_w[(long long)i * WARP + lane];
             xv = clip_to(xv, r.x, r.y);
         }
         p.emit_direct(i, k, start, xv, cc);
     }
+}
+
+__device__ __forceinline__ float pick4(const float4 &q, int e)
+{
+    return e == 0 ? q.x : (e == 1 ? q.y : (e == 2 ? q.z : q.w));
 }
 
 template <class P, int RING>
@@ -388,7 +537,7 @@ __global__ void __launch_bounds__(128) chain_batch_kernel(P p_in, float2 *rec, f
     float2 *rec_w = rec + wg * (long long)max_len * WARP;
     float *crec_w = P::CREC ? crec + wg * (long long)max_len * WARP : nullptr;
 
-    RingStore<RING> S{&sm->ring[0][lane]};
+    RingStore<RING> S{(unsigned)__cvta_generic_to_shared(&sm->ring[0][lane])};
     DPState d;
     typename P::Acc acc;
     p.acc_init(acc);
@@ -405,26 +554,49 @@ __global__ void __launch_bounds__(128) chain_batch_kernel(P p_in, float2 *rec, f
         cp_async_wait<1>();
         __syncwarp();
 #pragma unroll 1
-        for (int j = 0; j < CH; ++j) {
-            const int i = ch * CH + j;
-            float c, w;
-            p.unary(sm->in, b, j, lane, i, n, k, c, w, acc);
-            if (i < n) {
-                if constexpr (P::CREC) crec_w[(long long)i * WARP + lane] = c;
-                if (alive) {
-                    float lm, hp;
-                    if (i == 0) {
-                        if (n == 1) {
-                            lm = hp = c;
-                        } else {
-                            dp_first(d, S, 0, c, w, lm, hp);
-                        }
-                    } else {
-                        alive = dp_step(d, S, RING, c, w, (float)(i + 1), lm, hp);
+        for (int j4 = 0; j4 < CH; j4 += 4) {
+            float4 q[P::NIN];
+            if constexpr (!P::COLS) {
+#pragma unroll
+                for (int a = 0; a < P::NIN; ++a)
+                    q[a] = *reinterpret_cast<const float4 *>(&sm->in[a][b][lane * RP + j4]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = j4 + e;
+                const int i = ch * CH + j;
+                float v[P::NIN];
+                float xr = 0.f;
+                if constexpr (P::COLS) {
+#pragma unroll
+                    for (int a = 0; a < P::NIN; ++a) v[a] = sm->in[a][b][j * CP + lane];
+                    if constexpr (P::NEIGH) {
+                        const float sh = __shfl_down_sync(0xffffffffu, v[0], 1);
+                        xr = (lane == WARP - 1) ? sm->in[0][b][j * CP + WARP] : sh;
                     }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < P::NIN; ++a) v[a] = pick4(q[a], e);
+                }
+                float c, w;
+                p.unary(v, xr, j, i, n, k, c, w, acc);
+                if (i < n) {
+                    if constexpr (P::CREC) crec_w[(long long)i * WARP + lane] = c;
                     if (alive) {
-                        if (i == n - 1) xlast = (n == 1) ? c : 0.5f * (lm + hp);
-                        else rec_w[(long long)i * WARP + lane] = make_float2(lm, hp);
+                        float lm, hp;
+                        if (i == 0) {
+                            if (n == 1) {
+                                lm = hp = c;
+                            } else {
+                                dp_first(d, S, 0, c, w, lm, hp);
+                            }
+                        } else {
+                            alive = dp_step(d, S, RING, c, w, (float)(i + 1), lm, hp);
+                        }
+                        if (alive) {
+                            if (i == n - 1) xlast = (n == 1) ? c : 0.5f * (lm + hp);
+                            else rec_w[(long long)i * WARP + lane] = make_float2(lm, hp);
+                        }
                     }
                 }
             }
@@ -447,7 +619,7 @@ __global__ void __launch_bounds__(128) chain_batch_kernel(P p_in, float2 *rec, f
         cp_async_commit();
         cp_async_wait<1>();
         __syncwarp();
-#pragma unroll 1
+#pragma unroll 4
         for (int j = CH - 1; j >= 0; --j) {
             const int i = ch * CH + j;
             if (i < n_eff) {
@@ -460,7 +632,7 @@ __global__ void __launch_bounds__(128) chain_batch_kernel(P p_in, float2 *rec, f
                 if constexpr (P::COLS) {
                     p.emit_cols(i, k, xv, cc);
                 } else {
-                    sm->out[lane][j] = xv;
+                    sm->out[lane * RP + j] = xv;
                 }
             }
         }
@@ -471,6 +643,7 @@ __global__ void __launch_bounds__(128) chain_batch_kernel(P p_in, float2 *rec, f
             __syncwarp();
 #pragma unroll
             for (int o = 0; o < P::NOUT; ++o) flush_outputs(p, sm, ch, lane, warp_chain0, o);
+            __syncwarp();
             if (!alive) sm->len[lane] = n;
         }
         __syncwarp();

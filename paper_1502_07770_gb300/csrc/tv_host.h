@@ -7,7 +7,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
-#include "../../include/tv.h"
+#include "tv.h"
 
 namespace tvh {
 

@@ -1,0 +1,38 @@
+// Launch of a batch-of-chains kernel, shared by the chain and 2D entry points:
+// launch shape, shared-memory opt-in, launch counting and optional per-launch
+// CUDA-event timing (for benchmarks; off by default).
+#pragma once
+#include "tv_dp.cuh"
+#include "tv_host.h"
+
+namespace tvh {
+
+enum ProfKind { PK_CHAIN = 0, PK_COL = 1, PK_ROW = 2, PK_INIT = 3, PK_N = 4 };
+
+void note_launch();
+bool prof_on();
+void prof_mark(int kind, cudaStream_t s, bool start);
+
+template <class P, int RING>
+tv_status launch_chains(const P &p, long long nchains, float2 *rec, float *crec, float2 *spill,
+                        tvk::WsHeader *hdr, cudaStream_t s, int kind)
+{
+    const long long warps = (nchains + tvk::WARP - 1) / tvk::WARP;
+    if (warps == 0) return TV_OK;
+    const Shape sh = batch_shape(warps, sm_count_current());
+    const size_t per_warp = sizeof(tvk::WarpSmem<P, RING>);
+    auto kern = tvk::chain_batch_kernel<P, RING>;
+    tv_status st = check_cuda(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * per_warp)),
+        "cudaFuncSetAttribute");
+    if (st != TV_OK) return st;
+    const bool prof = prof_on();
+    if (prof) prof_mark(kind, s, true);
+    kern<<<(unsigned)sh.blocks, sh.wpb * tvk::WARP, sh.wpb * per_warp, s>>>(p, rec, crec, spill, hdr);
+    st = check_cuda(cudaGetLastError(), "chain kernel launch");
+    if (st == TV_OK) note_launch();
+    if (prof) prof_mark(kind, s, false);
+    return st;
+}
+
+}  // namespace tvh
