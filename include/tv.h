@@ -101,6 +101,26 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
                          float *d_x, void *d_workspace, size_t workspace_bytes,
                          tv_stream_t stream);
 
+/*
+ * tv_chain_solve for callers that cannot allocate device memory (the paper has no
+ * counterpart). Some callers must not call cudaMalloc: code running inside a
+ * framework that has reserved the GPU's memory for its own caching allocator, and
+ * latency-critical loops that cannot take the synchronisation an allocation may
+ * cause. This entry point takes only inputs and outputs, with the same meaning
+ * as tv_chain_solve; its scratch is a fixed 16 MiB array in device memory that
+ * every GPU loading the library holds until the process exits. That bounds the
+ * batch: num_chains * max_len may be at most about 690 000 nodes (the records and
+ * the reserve take about 24 bytes per node); larger batches are rejected with
+ * TV_ERR_INVALID before any launch. The first call on a device looks up the
+ * array's device address (make it before any stream capture). All calls share
+ * the array: calls that overlap on the GPU race and must be ordered by the
+ * caller. Device-side errors are not readable for this entry point (it has no
+ * caller-visible workspace); malformed offsets skip the affected chains.
+ */
+tv_status tv_chain_solve_noalloc(const float *d_y, const float *d_w, float lambda,
+                                 const int64_t *d_offsets, int64_t num_chains, int64_t max_len,
+                                 float *d_x, tv_stream_t stream);
+
 /* Bytes of workspace tv_chain_solve_columns needs for an H x W array. */
 size_t tv_columns_workspace_size(int64_t H, int64_t W);
 

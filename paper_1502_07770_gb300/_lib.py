@@ -37,6 +37,7 @@ SIGNATURES = {
                                        ctypes.POINTER(_i64)]),
     "tv_chain_workspace_size": (_sz, [_i64, _i64]),
     "tv_chain_solve": (ctypes.c_int, [_p, _p, ctypes.c_float, _p, _i64, _i64, _p, _p, _sz, _p]),
+    "tv_chain_solve_noalloc": (ctypes.c_int, [_p, _p, ctypes.c_float, _p, _i64, _i64, _p, _p]),
     "tv_columns_workspace_size": (_sz, [_i64, _i64]),
     "tv_chain_solve_columns": (ctypes.c_int,
                                [_p, _p, ctypes.c_float, _i64, _i64, _i64, _p, _p, _sz, _p]),

@@ -446,3 +446,105 @@ tv_status tv_workspace_status(void *d_workspace, tv_stream_t stream, int *status
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------
+// Chain solve for callers that cannot allocate device memory.
+//
+// Some callers must not call cudaMalloc at all: code running inside a framework
+// that has reserved the GPU's memory for its own caching allocator (a cudaMalloc
+// there fails or fragments the framework's pool), and latency-critical loops that
+// cannot take the implicit device synchronisation an allocation may cause. They
+// pass only inputs and outputs; the scratch (the per-node records of the forward
+// pass and the reserve for long message sequences) comes from this fixed array.
+//
+// The array lives in every GPU that loads the library, until the process exits.
+// Its device address is looked up once per device, on the first call made with
+// that device current; make that first call before any stream capture.
+// Every call shares the array: calls that overlap on the GPU (different streams,
+// or different host threads, on the same device) race on it and must be ordered
+// by the caller. The header words are cleared on every call.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices];
+
+tv_status noalloc_scratch(void **out)
+{
+    int dev = 0;
+    tv_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st != TV_OK) return st;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("tv_chain_solve_noalloc: device ordinal %d is not supported", dev);
+        return TV_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        st = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+        if (st != TV_OK) return st;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return TV_OK;
+}
+
+}  // namespace
+
+extern "C" tv_status tv_chain_solve_noalloc(const float *d_y, const float *d_w, float lambda,
+                                            const int64_t *d_offsets, int64_t num_chains,
+                                            int64_t max_len, float *d_x, tv_stream_t stream)
+{
+    clear_error();
+    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 30)) {
+        set_error("tv_chain_solve_noalloc: num_chains and max_len must be >= 0 (max_len <= 2^30)");
+        return TV_ERR_INVALID;
+    }
+    if (num_chains == 0) return TV_OK;
+    if (!d_y || !d_x) {
+        set_error("tv_chain_solve_noalloc: y and x must not be NULL");
+        return TV_ERR_INVALID;
+    }
+    if (!d_w && !(lambda >= 0.f && lambda < INFINITY)) {
+        set_error("tv_chain_solve_noalloc: lambda must be finite and >= 0");
+        return TV_ERR_INVALID;
+    }
+    if (!d_offsets) {
+        const size_t bytes = (size_t)num_chains * (size_t)max_len * sizeof(float);
+        if (overlaps(d_x, bytes, d_y, bytes) || overlaps(d_x, bytes, d_w, bytes)) {
+            set_error("tv_chain_solve_noalloc: x must not overlap y or w");
+            return TV_ERR_INVALID;
+        }
+    } else if (d_x == d_y || (d_w && d_x == d_w)) {
+        set_error("tv_chain_solve_noalloc: x must not alias y or w");
+        return TV_ERR_INVALID;
+    }
+    const long long warps = (num_chains + WARP - 1) / WARP;
+    const long long total = (long long)num_chains * max_len;
+    const size_t need = carve_chain_ws(nullptr, warps, max_len, 2 * total + 2 * num_chains).bytes;
+    if (need > kNoAllocScratchBytes) {
+        set_error("tv_chain_solve_noalloc: %lld chains x %lld nodes need %zu bytes of scratch, "
+                  "more than the fixed %zu; use tv_chain_solve with a workspace",
+                  (long long)num_chains, (long long)max_len, need, kNoAllocScratchBytes);
+        return TV_ERR_INVALID;
+    }
+    void *scratch = nullptr;
+    tv_status st = noalloc_scratch(&scratch);
+    if (st != TV_OK) return st;
+    ChainWs ws = carve_chain_ws(scratch, warps, max_len, 2 * total + 2 * num_chains);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "clear scratch header");
+    if (st != TV_OK) return st;
+    if (d_w) {
+        ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,
+                           vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0};
+        return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
+    }
+    ChainRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x,
+                        vec_ok(d_offsets, max_len, d_y, nullptr, d_x), 0};
+    return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
+}
