@@ -55,10 +55,20 @@ struct Tv2dParams {
     double tau, sigma, theta_prev, tau_prev;  // tau_k, sigma_k, theta_{k-1}, tau_{k-1}
 };
 
+// The step sizes of eq. pd (accelerated variant, gamma = 1, tau_0 = sigma_0 = 1)
+// are computed on the host in FP64 and passed to the device by value, 256 per
+// launch; the first launch also resets the iteration state.
+constexpr int kParamChunk = 256;
+struct ParamChunk {
+    int first, count;
+    Tv2dParams p[kParamChunk];
+};
+
 __global__ void tv2d_init_state(Tv2dState *st, Tv2dParams *prm, int max_iters, double tol,
-                                double inv_N)
+                                double inv_N, ParamChunk chunk)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int q = threadIdx.x; q < chunk.count; q += blockDim.x) prm[chunk.first + q] = chunk.p[q];
+    if (threadIdx.x != 0 || chunk.first != 0) return;
     st->k = 0;
     st->done = 0;
     st->ticket_col = 0;
@@ -68,15 +78,6 @@ __global__ void tv2d_init_state(Tv2dState *st, Tv2dParams *prm, int max_iters, d
     st->tol = tol;
     st->inv_N = inv_N;
     st->gap = nan("");
-    double tau = 1.0, sigma = 1.0, theta_prev = 0.0, tau_prev = 1.0;
-    for (int k = 0; k <= max_iters; ++k) {
-        prm[k] = Tv2dParams{tau, sigma, theta_prev, tau_prev};
-        const double theta = 1.0 / sqrt(1.0 + 2.0 * tau);
-        tau_prev = tau;
-        tau *= theta;
-        sigma /= theta;
-        theta_prev = theta;
-    }
 }
 
 // Warp-level completion counter: returns true in lane 0 of the last warp of the grid.
@@ -252,47 +253,35 @@ struct RowPhaseP {
 };
 
 // ------------------------------------------------------------ dual step ------
-template <bool HAS_WV, bool HAS_WH>
+template <bool HAS_WV>
 struct ColPhaseP {
     static constexpr bool COLS = true;
-    static constexpr int IWV = 4;
-    static constexpr int IWH = HAS_WV ? 5 : 4;
-    static constexpr int NIN = 4 + (HAS_WV ? 1 : 0) + (HAS_WH ? 1 : 0);
-    static constexpr bool NEIGH = true;
+    static constexpr int NIN = HAS_WV ? 4 : 3;
+    static constexpr bool NEIGH = false;
     static constexpr bool CREC = true;
     static constexpr int NOUT = 0;
-    struct Acc {
-        double total;
-        float chunk;
-        float x_prev, wv_prev;
-    };
+    struct Acc {};
 
-    const float *f, *wv, *wh;
+    const float *wv;
     float lam;
     long long H, W;
     float *buf0, *buf1, *y;
     Tv2dState *st;
     const Tv2dParams *prm;
-    double *partials, *gaps;
     bool vec;
     // resolved per launch
     const float *xk, *xkm1;
-    float sigma, inv_sigma, theta, inv_tau_prev;
-    int k_iter;
-    bool gap_on;
+    float sigma, inv_sigma, theta;
 
     __device__ bool resolve()
     {
         if (st->done) return false;
         const int k = st->k;
-        k_iter = k;
         xk = (k & 1) ? buf1 : buf0;
         xkm1 = (k & 1) ? buf0 : buf1;
         sigma = (float)prm[k].sigma;
         inv_sigma = (float)(1.0 / prm[k].sigma);
         theta = (float)prm[k].theta_prev;
-        inv_tau_prev = (float)(1.0 / prm[k].tau_prev);
-        gap_on = k >= 1;
         return true;
     }
     __device__ long long num_chains() const { return W; }
@@ -305,43 +294,21 @@ struct ColPhaseP {
     }
     __device__ const float *in_ptr(int a) const
     {
-        switch (a) {
-        case 0: return xk;
-        case 1: return xkm1;
-        case 2: return y;
-        case 3: return f;
-        default: return (HAS_WV && a == IWV) ? wv : wh;
-        }
+        return a == 0 ? xk : (a == 1 ? xkm1 : (a == 2 ? y : wv));
     }
     __device__ long long in_off(int, long long, long long start) const { return start; }
-    __device__ int in_lim(int a, int n) const { return (HAS_WV && a == IWV) ? n - 1 : n; }
-    __device__ long long in_ld(int a) const { return (HAS_WH && a == IWH) ? W - 1 : W; }
-    __device__ long long in_kmax(int a) const { return (HAS_WH && a == IWH) ? W - 1 : W; }
-    __device__ bool in_vec(int a) const { return vec && !(HAS_WH && a == IWH); }
+    __device__ int in_lim(int a, int n) const { return a == 3 ? n - 1 : n; }
+    __device__ long long in_ld(int) const { return W; }
+    __device__ long long in_kmax(int) const { return W; }
+    __device__ bool in_vec(int) const { return vec; }
     __device__ bool out_vec() const { return false; }
-    __device__ void unary(const float (&v)[NIN], float xr, int j, int i, int n, long long col,
-                          float &c, float &w, Acc &acc) const
+    __device__ void unary(const float (&v)[NIN], float, int, int i, int n, long long, float &c,
+                          float &w, Acc &) const
     {
-        const float xv = v[0], xp = v[1], yv = v[2], fv = v[3];
-        float wvv = lam, whv = lam;
-        if constexpr (HAS_WV) wvv = v[IWV];
-        if constexpr (HAS_WH) whv = v[IWH];
-        const float xbar = xv + theta * (xv - xp);
-        c = yv * inv_sigma + xbar;  // eta / sigma
+        float wvv = lam;
+        if constexpr (HAS_WV) wvv = v[3];
+        c = v[2] * inv_sigma + (v[0] + theta * (v[0] - v[1]));  // eta / sigma
         w = (i < n - 1) ? wvv * inv_sigma : 0.f;
-        if (gap_on && i < n && col < W) {
-            const float z = xv + (xv - xp) * inv_tau_prev;
-            float t = 0.5f * (xv - fv) * (xv - fv) + 0.5f * (z - fv) * (z + fv);
-            if (i > 0) t += acc.wv_prev * fabsf(xv - acc.x_prev);
-            if (col < W - 1) t += whv * fabsf(xr - xv);
-            acc.chunk += t;
-        }
-        acc.x_prev = xv;
-        acc.wv_prev = wvv;
-        if (j == CH - 1 || i == n - 1) {
-            acc.total += (double)acc.chunk;
-            acc.chunk = 0.f;
-        }
     }
     __device__ void unary_direct(int i, int n, long long col, long long, float &c, float &w) const
     {
@@ -361,35 +328,285 @@ struct ColPhaseP {
         y[(long long)i * W + col] = sigma * (c - xhat);
     }
     __device__ long long spill_off(long long col, long long) const { return col * (2 * H + 2); }
-    __device__ void acc_init(Acc &a) const
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &) const {}
+    __device__ void finish_empty() const {}
+};
+
+// ============ the same three phases, one warp per chain (tv_coop.cuh) ============
+
+template <bool HAS_WH>
+struct CoopInitRowsP {
+    static constexpr bool CREC = false;
+    struct Raw {
+        float f, y, w;
+    };
+    struct Acc {};
+    const float *f, *y, *wh;
+    float lam;
+    long long H, W;
+    float *x0, *x1;
+
+    __device__ bool resolve() { return true; }
+    __device__ long long num_chains() const { return H; }
+    __device__ int max_len() const { return (int)W; }
+    __device__ bool chain(long long k, long long &start, int &n) const
     {
-        a.total = 0.0;
-        a.chunk = 0.f;
-        a.x_prev = 0.f;
-        a.wv_prev = 0.f;
+        start = k * W;
+        n = (int)W;
+        return true;
     }
-    __device__ void reduce_gap(double v) const
+    __device__ void fetch(long long k, long long start, int n, int i, Raw &r) const
     {
-        if (!gap_on) return;
+        r.f = (i < n) ? f[start + i] : 0.f;
+        r.y = (i < n) ? y[start + i] : 0.f;
+        if constexpr (HAS_WH) r.w = (i < n - 1) ? wh[k * (W - 1) + i] : 0.f;
+    }
+    __device__ void unary(long long, long long, int, int, const Raw &r, float &c, float &w,
+                          Acc &) const
+    {
+        c = r.f - r.y;
+        if constexpr (HAS_WH) w = r.w;
+        else w = lam;
+    }
+    __device__ void emit(long long, long long start, int i, float xv, float) const
+    {
+        x0[start + i] = xv;
+        x1[start + i] = xv;
+    }
+    __device__ void unary_direct(int i, int n, long long k, long long start, float &c,
+                                 float &w) const
+    {
+        c = f[start + i] - y[start + i];
+        if constexpr (HAS_WH) w = (i < n - 1) ? wh[k * (W - 1) + i] : 0.f;
+        else w = (i < n - 1) ? lam : 0.f;
+    }
+    __device__ void emit_direct(int i, long long k, long long start, float xv, float c) const
+    {
+        emit(k, start, i, xv, c);
+    }
+    __device__ long long spill_off(long long k, long long) const { return k * (2 * W + 2); }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &, int) const {}
+    __device__ void finish_empty() const {}
+};
+
+template <bool HAS_WH>
+struct CoopRowPhaseP {
+    static constexpr bool CREC = false;
+    struct Raw {
+        float f, x, y, w;
+    };
+    struct Acc {};
+    const float *f, *y, *wh;
+    float lam;
+    long long H, W;
+    float *buf0, *buf1;
+    Tv2dState *st;
+    const Tv2dParams *prm;
+    const float *xin;
+    float *xout;
+    float ca, cb;
+
+    __device__ bool resolve()
+    {
+        const int k = st->k;
+        if (st->done || k >= st->max_iters) return false;
+        xin = (k & 1) ? buf1 : buf0;
+        xout = (k & 1) ? buf0 : buf1;
+        const double tau = prm[k].tau;
+        ca = (float)(tau / (tau + 1.0));
+        cb = (float)(1.0 / (tau + 1.0));
+        return true;
+    }
+    __device__ long long num_chains() const { return H; }
+    __device__ int max_len() const { return (int)W; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        start = k * W;
+        n = (int)W;
+        return true;
+    }
+    __device__ void fetch(long long k, long long start, int n, int i, Raw &r) const
+    {
+        const bool in = i < n;
+        r.f = in ? f[start + i] : 0.f;
+        r.x = in ? xin[start + i] : 0.f;
+        r.y = in ? y[start + i] : 0.f;
+        if constexpr (HAS_WH) r.w = (i < n - 1) ? wh[k * (W - 1) + i] : 0.f;
+    }
+    __device__ void unary(long long, long long, int, int, const Raw &r, float &c, float &w,
+                          Acc &) const
+    {
+        c = ca * (r.f - r.y) + cb * r.x;
+        float wv = lam;
+        if constexpr (HAS_WH) wv = r.w;
+        w = ca * wv;
+    }
+    __device__ void emit(long long, long long start, int i, float xv, float) const
+    {
+        xout[start + i] = xv;
+    }
+    __device__ void unary_direct(int i, int n, long long k, long long start, float &c,
+                                 float &w) const
+    {
+        float wv = lam;
+        if constexpr (HAS_WH) wv = (i < n - 1) ? wh[k * (W - 1) + i] : 0.f;
+        c = ca * (f[start + i] - y[start + i]) + cb * xin[start + i];
+        w = (i < n - 1) ? ca * wv : 0.f;
+    }
+    __device__ void emit_direct(int i, long long k, long long start, float xv, float c) const
+    {
+        emit(k, start, i, xv, c);
+    }
+    __device__ long long spill_off(long long k, long long) const { return k * (2 * W + 2); }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void count_done() const
+    {
         const int lane = threadIdx.x & (WARP - 1);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        const long long wg = (long long)blockIdx.x * (blockDim.x / WARP) + threadIdx.x / WARP;
-        if (lane == 0) partials[wg] = v;
-        if (last_warp_done(&st->ticket_col, lane)) {
-            const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
-            double G = 0.0;
-            for (long long q = 0; q < nw; ++q) G += partials[q];
-            const double g = G * st->inv_N;
-            st->gap = g;
-            st->gap_k = k_iter - 1;
-            gaps[k_iter - 1] = g;
-            if (st->tol > 0.0 && g <= st->tol) st->done = 1;
+        if (last_warp_done(&st->ticket_row, lane)) st->k = st->k + 1;
+    }
+    __device__ void finish(Acc &, int) const { count_done(); }
+    __device__ void finish_empty() const { count_done(); }
+};
+
+template <bool HAS_WV>
+struct CoopColPhaseP {
+    static constexpr bool CREC = true;
+    struct Raw {
+        float x, xp, y, wv;
+    };
+    struct Acc {};
+    const float *wv;
+    float lam;
+    long long H, W;
+    float *buf0, *buf1, *y;
+    Tv2dState *st;
+    const Tv2dParams *prm;
+    const float *xk, *xkm1;
+    float sigma, inv_sigma, theta;
+
+    __device__ bool resolve()
+    {
+        if (st->done) return false;
+        const int k = st->k;
+        xk = (k & 1) ? buf1 : buf0;
+        xkm1 = (k & 1) ? buf0 : buf1;
+        sigma = (float)prm[k].sigma;
+        inv_sigma = (float)(1.0 / prm[k].sigma);
+        theta = (float)prm[k].theta_prev;
+        return true;
+    }
+    __device__ long long num_chains() const { return W; }
+    __device__ int max_len() const { return (int)H; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        start = k;
+        n = (int)H;
+        return true;
+    }
+    __device__ void fetch(long long col, long long, int n, int i, Raw &r) const
+    {
+        const bool in = i < n;
+        const long long o = (long long)i * W + col;
+        r.x = in ? xk[o] : 0.f;
+        r.xp = in ? xkm1[o] : 0.f;
+        r.y = in ? y[o] : 0.f;
+        if constexpr (HAS_WV) r.wv = (i < n - 1) ? wv[o] : 0.f;
+    }
+    __device__ void unary(long long, long long, int, int, const Raw &r, float &c, float &w,
+                          Acc &) const
+    {
+        float wvv = lam;
+        if constexpr (HAS_WV) wvv = r.wv;
+        c = r.y * inv_sigma + (r.x + theta * (r.x - r.xp));  // eta / sigma
+        w = wvv * inv_sigma;
+    }
+    __device__ void emit(long long col, long long, int i, float xhat, float c) const
+    {
+        y[(long long)i * W + col] = sigma * (c - xhat);
+    }
+    __device__ void unary_direct(int i, int n, long long col, long long, float &c, float &w) const
+    {
+        (void)c;  // c comes from the forward-pass record
+        float wvv = lam;
+        if constexpr (HAS_WV) wvv = (i < n - 1) ? wv[(long long)i * W + col] : 0.f;
+        w = (i < n - 1) ? wvv * inv_sigma : 0.f;
+    }
+    __device__ void emit_direct(int i, long long col, long long start, float xhat, float c) const
+    {
+        emit(col, start, i, xhat, c);
+    }
+    __device__ long long spill_off(long long col, long long) const { return col * (2 * H + 2); }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &, int) const {}
+    __device__ void finish_empty() const {}
+};
+
+// ------------------------------------------------------------------ gap ------
+// G_k after the primal step of iteration k (k = st->k - 1 once the row kernel has
+// counted itself): the per-pixel terms 1/2 (x - f)^2 + 1/2 (z - f)(z + f) with
+// z = x^{k+1} + (x^{k+1} - x^k)/tau_k, plus w |difference| over the right and lower
+// neighbour of every pixel. One pass over the image; FP32 within a thread, FP64
+// across threads; the last block reduces the block partials in a fixed order and
+// raises the stop flag.
+constexpr int kGapThreads = 256;
+
+__global__ void __launch_bounds__(kGapThreads)
+    tv2d_gap_kernel(const float *f, const float *wh, const float *wv, float lam, long long H,
+                    long long W, const float *buf0, const float *buf1, Tv2dState *st,
+                    const Tv2dParams *prm, double *partials, double *gaps, unsigned *ticket)
+{
+    __shared__ double red[kGapThreads / WARP];
+    if (st->done) return;
+    const int kp1 = st->k;  // x^{k+1} is the newest iterate
+    if (kp1 < 1) return;
+    const int k = kp1 - 1;
+    const float *x1 = (kp1 & 1) ? buf1 : buf0;  // x^{k+1}
+    const float *x0 = (kp1 & 1) ? buf0 : buf1;  // x^k
+    const float inv_tau = (float)(1.0 / prm[k].tau);
+    const long long N = H * W;
+    double acc = 0.0;
+    float part = 0.f;
+    int cnt = 0;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long r = q / W, c = q - r * W;
+        const float xv = x1[q], fv = f[q];
+        const float z = xv + (xv - x0[q]) * inv_tau;
+        float t = 0.5f * (xv - fv) * (xv - fv) + 0.5f * (z - fv) * (z + fv);
+        if (c + 1 < W) t += (wh ? wh[r * (W - 1) + c] : lam) * fabsf(x1[q + 1] - xv);
+        if (r + 1 < H) t += (wv ? wv[q] : lam) * fabsf(x1[q + W] - xv);
+        part += t;
+        if (++cnt == 32) {
+            acc += (double)part;
+            part = 0.f;
+            cnt = 0;
         }
     }
-    __device__ void finish(Acc &a) const { reduce_gap(a.total); }
-    __device__ void finish_empty() const { reduce_gap(0.0); }
-};
+    acc += (double)part;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & (WARP - 1)) == 0) red[threadIdx.x / WARP] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < kGapThreads / WARP; ++w) b += red[w];
+        partials[blockIdx.x] = b;
+        __threadfence();
+        if (atomicAdd(ticket, 1u) == gridDim.x - 1) {
+            __threadfence();
+            double G = 0.0;
+            for (unsigned bq = 0; bq < gridDim.x; ++bq) G += partials[bq];
+            const double g = G * st->inv_N;
+            st->gap = g;
+            st->gap_k = k;
+            gaps[k] = g;
+            if (st->tol > 0.0 && g <= st->tol) st->done = 1;
+            *ticket = 0;
+        }
+    }
+}
 
 template <class P>
 tv_status launch(const P &p, long long nchains, float2 *rec, float *crec, float2 *spill,
@@ -421,7 +638,7 @@ Tv2dWs carve_tv2d(void *base, long long H, long long W, int max_iters)
     o.st = cv.take<Tv2dState>(1);
     o.prm = cv.take<Tv2dParams>((size_t)max_iters + 2);
     o.gaps = cv.take<double>((size_t)max_iters + 2);
-    o.partials = cv.take<double>((size_t)(wc + 8));
+    o.partials = cv.take<double>((size_t)4096);  // one per block of the gap kernel
     o.hdr = cv.take<WsHeader>(1);
     o.y = cv.take<float>((size_t)(H * W));
     o.buf1 = cv.take<float>((size_t)(H * W));
@@ -439,6 +656,10 @@ template <bool HAS_WH>
 tv_status launch_init(const float *img, const float *wh, float lam, long long H, long long W,
                       float *x0, const Tv2dWs &ws, cudaStream_t s)
 {
+    if (H <= kCoopMaxChains) {
+        CoopInitRowsP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1};
+        return launch_coop(p, H, (int)W, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_INIT);
+    }
     InitRowsP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1, ws.vec_rows};
     return launch(p, H, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_INIT);
 }
@@ -447,28 +668,54 @@ template <bool HAS_WH>
 tv_status launch_row(const float *img, const float *wh, float lam, long long H, long long W,
                      float *x0, const Tv2dWs &ws, cudaStream_t s)
 {
+    if (H <= kCoopMaxChains) {
+        CoopRowPhaseP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1, ws.st, ws.prm,
+                                nullptr, nullptr, 0.f, 0.f};
+        return launch_coop(p, H, (int)W, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_ROW);
+    }
     RowPhaseP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1, ws.st, ws.prm, ws.vec_rows,
                         nullptr, nullptr, 0.f, 0.f};
     return launch(p, H, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_ROW);
 }
 
-template <bool HAS_WV, bool HAS_WH>
-tv_status launch_col(const float *img, const float *wv, const float *wh, float lam, long long H,
-                     long long W, float *x0, const Tv2dWs &ws, cudaStream_t s)
+template <bool HAS_WV>
+tv_status launch_col(const float *wv, float lam, long long H, long long W, float *x0,
+                     const Tv2dWs &ws, cudaStream_t s)
 {
-    ColPhaseP<HAS_WV, HAS_WH> p{img, wv, wh, lam, H, W, x0, ws.buf1, ws.y, ws.st, ws.prm,
-                                ws.partials, ws.gaps, ws.vec_cols && aligned16(wv),
-                                nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 0, false};
+    if (W <= kCoopMaxChains) {
+        CoopColPhaseP<HAS_WV> p{wv, lam, H, W, x0, ws.buf1, ws.y, ws.st, ws.prm,
+                                nullptr, nullptr, 0.f, 0.f, 0.f};
+        return launch_coop(p, W, (int)H, ws.rec, ws.crec, ws.spill, ws.hdr, s, PK_COL);
+    }
+    ColPhaseP<HAS_WV> p{wv, lam, H, W, x0, ws.buf1, ws.y, ws.st, ws.prm,
+                        ws.vec_cols && aligned16(wv), nullptr, nullptr, 0.f, 0.f, 0.f};
     return launch(p, W, ws.rec, ws.crec, ws.spill, ws.hdr, s, PK_COL);
 }
 
-tv_status launch_col_any(const float *img, const float *wv, const float *wh, float lam,
-                         long long H, long long W, float *x0, const Tv2dWs &ws, cudaStream_t s)
+tv_status launch_col_any(const float *wv, float lam, long long H, long long W, float *x0,
+                         const Tv2dWs &ws, cudaStream_t s)
 {
-    if (wv && wh) return launch_col<true, true>(img, wv, wh, lam, H, W, x0, ws, s);
-    if (wv) return launch_col<true, false>(img, wv, wh, lam, H, W, x0, ws, s);
-    if (wh) return launch_col<false, true>(img, wv, wh, lam, H, W, x0, ws, s);
-    return launch_col<false, false>(img, wv, wh, lam, H, W, x0, ws, s);
+    return wv ? launch_col<true>(wv, lam, H, W, x0, ws, s)
+              : launch_col<false>(wv, lam, H, W, x0, ws, s);
+}
+
+int gap_blocks(long long H, long long W)
+{
+    long long b = (H * W + kGapThreads * 8 - 1) / (kGapThreads * 8);
+    const long long cap = 4LL * sm_count_current();
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+tv_status launch_gap(const float *img, const float *wh, const float *wv, float lam, long long H,
+                     long long W, float *x0, const Tv2dWs &ws, cudaStream_t s)
+{
+    const int blocks = gap_blocks(H, W);
+    tv2d_gap_kernel<<<blocks, kGapThreads, 0, s>>>(img, wh, wv, lam, H, W, x0, ws.buf1, ws.st,
+                                                   ws.prm, ws.partials, ws.gaps,
+                                                   &ws.st->ticket_col);
+    tv_status st = check_cuda(cudaGetLastError(), "gap kernel launch");
+    if (st == TV_OK) note_launch();
+    return st;
 }
 
 tv_status read_state(const Tv2dWs &ws, cudaStream_t s, Tv2dState &out)
@@ -531,9 +778,27 @@ tv_status tv2d_denoise(const float *d_img, int64_t H, int64_t W, const float *d_
     ws.vec_rows = ws.vec_cols = (W % 4 == 0) && aligned16(d_img) && aligned16(d_x);
     cudaStream_t s = (cudaStream_t)stream;
     tv_status st;
-    tv2d_init_state<<<1, 1, 0, s>>>(ws.st, ws.prm, max_iters, gap_tol, 1.0 / ((double)H * W));
-    if ((st = check_cuda(cudaGetLastError(), "init state")) != TV_OK) return st;
-    note_launch();
+    {
+        // step sizes of eq. pd, FP64 on the host
+        static thread_local ParamChunk chunk;
+        double tau = 1.0, sigma = 1.0, theta_prev = 0.0, tau_prev = 1.0;
+        for (int first = 0; first <= max_iters; first += kParamChunk) {
+            chunk.first = first;
+            chunk.count = (max_iters + 1 - first) < kParamChunk ? (max_iters + 1 - first) : kParamChunk;
+            for (int q = 0; q < chunk.count; ++q) {
+                chunk.p[q] = Tv2dParams{tau, sigma, theta_prev, tau_prev};
+                const double theta = 1.0 / sqrt(1.0 + 2.0 * tau);
+                tau_prev = tau;
+                tau *= theta;
+                sigma /= theta;
+                theta_prev = theta;
+            }
+            tv2d_init_state<<<1, 128, 0, s>>>(ws.st, ws.prm, max_iters, gap_tol,
+                                              1.0 / ((double)H * W), chunk);
+            if ((st = check_cuda(cudaGetLastError(), "init state")) != TV_OK) return st;
+            note_launch();
+        }
+    }
     if ((st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset")) != TV_OK)
         return st;
     st = d_y0 ? check_cuda(cudaMemcpyAsync(ws.y, d_y0, npx, cudaMemcpyDeviceToDevice, s), "copy y0")
@@ -543,8 +808,9 @@ tv_status tv2d_denoise(const float *d_img, int64_t H, int64_t W, const float *d_
               : launch_init<false>(d_img, d_wh, lambda, H, W, d_x, ws, s);
     if (st != TV_OK) return st;
 
-    // Launch iterations in small batches; the device stop flag turns the rest of a
-    // batch into immediate returns, and the host checks it once per batch.
+    // Each iteration: column (dual) phase, row (primal) phase, gap. Iterations are
+    // launched in small batches; the device stop flag turns the rest of a batch into
+    // immediate returns, and the host checks it once per batch.
     const int batch = 2;
     Tv2dState hs;
     int launched = 0;
@@ -552,19 +818,13 @@ tv_status tv2d_denoise(const float *d_img, int64_t H, int64_t W, const float *d_
     while (launched < max_iters && !done) {
         const int u = (max_iters - launched) < batch ? (max_iters - launched) : batch;
         for (int t = 0; t < u; ++t) {
-            if ((st = launch_col_any(d_img, d_wv, d_wh, lambda, H, W, d_x, ws, s)) != TV_OK)
-                return st;
+            if ((st = launch_col_any(d_wv, lambda, H, W, d_x, ws, s)) != TV_OK) return st;
             st = d_wh ? launch_row<true>(d_img, d_wh, lambda, H, W, d_x, ws, s)
                       : launch_row<false>(d_img, d_wh, lambda, H, W, d_x, ws, s);
             if (st != TV_OK) return st;
+            if ((st = launch_gap(d_img, d_wh, d_wv, lambda, H, W, d_x, ws, s)) != TV_OK) return st;
         }
         launched += u;
-        if ((st = read_state(ws, s, hs)) != TV_OK) return st;
-        done = hs.done != 0;
-    }
-    if (!done && max_iters > 0) {
-        // One more dual step computes the gap of the last primal iterate.
-        if ((st = launch_col_any(d_img, d_wv, d_wh, lambda, H, W, d_x, ws, s)) != TV_OK) return st;
         if ((st = read_state(ws, s, hs)) != TV_OK) return st;
         done = hs.done != 0;
     }

@@ -248,6 +248,134 @@ struct ChainColsP {
     __device__ void finish_empty() const {}
 };
 
+// ---- the same batches, one warp per chain (tv_coop.cuh) ----
+template <bool HAS_W>
+struct CoopRowsP {
+    static constexpr bool CREC = false;
+    struct Raw {
+        float y, w;
+    };
+    struct Acc {};
+
+    const float *y, *w;
+    float lam;
+    const int64_t *offsets;
+    long long nchains;
+    int maxlen;
+    float *x;
+    long long off0;
+
+    __device__ bool resolve()
+    {
+        off0 = offsets ? (long long)offsets[0] : 0;
+        return true;
+    }
+    __device__ long long num_chains() const { return nchains; }
+    __device__ int max_len() const { return maxlen; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        if (offsets) {
+            const long long a = offsets[k], b = offsets[k + 1];
+            if (a < off0 || b < a || b - a > maxlen || b - off0 > (k + 1) * (long long)maxlen)
+                return false;
+            start = a;
+            n = (int)(b - a);
+        } else {
+            start = k * (long long)maxlen;
+            n = maxlen;
+        }
+        return true;
+    }
+    __device__ void fetch(long long, long long start, int n, int i, Raw &r) const
+    {
+        r.y = (i < n) ? y[start + i] : 0.f;
+        if constexpr (HAS_W) r.w = (i < n - 1) ? w[start + i] : 0.f;
+    }
+    __device__ void unary(long long, long long, int, int, const Raw &r, float &c, float &wi,
+                          Acc &) const
+    {
+        c = r.y;
+        if constexpr (HAS_W) wi = r.w;
+        else wi = lam;
+    }
+    __device__ void emit(long long, long long start, int i, float xv, float) const
+    {
+        x[start + i] = xv;
+    }
+    __device__ void unary_direct(int i, int n, long long, long long start, float &c,
+                                 float &wi) const
+    {
+        c = y[start + i];
+        if constexpr (HAS_W) wi = (i < n - 1) ? w[start + i] : 0.f;
+        else wi = (i < n - 1) ? lam : 0.f;
+    }
+    __device__ void emit_direct(int i, long long, long long start, float xv, float) const
+    {
+        x[start + i] = xv;
+    }
+    __device__ long long spill_off(long long k, long long start) const
+    {
+        return 2 * (start - off0) + 2 * k;
+    }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &, int) const {}
+    __device__ void finish_empty() const {}
+};
+
+template <bool HAS_W>
+struct CoopColsP {
+    static constexpr bool CREC = false;
+    struct Raw {
+        float y, w;
+    };
+    struct Acc {};
+
+    const float *y, *w;
+    float lam;
+    long long H, W, ld;
+    float *x;
+
+    __device__ bool resolve() { return true; }
+    __device__ long long num_chains() const { return W; }
+    __device__ int max_len() const { return (int)H; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        start = k;
+        n = (int)H;
+        return true;
+    }
+    __device__ void fetch(long long k, long long, int n, int i, Raw &r) const
+    {
+        r.y = (i < n) ? y[(long long)i * ld + k] : 0.f;
+        if constexpr (HAS_W) r.w = (i < n - 1) ? w[(long long)i * ld + k] : 0.f;
+    }
+    __device__ void unary(long long, long long, int, int, const Raw &r, float &c, float &wi,
+                          Acc &) const
+    {
+        c = r.y;
+        if constexpr (HAS_W) wi = r.w;
+        else wi = lam;
+    }
+    __device__ void emit(long long k, long long, int i, float xv, float) const
+    {
+        x[(long long)i * ld + k] = xv;
+    }
+    __device__ void unary_direct(int i, int n, long long k, long long, float &c, float &wi) const
+    {
+        c = y[(long long)i * ld + k];
+        if constexpr (HAS_W) wi = (i < n - 1) ? w[(long long)i * ld + k] : 0.f;
+        else wi = (i < n - 1) ? lam : 0.f;
+    }
+    __device__ void emit_direct(int i, long long k, long long, float xv, float) const
+    {
+        x[(long long)i * ld + k] = xv;
+    }
+    __device__ long long spill_off(long long k, long long) const { return k * (2 * H + 2); }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &, int) const {}
+    __device__ void finish_empty() const {}
+};
+
 template <class P>
 tv_status launch_batch(const P &p, long long nchains, float2 *rec, float *crec, float2 *spill,
                        WsHeader *hdr, cudaStream_t s)
@@ -368,6 +496,14 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     cudaStream_t s = (cudaStream_t)stream;
     tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
     if (st != TV_OK) return st;
+    if (num_chains <= kCoopMaxChains) {
+        if (d_w) {
+            CoopRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x, 0};
+            return launch_coop(p, num_chains, (int)max_len, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_CHAIN);
+        }
+        CoopRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x, 0};
+        return launch_coop(p, num_chains, (int)max_len, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_CHAIN);
+    }
     if (d_w) {
         ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,
                            vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0};
@@ -418,6 +554,14 @@ tv_status tv_chain_solve_columns(const float *d_y, const float *d_w, float lambd
     cudaStream_t s = (cudaStream_t)stream;
     tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
     if (st != TV_OK) return st;
+    if (W <= kCoopMaxChains) {
+        if (d_w) {
+            CoopColsP<true> p{d_y, d_w, 0.f, H, W, ld, d_x};
+            return launch_coop(p, W, (int)H, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_CHAIN);
+        }
+        CoopColsP<false> p{d_y, nullptr, lambda, H, W, ld, d_x};
+        return launch_coop(p, W, (int)H, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_CHAIN);
+    }
     if (d_w) {
         ChainColsP<true> p{d_y, d_w, 0.f, H, W, ld, d_x, vec_ok(nullptr, ld, d_y, d_w, d_x)};
         return launch_batch(p, W, ws.rec, nullptr, ws.spill, ws.hdr, s);

@@ -40,9 +40,7 @@ static_assert(sizeof(WsHeader) == 64, "header size");
 struct DPState {
     int F, B;           // logical indices of the first and last breakpoint
     float fl, fs;       // entry F (lambda, stored slope)
-    float f1l, f1s;     // entry F+1 (equals entry B when the sequence has two entries)
     float bl, bs;       // entry B
-    float b1l, b1s;     // entry B-1 (equals entry F when the sequence has two entries)
     float w_prev;       // weight of the edge into the current node
 };
 
@@ -99,10 +97,6 @@ __host__ __device__ __forceinline__ void dp_first(DPState &d, const S &s, int F0
     d.fs = 0.f;   // true slope 1 between the two breakpoints
     d.bl = hp;
     d.bs = -1.f;  // -abar_0: the clipped flat right end
-    d.f1l = d.bl;
-    d.f1s = d.bs;
-    d.b1l = d.fl;
-    d.b1s = d.fs;
     d.w_prev = w0;
     s.st(d.F, make_float2(d.fl, d.fs));
     s.st(d.B, make_float2(d.bl, d.bs));
@@ -110,167 +104,123 @@ __host__ __device__ __forceinline__ void dp_first(DPState &d, const S &s, int F0
 
 // Message update for node i >= 1 (abar = i + 1), transformations (a) and (b) of
 // Sec. 4.1: the left scan removes breakpoints with m^_i < -w_i and places
-// lambda^-; the right scan removes breakpoints with m^_i > w_i (only among those
-// the left scan kept) and places lambda^+. Returns false, leaving the store and
-// state untouched, if the new sequence would exceed `cap` entries.
+// lambda^- on the segment to the right of the last one removed (or on the left
+// end segment, slope a_i = 1, if none was removed); the right scan does the
+// mirror image with +w_i over the breakpoints the left scan kept. Returns false,
+// leaving the store and state untouched, if the new sequence would exceed `cap`.
 //
-// The two entries nearest each end are kept in registers, so that removing at
-// most one breakpoint per side (the common case: one removal per side per node
-// on average, Sec. 4.1's amortised bound) needs no load from the store; longer
-// scans continue from the store. Each placement is lambda = base + num / slope
-// with an integer slope; the quotient uses the fast reciprocal (2 ulp), far
-// inside the FP32 error budget of the recursions.
+// Each scan carries an "anchor" (lambda, value, slope of the segment on which the
+// new breakpoint would lie) so that both placements are one formula,
+// lambda = anchor + (+-w_i - value) / slope, whatever the number removed; a warp
+// then runs one compact loop per side for as many removals as its slowest lane
+// needs. Quotients by the integer slopes use the fast reciprocal (2 ulp).
 template <class S>
 __host__ __device__ __forceinline__ bool dp_step(DPState &d, const S &s, int cap, float ci, float wi,
-                                        float abar, float &lm, float &hp)
+                                                 float abar, float &lm, float &hp)
 {
-    const float nwi = -wi;
     const int F = d.F, B = d.B;
+    const float nwi = -wi;
 
-    // ---------------- left scan ----------------
-    // Values at the first two breakpoints (forward recursion of Sec. 4.1).
-    const float vF = d.fl - ci - d.w_prev;
-    const float sF = d.fs + abar;                       // slope of segment F
-    const float vF1 = fmaf(sF, d.f1l - d.fl, vF);
-    int last_popped;
-    float lm_s, lbase, lnum, lslope;
-    float nf1l, nf1s;  // entry after the new first breakpoint (if it is kept)
-    if (vF >= nwi) {
-        // nothing removed: lambda^- on the left end segment (slope 1)
-        last_popped = F - 1;
-        lbase = d.fl; lnum = nwi - vF; lslope = 1.f;
-        lm_s = 1.f - abar;
-        nf1l = d.fl; nf1s = d.fs;
-    } else if (vF1 >= nwi) {
-        // exactly one removed: lambda^- on segment F
-        last_popped = F;
-        lbase = d.fl; lnum = nwi - vF; lslope = sF;
-        lm_s = d.fs;
-        nf1l = d.f1l; nf1s = d.f1s;
-    } else {
-        // two or more removed: continue from the store
-        int p = F + 1;
-        float pl = d.f1l, ps = d.f1s, v = vF1;
-        float ql = 0.f, qs = 0.f;
-        while (p < B) {
-            const float2 q = (p + 1 == B) ? make_float2(d.bl, d.bs) : s.ld(p + 1);
-            const float vq = fmaf(ps + abar, q.x - pl, v);
-            if (vq >= nwi) {
-                ql = q.x;
-                qs = q.y;
-                break;
-            }
+    // ---------------- left scan (forward recursion from the first breakpoint) ----
+    const float vF = d.fl - ci - d.w_prev;  // m^_i(lambda_F): incoming value -w_{i-1}
+    float al = d.fl, av = vF, asl = 1.f, as = 1.f - abar;  // anchor: nothing removed
+    int lastL = F - 1;
+    {
+        int p = F;
+        float pl = d.fl, ps = d.fs, v = vF;
+        bool go = v < nwi;
+        while (go) {  // remove breakpoint p
+            al = pl;
+            av = v;
+            asl = ps + abar;
+            as = ps;
+            lastL = p;
+            if (p == B) break;
+            const float2 q = s.ld(p + 1);
+            v = fmaf(asl, q.x - pl, v);
             ++p;
             pl = q.x;
             ps = q.y;
-            v = vq;
+            go = v < nwi;
         }
-        // Both end values of m^_i are known exactly (-w_{i-1} + lambda_F - c_i at
-        // the first breakpoint, w_{i-1} + lambda_B - c_i at the last). When the scan
-        // stopped nearer the last breakpoint, re-evaluate m^_i(lambda_p) by the
-        // backward recursion from there: the same value in exact arithmetic, but
-        // FP32 rounding of the breakpoints is no longer multiplied by the large
-        // slopes of the segments crossed. The walk is shorter than the one just
-        // made, so the update stays O(d_i + 1).
-        if (B - p < p - F) {
-            float vb = d.bl - ci + d.w_prev;
-            float el = d.bl;
-            for (int q = B - 1; q >= p; --q) {
-                const float2 e = (q == F + 1) ? make_float2(d.f1l, d.f1s) : s.ld(q);
-                vb = fmaf(-(e.y + abar), el - e.x, vb);
-                el = e.x;
-            }
-            v = vb;
-        }
-        last_popped = p;
-        lbase = pl; lnum = nwi - v; lslope = ps + abar;
-        lm_s = ps;
-        nf1l = ql; nf1s = qs;  // meaningful only if p < B
     }
-    lm = lbase + slope_div(lnum, lslope);
+    // Both end values of m^_i are known exactly (-w_{i-1} + lambda_F - c_i at the
+    // first breakpoint, w_{i-1} + lambda_B - c_i at the last). When the scan
+    // stopped nearer the last breakpoint, re-evaluate the anchor's value by the
+    // backward recursion from there: the same value in exact arithmetic, but FP32
+    // rounding of the breakpoints is no longer multiplied by the large slopes of
+    // the segments crossed. The walk is shorter than the scan, so the update
+    // stays O(d_i + 1).
+    if (lastL - F > B - lastL) {
+        float vb = d.bl - ci + d.w_prev;
+        float ql = d.bl;
+        for (int q = B - 1; q >= lastL; --q) {
+            const float2 e = s.ld(q);
+            vb = fmaf(-(e.y + abar), ql - e.x, vb);
+            ql = e.x;
+        }
+        av = vb;
+    }
+    lm = al + slope_div(nwi - av, asl);
+    const float lm_s = as;
 
-    // ---------------- right scan over the kept breakpoints ----------------
-    int new_last = last_popped;
-    bool from_lm = true;  // lambda^+ on the segment that starts at lambda^-
-    float rbase = 0.f, rnum = 0.f, rslope = 1.f;
-    float nb1l = 0.f, nb1s = 0.f;  // entry before the new last breakpoint (if kept)
-    if (B > last_popped) {
-        const float vB = d.bl - ci + d.w_prev;
-        if (vB <= wi) {
-            // nothing removed: lambda^+ on the right end segment (slope 1)
-            from_lm = false;
-            rbase = d.bl; rnum = wi - vB; rslope = 1.f;
-            new_last = B;
-            nb1l = d.bl; nb1s = d.bs;
-        } else if (B - 1 > last_popped) {
-            const float sB1 = d.b1s + abar;  // slope of segment B-1
-            const float vB1 = fmaf(-sB1, d.bl - d.b1l, vB);
-            if (vB1 <= wi) {
-                // exactly one removed: lambda^+ on segment B-1
-                from_lm = false;
-                rbase = d.bl; rnum = wi - vB; rslope = sB1;
-                new_last = B - 1;
-                nb1l = d.b1l; nb1s = d.b1s;
-            } else {
-                int q = B - 1;
-                float ql = d.b1l, vr = vB1;
-                for (;;) {
-                    if (q - 1 > last_popped) {
-                        const float2 e = (q - 1 == F) ? make_float2(d.fl, d.fs) : s.ld(q - 1);
-                        const float sl = e.y + abar;
-                        const float vp = fmaf(-sl, ql - e.x, vr);
-                        if (vp > wi) {
-                            --q;
-                            ql = e.x;
-                            vr = vp;
-                            continue;
-                        }
-                        if (q - F < B - q) {
-                            // nearer the first breakpoint: forward recursion from there
-                            // (the mirror image of the re-evaluation in the left scan)
-                            float vf = vF;
-                            float el = d.fl, es = d.fs;
-                            for (int t = F + 1; t <= q; ++t) {
-                                const float2 e2 = (t == F + 1) ? make_float2(d.f1l, d.f1s) : s.ld(t);
-                                vf = fmaf(es + abar, e2.x - el, vf);
-                                el = e2.x;
-                                es = e2.y;
-                            }
-                            vr = vf;
-                        }
-                        from_lm = false;
-                        rbase = ql; rnum = wi - vr; rslope = sl;
-                        nb1l = e.x; nb1s = e.y;
-                    }
-                    break;
-                }
-                new_last = q - 1;
+    // ---------------- right scan (backward recursion from the last breakpoint) ---
+    // over the breakpoints with index > lastL
+    float bl2 = d.bl, bv = d.bl - ci + d.w_prev, bsl = 1.f;  // anchor: nothing removed
+    int lastR = B + 1;
+    bool from_lm = B <= lastL;  // every breakpoint went left of lambda^-
+    if (!from_lm) {
+        int q = B;
+        float ql = d.bl, v = bv;
+        bool go = v > wi;
+        while (go) {  // remove breakpoint q
+            lastR = q;
+            if (q - 1 <= lastL) {
+                from_lm = true;  // lambda^+ on the segment that starts at lambda^-
+                break;
             }
-        } else {
-            new_last = B - 1;  // == last_popped: every other breakpoint was removed
+            const float2 e = s.ld(q - 1);
+            const float sl = e.y + abar;
+            bl2 = ql;
+            bv = v;
+            bsl = sl;
+            v = fmaf(-sl, ql - e.x, v);
+            --q;
+            ql = e.x;
+            go = v > wi;
+        }
+        // mirror image of the re-evaluation above
+        if (!from_lm && lastR <= B && B - lastR > lastR - F) {
+            float vf = vF;
+            float el = d.fl, es = d.fs;
+            for (int t = F + 1; t <= lastR; ++t) {
+                const float2 e2 = s.ld(t);
+                vf = fmaf(es + abar, e2.x - el, vf);
+                el = e2.x;
+                es = e2.y;
+            }
+            bv = vf;
         }
     }
     if (from_lm) {
-        rbase = lm; rnum = wi + wi; rslope = lm_s + abar;
+        bl2 = lm;
+        bv = nwi;
+        bsl = lm_s + abar;
     }
-    hp = rbase + slope_div(rnum, rslope);
+    hp = bl2 + slope_div(wi - bv, bsl);
 
-    const int nF = last_popped;
-    const int nB = (new_last > nF ? new_last : nF) + 1;
+    const int nF = lastL;
+    const int keptR = lastR - 1;  // last breakpoint kept on the right
+    const int nB = (keptR > nF ? keptR : nF) + 1;
     if (nB - nF + 1 > cap) return false;
     s.st(nF, make_float2(lm, lm_s));
     s.st(nB, make_float2(hp, -abar));
-    const bool ntwo = (nB == nF + 1);
     d.F = nF;
     d.B = nB;
     d.fl = lm;
     d.fs = lm_s;
     d.bl = hp;
     d.bs = -abar;
-    d.f1l = ntwo ? hp : nf1l;
-    d.f1s = ntwo ? -abar : nf1s;
-    d.b1l = ntwo ? lm : nb1l;
-    d.b1s = ntwo ? lm_s : nb1s;
     d.w_prev = wi;
     return true;
 }

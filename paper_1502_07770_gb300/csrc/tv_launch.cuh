@@ -2,6 +2,7 @@
 // launch shape, shared-memory opt-in, launch counting and optional per-launch
 // CUDA-event timing (for benchmarks; off by default).
 #pragma once
+#include "tv_coop.cuh"
 #include "tv_dp.cuh"
 #include "tv_host.h"
 
@@ -34,5 +35,39 @@ tv_status launch_chains(const P &p, long long nchains, float2 *rec, float *crec,
     if (prof) prof_mark(kind, s, false);
     return st;
 }
+
+// Warp-cooperative launch: one warp per chain, `wpb` warps per block. The records
+// of a chain stay in shared memory when max_len <= kCoopSmemNodes.
+constexpr int kCoopSmemNodes = 4096;
+
+template <class P>
+tv_status launch_coop(const P &p, long long nchains, int max_len, float2 *rec, float *crec,
+                      float2 *spill, tvk::WsHeader *hdr, cudaStream_t s, int kind, int wpb = 4)
+{
+    if (nchains <= 0) return TV_OK;
+    const long long blocks = (nchains + wpb - 1) / wpb;
+    // records in shared memory when a block's share fits in ~200 KB, else in the workspace
+    const bool fits = max_len <= kCoopSmemNodes &&
+                      wpb * tvk::coop_smem_per_warp<P>(max_len) <= (size_t)200 * 1024;
+    const int smem_nodes = fits ? max_len : 0;
+    const size_t smem = wpb * tvk::coop_smem_per_warp<P>(smem_nodes);
+    auto kern = tvk::coop_chain_kernel<P>;
+    tv_status st = check_cuda(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        "cudaFuncSetAttribute");
+    if (st != TV_OK) return st;
+    const bool prof = prof_on();
+    if (prof) prof_mark(kind, s, true);
+    kern<<<(unsigned)blocks, wpb * tvk::WARP, smem, s>>>(p, rec, crec, spill, hdr, smem_nodes);
+    st = check_cuda(cudaGetLastError(), "cooperative chain kernel launch");
+    if (st == TV_OK) note_launch();
+    if (prof) prof_mark(kind, s, false);
+    return st;
+}
+
+// Batches of fewer chains than this run one warp per chain (the update of one
+// chain is then latency-bound, and a warp shortens its critical path); larger
+// batches run one thread per chain.
+constexpr long long kCoopMaxChains = 2048;
 
 }  // namespace tvh
