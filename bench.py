@@ -306,6 +306,34 @@ def main():
     chain_kernel_ms = kms / max(kn, 1)
     chain_achieved = 8.0 * nodes / (chain_kernel_ms * 1e-3) / 1e9
 
+    # ---------------- differentiable prox: forward + backward ----------------
+    DB, DN = 4096, 1024
+    yd = torch.from_numpy(synth.chain_batch(DB, DN, seed0=1000)).to(dev)
+    cd = torch.from_numpy(synth.gaussian_vector(DB * DN, seed=7).reshape(DB, DN)).to(dev)
+    xd = torch.empty_like(yd)
+    wsd = _lib.workspace(_lib.load().tv_chain_workspace_size(DB, DN), dev, "benchdiff")
+    for _ in range(3):
+        _lib.chain_prox(yd, lam=0.15, out=xd, ws=wsd)
+        _lib.chain_prox_backward(xd, cd)
+    _lib.profile_enable(True)
+    _lib.profile_read("grad")
+    diff_ms = []
+    for _ in range(max(5, args.steps // 5)):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _lib.chain_prox(yd, lam=0.15, out=xd, ws=wsd)
+        _lib.chain_prox_backward(xd, cd)
+        b.record(stream)
+        b.synchronize()
+        diff_ms.append(a.elapsed_time(b))
+    gms, gn = _lib.profile_read("grad")
+    _lib.profile_enable(False)
+    grad_kernel_ms = gms / max(gn, 1)
+    grad_achieved = 12.0 * DB * DN / (grad_kernel_ms * 1e-3) / 1e9
+    dms = float(np.median(diff_ms))
+
     # ---------------- roofline of the dominant kernel of the step ----------------
     # algorithmic bytes: column (dual) phase reads x^k, x^{k-1}, y, f and writes y
     # (16 B/pixel); row (primal) phase reads f, x^k, y and writes x^{k+1} (16 B/pixel).
@@ -351,6 +379,13 @@ def main():
                                     "unit": "GB/s", "frac": chain_achieved / hbm,
                                     "traffic": recorded_traffic("chain"),
                                     "bytes_per_node": 8}},
+        "diff_prox": {"value": DB * DN / (dms * 1e-3) / 1e9, "unit": "Gnode/s",
+                      "workload": f"{DB} chains x {DN}, lambda 0.15, forward + backward "
+                                  "(loss sum c_i x_i, c ~ N(0,1)), L2 flushed",
+                      "ms": dms, "backward_kernel_ms": grad_kernel_ms,
+                      "backward_roofline": {"bound": "hbm", "achieved": grad_achieved,
+                                            "peak": hbm, "unit": "GB/s",
+                                            "frac": grad_achieved / hbm, "bytes_per_node": 12}},
         "clocks": clk,
     }
     if rank == 0 and world == 1:

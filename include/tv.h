@@ -65,7 +65,8 @@ int64_t tv_launch_count(void);
  * recorded events of one kind, returns their summed duration in milliseconds and
  * the number of launches since the previous read, and resets both. Kinds:
  * 0 chain batches (tv_chain_solve, tv_chain_solve_columns), 1 the 2D column
- * (dual) phase, 2 the 2D row (primal) phase, 3 the 2D initial row solve.
+ * (dual) phase, 2 the 2D row (primal) phase, 3 the 2D initial row solve,
+ * 4 tv_chain_solve_backward.
  * Events are created on first use and reused; TV_ERR_INVALID for a bad kind.
  */
 tv_status tv_profile_enable(int on);
@@ -120,6 +121,29 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
 tv_status tv_chain_solve_noalloc(const float *d_y, const float *d_w, float lambda,
                                  const int64_t *d_offsets, int64_t num_chains, int64_t max_len,
                                  float *d_x, tv_stream_t stream);
+
+/*
+ * Backward of the chain prox (vector-Jacobian product), for a differentiable TV
+ * layer. From the optimality conditions of eq. 1D-ROF, on every maximal run S of
+ * equal values of the solution x ("segment"), x_S = mean(y_S) + (u_r - u_{l-1})/|S|
+ * with u_e = w_e sign(x_{e+1} - x_e) at the jump edges bounding S. Hence
+ *     grad_y_j = mean of grad_x over the segment containing j,
+ *     grad_w_e = sign(x_{e+1} - x_e) (mean_left - mean_right) at a jump edge e, and 0
+ *                on edges inside a segment (grad of a uniform lambda = sum of grad_w).
+ *   d_x        the solution returned by tv_chain_solve (segments are read off it:
+ *              fused neighbours are bitwise equal)
+ *   d_grad_x   upstream gradient, same layout
+ *   d_offsets, num_chains, max_len   as for tv_chain_solve
+ *   d_grad_y   output, same layout; d_grad_w optional output, same layout (the
+ *              entry at a chain's last node is not written)
+ *   workspace  at least 64 bytes (a device error word, read by tv_workspace_status)
+ * Outputs must not alias the inputs. The derivative is the one of the solution map
+ * away from degenerate points (where a jump of x is exactly zero).
+ */
+tv_status tv_chain_solve_backward(const float *d_x, const float *d_grad_x,
+                                  const int64_t *d_offsets, int64_t num_chains, int64_t max_len,
+                                  float *d_grad_y, float *d_grad_w, void *d_workspace,
+                                  size_t workspace_bytes, tv_stream_t stream);
 
 /* Bytes of workspace tv_chain_solve_columns needs for an H x W array. */
 size_t tv_columns_workspace_size(int64_t H, int64_t W);

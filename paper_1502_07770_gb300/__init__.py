@@ -8,12 +8,13 @@ Lagrangian-decomposition primal-dual ROF solver (Sec. 6.1) built on it.
 The CUDA binding is imported lazily so that ``synth`` (input generators) can
 be used without a GPU.
 """
-__all__ = ["chain_prox", "chain_prox_columns", "tv2d_denoise", "workspace_status", "synth"]
+__all__ = ["chain_prox", "chain_prox_columns", "chain_prox_backward", "chain_prox_diff",
+           "ChainProxFn", "tv2d_denoise", "workspace_status", "synth"]
 
 
 def __getattr__(name):
-    if name in ("chain_prox", "chain_prox_columns", "tv2d_denoise", "workspace_status", "load",
-                "TVError"):
+    if name in ("chain_prox", "chain_prox_columns", "chain_prox_backward", "chain_prox_diff",
+                "ChainProxFn", "tv2d_denoise", "workspace_status", "load", "TVError"):
         from . import _lib
         return getattr(_lib, name)
     raise AttributeError(name)

@@ -38,6 +38,7 @@ SIGNATURES = {
     "tv_chain_workspace_size": (_sz, [_i64, _i64]),
     "tv_chain_solve": (ctypes.c_int, [_p, _p, ctypes.c_float, _p, _i64, _i64, _p, _p, _sz, _p]),
     "tv_chain_solve_noalloc": (ctypes.c_int, [_p, _p, ctypes.c_float, _p, _i64, _i64, _p, _p]),
+    "tv_chain_solve_backward": (ctypes.c_int, [_p, _p, _p, _i64, _i64, _p, _p, _p, _sz, _p]),
     "tv_columns_workspace_size": (_sz, [_i64, _i64]),
     "tv_chain_solve_columns": (ctypes.c_int,
                                [_p, _p, ctypes.c_float, _i64, _i64, _i64, _p, _p, _sz, _p]),
@@ -157,6 +158,58 @@ def chain_prox_columns(y, w=None, lam: float = 0.0, out=None, ws=None):
     return x
 
 
+def chain_prox_backward(x, grad_x, offsets=None, max_len=None, with_w=False, ws=None):
+    """Backward of ``chain_prox``: (grad_y, grad_w or None) for upstream ``grad_x``.
+
+    Layouts as in ``chain_prox``; ``grad_w`` has the layout of ``x`` (the entry at a
+    chain's last node is zero)."""
+    lib = load()
+    _require_cuda(x, grad_x)
+    if offsets is None:
+        num_chains, max_len = x.shape
+        offp = None
+    else:
+        num_chains = offsets.numel() - 1
+        if max_len is None:
+            raise ValueError("max_len is required with offsets")
+        offp = _ptr(offsets)
+    gy = torch.empty_like(x)
+    gw = torch.zeros_like(x) if with_w else None
+    wsb = ws if ws is not None else workspace(256, x.device, "grad")
+    _check(lib.tv_chain_solve_backward(_ptr(x), _ptr(grad_x), offp, num_chains, max_len,
+                                       _ptr(gy), _ptr(gw), _ptr(wsb), wsb.numel(),
+                                       _stream(x.device)))
+    return gy, gw
+
+
+class ChainProxFn(torch.autograd.Function):
+    """Differentiable chain TV prox: x = argmin 1/2||x - y||^2 + sum w_e |x_{e+1} - x_e|
+    on each row of ``y`` (B, n). ``w`` is a (B, n) tensor of per-node edge weights or a
+    Python float; gradients flow to ``y`` and to a tensor ``w``."""
+
+    @staticmethod
+    def forward(ctx, y, w):
+        if isinstance(w, torch.Tensor):
+            x = chain_prox(y.contiguous(), w.contiguous())
+        else:
+            x = chain_prox(y.contiguous(), lam=float(w))
+        ctx.w_is_tensor = isinstance(w, torch.Tensor)
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        (x,) = ctx.saved_tensors
+        need_w = ctx.w_is_tensor and ctx.needs_input_grad[1]
+        gy, gw = chain_prox_backward(x, grad_x.contiguous(), with_w=need_w)
+        return gy, (gw if need_w else None)
+
+
+def chain_prox_diff(y, w):
+    """Autograd entry point of the chain prox (see ``ChainProxFn``)."""
+    return ChainProxFn.apply(y, w)
+
+
 def workspace_status(ws, device=None):
     """(status, overflowed chains) of a chain workspace; clears the device word."""
     lib = load()
@@ -167,7 +220,7 @@ def workspace_status(ws, device=None):
     return st.value, ov.value
 
 
-PROFILE_KINDS = {"chain": 0, "col": 1, "row": 2, "init": 3}
+PROFILE_KINDS = {"chain": 0, "col": 1, "row": 2, "init": 3, "grad": 4}
 
 
 def launch_count() -> int:

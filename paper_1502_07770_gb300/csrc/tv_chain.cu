@@ -436,7 +436,7 @@ tv_status tv_profile_read(int kind, double *total_ms, int64_t *launches)
 {
     clear_error();
     if (kind < 0 || kind >= PK_N || !total_ms || !launches) {
-        set_error("tv_profile_read: kind must be 0..3 and the outputs non-NULL");
+        set_error("tv_profile_read: kind must be 0..4 and the outputs non-NULL");
         return TV_ERR_INVALID;
     }
     std::lock_guard<std::mutex> lk(tvh::g_prof_mu);

@@ -8,7 +8,7 @@
 
 namespace tvh {
 
-enum ProfKind { PK_CHAIN = 0, PK_COL = 1, PK_ROW = 2, PK_INIT = 3, PK_N = 4 };
+enum ProfKind { PK_CHAIN = 0, PK_COL = 1, PK_ROW = 2, PK_INIT = 3, PK_GRAD = 4, PK_N = 5 };
 
 void note_launch();
 bool prof_on();
