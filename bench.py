@@ -334,6 +334,33 @@ def main():
     grad_achieved = 12.0 * DB * DN / (grad_kernel_ms * 1e-3) / 1e9
     dms = float(np.median(diff_ms))
 
+    # ---------------- batched uneven images (64 images, 128x96 .. 2048x1536) ----------------
+    sizes, blams = synth.uneven_image_sizes(64, seed=100)
+    bfs = [synth.shapes_image(h, w, seed=100 + m)[1] for m, (h, w) in enumerate(sizes)]
+    bws = [synth.edge_aware_weights(fm, blams[m]) for m, fm in enumerate(bfs)]
+    bimg = [torch.from_numpy(fm).to(dev) for fm in bfs]
+    bwh = [torch.from_numpy(w[0]).to(dev) for w in bws]
+    bwv = [torch.from_numpy(w[1]).to(dev) for w in bws]
+    bouts = [torch.empty_like(t) for t in bimg]
+    bpix = sum(h * w for h, w in sizes)
+
+    def batched():
+        return _lib.tv2d_denoise_batched(bimg, blams, bwh, bwv, max_iters=MAX_ITERS, tol=TOL,
+                                         outs=bouts)
+    r = batched()
+    b_iters = r[1]
+    batched_ms = []
+    for _ in range(max(3, args.steps // 10)):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        batched()
+        b.record(stream)
+        b.synchronize()
+        batched_ms.append(a.elapsed_time(b))
+    bms = float(np.median(batched_ms))
+
     # ---------------- roofline of the dominant kernel of the step ----------------
     # algorithmic bytes: column (dual) phase reads x^k, x^{k-1}, y, f and writes y
     # (16 B/pixel); row (primal) phase reads f, x^k, y and writes x^{k+1} (16 B/pixel).
@@ -386,6 +413,12 @@ def main():
                       "backward_roofline": {"bound": "hbm", "achieved": grad_achieved,
                                             "peak": hbm, "unit": "GB/s",
                                             "frac": grad_achieved / hbm, "bytes_per_node": 12}},
+        "batched": {"ms": bms, "images": len(sizes), "megapixels": bpix / 1e6,
+                    "Mpixel_per_s": bpix / (bms * 1e-3) / 1e6,
+                    "iterations_max": int(max(b_iters)), "iterations_mean": float(np.mean(b_iters)),
+                    "graph_loop": int(_lib.load().tv2d_batched_last_mode()),
+                    "workload": "64 images, W ~ U{128..2048}, H ~ U{96..1536}, lambda ~ U[0.05,0.3], "
+                                "edge-aware weights lambda*exp(-|df|/0.2), to per-pixel gap 1e-4"},
         "clocks": clk,
     }
     if rank == 0 and world == 1:

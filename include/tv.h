@@ -197,6 +197,49 @@ tv_status tv2d_denoise(const float *d_img, int64_t H, int64_t W, const float *d_
                        double gap_tol, float *d_x, int *iters_out, double *gap_out,
                        void *d_workspace, size_t workspace_bytes, tv_stream_t stream);
 
+/* ------------------------------------------------------------ 2D, batched ---- */
+
+/* One image of a batch (all pointers on the device; the caller owns them). */
+typedef struct {
+    const float *img;   /* H x W row-major noisy image */
+    int64_t H, W;
+    const float *wh;    /* H x (W-1) horizontal edge weights, or NULL */
+    const float *wv;    /* (H-1) x W vertical edge weights, or NULL */
+    float lambda;       /* uniform weight for whichever of wh / wv is NULL */
+    const float *y0;    /* optional H x W initial dual (warm start), or NULL */
+    float *x;           /* H x W output; must not alias the inputs */
+} tv_image_desc;
+
+/* Bytes of workspace tv2d_denoise_batched needs for these images (0 if malformed). */
+size_t tv2d_batched_workspace_size(const tv_image_desc *imgs, int n_imgs, int max_iters);
+
+/*
+ * Denoise a batch of images of any sizes with the method of tv2d_denoise (Sec. 6.1,
+ * eq. pd): every image iterates until its own per-pixel gap reaches gap_tol (or
+ * max_iters). Each phase of an iteration is one launch over the chains of all
+ * still-running images (the images' independent 1D subproblems, solved in
+ * parallel); the iterations run inside one CUDA graph with a device-side loop
+ * condition. `imgs` is a HOST array of n_imgs descriptors; iters_out and gap_out
+ * are optional HOST arrays of n_imgs entries. Returns after the solve, TV_OK if
+ * every image converged, TV_ERR_NOT_CONVERGED (outputs still written) otherwise.
+ */
+tv_status tv2d_denoise_batched(const tv_image_desc *imgs, int n_imgs, int max_iters,
+                               double gap_tol, int *iters_out, double *gap_out,
+                               void *d_workspace, size_t workspace_bytes, tv_stream_t stream);
+
+/* How the calling thread's last tv2d_denoise_batched ran its iterations: 1 as one
+ * CUDA graph with a device-side loop condition, 0 replayed from the host (conditional
+ * graph nodes unavailable), -1 no batched solve yet. */
+int tv2d_batched_last_mode(void);
+
+/*
+ * Tuning knobs set by the autotuner (the paper has no counterpart): warps per block
+ * of the batched phase kernels (1, 2, 4 or 8), and the largest chain batch solved
+ * with one warp per chain instead of one thread per chain (0 restores the default).
+ */
+tv_status tv_set_batched_warps(int warps_per_block);
+tv_status tv_set_coop_max_chains(int64_t max_chains);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,12 +9,14 @@ The CUDA binding is imported lazily so that ``synth`` (input generators) can
 be used without a GPU.
 """
 __all__ = ["chain_prox", "chain_prox_columns", "chain_prox_backward", "chain_prox_diff",
-           "ChainProxFn", "tv2d_denoise", "workspace_status", "synth"]
+           "ChainProxFn", "tv2d_denoise", "tv2d_denoise_batched", "workspace_status", "synth",
+           "autotune"]
 
 
 def __getattr__(name):
     if name in ("chain_prox", "chain_prox_columns", "chain_prox_backward", "chain_prox_diff",
-                "ChainProxFn", "tv2d_denoise", "workspace_status", "load", "TVError"):
+                "ChainProxFn", "tv2d_denoise", "tv2d_denoise_batched", "workspace_status", "load",
+                "TVError"):
         from . import _lib
         return getattr(_lib, name)
     raise AttributeError(name)

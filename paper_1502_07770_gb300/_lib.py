@@ -27,6 +27,13 @@ _p = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _sz = ctypes.c_size_t
 
+class ImageDesc(ctypes.Structure):
+    """tv_image_desc of include/tv.h: one image of a batch (device pointers)."""
+    _fields_ = [("img", ctypes.c_void_p), ("H", ctypes.c_int64), ("W", ctypes.c_int64),
+                ("wh", ctypes.c_void_p), ("wv", ctypes.c_void_p), ("lam", ctypes.c_float),
+                ("y0", ctypes.c_void_p), ("x", ctypes.c_void_p)]
+
+
 # name -> (restype, argtypes), mirroring include/tv.h
 SIGNATURES = {
     "tv_last_error": (ctypes.c_char_p, []),
@@ -45,6 +52,13 @@ SIGNATURES = {
     "tv_workspace_status": (ctypes.c_int, [_p, _p, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(_i64)]),
     "tv2d_workspace_size": (_sz, [_i64, _i64, ctypes.c_int]),
+    "tv2d_batched_workspace_size": (_sz, [ctypes.POINTER(ImageDesc), ctypes.c_int, ctypes.c_int]),
+    "tv2d_denoise_batched": (ctypes.c_int, [ctypes.POINTER(ImageDesc), ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_double), _p, _sz, _p]),
+    "tv_set_batched_warps": (ctypes.c_int, [ctypes.c_int]),
+    "tv2d_batched_last_mode": (ctypes.c_int, []),
+    "tv_set_coop_max_chains": (ctypes.c_int, [_i64]),
     "tv2d_denoise": (ctypes.c_int, [_p, _i64, _i64, _p, _p, ctypes.c_float, _p, ctypes.c_int,
                                     ctypes.c_double, _p, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_double), _p, _sz, _p]),
@@ -260,3 +274,48 @@ def tv2d_denoise(img, lam: float = 0.1, w_h=None, w_v=None, y0=None, max_iters: 
     if st not in (TV_OK, TV_ERR_NOT_CONVERGED):
         _check(st)
     return x, it.value, gap.value, st == TV_OK
+
+
+def tv2d_denoise_batched(images, lams, w_hs=None, w_vs=None, y0s=None, max_iters: int = 200,
+                         tol: float = 1e-4, outs=None, ws=None):
+    """Denoise a list of (H_i, W_i) images of any sizes in one batched solve.
+
+    ``lams``: per-image uniform weights (used where the image has no w_h / w_v);
+    ``w_hs`` / ``w_vs`` / ``y0s``: optional per-image lists (entries may be None).
+    Returns ``(xs, iterations, per-pixel gaps, all converged)``.
+    """
+    lib = load()
+    n = len(images)
+    w_hs = w_hs or [None] * n
+    w_vs = w_vs or [None] * n
+    y0s = y0s or [None] * n
+    _require_cuda(*images, *[t for t in w_hs + w_vs + y0s if t is not None])
+    xs = outs if outs is not None else [torch.empty_like(im) for im in images]
+    descs = (ImageDesc * n)()
+    for m, im in enumerate(images):
+        H, W = im.shape
+        descs[m] = ImageDesc(im.data_ptr(), H, W,
+                             w_hs[m].data_ptr() if w_hs[m] is not None else None,
+                             w_vs[m].data_ptr() if w_vs[m] is not None else None,
+                             float(lams[m]),
+                             y0s[m].data_ptr() if y0s[m] is not None else None,
+                             xs[m].data_ptr())
+    nbytes = lib.tv2d_batched_workspace_size(descs, n, int(max_iters))
+    if nbytes == 0:
+        raise ValueError("malformed image batch")
+    wsb = ws if ws is not None else workspace(nbytes, images[0].device, "batched")
+    iters = (ctypes.c_int * n)()
+    gaps = (ctypes.c_double * n)()
+    st = lib.tv2d_denoise_batched(descs, n, int(max_iters), float(tol), iters, gaps, _ptr(wsb),
+                                  wsb.numel(), _stream(images[0].device))
+    if st not in (TV_OK, TV_ERR_NOT_CONVERGED):
+        _check(st)
+    return xs, list(iters), list(gaps), st == TV_OK
+
+
+def set_batched_warps(wpb: int):
+    _check(load().tv_set_batched_warps(int(wpb)))
+
+
+def set_coop_max_chains(n: int):
+    _check(load().tv_set_coop_max_chains(int(n)))

@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "tv2d_common.cuh"
 #include "tv_launch.cuh"
 
 using namespace tvk;
@@ -49,19 +50,6 @@ struct Tv2dState {
     double tol;           // per-pixel tolerance; 0 never stops early
     double inv_N;         // 1 / (H W)
     double gap;           // last per-pixel gap G_{gap_k} / (H W)
-};
-
-struct Tv2dParams {
-    double tau, sigma, theta_prev, tau_prev;  // tau_k, sigma_k, theta_{k-1}, tau_{k-1}
-};
-
-// The step sizes of eq. pd (accelerated variant, gamma = 1, tau_0 = sigma_0 = 1)
-// are computed on the host in FP64 and passed to the device by value, 256 per
-// launch; the first launch also resets the iteration state.
-constexpr int kParamChunk = 256;
-struct ParamChunk {
-    int first, count;
-    Tv2dParams p[kParamChunk];
 };
 
 __global__ void tv2d_init_state(Tv2dState *st, Tv2dParams *prm, int max_iters, double tol,
@@ -656,7 +644,7 @@ template <bool HAS_WH>
 tv_status launch_init(const float *img, const float *wh, float lam, long long H, long long W,
                       float *x0, const Tv2dWs &ws, cudaStream_t s)
 {
-    if (H <= kCoopMaxChains) {
+    if (H <= coop_max_chains()) {
         CoopInitRowsP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1};
         return launch_coop(p, H, (int)W, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_INIT);
     }
@@ -668,7 +656,7 @@ template <bool HAS_WH>
 tv_status launch_row(const float *img, const float *wh, float lam, long long H, long long W,
                      float *x0, const Tv2dWs &ws, cudaStream_t s)
 {
-    if (H <= kCoopMaxChains) {
+    if (H <= coop_max_chains()) {
         CoopRowPhaseP<HAS_WH> p{img, ws.y, wh, lam, H, W, x0, ws.buf1, ws.st, ws.prm,
                                 nullptr, nullptr, 0.f, 0.f};
         return launch_coop(p, H, (int)W, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_ROW);
@@ -682,7 +670,7 @@ template <bool HAS_WV>
 tv_status launch_col(const float *wv, float lam, long long H, long long W, float *x0,
                      const Tv2dWs &ws, cudaStream_t s)
 {
-    if (W <= kCoopMaxChains) {
+    if (W <= coop_max_chains()) {
         CoopColPhaseP<HAS_WV> p{wv, lam, H, W, x0, ws.buf1, ws.y, ws.st, ws.prm,
                                 nullptr, nullptr, 0.f, 0.f, 0.f};
         return launch_coop(p, W, (int)H, ws.rec, ws.crec, ws.spill, ws.hdr, s, PK_COL);

@@ -53,6 +53,9 @@ static double g_prof_ms[PK_N];
 static long long g_prof_n[PK_N];
 
 void note_launch() { g_launches.fetch_add(1); }
+
+static std::atomic<long long> g_coop_max{kCoopMaxChainsDefault};
+long long coop_max_chains() { return g_coop_max.load(); }
 bool prof_on() { return g_prof_on; }
 
 void prof_mark(int kind, cudaStream_t s, bool start)
@@ -425,6 +428,17 @@ int tv_version(void) { return 100; }
 
 int64_t tv_launch_count(void) { return (int64_t)tvh::g_launches.load(); }
 
+tv_status tv_set_coop_max_chains(int64_t max_chains)
+{
+    clear_error();
+    if (max_chains < 0) {
+        set_error("tv_set_coop_max_chains: must be >= 0");
+        return TV_ERR_INVALID;
+    }
+    tvh::g_coop_max.store(max_chains == 0 ? kCoopMaxChainsDefault : max_chains);
+    return TV_OK;
+}
+
 tv_status tv_profile_enable(int on)
 {
     std::lock_guard<std::mutex> lk(tvh::g_prof_mu);
@@ -496,7 +510,7 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     cudaStream_t s = (cudaStream_t)stream;
     tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
     if (st != TV_OK) return st;
-    if (num_chains <= kCoopMaxChains) {
+    if (num_chains <= coop_max_chains()) {
         if (d_w) {
             CoopRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x, 0};
             return launch_coop(p, num_chains, (int)max_len, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_CHAIN);
@@ -554,7 +568,7 @@ tv_status tv_chain_solve_columns(const float *d_y, const float *d_w, float lambd
     cudaStream_t s = (cudaStream_t)stream;
     tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
     if (st != TV_OK) return st;
-    if (W <= kCoopMaxChains) {
+    if (W <= coop_max_chains()) {
         if (d_w) {
             CoopColsP<true> p{d_y, d_w, 0.f, H, W, ld, d_x};
             return launch_coop(p, W, (int)H, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_CHAIN);

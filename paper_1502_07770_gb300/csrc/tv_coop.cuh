@@ -178,36 +178,15 @@ __device__ __forceinline__ bool coop_step(float &lam, float &V, int &size, float
 //   unary_direct(i, n, k, start, &c, &w), emit_direct(i, k, start, xhat, c)   overflow path
 //   spill_off(k, start), acc_init(Acc&), finish(Acc&, lane), finish_empty()
 
+// One chain (index k, first node `start`, n nodes) solved by the calling warp:
+// forward message pass, records, backward clips, output through the policy.
+// Records stay in sm_rec/sm_crec (smem_nodes entries) when the chain fits, else in
+// rec_g/crec_g at slot k * max_len; `spill` is the chain's overflow reserve base.
 template <class P>
-__global__ void __launch_bounds__(256) coop_chain_kernel(P p_in, float2 *rec_g, float *crec_g,
-                                                         float2 *spill, WsHeader *hdr,
-                                                         int smem_nodes)
+__device__ void coop_solve_chain(const P &p, typename P::Acc &acc, long long k, long long start,
+                                 int n, int lane, float2 *sm_rec, float *sm_crec, int smem_nodes,
+                                 float2 *rec_g, float *crec_g, float2 *spill, WsHeader *hdr)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    P p = p_in;
-    if (!p.resolve()) return;
-    const int lane = threadIdx.x & (WARP - 1);
-    const int warp = threadIdx.x / WARP;
-    const int wpb = blockDim.x / WARP;
-    float2 *sm_rec = reinterpret_cast<float2 *>(smem_raw) + (size_t)warp * smem_nodes;
-    float *sm_crec = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem_raw) +
-                                               (size_t)wpb * smem_nodes) +
-                     (size_t)warp * smem_nodes;
-    const long long k = (long long)blockIdx.x * wpb + warp;  // this warp's chain
-    typename P::Acc acc;
-    p.acc_init(acc);
-    long long start = 0;
-    int n = 0;
-    if (k < p.num_chains()) {
-        if (!p.chain(k, start, n)) {
-            if (lane == 0) atomicOr(&hdr->status, ERR_BAD_CHAIN);
-            n = 0;
-        }
-    }
-    if (n == 0) {
-        p.finish_empty();
-        return;
-    }
     const int max_len = p.max_len();
     // records: shared memory when the chain fits, else this chain's global slot
     const bool in_smem = n <= smem_nodes;
@@ -290,11 +269,45 @@ __global__ void __launch_bounds__(256) coop_chain_kernel(P p_in, float2 *rec_g, 
     } else {
         if (lane == 0) {
             atomicAdd(&hdr->overflowed, 1ull);
-            solve_chain_global_lane0(p, k, start, n, spill + p.spill_off(k, start),
-                                     rec_g + k * (long long)max_len, crecp);
+            solve_chain_global_lane0(p, k, start, n, spill, rec_g + k * (long long)max_len,
+                                     crecp);
         }
         __syncwarp();
     }
+}
+
+template <class P>
+__global__ void __launch_bounds__(256) coop_chain_kernel(P p_in, float2 *rec_g, float *crec_g,
+                                                         float2 *spill, WsHeader *hdr,
+                                                         int smem_nodes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P p = p_in;
+    if (!p.resolve()) return;
+    const int lane = threadIdx.x & (WARP - 1);
+    const int warp = threadIdx.x / WARP;
+    const int wpb = blockDim.x / WARP;
+    float2 *sm_rec = reinterpret_cast<float2 *>(smem_raw) + (size_t)warp * smem_nodes;
+    float *sm_crec = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem_raw) +
+                                               (size_t)wpb * smem_nodes) +
+                     (size_t)warp * smem_nodes;
+    const long long k = (long long)blockIdx.x * wpb + warp;  // this warp's chain
+    typename P::Acc acc;
+    p.acc_init(acc);
+    long long start = 0;
+    int n = 0;
+    if (k < p.num_chains()) {
+        if (!p.chain(k, start, n)) {
+            if (lane == 0) atomicOr(&hdr->status, ERR_BAD_CHAIN);
+            n = 0;
+        }
+    }
+    if (n == 0) {
+        p.finish_empty();
+        return;
+    }
+    coop_solve_chain(p, acc, k, start, n, lane, sm_rec, sm_crec, smem_nodes, rec_g, crec_g,
+                     spill + p.spill_off(k, start), hdr);
     p.finish(acc, lane);
 }
 
