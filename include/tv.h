@@ -208,6 +208,7 @@ typedef struct {
     float lambda;       /* uniform weight for whichever of wh / wv is NULL */
     const float *y0;    /* optional H x W initial dual (warm start), or NULL */
     float *x;           /* H x W output; must not alias the inputs */
+    float *y_out;       /* optional H x W output: the final dual y (e.g. as a training target) */
 } tv_image_desc;
 
 /* Bytes of workspace tv2d_denoise_batched needs for these images (0 if malformed). */
@@ -239,6 +240,54 @@ int tv2d_batched_last_mode(void);
  */
 tv_status tv_set_batched_warps(int warps_per_block);
 tv_status tv_set_coop_max_chains(int64_t max_chains);
+
+/* ------------------------------------------ learned dual warm start (net) ---- */
+/*
+ * Building blocks of a small convolutional network that predicts a warm start y^0
+ * for tv2d_denoise from the noisy image and lambda (the paper has no network: any
+ * y^0 is a valid start of eq. pd). Tensors are NHWC bfloat16 (stored as uint16
+ * bits) with 16 or 32 channels, zero-padded; weights are [cout][3][3][cin] bfloat16;
+ * biases, pre-activations and gradients FP32. Convolutions are 3x3, stride 1, zero
+ * padding 1 (cross-correlation), computed on BF16 tensor cores with FP32 accumulate.
+ */
+/* y = conv(x) + bias (bias may be NULL), optionally ReLU'd into act_out (BF16, may be
+ * NULL); pre_out (FP32, may be NULL) receives the value before the ReLU; at least one of
+ * the two outputs is given. All tensor pointers 16-byte aligned; B <= 65535. */
+tv_status tv_net_conv3x3(const void *d_x, int B, int H, int W, int cin, const void *d_w,
+                         const float *d_bias, int cout, int relu, float *d_pre_out,
+                         void *d_act_out, tv_stream_t stream);
+/* dx = (conv^T dy) * (mask_pre > 0): gradient with respect to the input of a
+ * convolution whose input was ReLU(mask_pre). scratch_w: cout*9*cin BF16 entries. */
+tv_status tv_net_conv3x3_backward_data(const void *d_dy, int B, int H, int W, int cout,
+                                       const void *d_w, int cin, const float *d_mask_pre,
+                                       void *d_dx, void *d_scratch_w, tv_stream_t stream);
+/* Bytes of the workspace that tv_net_conv3x3_backward_weight and tv_net_dual_head
+ * (with a loss) need for a B x H x W batch on the current device (0 for a bad shape). */
+size_t tv_net_workspace_size(int B, int H, int W);
+/* dw += sum_p dy[p] x[p+tap]^T and db += sum_p dy[p] (FP32, accumulated: zero them first;
+ * d_db may be NULL). Per-block partial sums go to the workspace and are added in a fixed
+ * order, so the result is deterministic. */
+tv_status tv_net_conv3x3_backward_weight(const void *d_x, const void *d_dy, int B, int H, int W,
+                                         int cin, int cout, float *d_dw, float *d_db,
+                                         void *d_ws, size_t ws_bytes, tv_stream_t stream);
+/* Network input: channel 0 the image f, channel 1 its lambda (per image), 2..15 zero. */
+tv_status tv_net_pack_input(const float *d_f, int B, int H, int W, const float *d_lam, void *d_x,
+                            tv_stream_t stream);
+/* Output head: p_v = lambda * tanh(o) on vertical edges (o = channel 0 of a 16-channel
+ * FP32 tensor), y = D_v^T p_v (y[r] = p[r-1] - p[r]), a dual-feasible warm start. With
+ * d_target: *d_loss = mean (y - target)^2 if d_loss (block partials in the workspace,
+ * summed in a fixed order) and, if d_grad_o, its gradient with respect to o (BF16, 16
+ * channels, channels 1..15 zero). d_ws may be NULL when d_loss is. */
+tv_status tv_net_dual_head(const float *d_o, int B, int H, int W, const float *d_lam,
+                           const float *d_target, float *d_y, float *d_loss, void *d_grad_o,
+                           void *d_ws, size_t ws_bytes, tv_stream_t stream);
+/* out[i] = bfloat16(a[i]) (round to nearest even), i < n. */
+tv_status tv_net_cast_bf16(const float *d_a, int64_t n, void *d_out, tv_stream_t stream);
+/* One Adam step on n FP32 parameters (step counts from 1); the gradient is read and
+ * then cleared; w_bf16 (may be NULL) receives a BF16 copy of the new weights. */
+tv_status tv_net_adam(float *d_w, float *d_m, float *d_v, float *d_g, int64_t n, float lr,
+                      float beta1, float beta2, float eps, int step, void *d_w_bf16,
+                      tv_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ class ImageDesc(ctypes.Structure):
     """tv_image_desc of include/tv.h: one image of a batch (device pointers)."""
     _fields_ = [("img", ctypes.c_void_p), ("H", ctypes.c_int64), ("W", ctypes.c_int64),
                 ("wh", ctypes.c_void_p), ("wv", ctypes.c_void_p), ("lam", ctypes.c_float),
-                ("y0", ctypes.c_void_p), ("x", ctypes.c_void_p)]
+                ("y0", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y_out", ctypes.c_void_p)]
 
 
 # name -> (restype, argtypes), mirroring include/tv.h
@@ -59,6 +59,22 @@ SIGNATURES = {
     "tv_set_batched_warps": (ctypes.c_int, [ctypes.c_int]),
     "tv2d_batched_last_mode": (ctypes.c_int, []),
     "tv_set_coop_max_chains": (ctypes.c_int, [_i64]),
+    "tv_net_conv3x3": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      _p, _p, ctypes.c_int, ctypes.c_int, _p, _p, _p]),
+    "tv_net_conv3x3_backward_data": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_int, _p, ctypes.c_int, _p, _p, _p,
+                                                    _p]),
+    "tv_net_workspace_size": (_sz, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "tv_net_conv3x3_backward_weight": (ctypes.c_int, [_p, _p, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                      _p, _p, _p, _sz, _p]),
+    "tv_net_pack_input": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _p,
+                                         _p]),
+    "tv_net_dual_head": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _p, _p,
+                                        _p, _p, _p, _sz, _p]),
+    "tv_net_cast_bf16": (ctypes.c_int, [_p, _i64, _p, _p]),
+    "tv_net_adam": (ctypes.c_int, [_p, _p, _p, _p, _i64, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, ctypes.c_int, _p, _p]),
     "tv2d_denoise": (ctypes.c_int, [_p, _i64, _i64, _p, _p, ctypes.c_float, _p, ctypes.c_int,
                                     ctypes.c_double, _p, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_double), _p, _sz, _p]),
@@ -277,7 +293,7 @@ def tv2d_denoise(img, lam: float = 0.1, w_h=None, w_v=None, y0=None, max_iters: 
 
 
 def tv2d_denoise_batched(images, lams, w_hs=None, w_vs=None, y0s=None, max_iters: int = 200,
-                         tol: float = 1e-4, outs=None, ws=None):
+                         tol: float = 1e-4, outs=None, ws=None, y_outs=None):
     """Denoise a list of (H_i, W_i) images of any sizes in one batched solve.
 
     ``lams``: per-image uniform weights (used where the image has no w_h / w_v);
@@ -289,6 +305,7 @@ def tv2d_denoise_batched(images, lams, w_hs=None, w_vs=None, y0s=None, max_iters
     w_hs = w_hs or [None] * n
     w_vs = w_vs or [None] * n
     y0s = y0s or [None] * n
+    y_outs = y_outs or [None] * n
     _require_cuda(*images, *[t for t in w_hs + w_vs + y0s if t is not None])
     xs = outs if outs is not None else [torch.empty_like(im) for im in images]
     descs = (ImageDesc * n)()
@@ -299,7 +316,8 @@ def tv2d_denoise_batched(images, lams, w_hs=None, w_vs=None, y0s=None, max_iters
                              w_vs[m].data_ptr() if w_vs[m] is not None else None,
                              float(lams[m]),
                              y0s[m].data_ptr() if y0s[m] is not None else None,
-                             xs[m].data_ptr())
+                             xs[m].data_ptr(),
+                             y_outs[m].data_ptr() if y_outs[m] is not None else None)
     nbytes = lib.tv2d_batched_workspace_size(descs, n, int(max_iters))
     if nbytes == 0:
         raise ValueError("malformed image batch")

@@ -641,6 +641,13 @@ tv_status tv2d_denoise_batched(const tv_image_desc *imgs, int n_imgs, int max_it
         all = all && hs[m].done == 1;
         kernels = std::max(kernels, (long long)hs[m].k);
     }
+    for (int m = 0; m < n_imgs; ++m) {
+        if (!imgs[m].y_out) continue;
+        st = check_cuda(cudaMemcpyAsync(imgs[m].y_out, plan.imgs[m].y,
+                                        sizeof(float) * (size_t)(imgs[m].H * imgs[m].W),
+                                        cudaMemcpyDeviceToDevice, s), "copy y");
+        if (st != TV_OK) return st;
+    }
     for (long long q = 0; q < 3 * kernels; ++q) note_launch();  // column, row, gap per iteration
     st = check_cuda(cudaStreamSynchronize(s), "synchronize");
     if (st != TV_OK) return st;

@@ -1,0 +1,667 @@
+// Kernels of the dual warm-start network: a small 3x3 convolutional net that
+// maps a noisy image and its weight lambda to an initial dual of the 2D primal-
+// dual iteration (the warm start y^0 of eq. pd). The network is not part of the
+// paper; the 2D solver accepts any y^0 and still converges.
+//
+// Tensors are NHWC with channel counts of 16 or 32 (zero-padded). Convolutions
+// are implicit GEMMs on BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate):
+//   forward:        M = pixels, N = Cout, K = 9 * Cin
+//   backward data:  the same with the kernel flipped and Cin/Cout swapped
+//   backward weight: M = Cout, N = 9 * Cin, K = pixels (persistent blocks, FP32
+//                    partial tiles, atomics into the FP32 gradient)
+// Each block of the two pixel-major kernels computes an 8 x 16 pixel tile for all
+// output channels from a zero-padded 10 x 18 input patch in shared memory; A and B
+// fragments are read with ldmatrix from rows padded by 16 bytes (conflict-free).
+#include <cstdint>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "tv_launch.cuh"
+
+using namespace tvk;
+using namespace tvh;
+
+namespace {
+
+constexpr int TH = 8, TW = 16;  // output tile (rows x cols) of one block
+constexpr int PH = TH + 2, PW = TW + 2;
+constexpr int NTHR = 128;       // 4 warps, 2 tile rows each
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2,
+                                        unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(unsigned addr, unsigned &r0, unsigned &r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2,
+                                          unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_t(unsigned addr, unsigned &r0, unsigned &r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2,
+                                         unsigned a3, unsigned b0, unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Load the zero-padded (TH+2) x (TW+2) x C input patch of tile (ty, tx) of image b.
+template <int C>
+__device__ __forceinline__ void load_patch(__nv_bfloat16 *patch, const __nv_bfloat16 *X, int b,
+                                           int H, int W, int y0, int x0)
+{
+    constexpr int PS = C + 8;   // padded pixel stride (bf16)
+    constexpr int V = C / 8;    // 16-byte vectors per pixel
+    for (int t = threadIdx.x; t < PH * PW * V; t += blockDim.x) {
+        const int v = t % V, pix = t / V;
+        const int py = pix / PW, px = pix % PW;
+        const int gy = y0 + py - 1, gx = x0 + px - 1;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            val = *reinterpret_cast<const uint4 *>(X + (((long long)b * H + gy) * W + gx) * C + v * 8);
+        *reinterpret_cast<uint4 *>(patch + pix * PS + v * 8) = val;
+    }
+}
+
+// Output-tile convolution. MODE 0: forward, out = conv + bias, optional ReLU;
+// writes the FP32 pre-activation (if pre_out) and the BF16 activation.
+// MODE 1: backward data: out = conv (weights already flipped/transposed), times
+// the ReLU mask (mask_pre > 0) of the layer below; writes BF16.
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(NTHR)
+    conv3x3_tile(const __nv_bfloat16 *X, int H, int W, const __nv_bfloat16 *Wt, const float *bias,
+                 int relu, const float *mask_pre, float *pre_out, __nv_bfloat16 *act_out)
+{
+    constexpr int PS = CIN + 8;
+    constexpr int K = 9 * CIN;
+    constexpr int KS = K + 8;      // padded weight row (bf16)
+    constexpr int NT = COUT / 8;   // n8 tiles
+    __shared__ __align__(16) __nv_bfloat16 patch[PH * PW * PS];
+    __shared__ __align__(16) __nv_bfloat16 wsm[COUT * KS];
+    const int b = blockIdx.z, y0 = blockIdx.y * TH, x0 = blockIdx.x * TW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < COUT * (K / 8); t += blockDim.x) {
+        const int n = t / (K / 8), v = t % (K / 8);
+        *reinterpret_cast<uint4 *>(wsm + n * KS + v * 8) =
+            *reinterpret_cast<const uint4 *>(Wt + (long long)n * K + v * 8);
+    }
+    load_patch<CIN>(patch, X, b, H, W, y0, x0);
+    __syncthreads();
+
+    float acc[2][NT][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[m][j][0] = acc[m][j][1] = acc[m][j][2] = acc[m][j][3] = 0.f;
+    // warp w owns tile rows 2w and 2w+1 (16 pixels each = one m16 tile each)
+    const int arow = lane & 15;            // A row = pixel column within the tile row
+    const int acol = (lane >> 4) * 8;      // A k offset (channels) 0 or 8
+    const int brow = lane & 7;             // B row = output channel within an n8 tile
+    const int bcol = ((lane >> 3) & 1) * 8;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+        for (int c0 = 0; c0 < CIN; c0 += 16) {
+            const int k0 = tap * CIN + c0;
+            unsigned bf[NT][2];
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+                ldsm_x2(smem_u32(wsm + (j * 8 + brow) * KS + k0 + bcol), bf[j][0], bf[j][1]);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int py = warp * 2 + m + ky, px = arow + kx;
+                unsigned a0, a1, a2, a3;
+                ldsm_x4(smem_u32(patch + (py * PW + px) * PS + c0 + acol), a0, a1, a2, a3);
+#pragma unroll
+                for (int j = 0; j < NT; ++j) mma_bf16(acc[m][j], a0, a1, a2, a3, bf[j][0], bf[j][1]);
+            }
+        }
+    }
+    // epilogue: C fragment rows = pixels (groupID, groupID + 8), cols = channels
+    const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int y = y0 + warp * 2 + m;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int x = x0 + g + half * 8;
+            if (y >= H || x >= W) continue;
+            const long long base = (((long long)b * H + y) * W + x) * COUT;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int co = j * 8 + tq * 2;
+                float v0 = acc[m][j][half * 2 + 0], v1 = acc[m][j][half * 2 + 1];
+                if (MODE == 0) {
+                    if (bias) {
+                        v0 += bias[co];
+                        v1 += bias[co + 1];
+                    }
+                    if (pre_out) *reinterpret_cast<float2 *>(pre_out + base + co) = make_float2(v0, v1);
+                    if (relu) {
+                        v0 = fmaxf(v0, 0.f);
+                        v1 = fmaxf(v1, 0.f);
+                    }
+                } else {
+                    const float2 mp = *reinterpret_cast<const float2 *>(mask_pre + base + co);
+                    v0 = mp.x > 0.f ? v0 : 0.f;
+                    v1 = mp.y > 0.f ? v1 : 0.f;
+                }
+                if (act_out)
+                    *reinterpret_cast<__nv_bfloat162 *>(act_out + base + co) = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
+}
+
+// Partial sums of dW[co][tap][ci] = sum over pixels p of dY[p][co] * X[p + tap][ci]
+// and db[co] = sum_p dY[p][co]. Each block walks tiles blockIdx.x, +gridDim.x, ...,
+// keeps its partial dW in registers (warp w owns the n8 column tiles w, w+4, ... of
+// N = 9 * CIN; both m16 tiles (co 0..31) or one (co 0..15)) and stores it, with its
+// partial db, to row blockIdx.x of P (row length 9 * CIN * COUT + COUT); the rows
+// are summed in a fixed order by wgrad_reduce, so the result is deterministic.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(NTHR)
+    conv3x3_wgrad(const __nv_bfloat16 *X, const __nv_bfloat16 *dY, int B, int H, int W,
+                  float *P)
+{
+    constexpr int PS = CIN + 8;
+    constexpr int DS = COUT + 8;
+    constexpr int N = 9 * CIN;
+    constexpr int NT = N / 8;
+    constexpr int NTW = (NT + 3) / 4;   // column tiles per warp
+    constexpr int MT = COUT / 16;
+    __shared__ __align__(16) __nv_bfloat16 patch[PH * PW * PS];
+    __shared__ __align__(16) __nv_bfloat16 dys[TH * TW * DS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    const long long ntiles = (long long)B * tiles_x * tiles_y;
+    float acc[MT][NTW][4];
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int j = 0; j < NTW; ++j) acc[m][j][0] = acc[m][j][1] = acc[m][j][2] = acc[m][j][3] = 0.f;
+    float bsum = 0.f;  // thread t < COUT sums channel t
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int b = (int)(tile / (tiles_x * tiles_y));
+        const int rem = (int)(tile % (tiles_x * tiles_y));
+        const int y0 = (rem / tiles_x) * TH, x0 = (rem % tiles_x) * TW;
+        __syncthreads();
+        load_patch<CIN>(patch, X, b, H, W, y0, x0);
+        for (int t = threadIdx.x; t < TH * TW * (COUT / 8); t += blockDim.x) {
+            const int v = t % (COUT / 8), pix = t / (COUT / 8);
+            const int yy = y0 + pix / TW, xx = x0 + pix % TW;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (yy < H && xx < W)
+                val = *reinterpret_cast<const uint4 *>(dY + (((long long)b * H + yy) * W + xx) * COUT + v * 8);
+            *reinterpret_cast<uint4 *>(dys + pix * DS + v * 8) = val;
+        }
+        __syncthreads();
+        if (threadIdx.x < COUT)
+            for (int pix = 0; pix < TH * TW; ++pix) bsum += __bfloat162float(dys[pix * DS + threadIdx.x]);
+        // K loop over the 128 pixels of the tile, 16 at a time (one tile row)
+#pragma unroll 1
+        for (int r = 0; r < TH; ++r) {
+            // A = dY^T (m = co, k = pixel): transposed 8x8 loads of dys rows r*16 .. r*16+15
+            unsigned af[MT][4];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                // matrices: (co 0-7, px 0-7), (co 8-15, px 0-7), (co 0-7, px 8-15), (co 8-15, px 8-15)
+                const int mat = lane >> 3, rr = lane & 7;
+                const int pix = r * TW + (mat >> 1) * 8 + rr;
+                const int co = m * 16 + (mat & 1) * 8;
+                ldsm_x4_t(smem_u32(dys + pix * DS + co), af[m][0], af[m][1], af[m][2], af[m][3]);
+            }
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) {
+                const int nt = warp + 4 * j;
+                if (nt < NT) {
+                    // B (k = pixel, n = (tap, ci)) from the patch: rows = pixels, ci contiguous
+                    const int n0 = nt * 8, tap = n0 / CIN, ci = n0 % CIN;
+                    const int ky = tap / 3, kx = tap % 3;
+                    const int mat = (lane >> 3) & 1, rr = lane & 7;
+                    const int px = mat * 8 + rr;  // pixel within the 16-pixel row
+                    unsigned b0, b1;
+                    ldsm_x2_t(smem_u32(patch + ((r + ky) * PW + px + kx) * PS + ci), b0, b1);
+#pragma unroll
+                    for (int m = 0; m < MT; ++m)
+                        mma_bf16(acc[m][j], af[m][0], af[m][1], af[m][2], af[m][3], b0, b1);
+                }
+            }
+        }
+    }
+    // store the block's partial gradient
+    float *row = P + (long long)blockIdx.x * (COUT * N + COUT);
+    const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int j = 0; j < NTW; ++j) {
+            const int nt = warp + 4 * j;
+            if (nt >= NT) continue;
+            const int n = nt * 8 + tq * 2;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int co = m * 16 + g + half * 8;
+                *reinterpret_cast<float2 *>(row + co * N + n) =
+                    make_float2(acc[m][j][half * 2], acc[m][j][half * 2 + 1]);
+            }
+        }
+    if (threadIdx.x < COUT) row[COUT * N + threadIdx.x] = bsum;
+}
+
+// dW[e] += sum_b P[b][e] (e < nw) and db[e - nw] += sum_b P[b][e] (nw <= e < stride),
+// summed in a fixed order: 32 consecutive e per block row of threads, 8 interleaved
+// groups of b per column, the 8 group sums combined in order.
+constexpr int RED_E = 32, RED_G = 8;
+__global__ void __launch_bounds__(RED_E * RED_G)
+    wgrad_reduce(const float *P, int nblocks, int stride, int nw, float *dW, float *db)
+{
+    __shared__ float part[RED_G][RED_E];
+    const int te = threadIdx.x % RED_E, tg = threadIdx.x / RED_E;
+    const int e = blockIdx.x * RED_E + te;
+    float sum = 0.f;
+    if (e < stride) {
+#pragma unroll 4
+        for (int b = tg; b < nblocks; b += RED_G) sum += P[(long long)b * stride + e];
+    }
+    part[tg][te] = sum;
+    __syncthreads();
+    if (tg == 0 && e < stride) {
+        float tot = 0.f;
+#pragma unroll
+        for (int q = 0; q < RED_G; ++q) tot += part[q][te];
+        if (e < nw) dW[e] += tot;
+        else if (db) db[e - nw] += tot;
+    }
+}
+
+// Blocks of the weight-gradient kernel for a B x H x W batch.
+long long wgrad_blocks(int B, int H, int W)
+{
+    const long long ntiles = (long long)B * ((W + TW - 1) / TW) * ((H + TH - 1) / TH);
+    return std::min<long long>(4LL * sm_count_current(), ntiles);
+}
+
+template <int CIN, int COUT, int MODE>
+tv_status launch_conv(const __nv_bfloat16 *X, int B, int H, int W, const __nv_bfloat16 *Wt,
+                      const float *bias, int relu, const float *mask_pre, float *pre_out,
+                      __nv_bfloat16 *act_out, cudaStream_t s)
+{
+    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, B);
+    conv3x3_tile<CIN, COUT, MODE><<<grid, NTHR, 0, s>>>(X, H, W, Wt, bias, relu, mask_pre, pre_out,
+                                                         act_out);
+    tv_status st = check_cuda(cudaGetLastError(), "conv launch");
+    if (st == TV_OK) note_launch();
+    return st;
+}
+
+template <int CIN, int COUT>
+tv_status launch_wgrad(const __nv_bfloat16 *X, const __nv_bfloat16 *dY, int B, int H, int W,
+                       float *dW, float *db, float *P, cudaStream_t s)
+{
+    const long long blocks = wgrad_blocks(B, H, W);
+    conv3x3_wgrad<CIN, COUT><<<(unsigned)blocks, NTHR, 0, s>>>(X, dY, B, H, W, P);
+    tv_status st = check_cuda(cudaGetLastError(), "weight-gradient launch");
+    if (st != TV_OK) return st;
+    note_launch();
+    constexpr int nw = COUT * 9 * CIN, stride = nw + COUT;
+    wgrad_reduce<<<(stride + RED_E - 1) / RED_E, RED_E * RED_G, 0, s>>>(P, (int)blocks, stride, nw,
+                                                                        dW, db);
+    st = check_cuda(cudaGetLastError(), "weight-gradient reduction");
+    if (st == TV_OK) note_launch();
+    return st;
+}
+
+bool valid_channels(int cin, int cout)
+{
+    return (cin == 16 || cin == 32) && (cout == 16 || cout == 32);
+}
+
+// ---------------------------------------------------------------- elementwise --
+// Head of the network: p_v = lam * tanh(o) on vertical edges (rows 0..H-2), and the
+// dual y = D_v^T p_v (y[r] = p[r-1] - p[r], p[-1] = p[H-1] = 0), always feasible
+// for |p_v| <= lam. With a target, also the loss sum (y - t)^2 / N (accumulated
+// into *loss) and the gradient with respect to o (channel 0 of a 16-channel
+// BF16 tensor, other channels zero).
+__global__ void __launch_bounds__(256)
+    dual_head(const float *o, int B, int H, int W, const float *lam, const float *target, float *y,
+              float *loss_part, float inv_count)
+{
+    const long long N = (long long)B * H * W;
+    float lsum = 0.f;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(q / ((long long)H * W));
+        const long long rem = q % ((long long)H * W);
+        const int r = (int)(rem / W);
+        const float L = lam[b];
+        auto pv = [&](long long qq, int rr) -> float {
+            return (rr >= 0 && rr < H - 1) ? L * tanhf(o[qq * 16]) : 0.f;
+        };
+        const float yv = pv(q - W, r - 1) - pv(q, r);
+        if (y) y[q] = yv;
+        if (target) {
+            const float e = yv - target[q];
+            lsum += e * e;
+        }
+    }
+    if (target && loss_part) {
+        __shared__ float wsum[8];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = lsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += wsum[q];
+            loss_part[blockIdx.x] = t * inv_count;
+        }
+    }
+}
+
+// *loss = sum of n block partials, in a fixed order (one block).
+__global__ void __launch_bounds__(256) sum_partials(const float *part, int n, float *loss)
+{
+    __shared__ float s[256];
+    float t = 0.f;
+    for (int i = threadIdx.x; i < n; i += 256) t += part[i];
+    s[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = s[0];
+}
+
+// d loss / d o at every pixel: dL/dp[r] = dL/dy[r+1] - dL/dy[r] for r < H-1 (0 on the
+// last row), dL/dy = 2 (y - t) / count, times lam (1 - tanh(o)^2).
+__global__ void dual_head_grad(const float *o, int B, int H, int W, const float *lam,
+                               const float *y, const float *target, __nv_bfloat16 *d_o,
+                               float inv_count)
+{
+    const long long N = (long long)B * H * W;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(q / ((long long)H * W));
+        const int r = (int)((q % ((long long)H * W)) / W);
+        float g = 0.f;
+        if (r < H - 1) {
+            const float dy_next = 2.f * (y[q + W] - target[q + W]) * inv_count;
+            const float dy_here = 2.f * (y[q] - target[q]) * inv_count;
+            const float th = tanhf(o[q * 16]);
+            g = (dy_next - dy_here) * lam[b] * (1.f - th * th);
+        }
+        __nv_bfloat16 *dst = d_o + q * 16;
+        dst[0] = __float2bfloat16(g);
+#pragma unroll
+        for (int c = 1; c < 16; ++c) dst[c] = __float2bfloat16(0.f);
+    }
+}
+
+// Network input: channel 0 the image, channel 1 its lambda, 2..15 zero (BF16 NHWC).
+__global__ void pack_input(const float *f, int B, int H, int W, const float *lam,
+                           __nv_bfloat16 *x)
+{
+    const long long N = (long long)B * H * W;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(q / ((long long)H * W));
+        __nv_bfloat16 *dst = x + q * 16;
+        dst[0] = __float2bfloat16(f[q]);
+        dst[1] = __float2bfloat16(lam[b]);
+#pragma unroll
+        for (int c = 2; c < 16; ++c) dst[c] = __float2bfloat16(0.f);
+    }
+}
+
+// Adam step with FP32 master weights and a BF16 copy for the forward pass.
+__global__ void adam_step(float *w, float *m, float *v, float *g, long long n, float lr,
+                          float b1, float b2, float eps, float bc1, float bc2, __nv_bfloat16 *w16)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        g[i] = 0.f;  // ready for the next accumulation
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        w[i] = wi;
+        if (w16) w16[i] = __float2bfloat16(wi);
+    }
+}
+
+// Flip a kernel and swap its channel roles: Wf[ci][tap'][co] = W[co][8 - tap'][ci]
+// (the weights of the backward-data convolution).
+__global__ void flip_weights(const __nv_bfloat16 *Wt, int cin, int cout, __nv_bfloat16 *Wf)
+{
+    const int n = cin * 9 * cout;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int co = i % cout, tap = (i / cout) % 9, ci = i / (cout * 9);
+        Wf[i] = Wt[((long long)co * 9 + (8 - tap)) * cin + ci];
+    }
+}
+
+int ew_blocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 8LL * sm_count_current()); }
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+// grid.y = ceil(H / TH) and grid.z = B are limited to 65535
+bool valid_shape(int B, int H, int W)
+{
+    return B >= 1 && H >= 1 && W >= 1 && B <= 65535 && (H + TH - 1) / TH <= 65535;
+}
+
+__global__ void cast_bf16(const float *a, long long n, __nv_bfloat16 *out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16(a[i]);
+}
+
+}  // namespace
+
+extern "C" {
+
+tv_status tv_net_conv3x3(const void *d_x, int B, int H, int W, int cin, const void *d_w,
+                         const float *d_bias, int cout, int relu, float *d_pre_out,
+                         void *d_act_out, tv_stream_t stream)
+{
+    clear_error();
+    if (!d_x || !d_w || (!d_act_out && !d_pre_out) || !valid_shape(B, H, W) ||
+        !valid_channels(cin, cout)) {
+        set_error("tv_net_conv3x3: need x, w, an output, 1 <= B <= 65535, H, W >= 1 and "
+                  "channels in {16, 32}");
+        return TV_ERR_INVALID;
+    }
+    if (!aligned16(d_x) || !aligned16(d_w) || !aligned16(d_act_out) || !aligned16(d_pre_out)) {
+        set_error("tv_net_conv3x3: x, w and outputs must be 16-byte aligned");
+        return TV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto X = static_cast<const __nv_bfloat16 *>(d_x);
+    auto Wt = static_cast<const __nv_bfloat16 *>(d_w);
+    auto A = static_cast<__nv_bfloat16 *>(d_act_out);
+    if (cin == 16 && cout == 32) return launch_conv<16, 32, 0>(X, B, H, W, Wt, d_bias, relu, nullptr, d_pre_out, A, s);
+    if (cin == 32 && cout == 32) return launch_conv<32, 32, 0>(X, B, H, W, Wt, d_bias, relu, nullptr, d_pre_out, A, s);
+    if (cin == 32 && cout == 16) return launch_conv<32, 16, 0>(X, B, H, W, Wt, d_bias, relu, nullptr, d_pre_out, A, s);
+    return launch_conv<16, 16, 0>(X, B, H, W, Wt, d_bias, relu, nullptr, d_pre_out, A, s);
+}
+
+tv_status tv_net_conv3x3_backward_data(const void *d_dy, int B, int H, int W, int cout,
+                                       const void *d_w, int cin, const float *d_mask_pre,
+                                       void *d_dx, void *d_scratch_w, tv_stream_t stream)
+{
+    clear_error();
+    if (!d_dy || !d_w || !d_mask_pre || !d_dx || !d_scratch_w || !valid_shape(B, H, W) ||
+        !valid_channels(cin, cout) || !aligned16(d_dy) || !aligned16(d_scratch_w) ||
+        !aligned16(d_mask_pre) || !aligned16(d_dx)) {
+        set_error("tv_net_conv3x3_backward_data: bad arguments (null, shape, channels or "
+                  "alignment)");
+        return TV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto Wf = static_cast<__nv_bfloat16 *>(d_scratch_w);
+    flip_weights<<<ew_blocks(cin * 9 * cout), 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(d_w),
+                                                           cin, cout, Wf);
+    tv_status st = check_cuda(cudaGetLastError(), "flip weights");
+    if (st != TV_OK) return st;
+    note_launch();
+    auto dY = static_cast<const __nv_bfloat16 *>(d_dy);
+    auto dX = static_cast<__nv_bfloat16 *>(d_dx);
+    // the convolution of dY (cout channels) with the flipped kernel gives cin channels
+    if (cout == 32 && cin == 32) return launch_conv<32, 32, 1>(dY, B, H, W, Wf, nullptr, 0, d_mask_pre, nullptr, dX, s);
+    if (cout == 16 && cin == 32) return launch_conv<16, 32, 1>(dY, B, H, W, Wf, nullptr, 0, d_mask_pre, nullptr, dX, s);
+    if (cout == 32 && cin == 16) return launch_conv<32, 16, 1>(dY, B, H, W, Wf, nullptr, 0, d_mask_pre, nullptr, dX, s);
+    return launch_conv<16, 16, 1>(dY, B, H, W, Wf, nullptr, 0, d_mask_pre, nullptr, dX, s);
+}
+
+size_t tv_net_workspace_size(int B, int H, int W)
+{
+    if (!valid_shape(B, H, W)) return 0;
+    const size_t wg = (size_t)wgrad_blocks(B, H, W) * (32 * 9 * 32 + 32) * sizeof(float);
+    const size_t hd = (size_t)ew_blocks((long long)B * H * W) * sizeof(float);
+    return std::max<size_t>(std::max(wg, hd), 256);
+}
+
+tv_status tv_net_conv3x3_backward_weight(const void *d_x, const void *d_dy, int B, int H, int W,
+                                         int cin, int cout, float *d_dw, float *d_db,
+                                         void *d_ws, size_t ws_bytes, tv_stream_t stream)
+{
+    clear_error();
+    if (!d_x || !d_dy || !d_dw || !d_ws || !valid_shape(B, H, W) || !valid_channels(cin, cout) ||
+        !aligned16(d_x) || !aligned16(d_dy) || !aligned16(d_ws)) {
+        set_error("tv_net_conv3x3_backward_weight: bad arguments (null, shape, channels or "
+                  "alignment)");
+        return TV_ERR_INVALID;
+    }
+    if (ws_bytes < (size_t)wgrad_blocks(B, H, W) * (cout * 9 * cin + cout) * sizeof(float)) {
+        set_error("tv_net_conv3x3_backward_weight: workspace smaller than tv_net_workspace_size");
+        return TV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto X = static_cast<const __nv_bfloat16 *>(d_x);
+    auto dY = static_cast<const __nv_bfloat16 *>(d_dy);
+    auto P = static_cast<float *>(d_ws);
+    if (cin == 16 && cout == 32) return launch_wgrad<16, 32>(X, dY, B, H, W, d_dw, d_db, P, s);
+    if (cin == 32 && cout == 32) return launch_wgrad<32, 32>(X, dY, B, H, W, d_dw, d_db, P, s);
+    if (cin == 32 && cout == 16) return launch_wgrad<32, 16>(X, dY, B, H, W, d_dw, d_db, P, s);
+    return launch_wgrad<16, 16>(X, dY, B, H, W, d_dw, d_db, P, s);
+}
+
+tv_status tv_net_pack_input(const float *d_f, int B, int H, int W, const float *d_lam, void *d_x,
+                            tv_stream_t stream)
+{
+    clear_error();
+    if (!d_f || !d_lam || !d_x || !valid_shape(B, H, W)) {
+        set_error("tv_net_pack_input: bad arguments");
+        return TV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    pack_input<<<ew_blocks((long long)B * H * W), 256, 0, s>>>(d_f, B, H, W, d_lam,
+                                                               static_cast<__nv_bfloat16 *>(d_x));
+    tv_status st = check_cuda(cudaGetLastError(), "pack input");
+    if (st == TV_OK) note_launch();
+    return st;
+}
+
+tv_status tv_net_dual_head(const float *d_o, int B, int H, int W, const float *d_lam,
+                           const float *d_target, float *d_y, float *d_loss, void *d_grad_o,
+                           void *d_ws, size_t ws_bytes, tv_stream_t stream)
+{
+    clear_error();
+    if (!d_o || !d_lam || !d_y || !valid_shape(B, H, W) || (d_grad_o && !d_target) ||
+        (d_loss && !d_target)) {
+        set_error("tv_net_dual_head: need o, lam, y (and a target for the loss or gradient)");
+        return TV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = (long long)B * H * W;
+    const int blocks = ew_blocks(N);
+    if (d_loss && (!d_ws || ws_bytes < (size_t)blocks * sizeof(float))) {
+        set_error("tv_net_dual_head: the loss needs a workspace of tv_net_workspace_size bytes");
+        return TV_ERR_INVALID;
+    }
+    const float inv = 1.f / (float)N;
+    float *part = d_loss ? static_cast<float *>(d_ws) : nullptr;
+    dual_head<<<blocks, 256, 0, s>>>(d_o, B, H, W, d_lam, d_target, d_y, part, inv);
+    tv_status st = check_cuda(cudaGetLastError(), "dual head");
+    if (st != TV_OK) return st;
+    note_launch();
+    if (d_loss) {
+        sum_partials<<<1, 256, 0, s>>>(part, blocks, d_loss);
+        st = check_cuda(cudaGetLastError(), "loss sum");
+        if (st != TV_OK) return st;
+        note_launch();
+    }
+    if (d_grad_o) {
+        dual_head_grad<<<blocks, 256, 0, s>>>(d_o, B, H, W, d_lam, d_y, d_target,
+                                               static_cast<__nv_bfloat16 *>(d_grad_o), inv);
+        st = check_cuda(cudaGetLastError(), "dual head gradient");
+        if (st == TV_OK) note_launch();
+    }
+    return st;
+}
+
+tv_status tv_net_adam(float *d_w, float *d_m, float *d_v, float *d_g, int64_t n, float lr,
+                      float beta1, float beta2, float eps, int step, void *d_w_bf16,
+                      tv_stream_t stream)
+{
+    clear_error();
+    if (!d_w || !d_m || !d_v || !d_g || n < 0 || step < 1) {
+        set_error("tv_net_adam: bad arguments");
+        return TV_ERR_INVALID;
+    }
+    if (n == 0) return TV_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float bc1 = 1.f - powf(beta1, (float)step), bc2 = 1.f - powf(beta2, (float)step);
+    adam_step<<<ew_blocks(n), 256, 0, s>>>(d_w, d_m, d_v, d_g, n, lr, beta1, beta2, eps, bc1, bc2,
+                                           static_cast<__nv_bfloat16 *>(d_w_bf16));
+    tv_status st = check_cuda(cudaGetLastError(), "adam");
+    if (st == TV_OK) note_launch();
+    return st;
+}
+
+tv_status tv_net_cast_bf16(const float *d_a, int64_t n, void *d_out, tv_stream_t stream)
+{
+    clear_error();
+    if (n < 0 || (n > 0 && (!d_a || !d_out))) {
+        set_error("tv_net_cast_bf16: bad arguments");
+        return TV_ERR_INVALID;
+    }
+    if (n == 0) return TV_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cast_bf16<<<ew_blocks(n), 256, 0, s>>>(d_a, n, static_cast<__nv_bfloat16 *>(d_out));
+    tv_status st = check_cuda(cudaGetLastError(), "cast");
+    if (st == TV_OK) note_launch();
+    return st;
+}
+
+}  // extern "C"

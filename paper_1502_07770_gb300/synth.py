@@ -120,3 +120,12 @@ def uneven_image_sizes(count: int, seed: int, w_range=(128, 2048), h_range=(96, 
 def gaussian_vector(n: int, seed: int) -> np.ndarray:
     """i.i.d. N(0, 1) float32 vector (the loss weights of the differentiable-prox workload)."""
     return _rng(seed).normal(0.0, 1.0, size=n).astype(np.float32)
+
+
+def warm_start_sample(H: int, W: int, seed: int, lam_range=(0.05, 0.3)):
+    """One sample of the learned warm-start workload: the noisy ``shapes_image`` of
+    ``seed`` and a lambda uniform in ``lam_range`` drawn from an independent stream
+    (PCG64 seeded with ``seed + 2**40``). Returns ``(noisy float32 (H, W), lambda)``."""
+    _, noisy = shapes_image(H, W, seed)
+    lam = float(_rng(seed + (1 << 40)).uniform(lam_range[0], lam_range[1]))
+    return noisy, lam
