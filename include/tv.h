@@ -230,8 +230,15 @@ tv_status tv2d_denoise_batched(const tv_image_desc *imgs, int n_imgs, int max_it
 
 /* How the calling thread's last tv2d_denoise_batched ran its iterations: 1 as one
  * CUDA graph with a device-side loop condition, 0 replayed from the host (conditional
- * graph nodes unavailable), -1 no batched solve yet. */
+ * graph nodes unavailable, or disabled), -1 no batched solve yet. */
 int tv2d_batched_last_mode(void);
+
+/* Allow (1, the default) or forbid (0) the conditional-graph outer loop of
+ * tv2d_denoise_batched, for every thread; forbidden, the same kernels are replayed
+ * from the host (for tools that cannot follow a device-side loop, such as kernel
+ * profilers). The environment variable TV_BATCHED_GRAPH=0 sets the initial value.
+ * The two modes give bitwise identical results. */
+tv_status tv_set_batched_graph(int on);
 
 /*
  * Tuning knobs set by the autotuner (the paper has no counterpart): warps per block
@@ -240,6 +247,11 @@ int tv2d_batched_last_mode(void);
  */
 tv_status tv_set_batched_warps(int warps_per_block);
 tv_status tv_set_coop_max_chains(int64_t max_chains);
+/* One warp per chain (0) or two (1, the default): with two, the chain is rooted at its
+ * middle node and the two halves' forward passes run at once (Algorithm 2 allows any
+ * root), for chains of 64 nodes or more. Both give the same solution up to FP32
+ * rounding. */
+tv_status tv_set_coop_split(int on);
 
 /* ------------------------------------------ learned dual warm start (net) ---- */
 /*

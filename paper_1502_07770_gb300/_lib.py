@@ -58,7 +58,9 @@ SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_double), _p, _sz, _p]),
     "tv_set_batched_warps": (ctypes.c_int, [ctypes.c_int]),
     "tv2d_batched_last_mode": (ctypes.c_int, []),
+    "tv_set_batched_graph": (ctypes.c_int, [ctypes.c_int]),
     "tv_set_coop_max_chains": (ctypes.c_int, [_i64]),
+    "tv_set_coop_split": (ctypes.c_int, [ctypes.c_int]),
     "tv_net_conv3x3": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       _p, _p, ctypes.c_int, ctypes.c_int, _p, _p, _p]),
     "tv_net_conv3x3_backward_data": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -333,6 +335,14 @@ def tv2d_denoise_batched(images, lams, w_hs=None, w_vs=None, y0s=None, max_iters
 
 def set_batched_warps(wpb: int):
     _check(load().tv_set_batched_warps(int(wpb)))
+
+
+def set_batched_graph(on: bool):
+    _check(load().tv_set_batched_graph(int(bool(on))))
+
+
+def set_coop_split(on: bool):
+    _check(load().tv_set_coop_split(int(bool(on))))
 
 
 def set_coop_max_chains(n: int):

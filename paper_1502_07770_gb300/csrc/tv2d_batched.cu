@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -464,6 +466,20 @@ tv_status upload(T *dst, const std::vector<T> &src, cudaStream_t s)
 std::mutex g_capture_mu;
 cudaStream_t g_capture_stream = nullptr;
 thread_local int g_last_graphed = -1;
+// 1: run the outer loop as a conditional graph when available; 0: always replay it
+// from the host. Initial value from TV_BATCHED_GRAPH ("0" disables the graph).
+std::atomic<int> g_graph_mode{-1};
+
+bool graph_mode_on()
+{
+    int m = g_graph_mode.load();
+    if (m < 0) {
+        const char *e = std::getenv("TV_BATCHED_GRAPH");
+        m = (e && e[0] == '0') ? 0 : 1;
+        g_graph_mode.store(m);
+    }
+    return m == 1;
+}
 
 }  // namespace
 
@@ -479,6 +495,17 @@ size_t tv2d_batched_workspace_size(const tv_image_desc *imgs, int n_imgs, int ma
 }
 
 int tv2d_batched_last_mode(void) { return g_last_graphed; }
+
+tv_status tv_set_batched_graph(int on)
+{
+    clear_error();
+    if (on != 0 && on != 1) {
+        set_error("tv_set_batched_graph: 0 or 1");
+        return TV_ERR_INVALID;
+    }
+    g_graph_mode.store(on);
+    return TV_OK;
+}
 
 tv_status tv_set_batched_warps(int warps_per_block)
 {
@@ -565,7 +592,9 @@ tv_status tv2d_denoise_batched(const tv_image_desc *imgs, int n_imgs, int max_it
     if (max_iters > 0) {
         // The outer loop as one graph: a WHILE node whose body is one iteration.
         bool graphed = false;
-        {
+        if (!graph_mode_on()) {
+            g_last_graphed = 0;
+        } else {
             std::lock_guard<std::mutex> lk(g_capture_mu);
             if (!g_capture_stream)
                 cudaStreamCreateWithFlags(&g_capture_stream, cudaStreamNonBlocking);

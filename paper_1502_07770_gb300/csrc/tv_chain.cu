@@ -56,6 +56,8 @@ void note_launch() { g_launches.fetch_add(1); }
 
 static std::atomic<long long> g_coop_max{kCoopMaxChainsDefault};
 long long coop_max_chains() { return g_coop_max.load(); }
+static std::atomic<int> g_coop_split{1};
+bool coop_split() { return g_coop_split.load() != 0; }
 bool prof_on() { return g_prof_on; }
 
 void prof_mark(int kind, cudaStream_t s, bool start)
@@ -436,6 +438,17 @@ tv_status tv_set_coop_max_chains(int64_t max_chains)
         return TV_ERR_INVALID;
     }
     tvh::g_coop_max.store(max_chains == 0 ? kCoopMaxChainsDefault : max_chains);
+    return TV_OK;
+}
+
+tv_status tv_set_coop_split(int on)
+{
+    clear_error();
+    if (on != 0 && on != 1) {
+        set_error("tv_set_coop_split: 0 or 1");
+        return TV_ERR_INVALID;
+    }
+    tvh::g_coop_split.store(on);
     return TV_OK;
 }
 

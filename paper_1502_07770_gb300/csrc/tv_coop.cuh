@@ -276,6 +276,323 @@ __device__ void coop_solve_chain(const P &p, typename P::Acc &acc, long long k, 
     }
 }
 
+// ------------------------------------------------------------------------------
+// Two warps per chain. A chain is a tree, and Algorithm 2 may take any node as the
+// root: with the middle node s = n/2 as root, the messages into s from the left
+// (nodes 0..s-1, the usual forward pass) and from the right (nodes n-1..s+1, the same
+// pass on the reversed chain) are independent, so two warps compute them at once and
+// the sequential depth halves. x_s minimises the unary of s plus both messages: the
+// root of h(z) = z - c_s + mL'(z) + mR'(z), a continuous increasing piecewise-linear
+// function whose kinks are the two messages' breakpoints. Each warp then runs its
+// backward clips outward from s: x_i = clip(x_{i+1}, lambda^-_i, lambda^+_i) on the
+// left, x_i = clip(x_{i-1}, lambda^-_i, lambda^+_i) on the right (the records of the
+// reversed pass).
+
+// Composition of the clips of lanes 0..j applied to x_prev (the value of the node
+// before the block): lane j returns x of its node (the right warp's backward pass).
+__device__ __forceinline__ float clip_prefix(float lo, float hi, float x_prev, int lane, int valid)
+{
+    if (lane >= valid) {
+        lo = -INFINITY;
+        hi = INFINITY;
+    }
+#pragma unroll
+    for (int o = 1; o < WARP; o <<= 1) {
+        const float lo2 = __shfl_up_sync(FULL, lo, o);
+        const float hi2 = __shfl_up_sync(FULL, hi, o);
+        if (lane >= o) {
+            // this lane's clip applied after the clips of the lanes below (inner)
+            const float nlo = clip_to(lo2, lo, hi);
+            const float nhi = clip_to(hi2, lo, hi);
+            lo = nlo;
+            hi = nhi;
+        }
+    }
+    return clip_to(x_prev, lo, hi);
+}
+
+// A message (derivative) stored by a warp for its partner: breakpoints ascending,
+// the message's value at each; constant left of the first and right of the last.
+struct PairMsg {
+    float lam[WARP];
+    float val[WARP];
+    int size;
+    int ok;
+};
+struct alignas(16) PairXchg {
+    PairMsg m[2];  // [0]: message into s from the left warp, [1]: from the right warp
+    float xs;      // x of the root node
+};
+
+__device__ __forceinline__ void pair_barrier(int pair)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(pair + 1), "r"(2 * WARP) : "memory");
+}
+
+// Value at z of a stored message (linear between breakpoints).
+__device__ __forceinline__ float msg_eval(const PairMsg &m, float z)
+{
+    const int size = m.size;
+    if (z <= m.lam[0]) return m.val[0];
+    if (z >= m.lam[size - 1]) return m.val[size - 1];
+    int lo = 0, hi = size - 1;  // invariant: lam[lo] <= z < lam[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (m.lam[mid] <= z) lo = mid;
+        else hi = mid;
+    }
+    const float t = __fdividef(z - m.lam[lo], m.lam[hi] - m.lam[lo]);
+    return fmaf(t, m.val[hi] - m.val[lo], m.val[lo]);
+}
+
+// Root of h(z) = z - c + mL'(z) + mR'(z), computed by one warp: lane l evaluates h at
+// breakpoint l of each message; the largest point with h <= 0 and the smallest with
+// h > 0 are neighbours among all kinks, and h is linear between them.
+__device__ __forceinline__ float pair_root(const PairXchg &xc, float c, int lane)
+{
+    float lo_z = -INFINITY, lo_h = 0.f, hi_z = INFINITY, hi_h = 0.f;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const PairMsg &own = xc.m[side], &oth = xc.m[1 - side];
+        if (lane < own.size) {
+            const float z = own.lam[lane];
+            const float h = (z - c) + own.val[lane] + msg_eval(oth, z);
+            if (h <= 0.f) {
+                if (z > lo_z) {
+                    lo_z = z;
+                    lo_h = h;
+                }
+            } else if (z < hi_z) {
+                hi_z = z;
+                hi_h = h;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oz = __shfl_xor_sync(FULL, lo_z, o), oh = __shfl_xor_sync(FULL, lo_h, o);
+        if (oz > lo_z) {
+            lo_z = oz;
+            lo_h = oh;
+        }
+        const float pz = __shfl_xor_sync(FULL, hi_z, o), ph = __shfl_xor_sync(FULL, hi_h, o);
+        if (pz < hi_z) {
+            hi_z = pz;
+            hi_h = ph;
+        }
+    }
+    const PairMsg &L = xc.m[0], &R = xc.m[1];
+    if (lo_z == -INFINITY)  // left of every kink: both messages at their left values
+        return fminf(c - L.val[0] - R.val[0], hi_z);
+    if (hi_z == INFINITY)  // right of every kink
+        return fmaxf(c - L.val[L.size - 1] - R.val[R.size - 1], lo_z);
+    return fminf(fmaxf(fmaf(-lo_h, __fdividef(hi_z - lo_z, hi_h - lo_h), lo_z), lo_z), hi_z);
+}
+
+// Chains shorter than this are solved by the left warp alone.
+constexpr int kSplitMinLen = 64;
+
+// One chain solved by a warp pair (role 0: nodes 0..s, role 1: nodes n-1..s+1).
+template <class P>
+__device__ void coop_solve_chain_split(const P &p, typename P::Acc &acc, long long k,
+                                       long long start, int n, int lane, int role, int pair,
+                                       PairXchg &xc, float2 *sm_rec, float *sm_crec,
+                                       int smem_nodes, float2 *rec_g, float *crec_g,
+                                       float2 *spill, WsHeader *hdr)
+{
+    const int max_len = p.max_len();
+    const bool in_smem = n <= smem_nodes;
+    float2 *recp = in_smem ? sm_rec : rec_g + k * (long long)max_len;
+    float *crecp = nullptr;
+    if constexpr (P::CREC) crecp = in_smem ? sm_crec : crec_g + k * (long long)max_len;
+    const int s = n / 2;
+
+    float lam = 0.f, V = 0.f, lam0 = 0.f, lamL = 0.f, w_prev = 0.f;
+    int size = 0;
+    bool ok = true;
+    float c_s = 0.f;
+
+    // role 0 walks nodes 0, 1, .., s; role 1 walks n-1, n-2, .., s (node s only for
+    // its weight w_s). Position q of the walk is node i(q).
+    const int cntw = role == 0 ? s + 1 : n - s;
+    auto node = [&](int q) { return role == 0 ? q : n - 1 - q; };
+    auto fetch_at = [&](int q, typename P::Raw &r) {
+        p.fetch(k, start, n, q < cntw ? node(q) : n, r);
+    };
+    typename P::Raw raw, raw_next{};
+    fetch_at(lane, raw);
+    const int nblocks = (cntw + WARP - 1) / WARP;
+    for (int blk = 0; blk < nblocks; ++blk) {
+        const int base = blk * WARP;
+        if (blk + 1 < nblocks) fetch_at(base + WARP + lane, raw_next);
+        const int q = base + lane;
+        const int i_l = q < cntw ? node(q) : n;
+        float cv, wv;
+        p.unary(k, start, n, i_l, raw, cv, wv, acc);
+        if constexpr (P::CREC) {
+            // node s is recorded by the left warp
+            if (q < cntw && (role == 0 || i_l != s)) crecp[i_l] = cv;
+        }
+        // the right warp steps node i with the weight of edge (i-1, i): that of the
+        // next position; the block's last lane takes it from the next block
+        float wr = 0.f;
+        if (role == 1) {
+            wr = __shfl_down_sync(FULL, wv, 1);
+            float c2, w2;
+            p.unary(k, start, n, base + WARP < cntw ? node(base + WARP) : n, raw_next, c2, w2, acc);
+            const float w_nb = __shfl_sync(FULL, w2, 0);
+            if (lane == WARP - 1) wr = w_nb;
+        }
+        const int cnt = min(WARP, cntw - base);
+        if (ok) {
+            for (int j = 0; j < cnt; ++j) {
+                const int qq = base + j;
+                const float ci = __shfl_sync(FULL, cv, j);
+                if (role == 0 && qq == s) {
+                    c_s = ci;
+                    break;
+                }
+                if (role == 1 && qq == cntw - 1) break;  // node s: handled by the left warp
+                const float wi = __shfl_sync(FULL, role == 0 ? wv : wr, j);
+                float lmv, hpv;
+                if (qq == 0) {
+                    lmv = ci - wi;
+                    hpv = ci + wi;
+                    lam = (lane == 0) ? lmv : hpv;
+                    V = (lane == 0) ? -wi : wi;
+                    size = 2;
+                    lam0 = lmv;
+                    lamL = hpv;
+                    w_prev = wi;
+                } else if (!coop_step(lam, V, size, lam0, lamL, w_prev, ci, wi, lane, lmv, hpv)) {
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) recp[node(qq)] = make_float2(lmv, hpv);
+            }
+        }
+        raw = raw_next;
+    }
+    // hand the message into s to the partner
+    PairMsg &mine = xc.m[role];
+    mine.lam[lane] = lam;
+    mine.val[lane] = V;
+    if (lane == 0) {
+        mine.size = size;
+        mine.ok = ok ? 1 : 0;
+    }
+    __syncwarp();
+    pair_barrier(pair);
+    const bool both_ok = xc.m[0].ok && xc.m[1].ok;
+    if (!both_ok) {
+        if (role == 0 && lane == 0) {
+            atomicAdd(&hdr->overflowed, 1ull);
+            solve_chain_global_lane0(p, k, start, n, spill, rec_g + k * (long long)max_len, crecp);
+        }
+        __syncwarp();
+        pair_barrier(pair);  // keeps the two warps' barrier counts equal
+        return;
+    }
+    if (role == 0) {
+        const float xs = pair_root(xc, c_s, lane);
+        if (lane == 0) xc.xs = xs;
+        __syncwarp();
+    }
+    pair_barrier(pair);
+    const float xs = xc.xs;
+    if (role == 0) {
+        if (lane == 0) {
+            float cc = 0.f;
+            if constexpr (P::CREC) cc = c_s;
+            p.emit(k, start, s, xs, cc);
+        }
+        // nodes s-1 .. 0, 32 at a time from the top, composing clips
+        float x_next = xs;
+        for (int blk = (s - 1) / WARP; blk >= 0; --blk) {
+            const int base = blk * WARP;
+            const int i = base + lane;
+            float lo = -INFINITY, hi = INFINITY;
+            if (i < s) {
+                const float2 r = recp[i];
+                lo = r.x;
+                hi = r.y;
+            }
+            const float xv = clip_suffix(lo, hi, x_next, lane, min(WARP, s - base));
+            float cc = 0.f;
+            if constexpr (P::CREC) {
+                if (i < s) cc = crecp[i];
+            }
+            if (i < s) p.emit(k, start, i, xv, cc);
+            x_next = __shfl_sync(FULL, xv, 0);
+        }
+    } else {
+        // nodes s+1 .. n-1, 32 at a time from the bottom, composing clips
+        float x_prev = xs;
+        const int m = n - 1 - s;
+        for (int blk = 0; blk * WARP < m; ++blk) {
+            const int i = s + 1 + blk * WARP + lane;
+            float lo = -INFINITY, hi = INFINITY;
+            if (i < n) {
+                const float2 r = recp[i];
+                lo = r.x;
+                hi = r.y;
+            }
+            const float xv = clip_prefix(lo, hi, x_prev, lane, min(WARP, m - blk * WARP));
+            float cc = 0.f;
+            if constexpr (P::CREC) {
+                if (i < n) cc = crecp[i];
+            }
+            if (i < n) p.emit(k, start, i, xv, cc);
+            x_prev = __shfl_sync(FULL, xv, WARP - 1);
+        }
+    }
+}
+
+// Two warps per chain: warp pair q of a block solves chain blockIdx.x * pairs + q.
+// Shared memory: one PairXchg per pair, then the pairs' records (and c records).
+template <class P>
+__global__ void __launch_bounds__(256) coop_pair_kernel(P p_in, float2 *rec_g, float *crec_g,
+                                                        float2 *spill, WsHeader *hdr,
+                                                        int smem_nodes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P p = p_in;
+    if (!p.resolve()) return;
+    const int lane = threadIdx.x & (WARP - 1);
+    const int warp = threadIdx.x / WARP;
+    const int pairs = blockDim.x / (2 * WARP);
+    const int pair = warp >> 1, role = warp & 1;
+    PairXchg *xch = reinterpret_cast<PairXchg *>(smem_raw);
+    float2 *sm_rec = reinterpret_cast<float2 *>(xch + pairs) + (size_t)pair * smem_nodes;
+    float *sm_crec = reinterpret_cast<float *>(reinterpret_cast<float2 *>(xch + pairs) +
+                                               (size_t)pairs * smem_nodes) +
+                     (size_t)pair * smem_nodes;
+    const long long k = (long long)blockIdx.x * pairs + pair;  // this pair's chain
+    typename P::Acc acc;
+    p.acc_init(acc);
+    long long start = 0;
+    int n = 0;
+    if (k < p.num_chains()) {
+        if (!p.chain(k, start, n)) {
+            if (lane == 0 && role == 0) atomicOr(&hdr->status, ERR_BAD_CHAIN);
+            n = 0;
+        }
+    }
+    if (n == 0 || (n < kSplitMinLen && role == 1)) {
+        p.finish_empty();
+        return;
+    }
+    if (n < kSplitMinLen) {
+        coop_solve_chain(p, acc, k, start, n, lane, sm_rec, sm_crec, smem_nodes, rec_g,
+                         crec_g, spill + p.spill_off(k, start), hdr);
+    } else {
+        coop_solve_chain_split(p, acc, k, start, n, lane, role, pair, xch[pair], sm_rec,
+                               sm_crec, smem_nodes, rec_g, crec_g,
+                               spill + p.spill_off(k, start), hdr);
+    }
+    p.finish(acc, lane);
+}
+
 template <class P>
 __global__ void __launch_bounds__(256) coop_chain_kernel(P p_in, float2 *rec_g, float *crec_g,
                                                          float2 *spill, WsHeader *hdr,

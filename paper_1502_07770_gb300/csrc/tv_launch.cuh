@@ -40,18 +40,24 @@ tv_status launch_chains(const P &p, long long nchains, float2 *rec, float *crec,
 // of a chain stay in shared memory when max_len <= kCoopSmemNodes.
 constexpr int kCoopSmemNodes = 4096;
 
+bool coop_split();  // two warps per chain (see tv_set_coop_split)
+
 template <class P>
 tv_status launch_coop(const P &p, long long nchains, int max_len, float2 *rec, float *crec,
                       float2 *spill, tvk::WsHeader *hdr, cudaStream_t s, int kind, int wpb = 4)
 {
     if (nchains <= 0) return TV_OK;
-    const long long blocks = (nchains + wpb - 1) / wpb;
+    // two warps per chain (coop_pair_kernel) for chains long enough to split
+    const bool split = coop_split() && max_len >= tvk::kSplitMinLen && wpb % 2 == 0;
+    const int cpb = split ? wpb / 2 : wpb;  // chains per block
+    const long long blocks = (nchains + cpb - 1) / cpb;
     // records in shared memory when a block's share fits in ~200 KB, else in the workspace
+    const size_t xchg = split ? cpb * sizeof(tvk::PairXchg) : 0;
     const bool fits = max_len <= kCoopSmemNodes &&
-                      wpb * tvk::coop_smem_per_warp<P>(max_len) <= (size_t)200 * 1024;
+                      xchg + cpb * tvk::coop_smem_per_warp<P>(max_len) <= (size_t)200 * 1024;
     const int smem_nodes = fits ? max_len : 0;
-    const size_t smem = wpb * tvk::coop_smem_per_warp<P>(smem_nodes);
-    auto kern = tvk::coop_chain_kernel<P>;
+    const size_t smem = xchg + cpb * tvk::coop_smem_per_warp<P>(smem_nodes);
+    auto kern = split ? tvk::coop_pair_kernel<P> : tvk::coop_chain_kernel<P>;
     tv_status st = check_cuda(
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
         "cudaFuncSetAttribute");

@@ -1,0 +1,69 @@
+"""Small, fixed workloads for kernel profilers (one GPU, inputs resident).
+
+    python -m paper_1502_07770_gb300.profile_cases tv2d     [--reps R]   # 1024x1024 denoise, lambda 0.1
+    python -m paper_1502_07770_gb300.profile_cases chain    [--reps R] [--chains B] [--len N]
+    python -m paper_1502_07770_gb300.profile_cases backward [--reps R]   # 4096 x 1024 chain VJP
+    python -m paper_1502_07770_gb300.profile_cases net      [--reps R]   # warm-start inference 1024x1024
+    python -m paper_1502_07770_gb300.profile_cases train    [--reps R]   # one training step, 8 x 512x512
+    python -m paper_1502_07770_gb300.profile_cases batched  [--reps R]   # 16 uneven images, host-replayed loop
+
+Each case runs its workload R times (after one untimed call) and prints one line. The
+batched case forbids the conditional-graph loop so that every kernel is an ordinary
+launch that a profiler can replay.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+import torch
+
+from . import _lib, learned, synth
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["tv2d", "chain", "backward", "net", "train", "batched"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--chains", type=int, default=32768)
+    ap.add_argument("--len", type=int, default=1024)
+    a = ap.parse_args(argv)
+    dev = torch.device("cuda:0")
+    if a.case == "tv2d":
+        f = torch.from_numpy(synth.shapes_image(1024, 1024, seed=0)[1]).to(dev)
+        run = lambda: _lib.tv2d_denoise(f, lam=0.1, max_iters=200, tol=1e-4)
+    elif a.case == "chain":
+        base = synth.chain_batch(256, a.len, seed0=1000)
+        y = torch.from_numpy(np.tile(base, (max(1, a.chains // 256), 1))).to(dev)
+        x = torch.empty_like(y)
+        run = lambda: _lib.chain_prox(y, lam=0.15, out=x)
+    elif a.case == "backward":
+        y = torch.from_numpy(synth.chain_batch(4096, 1024, seed0=1000)).to(dev)
+        c = torch.from_numpy(synth.gaussian_vector(4096 * 1024, seed=7).reshape(4096, 1024)).to(dev)
+        x = _lib.chain_prox(y, lam=0.15)
+        run = lambda: _lib.chain_prox_backward(x, c)
+    elif a.case in ("net", "train"):
+        net = learned.load_weights(dev)
+        if a.case == "net":
+            f = torch.from_numpy(synth.shapes_image(1024, 1024, seed=0)[1]).to(dev)
+            run = lambda: net.predict_dual(f, 0.1)
+        else:
+            fs, lams, ys = learned.make_dataset(range(10000, 10008), H=512, W=512, device=dev,
+                                                tol=1e-4, max_iters=50)
+            run = lambda: net.train_step(fs, lams, ys)
+    else:
+        _lib.set_batched_graph(False)
+        sizes, lams = synth.uneven_image_sizes(16, seed=100)
+        fs = [torch.from_numpy(synth.shapes_image(h, w, seed=100 + m)[1]).to(dev)
+              for m, (h, w) in enumerate(sizes)]
+        run = lambda: _lib.tv2d_denoise_batched(fs, lams, max_iters=200, tol=1e-4)
+    run()
+    torch.cuda.synchronize(dev)
+    for _ in range(a.reps):
+        run()
+    torch.cuda.synchronize(dev)
+    print(f"{a.case}: {a.reps} runs done")
+
+
+if __name__ == "__main__":
+    main()

@@ -91,3 +91,26 @@ def test_autotune_runs_and_applies(tmp_path):
     assert again == params
     _lib.set_coop_max_chains(0)
     _lib.set_batched_warps(4)
+
+
+def test_host_replay_matches_graph_loop():
+    """The conditional-graph outer loop and its host replay give bitwise equal results."""
+    sizes = [(64, 80), (33, 120), (96, 40)]
+    lams = [0.1, 0.25, 0.05]
+    fs, whs, wvs = _batch(sizes, lams, seed0=70, edge=(1,))
+    runs = []
+    try:
+        for on in (1, 0):
+            _lib.set_batched_graph(on)
+            ys = [torch.empty(h, w, device=DEV) for h, w in sizes]
+            xs, its, gaps, ok = _lib.tv2d_denoise_batched(
+                [_gpu(f) for f in fs], lams, [_gpu(w) for w in whs], [_gpu(w) for w in wvs],
+                max_iters=100, tol=1e-4, y_outs=ys)
+            runs.append((xs, ys, its, gaps, _lib.load().tv2d_batched_last_mode()))
+    finally:
+        _lib.set_batched_graph(1)
+    (xa, ya, ia, ga, ma), (xb, yb, ib, gb, mb) = runs
+    assert mb == 0 and ma in (0, 1)
+    assert ia == ib and ga == gb
+    assert all(torch.equal(a, b) for a, b in zip(xa, xb))
+    assert all(torch.equal(a, b) for a, b in zip(ya, yb))

@@ -141,3 +141,27 @@ def test_bench_size_sampled():
     # identical inputs give identical outputs wherever they sit in the batch
     xv = x.view(B // 256, 256, n)
     assert torch.equal(xv[0], xv[-1])
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_two_warps_per_chain(split):
+    """Chains rooted at their middle node, two warps each (the default for batches solved
+    one chain per warp), and one warp each: both against the oracle, on lengths around
+    the split threshold (64), odd and even, and longer than the shared-memory records."""
+    lengths = [63, 64, 65, 66, 127, 128, 129, 2, 1, 300, 4097, 5000, 64, 1000]
+    y, off = synth.ragged_chain_batch(lengths, seed0=77)
+    w = np.random.default_rng(8).uniform(0, 0.3, size=y.shape).astype(np.float32)
+    try:
+        _lib.set_coop_split(split)
+        for weights in (None, w):
+            x = _lib.chain_prox(_gpu(y), None if weights is None else _gpu(weights), lam=0.2,
+                                offsets=_gpu(off), max_len=max(lengths)).cpu().numpy()
+            xr = oracle.chain_solve_batch(y, off, w=weights, lam=0.2)
+            assert np.abs(x - xr).max() <= TOL
+        # uniform batch as columns
+        yc = synth.chain_batch(40, 777, seed0=3)
+        xc = _lib.chain_prox_columns(_gpu(yc.T.copy()), lam=0.1).cpu().numpy().T
+        xr = oracle.chain_solve_batch(yc.ravel(), np.arange(41) * 777, lam=0.1).reshape(yc.shape)
+        assert np.abs(xc - xr).max() <= TOL
+    finally:
+        _lib.set_coop_split(1)
