@@ -379,6 +379,20 @@ def main():
         b.synchronize()
         batched_ms.append(a.elapsed_time(b))
     bms = float(np.median(batched_ms))
+    # the same images one call each (the plain method, image by image)
+    seq_ms = []
+    for _ in range(max(2, args.steps // 25)):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for m in range(len(bimg)):
+            _lib.tv2d_denoise(bimg[m], lam=blams[m], w_h=bwh[m], w_v=bwv[m], max_iters=MAX_ITERS,
+                              tol=TOL, out=bouts[m])
+        b.record(stream)
+        b.synchronize()
+        seq_ms.append(a.elapsed_time(b))
+    sms = float(np.median(seq_ms))
 
     # ---------------- learned dual warm start (stored network) ----------------
     from paper_1502_07770_gb300 import learned
@@ -466,6 +480,8 @@ def main():
                     "Mpixel_per_s": bpix / (bms * 1e-3) / 1e6,
                     "iterations_max": int(max(b_iters)), "iterations_mean": float(np.mean(b_iters)),
                     "graph_loop": int(_lib.load().tv2d_batched_last_mode()),
+                    "sequential_ms": sms,
+                    "speedup_vs_sequential": sms / bms,
                     "workload": "64 images, W ~ U{128..2048}, H ~ U{96..1536}, lambda ~ U[0.05,0.3], "
                                 "edge-aware weights lambda*exp(-|df|/0.2), to per-pixel gap 1e-4"},
         "learned_warm_start": {

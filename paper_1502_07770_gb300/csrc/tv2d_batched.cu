@@ -215,6 +215,248 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ------------------------------------------------ one thread per chain ------
+// Large batches: a warp takes a group of up to 32 consecutive rows (or columns) of
+// one image and runs the one-thread-per-chain dynamic program of tv_dp.cuh on them;
+// the groups of all images form one launch per phase (longest chains first).
+// Records of a group: 32 slots x its chain length, from the group's rec0.
+struct BGroup {
+    int img, first, count, pad;
+    long long rec0;
+};
+
+constexpr int kBRing = 32;
+
+__device__ __forceinline__ bool al16(const void *q) { return ((uintptr_t)q & 15) == 0; }
+
+template <int PHASE>  // 0: x^0 rows, 1: primal rows
+struct BRowsTP {
+    static constexpr bool COLS = false;
+    static constexpr int NIN = PHASE == 0 ? 3 : 4;  // f, y, (x^k), w_h
+    static constexpr int WI = NIN - 1;              // the weights input
+    static constexpr bool NEIGH = false;
+    static constexpr bool CREC = false;
+    static constexpr int NOUT = PHASE == 0 ? 2 : 1;
+    struct Acc {};
+    const BImg *imgs;
+    const BState *st;
+    const BGroup *groups;
+    long long nslots;
+    int maxlen;
+    const Tv2dParams *prm;
+    const float2 *spill_base;
+    // bound per warp
+    const BImg *im;
+    int r0, cnt;
+    long long rec0;
+    const float *xin;
+    float *xout;
+    float ca, cb;
+    bool vec, vecw;
+
+    __device__ bool resolve() { return true; }
+    __device__ long long num_chains() const { return nslots; }
+    __device__ int max_len() const { return maxlen; }
+    __device__ bool bind_warp(long long wc0)
+    {
+        const BGroup g = groups[wc0 / WARP];
+        const BState &s = st[g.img];
+        if (PHASE != 0 && s.done) return false;
+        im = imgs + g.img;
+        r0 = g.first;
+        cnt = g.count;
+        rec0 = g.rec0;
+        xin = xout = nullptr;
+        ca = cb = 0.f;
+        if (PHASE == 1) {
+            const int k = s.k;
+            xin = (k & 1) ? im->x1 : im->x0;
+            xout = (k & 1) ? im->x0 : im->x1;
+            const double tau = prm[k].tau;
+            ca = (float)(tau / (tau + 1.0));
+            cb = (float)(1.0 / (tau + 1.0));
+        }
+        vec = im->W % 4 == 0 && al16(im->f) && al16(im->y) && al16(im->x0) && al16(im->x1);
+        vecw = im->wh != nullptr && (im->W - 1) % 4 == 0 && al16(im->wh);
+        return true;
+    }
+    __device__ long long rec_slot(long long, int) const { return rec0; }
+    __device__ int row_of(long long k) const { return r0 + (int)(k & (WARP - 1)); }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        start = 0;
+        n = 0;
+        if ((int)(k & (WARP - 1)) < cnt) {
+            start = (long long)row_of(k) * im->W;
+            n = im->W;
+        }
+        return true;
+    }
+    __device__ const float *in_ptr(int a) const
+    {
+        if (a == 0) return im->f;
+        if (a == 1) return im->y;
+        if (PHASE == 1 && a == 2) return xin;
+        return im->wh;  // may be NULL: lambda then
+    }
+    __device__ long long in_off(int a, long long k, long long start) const
+    {
+        return a == WI ? (long long)row_of(k) * (im->W - 1) : start;
+    }
+    __device__ int in_lim(int a, int n) const { return a == WI ? n - 1 : n; }
+    __device__ bool in_vec(int a) const { return a == WI ? vecw : vec; }
+    __device__ bool out_vec() const { return vec; }
+    __device__ __forceinline__ void unary_vals(float fv, float yv, float xv, float wv, int i, int n,
+                                               float &c, float &w) const
+    {
+        if (PHASE == 0) {
+            c = fv - yv;
+            w = (i < n - 1) ? wv : 0.f;
+        } else {
+            c = ca * (fv - yv) + cb * xv;
+            w = (i < n - 1) ? ca * wv : 0.f;
+        }
+    }
+    __device__ void unary(const float (&v)[NIN], float, int, int i, int n, long long, float &c,
+                          float &w, Acc &) const
+    {
+        const float wv = im->wh ? v[WI] : im->lam;
+        unary_vals(v[0], v[1], PHASE == 1 ? v[2] : 0.f, wv, i, n, c, w);
+    }
+    __device__ void unary_direct(int i, int n, long long k, long long start, float &c,
+                                 float &w) const
+    {
+        const float wv = (im->wh && i < n - 1) ? im->wh[(long long)row_of(k) * (im->W - 1) + i]
+                                               : im->lam;
+        unary_vals(im->f[start + i], im->y[start + i], PHASE == 1 ? xin[start + i] : 0.f, wv, i, n,
+                   c, w);
+    }
+    __device__ float *out_ptr(int o) const
+    {
+        if (PHASE == 0) return o == 0 ? im->x0 : im->x1;
+        return xout;
+    }
+    __device__ long long out_off(int, long long, long long start) const { return start; }
+    __device__ void emit_cols(int, long long, float, float) const {}
+    __device__ void emit_direct(int i, long long, long long start, float xv, float) const
+    {
+        if (PHASE == 0) {
+            im->x0[start + i] = xv;
+            im->x1[start + i] = xv;
+        } else {
+            xout[start + i] = xv;
+        }
+    }
+    __device__ long long spill_off(long long k, long long) const
+    {
+        return (im->spill - spill_base) + (long long)row_of(k) * (2LL * im->W + 2);
+    }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &) const {}
+    __device__ void finish_empty() const {}
+};
+
+// Dual (column) phase.
+struct BColsTP {
+    static constexpr bool COLS = true;
+    static constexpr int NIN = 4;  // x^k, x^{k-1}, y, w_v
+    static constexpr bool NEIGH = false;
+    static constexpr bool CREC = true;
+    static constexpr int NOUT = 0;
+    struct Acc {};
+    const BImg *imgs;
+    const BState *st;
+    const BGroup *groups;
+    long long nslots;
+    int maxlen;
+    const Tv2dParams *prm;
+    const float2 *spill_base;
+    // bound per warp
+    const BImg *im;
+    int c0, cnt;
+    long long rec0;
+    const float *xk, *xkm1;
+    float sigma, inv_sigma, theta;
+    bool vec;
+
+    __device__ bool resolve() { return true; }
+    __device__ long long num_chains() const { return nslots; }
+    __device__ int max_len() const { return maxlen; }
+    __device__ bool bind_warp(long long wc0)
+    {
+        const BGroup g = groups[wc0 / WARP];
+        const BState &s = st[g.img];
+        if (s.done) return false;
+        im = imgs + g.img;
+        c0 = g.first;
+        cnt = g.count;
+        rec0 = g.rec0;
+        const int k = s.k;
+        xk = (k & 1) ? im->x1 : im->x0;
+        xkm1 = (k & 1) ? im->x0 : im->x1;
+        sigma = (float)prm[k].sigma;
+        inv_sigma = (float)(1.0 / prm[k].sigma);
+        theta = (float)prm[k].theta_prev;
+        vec = im->W % 4 == 0 && al16(im->x0) && al16(im->x1) && al16(im->y) &&
+              (im->wv == nullptr || al16(im->wv));
+        return true;
+    }
+    __device__ long long col_base(long long) const { return c0; }
+    __device__ long long rec_slot(long long, int) const { return rec0; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        start = 0;
+        n = 0;
+        const int l = (int)(k & (WARP - 1));
+        if (l < cnt) {
+            start = c0 + l;  // the column
+            n = im->H;
+        }
+        return true;
+    }
+    __device__ const float *in_ptr(int a) const
+    {
+        return a == 0 ? xk : (a == 1 ? xkm1 : (a == 2 ? im->y : im->wv));
+    }
+    __device__ long long in_off(int, long long, long long start) const { return start; }
+    __device__ int in_lim(int a, int) const { return a == 3 ? im->H - 1 : im->H; }
+    __device__ long long in_ld(int) const { return im->W; }
+    __device__ long long in_kmax(int) const { return c0 + cnt; }
+    __device__ bool in_vec(int) const { return vec; }
+    __device__ bool out_vec() const { return false; }
+    __device__ void unary(const float (&v)[NIN], float, int, int i, int n, long long, float &c,
+                          float &w, Acc &) const
+    {
+        const float wvv = im->wv ? v[3] : im->lam;
+        c = v[2] * inv_sigma + (v[0] + theta * (v[0] - v[1]));  // eta / sigma
+        w = (i < n - 1) ? wvv * inv_sigma : 0.f;
+    }
+    __device__ void unary_direct(int i, int n, long long, long long col, float &c, float &w) const
+    {
+        (void)c;  // c comes from the forward-pass record
+        const float wvv = (im->wv && i < n - 1) ? im->wv[(long long)i * im->W + col] : im->lam;
+        w = (i < n - 1) ? wvv * inv_sigma : 0.f;
+    }
+    __device__ float *out_ptr(int) const { return nullptr; }
+    __device__ long long out_off(int, long long, long long) const { return 0; }
+    __device__ void emit_cols(int i, long long k, float xhat, float c) const
+    {
+        const int l = (int)(k & (WARP - 1));
+        if (l < cnt) im->y[(long long)i * im->W + c0 + l] = sigma * (c - xhat);
+    }
+    __device__ void emit_direct(int i, long long, long long col, float xhat, float c) const
+    {
+        im->y[(long long)i * im->W + col] = sigma * (c - xhat);
+    }
+    __device__ long long spill_off(long long, long long col) const
+    {
+        return (im->spill - spill_base) + col * (2LL * im->H + 2);
+    }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &) const {}
+    __device__ void finish_empty() const {}
+};
+
 constexpr int kBGapThreads = 256;
 
 __global__ void __launch_bounds__(kBGapThreads)
@@ -296,6 +538,8 @@ __global__ void __launch_bounds__(kBGapThreads)
 struct Plan {
     std::vector<BImg> imgs;
     std::vector<ChainRef> cols, rows;
+    std::vector<BGroup> rgroups, cgroups;  // one-thread-per-chain groups
+    bool thread_rows = false, thread_cols = false;
     std::vector<GapTile> tiles;
     std::vector<int> ntiles, tile0;
     int max_h = 0, max_w = 0;
@@ -307,6 +551,9 @@ struct BatchedWs {
     BImg *imgs;
     BState *st;
     ChainRef *cols, *rows;
+    BGroup *rgroups, *cgroups;
+    float2 *trec;  // records of the one-thread-per-chain launches
+    float *tcrec;
     GapTile *tiles;
     int *ntiles, *tile0;
     double *partials;
@@ -323,17 +570,26 @@ BatchedWs carve_batched(void *base, const tv_image_desc *d, int n, int max_iters
 {
     Carver cv(base);
     BatchedWs o;
-    long long ncols = 0, nrows = 0, ntiles = 0;
+    long long ncols = 0, nrows = 0, ntiles = 0, nrg = 0, ncg = 0, rrec = 0, crec = 0;
     for (int m = 0; m < n; ++m) {
         ncols += d[m].W;
         nrows += d[m].H;
         ntiles += (d[m].H * d[m].W + kGapTilePixels - 1) / kGapTilePixels;
+        const long long rg = (d[m].H + WARP - 1) / WARP, cg = (d[m].W + WARP - 1) / WARP;
+        nrg += rg;
+        ncg += cg;
+        rrec += rg * WARP * d[m].W;
+        crec += cg * WARP * d[m].H;
     }
     o.imgs = cv.take<BImg>((size_t)n);
     o.st = cv.take<BState>((size_t)n);
     o.cols = cv.take<ChainRef>((size_t)ncols);
     o.rows = cv.take<ChainRef>((size_t)nrows);
     o.tiles = cv.take<GapTile>((size_t)ntiles);
+    o.rgroups = cv.take<BGroup>((size_t)nrg);
+    o.cgroups = cv.take<BGroup>((size_t)ncg);
+    o.trec = cv.take<float2>((size_t)std::max(rrec, crec));
+    o.tcrec = cv.take<float>((size_t)crec);
     o.ntiles = cv.take<int>((size_t)n);
     o.tile0 = cv.take<int>((size_t)n);
     o.partials = cv.take<double>((size_t)ntiles);
@@ -376,6 +632,24 @@ void build_plan(const tv_image_desc *d, int n, Plan &plan)
         for (int c = 0; c < d[m].W; ++c) plan.cols.push_back(ChainRef{m, c});
     for (int m : by_w)
         for (int r = 0; r < d[m].H; ++r) plan.rows.push_back(ChainRef{m, r});
+    plan.rgroups.clear();
+    plan.cgroups.clear();
+    long long rrec = 0, crec = 0;
+    for (int m : by_w)
+        for (long long r = 0; r < d[m].H; r += WARP) {
+            plan.rgroups.push_back(
+                BGroup{m, (int)r, (int)std::min<long long>(WARP, d[m].H - r), 0, rrec});
+            rrec += (long long)WARP * d[m].W;
+        }
+    for (int m : by_h)
+        for (long long c = 0; c < d[m].W; c += WARP) {
+            plan.cgroups.push_back(
+                BGroup{m, (int)c, (int)std::min<long long>(WARP, d[m].W - c), 0, crec});
+            crec += (long long)WARP * d[m].H;
+        }
+    // batches larger than the warp-per-chain limit run one thread per chain
+    plan.thread_rows = (long long)plan.rows.size() > coop_max_chains();
+    plan.thread_cols = (long long)plan.cols.size() > coop_max_chains();
     plan.tiles.clear();
     plan.ntiles.assign(n, 0);
     plan.tile0.assign(n, 0);
@@ -442,12 +716,50 @@ tv_status launch_phase(const BatchedWs &ws, const Plan &plan, const ChainRef *ch
     return check_cuda(cudaGetLastError(), "batched phase launch");
 }
 
+template <class P>
+P thread_policy(const BatchedWs &ws, const Plan &plan, bool cols)
+{
+    P p{};
+    p.imgs = ws.imgs;
+    p.st = ws.st;
+    p.groups = cols ? ws.cgroups : ws.rgroups;
+    p.nslots = (long long)(cols ? plan.cgroups.size() : plan.rgroups.size()) * WARP;
+    p.maxlen = cols ? plan.max_h : plan.max_w;
+    p.prm = ws.prm;
+    p.spill_base = plan.imgs[0].spill;
+    return p;
+}
+
+template <class P>
+tv_status prepare_thread(long long nslots)
+{
+    const Shape sh = batch_shape(nslots / WARP, sm_count_current());
+    (void)sh;
+    return check_cuda(cudaFuncSetAttribute(chain_batch_kernel<P, kBRing>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(4 * sizeof(WarpSmem<P, kBRing>))),
+                      "cudaFuncSetAttribute");
+}
+
+template <class P>
+tv_status launch_thread(const BatchedWs &ws, const Plan &plan, bool cols, cudaStream_t s)
+{
+    const P p = thread_policy<P>(ws, plan, cols);
+    const Shape sh = batch_shape(p.nslots / WARP, sm_count_current());
+    chain_batch_kernel<P, kBRing><<<(unsigned)sh.blocks, sh.wpb * WARP,
+                                    sh.wpb * sizeof(WarpSmem<P, kBRing>), s>>>(
+        p, ws.trec, ws.tcrec, const_cast<float2 *>(p.spill_base), ws.hdr);
+    return check_cuda(cudaGetLastError(), "batched thread-per-chain launch");
+}
+
 tv_status launch_iteration(const BatchedWs &ws, const Plan &plan, cudaStream_t s,
                            cudaGraphConditionalHandle cond, int use_cond)
 {
-    tv_status st = launch_phase<2>(ws, plan, ws.cols, (int)plan.cols.size(), s);
+    tv_status st = plan.thread_cols ? launch_thread<BColsTP>(ws, plan, true, s)
+                                    : launch_phase<2>(ws, plan, ws.cols, (int)plan.cols.size(), s);
     if (st != TV_OK) return st;
-    st = launch_phase<1>(ws, plan, ws.rows, (int)plan.rows.size(), s);
+    st = plan.thread_rows ? launch_thread<BRowsTP<1>>(ws, plan, false, s)
+                          : launch_phase<1>(ws, plan, ws.rows, (int)plan.rows.size(), s);
     if (st != TV_OK) return st;
     batched_gap_kernel<<<(unsigned)plan.tiles.size(), kBGapThreads, 0, s>>>(
         ws.imgs, ws.st, ws.tiles, ws.prm, ws.partials, ws.ctl, cond, use_cond);
@@ -567,6 +879,11 @@ tv_status tv2d_denoise_batched(const tv_image_desc *imgs, int n_imgs, int max_it
     if ((st = prepare_phase<0>(plan, (int)plan.rows.size(), plan.max_w)) != TV_OK) return st;
     if ((st = prepare_phase<1>(plan, (int)plan.rows.size(), plan.max_w)) != TV_OK) return st;
     if ((st = prepare_phase<2>(plan, (int)plan.cols.size(), plan.max_h)) != TV_OK) return st;
+    if ((st = upload(ws.rgroups, plan.rgroups, s)) != TV_OK) return st;
+    if ((st = upload(ws.cgroups, plan.cgroups, s)) != TV_OK) return st;
+    if ((st = prepare_thread<BRowsTP<0>>(0)) != TV_OK) return st;
+    if ((st = prepare_thread<BRowsTP<1>>(0)) != TV_OK) return st;
+    if ((st = prepare_thread<BColsTP>(0)) != TV_OK) return st;
     {
         static thread_local ParamChunk chunk;
         for (int first = 0; first <= max_iters; first += kParamChunk) {
@@ -586,7 +903,9 @@ tv_status tv2d_denoise_batched(const tv_image_desc *imgs, int n_imgs, int max_it
                         : check_cuda(cudaMemsetAsync(plan.imgs[m].y, 0, bytes, s), "zero y");
         if (st != TV_OK) return st;
     }
-    if ((st = launch_phase<0>(ws, plan, ws.rows, (int)plan.rows.size(), s)) != TV_OK) return st;
+    st = plan.thread_rows ? launch_thread<BRowsTP<0>>(ws, plan, false, s)
+                          : launch_phase<0>(ws, plan, ws.rows, (int)plan.rows.size(), s);
+    if (st != TV_OK) return st;
     note_launch();
 
     if (max_iters > 0) {

@@ -21,7 +21,37 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace tvk {
+
+// Optional policy hooks of the one-thread-per-chain kernel, for policies whose
+// warps each serve one group of chains of a larger structure (the batched images):
+//   bool bind_warp(warp_chain0)   per-warp set-up; false skips the whole warp
+//   long long col_base(warp_chain0)   column index of lane 0 (column layouts)
+//   long long rec_slot(wg, max_len)   first record of warp wg (default wg*max_len*32)
+template <class P, class = void>
+struct has_bind : std::false_type {};
+template <class P>
+struct has_bind<P, std::void_t<decltype(std::declval<P &>().bind_warp(0LL))>> : std::true_type {};
+template <class P, class = void>
+struct has_col_base : std::false_type {};
+template <class P>
+struct has_col_base<P, std::void_t<decltype(std::declval<const P &>().col_base(0LL))>>
+    : std::true_type {};
+template <class P, class = void>
+struct has_rec_slot : std::false_type {};
+template <class P>
+struct has_rec_slot<P, std::void_t<decltype(std::declval<const P &>().rec_slot(0LL, 0))>>
+    : std::true_type {};
+
+template <class P>
+__device__ __forceinline__ long long col_base_of(const P &p, long long warp_chain0)
+{
+    if constexpr (has_col_base<P>::value) return p.col_base(warp_chain0);
+    else return warp_chain0;
+}
 
 constexpr int WARP = 32;
 constexpr int CH = 16;  // nodes per staged chunk
@@ -281,13 +311,21 @@ __device__ __forceinline__ void cp_async_wait()
 constexpr int RP = CH + 4;
 constexpr int CP = WARP + 4;
 
+// The forward pass uses the input tiles and the ring, the backward pass the record
+// tiles and the output tile: the two sets share their shared memory.
 template <class P, int RING>
 struct alignas(16) WarpSmem {
-    float in[P::NIN][2][P::COLS ? CH * CP : WARP * RP];
-    float2 rec[2][CH][WARP];
-    float crec[P::CREC ? 2 : 1][P::CREC ? CH : 1][WARP];
-    float out[P::COLS ? 4 : WARP * RP];
-    float2 ring[RING][WARP];
+    union {
+        struct {
+            float in[P::NIN][2][P::COLS ? CH * CP : WARP * RP];
+            float2 ring[RING][WARP];
+        } f;
+        struct {
+            float2 rec[2][CH][WARP];
+            float crec[P::CREC ? 2 : 1][P::CREC ? CH : 1][WARP];
+            float out[P::COLS ? 4 : WARP * RP];
+        } b;
+    } u;
     long long start[WARP];
     int len[WARP];
 };
@@ -299,8 +337,10 @@ __device__ __forceinline__ void fill_inputs(const P &p, WarpSmem<P, RING> *sm, i
 #pragma unroll
     for (int a = 0; a < P::NIN; ++a) {
         const float *src = p.in_ptr(a);
-        float *tile = sm->in[a][b];
+        if (src == nullptr) continue;  // an optional input this warp does not have
+        float *tile = sm->u.f.in[a][b];
         if constexpr (P::COLS) {
+            const long long kb = col_base_of(p, warp_chain0);
             const long long ld = p.in_ld(a);
             const long long kmax = p.in_kmax(a);
             const int lim = p.in_lim(a, p.max_len());
@@ -311,7 +351,7 @@ __device__ __forceinline__ void fill_inputs(const P &p, WarpSmem<P, RING> *sm, i
                     const int jn = 4 * u + (lane >> 3);
                     const int i = chunk * CH + jn;
                     const int c4 = (lane & 7) * 4;
-                    const long long k = warp_chain0 + c4;
+                    const long long k = kb + c4;
                     if (i < lim) {
                         if (k + 3 < kmax) {
                             cp_async16(&tile[jn * CP + c4], src + (long long)i * ld + k);
@@ -324,7 +364,7 @@ __device__ __forceinline__ void fill_inputs(const P &p, WarpSmem<P, RING> *sm, i
                     }
                 }
             } else {
-                const long long k = warp_chain0 + lane;
+                const long long k = kb + lane;
                 if (k < kmax) {
 #pragma unroll 4
                     for (int u = 0; u < CH; ++u) {
@@ -334,7 +374,7 @@ __device__ __forceinline__ void fill_inputs(const P &p, WarpSmem<P, RING> *sm, i
                 }
             }
             if (P::NEIGH && a == 0 && lane < CH) {
-                const long long kn = warp_chain0 + WARP;
+                const long long kn = kb + WARP;
                 const int i = chunk * CH + lane;
                 if (kn < kmax && i < lim) cp_async4(&tile[lane * CP + WARP], src + (long long)i * ld + kn);
             }
@@ -373,9 +413,9 @@ __device__ __forceinline__ void fill_records(WarpSmem<P, RING> *sm, int b, int c
     for (int u = 0; u < CH; ++u) {
         const int i = chunk * CH + u;
         if (i < n) {
-            cp_async8(&sm->rec[b][u][lane], rec_w + (long long)i * WARP + lane);
+            cp_async8(&sm->u.b.rec[b][u][lane], rec_w + (long long)i * WARP + lane);
             if constexpr (P::CREC)
-                cp_async4(&sm->crec[b][u][lane], crec_w + (long long)i * WARP + lane);
+                cp_async4(&sm->u.b.crec[b][u][lane], crec_w + (long long)i * WARP + lane);
         }
     }
 }
@@ -393,7 +433,7 @@ __device__ __forceinline__ void flush_outputs(const P &p, WarpSmem<P, RING> *sm,
             const int i = chunk * CH + q;
             if (i < sm->len[jj])
                 *reinterpret_cast<float4 *>(dst + p.out_off(o, warp_chain0 + jj, sm->start[jj]) + i) =
-                    *reinterpret_cast<const float4 *>(&sm->out[jj * RP + q]);
+                    *reinterpret_cast<const float4 *>(&sm->u.b.out[jj * RP + q]);
         }
     } else {
 #pragma unroll 4
@@ -402,7 +442,7 @@ __device__ __forceinline__ void flush_outputs(const P &p, WarpSmem<P, RING> *sm,
             const int jj = t / CH, node = t % CH;
             const int i = chunk * CH + node;
             if (i < sm->len[jj])
-                dst[p.out_off(o, warp_chain0 + jj, sm->start[jj]) + i] = sm->out[jj * RP + node];
+                dst[p.out_off(o, warp_chain0 + jj, sm->start[jj]) + i] = sm->u.b.out[jj * RP + node];
         }
     }
 }
@@ -463,6 +503,12 @@ __global__ void __launch_bounds__(128) chain_batch_kernel(P p_in, float2 *rec, f
     const long long wg = (long long)blockIdx.x * wpb + warp;
     const long long warp_chain0 = wg * WARP;
     const long long k = warp_chain0 + lane;
+    if constexpr (has_bind<P>::value) {
+        if (warp_chain0 >= p.num_chains() || !p.bind_warp(warp_chain0)) {
+            p.finish_empty();
+            return;
+        }
+    }
     const int max_len = p.max_len();
 
     long long start = 0;
@@ -484,10 +530,12 @@ __global__ void __launch_bounds__(128) chain_batch_kernel(P p_in, float2 *rec, f
         return;
     }
     const int nchunks = (nmax + CH - 1) / CH;
-    float2 *rec_w = rec + wg * (long long)max_len * WARP;
-    float *crec_w = P::CREC ? crec + wg * (long long)max_len * WARP : nullptr;
+    long long slot = wg * (long long)max_len * WARP;
+    if constexpr (has_rec_slot<P>::value) slot = p.rec_slot(wg, max_len);
+    float2 *rec_w = rec + slot;
+    float *crec_w = P::CREC ? crec + slot : nullptr;
 
-    RingStore<RING> S{(unsigned)__cvta_generic_to_shared(&sm->ring[0][lane])};
+    RingStore<RING> S{(unsigned)__cvta_generic_to_shared(&sm->u.f.ring[0][lane])};
     DPState d;
     typename P::Acc acc;
     p.acc_init(acc);
@@ -509,7 +557,7 @@ __global__ void __launch_bounds__(128) chain_batch_kernel(P p_in, float2 *rec, f
             if constexpr (!P::COLS) {
 #pragma unroll
                 for (int a = 0; a < P::NIN; ++a)
-                    q[a] = *reinterpret_cast<const float4 *>(&sm->in[a][b][lane * RP + j4]);
+                    q[a] = *reinterpret_cast<const float4 *>(&sm->u.f.in[a][b][lane * RP + j4]);
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -519,10 +567,10 @@ __global__ void __launch_bounds__(128) chain_batch_kernel(P p_in, float2 *rec, f
                 float xr = 0.f;
                 if constexpr (P::COLS) {
 #pragma unroll
-                    for (int a = 0; a < P::NIN; ++a) v[a] = sm->in[a][b][j * CP + lane];
+                    for (int a = 0; a < P::NIN; ++a) v[a] = sm->u.f.in[a][b][j * CP + lane];
                     if constexpr (P::NEIGH) {
                         const float sh = __shfl_down_sync(0xffffffffu, v[0], 1);
-                        xr = (lane == WARP - 1) ? sm->in[0][b][j * CP + WARP] : sh;
+                        xr = (lane == WARP - 1) ? sm->u.f.in[0][b][j * CP + WARP] : sh;
                     }
                 } else {
 #pragma unroll
@@ -574,15 +622,15 @@ __global__ void __launch_bounds__(128) chain_batch_kernel(P p_in, float2 *rec, f
             const int i = ch * CH + j;
             if (i < n_eff) {
                 if (i < n - 1) {
-                    const float2 r = sm->rec[b][j][lane];
+                    const float2 r = sm->u.b.rec[b][j][lane];
                     xv = clip_to(xv, r.x, r.y);
                 }
                 float cc = 0.f;
-                if constexpr (P::CREC) cc = sm->crec[b][j][lane];
+                if constexpr (P::CREC) cc = sm->u.b.crec[b][j][lane];
                 if constexpr (P::COLS) {
                     p.emit_cols(i, k, xv, cc);
                 } else {
-                    sm->out[lane * RP + j] = xv;
+                    sm->u.b.out[lane * RP + j] = xv;
                 }
             }
         }

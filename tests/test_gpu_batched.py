@@ -114,3 +114,26 @@ def test_host_replay_matches_graph_loop():
     assert ia == ib and ga == gb
     assert all(torch.equal(a, b) for a, b in zip(xa, xb))
     assert all(torch.equal(a, b) for a, b in zip(ya, yb))
+
+
+@pytest.mark.parametrize("case", ["mixed", "cap"])
+def test_thread_per_chain_path(case):
+    """Batches above the warp-per-chain limit run one thread per chain (groups of 32 rows
+    or columns of one image): forced here on small images, against the oracle."""
+    try:
+        _lib.set_coop_max_chains(1)
+        if case == "mixed":
+            sizes = [(37, 50), (64, 64), (100, 33), (1, 40), (40, 1), (128, 96), (2, 2), (70, 129)]
+            lams = [0.05, 0.1, 0.3, 0.2, 0.15, 0.25, 0.1, 0.12]
+            fs, whs, wvs = _batch(sizes, lams, seed0=110, edge=(1, 5, 7))
+            y0s = [None] * len(fs)
+            y0s[2] = (0.02 * synth.shapes_image(100, 33, seed=98, n_shapes=5)[1]).astype(np.float32)
+            its = _check(fs, whs, wvs, lams, y0s=y0s)
+            assert len(set(its)) > 1
+        else:
+            sizes = [(48, 52), (30, 70), (33, 31)]
+            lams = [0.2, 0.1, 0.3]
+            fs, whs, wvs = _batch(sizes, lams, seed0=140, edge=(0,))
+            _check(fs, whs, wvs, lams, max_iters=3, tol=0.0)
+    finally:
+        _lib.set_coop_max_chains(0)
