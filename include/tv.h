@@ -247,11 +247,12 @@ tv_status tv_set_batched_graph(int on);
  */
 tv_status tv_set_batched_warps(int warps_per_block);
 tv_status tv_set_coop_max_chains(int64_t max_chains);
-/* One warp per chain (0) or two (1, the default): with two, the chain is rooted at its
- * middle node and the two halves' forward passes run at once (Algorithm 2 allows any
- * root), for chains of 64 nodes or more. Both give the same solution up to FP32
- * rounding. */
-tv_status tv_set_coop_split(int on);
+/* How a chain of 64 nodes or more is solved when its batch runs one warp per chain:
+ * 0 by the whole warp from one end; 1 (the default) rooted at its middle node, the two
+ * halves' forward passes run at once by the warp's two 16-lane halves (Algorithm 2
+ * allows any root); 2 rooted at its middle node by two warps. All give the same
+ * solution up to FP32 rounding. */
+tv_status tv_set_coop_split(int mode);
 
 /* ------------------------------------------ learned dual warm start (net) ---- */
 /*

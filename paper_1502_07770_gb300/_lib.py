@@ -341,8 +341,10 @@ def set_batched_graph(on: bool):
     _check(load().tv_set_batched_graph(int(bool(on))))
 
 
-def set_coop_split(on: bool):
-    _check(load().tv_set_coop_split(int(bool(on))))
+def set_coop_split(mode: int):
+    """0: one warp per chain from one end; 1: two 16-lane halves from the middle (default);
+    2: two warps from the middle."""
+    _check(load().tv_set_coop_split(int(mode)))
 
 
 def set_coop_max_chains(n: int):

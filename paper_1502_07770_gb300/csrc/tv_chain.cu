@@ -57,7 +57,7 @@ void note_launch() { g_launches.fetch_add(1); }
 static std::atomic<long long> g_coop_max{kCoopMaxChainsDefault};
 long long coop_max_chains() { return g_coop_max.load(); }
 static std::atomic<int> g_coop_split{1};
-bool coop_split() { return g_coop_split.load() != 0; }
+int coop_split() { return g_coop_split.load(); }
 bool prof_on() { return g_prof_on; }
 
 void prof_mark(int kind, cudaStream_t s, bool start)
@@ -444,8 +444,8 @@ tv_status tv_set_coop_max_chains(int64_t max_chains)
 tv_status tv_set_coop_split(int on)
 {
     clear_error();
-    if (on != 0 && on != 1) {
-        set_error("tv_set_coop_split: 0 or 1");
+    if (on < 0 || on > 2) {
+        set_error("tv_set_coop_split: 0, 1 or 2");
         return TV_ERR_INVALID;
     }
     tvh::g_coop_split.store(on);

@@ -548,6 +548,219 @@ __device__ void coop_solve_chain_split(const P &p, typename P::Acc &acc, long lo
     }
 }
 
+// ------------------------------------------------------------------------------
+// The same middle-rooted split in ONE warp: lanes 0-15 run the left half, lanes
+// 16-31 the reversed right half, each half a 16-lane copy of the update above
+// (breakpoint k of a half in its lane k, at most 16). Both halves advance in the
+// same instructions, so a chain costs half the instructions of the two-warp form;
+// a message of more than 16 breakpoints sends the chain to the overflow path.
+constexpr int SEG = 16;
+
+__device__ __forceinline__ bool coop_half_step(float &lam, float &V, int &size, float &lam0,
+                                               float &lamL, float &w_prev, float ci, float wi,
+                                               int sl, int seg_shift, bool active, float &lm,
+                                               float &hp)
+{
+    const bool valid = sl < size;
+    const bool last = sl == size - 1;
+    const float v = V + lam - ci;         // m^_i at breakpoint `sl`
+    const float v0 = lam0 - ci - w_prev;  // m^_i at the first breakpoint
+    float lam_n = __shfl_down_sync(FULL, lam, 1, SEG);
+    float v_n = __shfl_down_sync(FULL, v, 1, SEG);
+    // this half's lanes with m^_i >= -w_i and with m^_i <= w_i
+    const unsigned mge = (__ballot_sync(FULL, valid && v >= -wi) >> seg_shift) & 0xffffu;
+    const unsigned mle = (__ballot_sync(FULL, valid && v <= wi) >> seg_shift) & 0xffffu;
+    const int ell = min(mge ? __ffs((int)mge) - 1 : SEG, size);  // removed on the left
+    const int kl = mle ? 31 - __clz((int)mle) : -1;
+    const int keep_last = kl > ell - 1 ? kl : ell - 1;
+    const int K = keep_last - ell + 1;
+    if (__any_sync(FULL, active && K + 2 > SEG)) return false;
+
+    float fl, fr;
+    if (last) {
+        fl = -wi - v;
+        fr = wi - v;
+        lam_n = lam + 1.f;
+    } else {
+        const float dv = v_n - v;
+        fl = seg_frac(-wi - v, dv);
+        fr = seg_frac(wi - v, dv);
+    }
+    const float dl = lam_n - lam;
+    const float candL = fmaf(fl, dl, lam);
+    const float candR = fmaf(fr, dl, lam);
+    const float gl = __shfl_sync(FULL, candL, (ell - 1) & (SEG - 1), SEG);
+    const float gr = __shfl_sync(FULL, candR, keep_last & (SEG - 1), SEG);
+    lm = (ell == 0) ? lam0 - (v0 + wi) : gl;
+    hp = (keep_last < 0) ? lam0 + (wi - v0) : gr;
+    const int src = (sl - 1 + ell) & (SEG - 1);
+    const float nl = __shfl_sync(FULL, lam, src, SEG);
+    const float nv = __shfl_sync(FULL, v, src, SEG);
+    if (active) {
+        lam = (sl == 0) ? lm : ((sl == K + 1) ? hp : nl);
+        V = (sl == 0) ? -wi : ((sl == K + 1) ? wi : nv);
+        size = K + 2;
+        lam0 = lm;
+        lamL = hp;
+        w_prev = wi;
+    }
+    return true;
+}
+
+// Composition over a 16-lane segment: segment lane j gets the clips of lanes j..15
+// applied to x_next (lanes that are not in the block are the identity).
+__device__ __forceinline__ float clip_suffix16(float lo, float hi, float x_next, int sl, bool inb)
+{
+    if (!inb) {
+        lo = -INFINITY;
+        hi = INFINITY;
+    }
+#pragma unroll
+    for (int o = 1; o < SEG; o <<= 1) {
+        const float lo2 = __shfl_down_sync(FULL, lo, o, SEG);
+        const float hi2 = __shfl_down_sync(FULL, hi, o, SEG);
+        if (sl + o < SEG) {
+            const float nlo = clip_to(lo2, lo, hi);
+            const float nhi = clip_to(hi2, lo, hi);
+            lo = nlo;
+            hi = nhi;
+        }
+    }
+    return clip_to(x_next, lo, hi);
+}
+
+template <class P>
+__device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long long k,
+                                        long long start, int n, int lane, PairXchg &xc,
+                                        float2 *sm_rec, float *sm_crec, int smem_nodes,
+                                        float2 *rec_g, float *crec_g, float2 *spill,
+                                        WsHeader *hdr)
+{
+    const int max_len = p.max_len();
+    const bool in_smem = n <= smem_nodes;
+    float2 *recp = in_smem ? sm_rec : rec_g + k * (long long)max_len;
+    float *crecp = nullptr;
+    if constexpr (P::CREC) crecp = in_smem ? sm_crec : crec_g + k * (long long)max_len;
+    const int s = n / 2;
+    const int half = lane >> 4, sl = lane & (SEG - 1), seg_shift = half * SEG;
+    // the left half walks nodes 0..s, the right half n-1..s (node s for its weight)
+    const int cntw = half == 0 ? s + 1 : n - s;
+    const int cnt_all = (s + 1 > n - s) ? s + 1 : n - s;
+    auto node = [&](int q) { return half == 0 ? q : n - 1 - q; };
+    auto fetch_at = [&](int q, typename P::Raw &r) {
+        p.fetch(k, start, n, q < cntw ? node(q) : n, r);
+    };
+
+    float lam = 0.f, V = 0.f, lam0 = 0.f, lamL = 0.f, w_prev = 0.f, c_s = 0.f;
+    int size = 0;
+    bool ok = true;
+    typename P::Raw raw, raw_next{};
+    fetch_at(sl, raw);
+    const int nblocks = (cnt_all + SEG - 1) / SEG;
+    for (int blk = 0; blk < nblocks; ++blk) {
+        const int base = blk * SEG;
+        if (blk + 1 < nblocks) fetch_at(base + SEG + sl, raw_next);
+        const int q = base + sl;
+        const int i_l = q < cntw ? node(q) : n;
+        float cv, wv;
+        p.unary(k, start, n, i_l, raw, cv, wv, acc);
+        if constexpr (P::CREC) {
+            if (q < cntw && (half == 0 || i_l != s)) crecp[i_l] = cv;  // node s: left half
+        }
+        // the right half steps node i with the weight of edge (i-1, i): that of the
+        // next position; the segment's last lane takes it from the next block
+        float wr = __shfl_down_sync(FULL, wv, 1, SEG);
+        {
+            float c2, w2;
+            p.unary(k, start, n, base + SEG < cntw ? node(base + SEG) : n, raw_next, c2, w2, acc);
+            const float w_nb = __shfl_sync(FULL, w2, 0, SEG);
+            if (sl == SEG - 1) wr = w_nb;
+        }
+        const float wsel = half == 0 ? wv : wr;
+        const int cnt = min(SEG, cnt_all - base);
+        if (ok) {
+            for (int j = 0; j < cnt; ++j) {
+                const int qq = base + j;
+                const float ci = __shfl_sync(FULL, cv, j, SEG);
+                const float wi = __shfl_sync(FULL, wsel, j, SEG);
+                const bool stepping = qq < cntw - 1;
+                if (half == 0 && qq == cntw - 1) c_s = ci;
+                float lmv = 0.f, hpv = 0.f;
+                if (qq == 0) {  // n >= 64: both halves step here
+                    lmv = ci - wi;
+                    hpv = ci + wi;
+                    lam = (sl == 0) ? lmv : hpv;
+                    V = (sl == 0) ? -wi : wi;
+                    size = 2;
+                    lam0 = lmv;
+                    lamL = hpv;
+                    w_prev = wi;
+                } else if (!coop_half_step(lam, V, size, lam0, lamL, w_prev, ci, wi, sl, seg_shift,
+                                           stepping, lmv, hpv)) {
+                    ok = false;
+                    break;
+                }
+                if (stepping && sl == 0) recp[node(qq)] = make_float2(lmv, hpv);
+            }
+        }
+        raw = raw_next;
+    }
+    __syncwarp();
+    if (!ok) {
+        if (lane == 0) {
+            atomicAdd(&hdr->overflowed, 1ull);
+            solve_chain_global_lane0(p, k, start, n, spill, rec_g + k * (long long)max_len, crecp);
+        }
+        __syncwarp();
+        return;
+    }
+    PairMsg &mine = xc.m[half];
+    mine.lam[sl] = lam;
+    mine.val[sl] = V;
+    if (sl == 0) mine.size = size;
+    __syncwarp();
+    const float cs_all = __shfl_sync(FULL, c_s, 0);
+    const float xs = pair_root(xc, cs_all, lane);
+    if (lane == 0) {
+        float cc = 0.f;
+        if constexpr (P::CREC) cc = cs_all;
+        p.emit(k, start, s, xs, cc);
+    }
+    // backward, 16 nodes per half and step, outward from s: the left half takes
+    // nodes top-down (lane j: node blk*16 + j), the right half bottom-up with its
+    // lanes reversed (lane j: node s+1 + t*16 + 15 - j), so that both compose their
+    // clips as a suffix over the segment
+    const int nbl_l = (s + SEG - 1) / SEG;
+    const int nbl_r = (n - 1 - s + SEG - 1) / SEG;
+    const int nbb = nbl_l > nbl_r ? nbl_l : nbl_r;
+    float x_next = xs;
+    for (int t = 0; t < nbb; ++t) {
+        int i;
+        bool inb;
+        if (half == 0) {
+            const int blk = nbl_l - 1 - t;
+            i = blk * SEG + sl;
+            inb = blk >= 0 && i < s;
+        } else {
+            i = s + 1 + t * SEG + (SEG - 1 - sl);
+            inb = t < nbl_r && i < n;
+        }
+        float lo = -INFINITY, hi = INFINITY;
+        if (inb) {
+            const float2 r = recp[i];
+            lo = r.x;
+            hi = r.y;
+        }
+        const float xv = clip_suffix16(lo, hi, x_next, sl, inb);
+        if (inb) {
+            float cc = 0.f;
+            if constexpr (P::CREC) cc = crecp[i];
+            p.emit(k, start, i, xv, cc);
+        }
+        x_next = __shfl_sync(FULL, xv, 0, SEG);
+    }
+}
+
 // Two warps per chain: warp pair q of a block solves chain blockIdx.x * pairs + q.
 // Shared memory: one PairXchg per pair, then the pairs' records (and c records).
 template <class P>
@@ -593,7 +806,10 @@ __global__ void __launch_bounds__(256) coop_pair_kernel(P p_in, float2 *rec_g, f
     p.finish(acc, lane);
 }
 
-template <class P>
+// One warp per chain; with HALVES, chains of kSplitMinLen nodes or more are rooted
+// at their middle node and solved as two 16-lane halves. Shared memory: (HALVES)
+// one PairXchg per warp, then the warps' records (and c records).
+template <class P, bool HALVES>
 __global__ void __launch_bounds__(256) coop_chain_kernel(P p_in, float2 *rec_g, float *crec_g,
                                                          float2 *spill, WsHeader *hdr,
                                                          int smem_nodes)
@@ -604,8 +820,10 @@ __global__ void __launch_bounds__(256) coop_chain_kernel(P p_in, float2 *rec_g, 
     const int lane = threadIdx.x & (WARP - 1);
     const int warp = threadIdx.x / WARP;
     const int wpb = blockDim.x / WARP;
-    float2 *sm_rec = reinterpret_cast<float2 *>(smem_raw) + (size_t)warp * smem_nodes;
-    float *sm_crec = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem_raw) +
+    PairXchg *xch = reinterpret_cast<PairXchg *>(smem_raw);
+    unsigned char *rec_base = smem_raw + (HALVES ? wpb * sizeof(PairXchg) : 0);
+    float2 *sm_rec = reinterpret_cast<float2 *>(rec_base) + (size_t)warp * smem_nodes;
+    float *sm_crec = reinterpret_cast<float *>(reinterpret_cast<float2 *>(rec_base) +
                                                (size_t)wpb * smem_nodes) +
                      (size_t)warp * smem_nodes;
     const long long k = (long long)blockIdx.x * wpb + warp;  // this warp's chain
@@ -623,8 +841,12 @@ __global__ void __launch_bounds__(256) coop_chain_kernel(P p_in, float2 *rec_g, 
         p.finish_empty();
         return;
     }
-    coop_solve_chain(p, acc, k, start, n, lane, sm_rec, sm_crec, smem_nodes, rec_g, crec_g,
-                     spill + p.spill_off(k, start), hdr);
+    if (HALVES && n >= kSplitMinLen)
+        coop_solve_chain_halves(p, acc, k, start, n, lane, xch[warp], sm_rec, sm_crec, smem_nodes,
+                                rec_g, crec_g, spill + p.spill_off(k, start), hdr);
+    else
+        coop_solve_chain(p, acc, k, start, n, lane, sm_rec, sm_crec, smem_nodes, rec_g, crec_g,
+                         spill + p.spill_off(k, start), hdr);
     p.finish(acc, lane);
 }
 

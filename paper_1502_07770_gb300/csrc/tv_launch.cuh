@@ -40,24 +40,27 @@ tv_status launch_chains(const P &p, long long nchains, float2 *rec, float *crec,
 // of a chain stay in shared memory when max_len <= kCoopSmemNodes.
 constexpr int kCoopSmemNodes = 4096;
 
-bool coop_split();  // two warps per chain (see tv_set_coop_split)
+int coop_split();  // 0 one warp per chain, 1 two halves in one warp, 2 two warps
 
 template <class P>
 tv_status launch_coop(const P &p, long long nchains, int max_len, float2 *rec, float *crec,
                       float2 *spill, tvk::WsHeader *hdr, cudaStream_t s, int kind, int wpb = 4)
 {
     if (nchains <= 0) return TV_OK;
-    // two warps per chain (coop_pair_kernel) for chains long enough to split
-    const bool split = coop_split() && max_len >= tvk::kSplitMinLen && wpb % 2 == 0;
-    const int cpb = split ? wpb / 2 : wpb;  // chains per block
+    // chains long enough to split: two 16-lane halves in one warp (mode 1) or two
+    // warps (mode 2, coop_pair_kernel)
+    const int mode = max_len >= tvk::kSplitMinLen ? coop_split() : 0;
+    const bool pair = mode == 2 && wpb % 2 == 0;
+    const int cpb = pair ? wpb / 2 : wpb;  // chains per block
     const long long blocks = (nchains + cpb - 1) / cpb;
     // records in shared memory when a block's share fits in ~200 KB, else in the workspace
-    const size_t xchg = split ? cpb * sizeof(tvk::PairXchg) : 0;
+    const size_t xchg = mode != 0 ? cpb * sizeof(tvk::PairXchg) : 0;
     const bool fits = max_len <= kCoopSmemNodes &&
                       xchg + cpb * tvk::coop_smem_per_warp<P>(max_len) <= (size_t)200 * 1024;
     const int smem_nodes = fits ? max_len : 0;
     const size_t smem = xchg + cpb * tvk::coop_smem_per_warp<P>(smem_nodes);
-    auto kern = split ? tvk::coop_pair_kernel<P> : tvk::coop_chain_kernel<P>;
+    auto kern = pair ? tvk::coop_pair_kernel<P>
+                     : (mode == 1 ? tvk::coop_chain_kernel<P, true> : tvk::coop_chain_kernel<P, false>);
     tv_status st = check_cuda(
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
         "cudaFuncSetAttribute");

@@ -143,11 +143,12 @@ def test_bench_size_sampled():
     assert torch.equal(xv[0], xv[-1])
 
 
-@pytest.mark.parametrize("split", [0, 1])
-def test_two_warps_per_chain(split):
-    """Chains rooted at their middle node, two warps each (the default for batches solved
-    one chain per warp), and one warp each: both against the oracle, on lengths around
-    the split threshold (64), odd and even, and longer than the shared-memory records."""
+@pytest.mark.parametrize("split", [0, 1, 2])
+def test_middle_rooted_chains(split):
+    """Chains solved by one warp from one end (0), rooted at their middle node with the
+    two halves in one warp (1, the default for batches solved one chain per warp) or in
+    two warps (2): against the oracle, on lengths around the split threshold (64), odd
+    and even, and longer than the shared-memory records."""
     lengths = [63, 64, 65, 66, 127, 128, 129, 2, 1, 300, 4097, 5000, 64, 1000]
     y, off = synth.ragged_chain_batch(lengths, seed0=77)
     w = np.random.default_rng(8).uniform(0, 0.3, size=y.shape).astype(np.float32)
