@@ -94,77 +94,96 @@ __host__ __device__ constexpr size_t coop_smem_per_warp(int nodes)
     return (size_t)nodes * (sizeof(float2) + (P::CREC ? sizeof(float) : 0));
 }
 
-// The warp-cooperative message update of one node (abar = i + 1 is implicit).
-// Lane k holds breakpoint lambda_k of the message m_{i-1,i} and its value V_k
-// there (valid for k < size); lam0/lamL are the first and last breakpoint, whose
-// values are -w_{i-1} and +w_{i-1}. Storing values instead of the implicit slopes
-// of Sec. 4.1 makes transformation (a), m^_i = m_{i-1,i} + z - c_i, the lane-local
-// update v_k = V_k + lambda_k - c_i (no scan), and each new breakpoint is where
-// the linear piece of m^_i between two neighbouring breakpoints crosses -w_i or
-// +w_i. The message is the same piecewise-linear function; the values are also
-// more precise in FP32, since they are never rebuilt through large slopes.
-// Returns false (state untouched) if the new message would exceed 32 breakpoints.
+// The warp-cooperative message update of one node. Lane k of a group of G lanes
+// (the warp, G = 32, or a 16-lane half) holds breakpoint lambda_k of the message
+// m_{i-1,i} (a derivative: continuous, increasing, piecewise linear, -w_{i-1} left
+// of the first breakpoint and +w_{i-1} right of the last), the message's value V_k
+// there and its slope T_k on the piece to the right (an integer, the number of
+// nodes fused on that piece; 0 right of the last breakpoint). Transformation (a),
+// m^_i = m_{i-1,i} + z - c_i, is the lane-local v_k = V_k + lambda_k - c_i with
+// slope S_k = T_k + 1; the left scan removes the prefix with v < -w_i, the right
+// scan the suffix with v > w_i among the rest, and lambda^-, lambda^+ are where the
+// piece right of the last removed (resp. last kept) breakpoint crosses -w_i, +w_i:
+// lambda_k + (+-w_i - v_k) / S_k, clamped to the piece. The quotient's reciprocal
+// depends only on the stored slope, so it is off the step's critical path, and the
+// exact integer slopes keep the crossings precise in FP32.
+// A new message of more than G breakpoints sets `ovf` (sticky); the state is then
+// meaningless and the caller re-solves the chain on the overflow path.
 __device__ __forceinline__ float seg_frac(float num, float den)
 {
     // fraction along a segment, clamped to [0, 1] (0 for a zero-length segment)
     return fminf(fmaxf(__fdividef(num, den), 0.f), 1.f);
 }
 
-__device__ __forceinline__ bool coop_step(float &lam, float &V, int &size, float &lam0,
-                                          float &lamL, float &w_prev, float ci, float wi,
-                                          int lane, float &lm, float &hp)
+template <int G>
+__device__ __forceinline__ void coop_update(float &lam, float &V, float &T, int &size,
+                                            float &lam0, float &w_prev, float ci, float wi,
+                                            int sl, int seg_shift, bool active, bool &ovf,
+                                            float &lm, float &hp)
 {
-    const bool valid = lane < size;
-    const bool last = lane == size - 1;
-    const float v = V + lam - ci;           // m^_i at breakpoint `lane`
-    const float v0 = lam0 - ci - w_prev;    // m^_i at the first breakpoint
-    float lam_n = __shfl_down_sync(FULL, lam, 1);
-    float v_n = __shfl_down_sync(FULL, v, 1);
-    // left scan: breakpoints with m^_i < -w_i (a prefix); right scan: those with
-    // m^_i > w_i among the rest (a suffix). The breakpoints removed on the left have
-    // m^_i < -w_i <= w_i, so the last one not above w_i is never left of ell - 1.
-    const int ell = min((int)__reduce_min_sync(FULL, (unsigned)((valid && v >= -wi) ? lane : WARP)),
-                        size);                                          // removed on the left
-    const int kl = __reduce_max_sync(FULL, (valid && v <= wi) ? lane : -1);
+    const bool valid = sl < size;
+    const bool last = sl == size - 1;
+    const float S = T + 1.f;              // slope of m^_i right of this breakpoint
+    const float v = V + lam - ci;         // m^_i at this breakpoint
+    const float v0 = lam0 - ci - w_prev;  // m^_i at the first breakpoint
+    const float lam_n = __shfl_down_sync(FULL, lam, 1, G);
+    float candL = fmaxf(lam + __fdividef(-wi - v, S), lam);
+    float candR = fmaxf(lam + __fdividef(wi - v, S), lam);
+    if (!last) {
+        candL = fminf(candL, lam_n);
+        candR = fminf(candR, lam_n);
+    }
+    int ell, kl;
+    if constexpr (G == WARP) {
+        ell = min((int)__reduce_min_sync(FULL, (unsigned)((valid && v >= -wi) ? sl : WARP)), size);
+        kl = __reduce_max_sync(FULL, (valid && v <= wi) ? sl : -1);
+    } else {
+        const unsigned mge = (__ballot_sync(FULL, valid && v >= -wi) >> seg_shift) & ((1u << G) - 1u);
+        const unsigned mle = (__ballot_sync(FULL, valid && v <= wi) >> seg_shift) & ((1u << G) - 1u);
+        ell = min(mge ? __ffs((int)mge) - 1 : G, size);
+        kl = mle ? 31 - __clz((int)mle) : -1;
+    }
     const int keep_last = kl > ell - 1 ? kl : ell - 1;  // last kept breakpoint (-1: none)
     const int K = keep_last - ell + 1;
-    if (K + 2 > WARP) return false;
-
-    // Crossings of -w_i and +w_i on the piece right of this breakpoint: between it
-    // and the next one (clamped to the segment), or, for the last breakpoint, on the
-    // right end piece of slope a_i = 1.
-    float fl, fr;
-    if (last) {
-        fl = -wi - v;
-        fr = wi - v;
-        lam_n = lam + 1.f;
-    } else {
-        const float dv = v_n - v;
-        fl = seg_frac(-wi - v, dv);
-        fr = seg_frac(wi - v, dv);
-    }
-    const float dl = lam_n - lam;
-    const float candL = fmaf(fl, dl, lam);
-    const float candR = fmaf(fr, dl, lam);
-    // lambda^- lies on the piece right of the last breakpoint removed on the left,
-    // lambda^+ on the piece right of the last one kept (which may hold both); with
-    // none, on the left end piece of slope 1.
-    const float gl = __shfl_sync(FULL, candL, (ell - 1) & (WARP - 1));
-    const float gr = __shfl_sync(FULL, candR, keep_last & (WARP - 1));
+    ovf = ovf || (active && K + 2 > G);
+    // lambda^- on the piece right of the last breakpoint removed on the left,
+    // lambda^+ on the piece right of the last one kept; with none, on the left end
+    // piece (slope 1)
+    const int il = (ell - 1) & (G - 1);
+    const float gl = __shfl_sync(FULL, candL, il, G);
+    const float Sl = __shfl_sync(FULL, S, il, G);
+    const float gr = __shfl_sync(FULL, candR, keep_last & (G - 1), G);
     lm = (ell == 0) ? lam0 - (v0 + wi) : gl;
     hp = (keep_last < 0) ? lam0 + (wi - v0) : gr;
-    // new message m_{i,i+1}: lambda^- (value -w_i), kept breakpoints with their
-    // values unchanged by the clip, lambda^+ (value +w_i)
-    const int src = (lane - 1 + ell) & (WARP - 1);
-    const float nl = __shfl_sync(FULL, lam, src);
-    const float nv = __shfl_sync(FULL, v, src);
-    lam = (lane == 0) ? lm : ((lane == K + 1) ? hp : nl);
-    V = (lane == 0) ? -wi : ((lane == K + 1) ? wi : nv);
-    size = K + 2;
+    // new message m_{i,i+1}: lambda^- (value -w_i, the slope of m^_i there), the kept
+    // breakpoints with their values and slopes, lambda^+ (value +w_i, flat beyond)
+    const int src = (sl - 1 + ell) & (G - 1);
+    const float nl = __shfl_sync(FULL, lam, src, G);
+    const float nv = __shfl_sync(FULL, v, src, G);
+    const float nS = __shfl_sync(FULL, S, src, G);
+    if (active) {
+        lam = (sl == 0) ? lm : ((sl == K + 1) ? hp : nl);
+        V = (sl == 0) ? -wi : ((sl == K + 1) ? wi : nv);
+        T = (sl == 0) ? ((ell == 0) ? 1.f : Sl) : ((sl == K + 1) ? 0.f : nS);
+        size = K + 2;
+        lam0 = lm;
+        w_prev = wi;
+    }
+}
+
+// Start of a message at the first node of a walk: m_{0,1} = clip(z - c_0, -w_0, w_0).
+__device__ __forceinline__ void coop_first(float &lam, float &V, float &T, int &size, float &lam0,
+                                           float &w_prev, float ci, float wi, int sl, float &lm,
+                                           float &hp)
+{
+    lm = ci - wi;
+    hp = ci + wi;
+    lam = (sl == 0) ? lm : hp;
+    V = (sl == 0) ? -wi : wi;
+    T = (sl == 0) ? 1.f : 0.f;
+    size = 2;
     lam0 = lm;
-    lamL = hp;
     w_prev = wi;
-    return true;
 }
 
 // Policy interface (P):
@@ -194,9 +213,9 @@ __device__ void coop_solve_chain(const P &p, typename P::Acc &acc, long long k, 
     float *crecp = nullptr;
     if constexpr (P::CREC) crecp = in_smem ? sm_crec : crec_g + k * (long long)max_len;
 
-    float lam = 0.f, s = 0.f /* value at the breakpoint */, lam0 = 0.f, lamL = 0.f, w_prev = 0.f;
+    float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, w_prev = 0.f;
     int size = 0;
-    bool ok = true;
+    bool ok = true, ovf = false;
     float xlast = 0.f;
 
     typename P::Raw raw, raw_next{};
@@ -218,26 +237,19 @@ __device__ void coop_solve_chain(const P &p, typename P::Acc &acc, long long k, 
                 const float wi = (i < n - 1) ? __shfl_sync(FULL, wv, j) : 0.f;
                 float lmv, hpv;
                 if (i == 0) {
-                    lmv = ci - wi;
-                    hpv = ci + wi;
                     if (n == 1) {
                         xlast = ci;
                         break;
                     }
-                    lam = (lane == 0) ? lmv : hpv;
-                    s = (lane == 0) ? -wi : wi;  // values of m_{0,1} at its breakpoints
-                    size = 2;
-                    lam0 = lmv;
-                    lamL = hpv;
-                    w_prev = wi;
-                } else if (!coop_step(lam, s, size, lam0, lamL, w_prev, ci, wi, lane, lmv,
-                                      hpv)) {
-                    ok = false;
-                    break;
+                    coop_first(lam, V, T, size, lam0, w_prev, ci, wi, lane, lmv, hpv);
+                } else {
+                    coop_update<WARP>(lam, V, T, size, lam0, w_prev, ci, wi, lane, 0, true, ovf,
+                                      lmv, hpv);
                 }
                 if (i == n - 1) xlast = 0.5f * (lmv + hpv);
                 else if (lane == 0) recp[i] = make_float2(lmv, hpv);
             }
+            ok = !ovf;  // warp-uniform: the group is the whole warp
         }
         raw = raw_next;
     }
@@ -407,9 +419,9 @@ __device__ void coop_solve_chain_split(const P &p, typename P::Acc &acc, long lo
     if constexpr (P::CREC) crecp = in_smem ? sm_crec : crec_g + k * (long long)max_len;
     const int s = n / 2;
 
-    float lam = 0.f, V = 0.f, lam0 = 0.f, lamL = 0.f, w_prev = 0.f;
+    float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, w_prev = 0.f;
     int size = 0;
-    bool ok = true;
+    bool ok = true, ovf = false;
     float c_s = 0.f;
 
     // role 0 walks nodes 0, 1, .., s; role 1 walks n-1, n-2, .., s (node s only for
@@ -455,21 +467,14 @@ __device__ void coop_solve_chain_split(const P &p, typename P::Acc &acc, long lo
                 if (role == 1 && qq == cntw - 1) break;  // node s: handled by the left warp
                 const float wi = __shfl_sync(FULL, role == 0 ? wv : wr, j);
                 float lmv, hpv;
-                if (qq == 0) {
-                    lmv = ci - wi;
-                    hpv = ci + wi;
-                    lam = (lane == 0) ? lmv : hpv;
-                    V = (lane == 0) ? -wi : wi;
-                    size = 2;
-                    lam0 = lmv;
-                    lamL = hpv;
-                    w_prev = wi;
-                } else if (!coop_step(lam, V, size, lam0, lamL, w_prev, ci, wi, lane, lmv, hpv)) {
-                    ok = false;
-                    break;
-                }
+                if (qq == 0)
+                    coop_first(lam, V, T, size, lam0, w_prev, ci, wi, lane, lmv, hpv);
+                else
+                    coop_update<WARP>(lam, V, T, size, lam0, w_prev, ci, wi, lane, 0, true, ovf,
+                                      lmv, hpv);
                 if (lane == 0) recp[node(qq)] = make_float2(lmv, hpv);
             }
+            ok = !ovf;
         }
         raw = raw_next;
     }
@@ -556,57 +561,6 @@ __device__ void coop_solve_chain_split(const P &p, typename P::Acc &acc, long lo
 // a message of more than 16 breakpoints sends the chain to the overflow path.
 constexpr int SEG = 16;
 
-__device__ __forceinline__ bool coop_half_step(float &lam, float &V, int &size, float &lam0,
-                                               float &lamL, float &w_prev, float ci, float wi,
-                                               int sl, int seg_shift, bool active, float &lm,
-                                               float &hp)
-{
-    const bool valid = sl < size;
-    const bool last = sl == size - 1;
-    const float v = V + lam - ci;         // m^_i at breakpoint `sl`
-    const float v0 = lam0 - ci - w_prev;  // m^_i at the first breakpoint
-    float lam_n = __shfl_down_sync(FULL, lam, 1, SEG);
-    float v_n = __shfl_down_sync(FULL, v, 1, SEG);
-    // this half's lanes with m^_i >= -w_i and with m^_i <= w_i
-    const unsigned mge = (__ballot_sync(FULL, valid && v >= -wi) >> seg_shift) & 0xffffu;
-    const unsigned mle = (__ballot_sync(FULL, valid && v <= wi) >> seg_shift) & 0xffffu;
-    const int ell = min(mge ? __ffs((int)mge) - 1 : SEG, size);  // removed on the left
-    const int kl = mle ? 31 - __clz((int)mle) : -1;
-    const int keep_last = kl > ell - 1 ? kl : ell - 1;
-    const int K = keep_last - ell + 1;
-    if (__any_sync(FULL, active && K + 2 > SEG)) return false;
-
-    float fl, fr;
-    if (last) {
-        fl = -wi - v;
-        fr = wi - v;
-        lam_n = lam + 1.f;
-    } else {
-        const float dv = v_n - v;
-        fl = seg_frac(-wi - v, dv);
-        fr = seg_frac(wi - v, dv);
-    }
-    const float dl = lam_n - lam;
-    const float candL = fmaf(fl, dl, lam);
-    const float candR = fmaf(fr, dl, lam);
-    const float gl = __shfl_sync(FULL, candL, (ell - 1) & (SEG - 1), SEG);
-    const float gr = __shfl_sync(FULL, candR, keep_last & (SEG - 1), SEG);
-    lm = (ell == 0) ? lam0 - (v0 + wi) : gl;
-    hp = (keep_last < 0) ? lam0 + (wi - v0) : gr;
-    const int src = (sl - 1 + ell) & (SEG - 1);
-    const float nl = __shfl_sync(FULL, lam, src, SEG);
-    const float nv = __shfl_sync(FULL, v, src, SEG);
-    if (active) {
-        lam = (sl == 0) ? lm : ((sl == K + 1) ? hp : nl);
-        V = (sl == 0) ? -wi : ((sl == K + 1) ? wi : nv);
-        size = K + 2;
-        lam0 = lm;
-        lamL = hp;
-        w_prev = wi;
-    }
-    return true;
-}
-
 // Composition over a 16-lane segment: segment lane j gets the clips of lanes j..15
 // applied to x_next (lanes that are not in the block are the identity).
 __device__ __forceinline__ float clip_suffix16(float lo, float hi, float x_next, int sl, bool inb)
@@ -651,9 +605,9 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
         p.fetch(k, start, n, q < cntw ? node(q) : n, r);
     };
 
-    float lam = 0.f, V = 0.f, lam0 = 0.f, lamL = 0.f, w_prev = 0.f, c_s = 0.f;
+    float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, w_prev = 0.f, c_s = 0.f;
     int size = 0;
-    bool ok = true;
+    bool ok = true, ovf = false;
     typename P::Raw raw, raw_next{};
     fetch_at(sl, raw);
     const int nblocks = (cnt_all + SEG - 1) / SEG;
@@ -686,22 +640,14 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
                 const bool stepping = qq < cntw - 1;
                 if (half == 0 && qq == cntw - 1) c_s = ci;
                 float lmv = 0.f, hpv = 0.f;
-                if (qq == 0) {  // n >= 64: both halves step here
-                    lmv = ci - wi;
-                    hpv = ci + wi;
-                    lam = (sl == 0) ? lmv : hpv;
-                    V = (sl == 0) ? -wi : wi;
-                    size = 2;
-                    lam0 = lmv;
-                    lamL = hpv;
-                    w_prev = wi;
-                } else if (!coop_half_step(lam, V, size, lam0, lamL, w_prev, ci, wi, sl, seg_shift,
-                                           stepping, lmv, hpv)) {
-                    ok = false;
-                    break;
-                }
+                if (qq == 0)  // n >= 64: both halves step here
+                    coop_first(lam, V, T, size, lam0, w_prev, ci, wi, sl, lmv, hpv);
+                else
+                    coop_update<SEG>(lam, V, T, size, lam0, w_prev, ci, wi, sl, seg_shift,
+                                     stepping, ovf, lmv, hpv);
                 if (stepping && sl == 0) recp[node(qq)] = make_float2(lmv, hpv);
             }
+            ok = !__any_sync(FULL, ovf);
         }
         raw = raw_next;
     }
