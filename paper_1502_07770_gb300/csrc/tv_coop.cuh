@@ -605,6 +605,8 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
         p.fetch(k, start, n, q < cntw ? node(q) : n, r);
     };
 
+    // Message state of this half; the empty message (size 0, lam0 = w_prev = 0) makes
+    // the first update produce m_{0,1} = clip(z - c_0, -w_0, w_0) exactly.
     float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, w_prev = 0.f, c_s = 0.f;
     int size = 0;
     bool ok = true, ovf = false;
@@ -622,29 +624,28 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
             if (q < cntw && (half == 0 || i_l != s)) crecp[i_l] = cv;  // node s: left half
         }
         // the right half steps node i with the weight of edge (i-1, i): that of the
-        // next position; the segment's last lane takes it from the next block
-        float wr = __shfl_down_sync(FULL, wv, 1, SEG);
-        {
-            float c2, w2;
-            p.unary(k, start, n, base + SEG < cntw ? node(base + SEG) : n, raw_next, c2, w2, acc);
-            const float w_nb = __shfl_sync(FULL, w2, 0, SEG);
-            if (sl == SEG - 1) wr = w_nb;
-        }
+        // next position (the next lane; for the segment's last lane, the first
+        // position of the next block, read when the last step needs it)
+        const float wr = __shfl_down_sync(FULL, wv, 1, SEG);
         const float wsel = half == 0 ? wv : wr;
-        const int cnt = min(SEG, cnt_all - base);
         if (ok) {
-            for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+            for (int j = 0; j < SEG; ++j) {
                 const int qq = base + j;
                 const float ci = __shfl_sync(FULL, cv, j, SEG);
-                const float wi = __shfl_sync(FULL, wsel, j, SEG);
+                float wi = __shfl_sync(FULL, wsel, j, SEG);
+                if (j == SEG - 1) {
+                    float c2, w2;
+                    p.unary(k, start, n, base + SEG < cntw ? node(base + SEG) : n, raw_next, c2,
+                            w2, acc);
+                    const float w_nb = __shfl_sync(FULL, w2, 0, SEG);
+                    if (half == 1) wi = w_nb;
+                }
                 const bool stepping = qq < cntw - 1;
                 if (half == 0 && qq == cntw - 1) c_s = ci;
-                float lmv = 0.f, hpv = 0.f;
-                if (qq == 0)  // n >= 64: both halves step here
-                    coop_first(lam, V, T, size, lam0, w_prev, ci, wi, sl, lmv, hpv);
-                else
-                    coop_update<SEG>(lam, V, T, size, lam0, w_prev, ci, wi, sl, seg_shift,
-                                     stepping, ovf, lmv, hpv);
+                float lmv, hpv;
+                coop_update<SEG>(lam, V, T, size, lam0, w_prev, ci, wi, sl, seg_shift, stepping,
+                                 ovf, lmv, hpv);
                 if (stepping && sl == 0) recp[node(qq)] = make_float2(lmv, hpv);
             }
             ok = !__any_sync(FULL, ovf);
