@@ -545,7 +545,8 @@ __global__ void __launch_bounds__(kGapThreads)
                     long long W, const float *buf0, const float *buf1, Tv2dState *st,
                     const Tv2dParams *prm, double *partials, double *gaps, unsigned *ticket)
 {
-    __shared__ double red[kGapThreads / WARP];
+    __shared__ double red[kGapThreads];
+    __shared__ bool last;
     if (st->done) return;
     const int kp1 = st->k;  // x^{k+1} is the newest iterate
     if (kp1 < 1) return;
@@ -554,45 +555,66 @@ __global__ void __launch_bounds__(kGapThreads)
     const float *x0 = (kp1 & 1) ? buf0 : buf1;  // x^k
     const float inv_tau = (float)(1.0 / prm[k].tau);
     const long long N = H * W;
+    // grid-stride walk over the pixels; row and column advance incrementally
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long dr = stride / W, dc = stride - dr * W;
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long r = q / W, c = q - r * W;
     double acc = 0.0;
     float part = 0.f;
     int cnt = 0;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
-         q += (long long)gridDim.x * blockDim.x) {
-        const long long r = q / W, c = q - r * W;
+    for (; q < N; q += stride) {
         const float xv = x1[q], fv = f[q];
         const float z = xv + (xv - x0[q]) * inv_tau;
         float t = 0.5f * (xv - fv) * (xv - fv) + 0.5f * (z - fv) * (z + fv);
         if (c + 1 < W) t += (wh ? wh[r * (W - 1) + c] : lam) * fabsf(x1[q + 1] - xv);
         if (r + 1 < H) t += (wv ? wv[q] : lam) * fabsf(x1[q + W] - xv);
         part += t;
-        if (++cnt == 32) {
+        if (++cnt == 32) {  // FP32 over at most 32 pixels, FP64 beyond
             acc += (double)part;
             part = 0.f;
             cnt = 0;
         }
+        c += dc;
+        r += dr;
+        if (c >= W) {
+            c -= W;
+            ++r;
+        }
     }
     acc += (double)part;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & (WARP - 1)) == 0) red[threadIdx.x / WARP] = acc;
+    // block sum in a fixed order
+    red[threadIdx.x] = acc;
     __syncthreads();
+    for (int h = kGapThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        double b = 0.0;
-        for (int w = 0; w < kGapThreads / WARP; ++w) b += red[w];
-        partials[blockIdx.x] = b;
+        partials[blockIdx.x] = red[0];
         __threadfence();
-        if (atomicAdd(ticket, 1u) == gridDim.x - 1) {
-            __threadfence();
-            double G = 0.0;
-            for (unsigned bq = 0; bq < gridDim.x; ++bq) G += partials[bq];
-            const double g = G * st->inv_N;
-            st->gap = g;
-            st->gap_k = k;
-            gaps[k] = g;
-            if (st->tol > 0.0 && g <= st->tol) st->done = 1;
-            *ticket = 0;
-        }
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last block sums the block partials in a fixed order
+    __threadfence();
+    double b = 0.0;
+    for (unsigned bq = threadIdx.x; bq < gridDim.x; bq += blockDim.x)
+        b += __ldcg(partials + bq);
+    red[threadIdx.x] = b;
+    __syncthreads();
+    for (int h = kGapThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double g = red[0] * st->inv_N;
+        st->gap = g;
+        st->gap_k = k;
+        gaps[k] = g;
+        if (st->tol > 0.0 && g <= st->tol) st->done = 1;
+        *ticket = 0;
     }
 }
 

@@ -478,8 +478,12 @@ __global__ void __launch_bounds__(kBGapThreads)
         const long long W = im->W, H = im->H;
         float part = 0.f;
         int cnt = 0;
-        for (long long q = t.first + threadIdx.x; q < t.first + t.count; q += blockDim.x) {
-            const long long r = q / W, c = q - r * W;
+        // row and column advance incrementally along the block-stride walk
+        const long long stride = blockDim.x;
+        const long long dr = stride / W, dc = stride - dr * W;
+        long long q = t.first + threadIdx.x;
+        long long r = q / W, c = q - r * W;
+        for (; q < t.first + t.count; q += stride) {
             const float xv = x1[q], fv = im->f[q];
             const float z = xv + (xv - x0[q]) * inv_tau;
             float v = 0.5f * (xv - fv) * (xv - fv) + 0.5f * (z - fv) * (z + fv);
@@ -490,6 +494,12 @@ __global__ void __launch_bounds__(kBGapThreads)
                 acc += (double)part;
                 part = 0.f;
                 cnt = 0;
+            }
+            c += dc;
+            r += dr;
+            if (c >= W) {
+                c -= W;
+                ++r;
             }
         }
         acc += (double)part;
@@ -509,7 +519,7 @@ __global__ void __launch_bounds__(kBGapThreads)
                 // last block of this image: reduce its tiles in order
                 __threadfence();
                 double G = 0.0;
-                for (int q = s.tile0; q < s.tile0 + s.ntiles; ++q) G += partials[q];
+                for (int q = s.tile0; q < s.tile0 + s.ntiles; ++q) G += __ldcg(partials + q);
                 s.ticket = 0;
                 const double g = G * im->inv_N;
                 s.gap = g;

@@ -138,10 +138,17 @@ __device__ __forceinline__ void coop_update(float &lam, float &V, float &T, int 
         ell = min((int)__reduce_min_sync(FULL, (unsigned)((valid && v >= -wi) ? sl : WARP)), size);
         kl = __reduce_max_sync(FULL, (valid && v <= wi) ? sl : -1);
     } else {
-        const unsigned mge = (__ballot_sync(FULL, valid && v >= -wi) >> seg_shift) & ((1u << G) - 1u);
-        const unsigned mle = (__ballot_sync(FULL, valid && v <= wi) >> seg_shift) & ((1u << G) - 1u);
-        ell = min(mge ? __ffs((int)mge) - 1 : G, size);
-        kl = mle ? 31 - __clz((int)mle) : -1;
+        // one warp reduction per half and side: the other half contributes the
+        // neutral element, each lane keeps its own half's result
+        const bool lo_half = seg_shift == 0;
+        const unsigned ge = (valid && v >= -wi) ? (unsigned)sl : (unsigned)G;
+        const int le = (valid && v <= wi) ? sl : -1;
+        const unsigned ell0 = __reduce_min_sync(FULL, lo_half ? ge : (unsigned)G);
+        const unsigned ell1 = __reduce_min_sync(FULL, lo_half ? (unsigned)G : ge);
+        const int kl0 = __reduce_max_sync(FULL, lo_half ? le : -1);
+        const int kl1 = __reduce_max_sync(FULL, lo_half ? -1 : le);
+        ell = min((int)(lo_half ? ell0 : ell1), size);
+        kl = lo_half ? kl0 : kl1;
     }
     const int keep_last = kl > ell - 1 ? kl : ell - 1;  // last kept breakpoint (-1: none)
     const int K = keep_last - ell + 1;
