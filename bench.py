@@ -325,6 +325,39 @@ def main():
     chain_kernel_ms = kms / max(kn, 1)
     chain_achieved = 8.0 * nodes / (chain_kernel_ms * 1e-3) / 1e9
 
+    # ---------------- chain-prox sweep: shapes and per-edge weights ----------------
+    sweep = []
+    for SB, SN in ((65536, 1024), (262144, 256), (16384, 4096)):
+        sbase = synth.chain_batch(256, SN, seed0=2000)
+        ys = torch.from_numpy(np.tile(sbase, (SB // 256, 1))).to(dev)
+        xs = torch.empty_like(ys)
+        wsw = _lib.workspace(_lib.load().tv_chain_workspace_size(SB, SN), dev, "benchsweep")
+        for weighted in (False, True):
+            wt = None
+            if weighted:
+                wrow = np.random.default_rng(3).uniform(0.05, 0.3, size=(256, SN)).astype(np.float32)
+                wt = torch.from_numpy(np.tile(wrow, (SB // 256, 1))).to(dev)
+            for _ in range(2):
+                _lib.chain_prox(ys, wt, lam=CHAIN_LAM, out=xs, ws=wsw)
+            tms = []
+            for _ in range(5):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                _lib.chain_prox(ys, wt, lam=CHAIN_LAM, out=xs, ws=wsw)
+                b.record(stream)
+                b.synchronize()
+                tms.append(a.elapsed_time(b))
+            t = float(np.median(tms))
+            bpn = 12.0 if weighted else 8.0
+            gbs = bpn * SB * SN / (t * 1e-3) / 1e9
+            sweep.append({"chains": SB, "nodes": SN, "weights": "per-edge" if weighted else "uniform",
+                          "ms": t, "Gnode_per_s": SB * SN / (t * 1e-3) / 1e9,
+                          "bytes_per_node": bpn, "GB_per_s": gbs, "frac": gbs / peaks()[0]})
+            del wt
+        del ys, xs
+
     # ---------------- differentiable prox: forward + backward ----------------
     DB, DN = 4096, 1024
     yd = torch.from_numpy(synth.chain_batch(DB, DN, seed0=1000)).to(dev)
@@ -469,6 +502,7 @@ def main():
                                     "unit": "GB/s", "frac": chain_achieved / hbm,
                                     "traffic": recorded_traffic("chain"),
                                     "bytes_per_node": 8}},
+        "chain_prox_sweep": sweep,
         "diff_prox": {"value": DB * DN / (dms * 1e-3) / 1e9, "unit": "Gnode/s",
                       "workload": f"{DB} chains x {DN}, lambda 0.15, forward + backward "
                                   "(loss sum c_i x_i, c ~ N(0,1)), L2 flushed",

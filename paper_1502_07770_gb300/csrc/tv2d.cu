@@ -819,13 +819,13 @@ tv_status tv2d_denoise(const float *d_img, int64_t H, int64_t W, const float *d_
     if (st != TV_OK) return st;
 
     // Each iteration: column (dual) phase, row (primal) phase, gap. Iterations are
-    // launched in small batches; the device stop flag turns the rest of a batch into
-    // immediate returns, and the host checks it once per batch.
-    const int batch = 2;
+    // launched in small batches (4, then 2 at a time); the device stop flag turns the
+    // rest of a batch into immediate returns, and the host checks it once per batch.
     Tv2dState hs;
     int launched = 0;
     bool done = false;
     while (launched < max_iters && !done) {
+        const int batch = launched == 0 ? 4 : 2;
         const int u = (max_iters - launched) < batch ? (max_iters - launched) : batch;
         for (int t = 0; t < u; ++t) {
             if ((st = launch_col_any(d_wv, lambda, H, W, d_x, ws, s)) != TV_OK) return st;
