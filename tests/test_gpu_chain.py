@@ -166,3 +166,61 @@ def test_middle_rooted_chains(split):
         assert np.abs(xc - xr).max() <= TOL
     finally:
         _lib.set_coop_split(1)
+
+
+@pytest.fixture
+def thread_path():
+    """Every batch on the one-thread-per-chain kernel."""
+    _lib.set_coop_max_chains(1)
+    yield
+    _lib.set_coop_max_chains(0)
+
+
+def test_thread_kernel_rows_columns_weights(thread_path):
+    y = synth.chain_batch(512, 256, seed0=0)
+    xr = oracle.chain_solve_batch(y.ravel(), np.arange(513) * 256, lam=0.2).reshape(y.shape)
+    assert np.abs(_rows(y, lam=0.2) - xr).max() <= TOL
+    x = _lib.chain_prox_columns(_gpu(np.ascontiguousarray(y.T)), lam=0.2).cpu().numpy()
+    assert np.abs(x.T - xr).max() <= TOL
+    rng = np.random.default_rng(3)
+    yw = synth.chain_batch(96, 203, seed0=40)
+    w = rng.uniform(0.0, 0.4, size=yw.shape).astype(np.float32)
+    w[:, ::17] = 0.0
+    xw = oracle.chain_solve_batch(yw.ravel(), np.arange(97) * 203, w=w.ravel()).reshape(yw.shape)
+    assert np.abs(_rows(yw, w=w) - xw).max() <= TOL
+    xc = _lib.chain_prox_columns(_gpu(yw.T.copy()), _gpu(w.T.copy())).cpu().numpy().T
+    assert np.abs(xc - xw).max() <= TOL
+
+
+def test_thread_kernel_ragged_long_and_overflow(thread_path):
+    lengths = [0, 1, 2, 3, 15, 16, 17, 31, 32, 33, 1000, 0, 5, 257, 1, 64, 4097, 2048] * 3
+    y, off = synth.ragged_chain_batch(lengths, seed0=12)
+    w = np.random.default_rng(5).uniform(0, 0.3, size=y.shape).astype(np.float32)
+    for weights in (None, w):
+        x = _lib.chain_prox(_gpu(y), None if weights is None else _gpu(weights), lam=0.15,
+                            offsets=_gpu(off), max_len=max(lengths)).cpu().numpy()
+        assert np.abs(x - oracle.chain_solve_batch(y, off, w=weights, lam=0.15)).max() <= TOL
+    # a steep ramp keeps ~n/2 breakpoints: more than the ring holds (overflow path)
+    n = 512
+    yy = synth.chain_batch(64, n, seed0=5)
+    yy[::3] = (-np.arange(n) / n).astype(np.float32)
+    ww = np.full(yy.shape, 0.05, dtype=np.float32)
+    ww[::3] = n / 16.0
+    ws = _lib.workspace(_lib.load().tv_chain_workspace_size(64, n), DEV, "overflow-thread")
+    x = _lib.chain_prox(_gpu(yy), _gpu(ww), ws=ws).cpu().numpy()
+    assert _lib.workspace_status(ws)[1] >= 20
+    xr = oracle.chain_solve_batch(yy.ravel(), np.arange(65) * n, w=ww.ravel()).reshape(yy.shape)
+    assert np.abs(x - xr).max() <= TOL
+
+
+def test_thread_kernel_closed_forms(thread_path):
+    y = synth.chain_batch(64, 300, seed0=9)
+    np.testing.assert_allclose(_rows(y, lam=0.0), y, atol=1e-6)
+    yy = synth.chain_batch(64, 64, seed0=9).astype(np.float64)
+    thr = np.abs(np.cumsum(yy.mean(axis=1, keepdims=True) - yy, axis=1)).max()
+    big = _rows(yy.astype(np.float32), lam=float(thr) * 1.01)
+    np.testing.assert_allclose(big, np.repeat(yy.mean(axis=1)[:, None], 64, 1), atol=TOL)
+    x = _rows(synth.chain_batch(32, 1024, seed0=21), lam=0.15).astype(np.float64)
+    yk = synth.chain_batch(32, 1024, seed0=21)
+    for k in range(32):
+        assert pins.kkt_residual(yk[k], 0.15, x[k]) < 2e-3
