@@ -741,10 +741,8 @@ P thread_policy(const BatchedWs &ws, const Plan &plan, bool cols)
 }
 
 template <class P>
-tv_status prepare_thread(long long nslots)
+tv_status prepare_thread()
 {
-    const Shape sh = batch_shape(nslots / WARP, sm_count_current());
-    (void)sh;
     return check_cuda(cudaFuncSetAttribute(chain_batch_kernel<P, kBRing>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(4 * sizeof(WarpSmem<P, kBRing>))),
@@ -755,7 +753,8 @@ template <class P>
 tv_status launch_thread(const BatchedWs &ws, const Plan &plan, bool cols, cudaStream_t s)
 {
     const P p = thread_policy<P>(ws, plan, cols);
-    const Shape sh = batch_shape(p.nslots / WARP, sm_count_current());
+    const Shape sh = chains_shape(p.nslots / WARP, (const void *)chain_batch_kernel<P, kBRing>,
+                                  sizeof(WarpSmem<P, kBRing>));
     chain_batch_kernel<P, kBRing><<<(unsigned)sh.blocks, sh.wpb * WARP,
                                     sh.wpb * sizeof(WarpSmem<P, kBRing>), s>>>(
         p, ws.trec, ws.tcrec, const_cast<float2 *>(p.spill_base), ws.hdr);
@@ -891,9 +890,9 @@ tv_status tv2d_denoise_batched(const tv_image_desc *imgs, int n_imgs, int max_it
     if ((st = prepare_phase<2>(plan, (int)plan.cols.size(), plan.max_h)) != TV_OK) return st;
     if ((st = upload(ws.rgroups, plan.rgroups, s)) != TV_OK) return st;
     if ((st = upload(ws.cgroups, plan.cgroups, s)) != TV_OK) return st;
-    if ((st = prepare_thread<BRowsTP<0>>(0)) != TV_OK) return st;
-    if ((st = prepare_thread<BRowsTP<1>>(0)) != TV_OK) return st;
-    if ((st = prepare_thread<BColsTP>(0)) != TV_OK) return st;
+    if ((st = prepare_thread<BRowsTP<0>>()) != TV_OK) return st;
+    if ((st = prepare_thread<BRowsTP<1>>()) != TV_OK) return st;
+    if ((st = prepare_thread<BColsTP>()) != TV_OK) return st;
     {
         static thread_local ParamChunk chunk;
         for (int first = 0; first <= max_iters; first += kParamChunk) {

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <array>
 #include <mutex>
 #include <vector>
 
@@ -102,6 +103,48 @@ Shape batch_shape(long long warps, int sm_count)
     if (wpb < 1) wpb = 1;
     if (wpb > 4) wpb = 4;
     return Shape{wpb, (warps + wpb - 1) / wpb};
+}
+
+Shape chains_shape(long long warps, const void *kern, size_t per_warp)
+{
+    const int sms = sm_count_current();
+    if (warps < 2LL * sms) return batch_shape(warps, sms);
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, std::array<int, 5>>> cache;
+    std::array<int, 5> per_sm{};  // resident blocks per SM for 1..4 warps per block
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        bool found = false;
+        for (auto &e : cache)
+            if (e.first == kern) {
+                per_sm = e.second;
+                found = true;
+            }
+        if (!found) {
+            for (int w = 1; w <= 4; ++w) {
+                int b = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, w * tvk::WARP, w * per_warp) !=
+                    cudaSuccess) {
+                    (void)cudaGetLastError();
+                    b = 0;
+                }
+                per_sm[w] = b;
+            }
+            cache.push_back({kern, per_sm});
+        }
+    }
+    int best = 0;
+    long long best_res = -1;
+    for (int w = 4; w >= 1; --w) {
+        const long long res = (long long)per_sm[w] * w * sms;
+        if (res >= warps) return Shape{w, (warps + w - 1) / w};
+        if (res > best_res) {
+            best_res = res;
+            best = w;
+        }
+    }
+    if (best == 0 || best_res <= 0) return batch_shape(warps, sms);
+    return Shape{best, (warps + best - 1) / best};
 }
 
 }  // namespace tvh

@@ -54,7 +54,8 @@ __device__ __forceinline__ long long col_base_of(const P &p, long long warp_chai
 }
 
 constexpr int WARP = 32;
-constexpr int CH = 16;  // nodes per staged chunk
+constexpr int CH = 8;   // nodes per staged chunk
+constexpr int QPC = CH / 4;  // 16-byte quads per chain and chunk
 
 // Device error word bits (workspace header).
 constexpr int ERR_BAD_CHAIN = 1;
@@ -380,11 +381,11 @@ __device__ __forceinline__ void fill_inputs(const P &p, WarpSmem<P, RING> *sm, i
             }
         } else {
             if (p.in_vec(a)) {
-                // 8 chains x 16 nodes per instruction, 16 bytes per lane
+                // 32 / QPC chains x CH nodes per instruction, 16 bytes per lane
 #pragma unroll
                 for (int u = 0; u < CH / 4; ++u) {
                     const int t = u * WARP + lane;
-                    const int jj = t >> 2, q = (t & 3) * 4;
+                    const int jj = t / QPC, q = (t % QPC) * 4;
                     const int i = chunk * CH + q;
                     if (i < p.in_lim(a, sm->len[jj]))
                         cp_async16(&tile[jj * RP + q],
@@ -429,7 +430,7 @@ __device__ __forceinline__ void flush_outputs(const P &p, WarpSmem<P, RING> *sm,
 #pragma unroll
         for (int u = 0; u < CH / 4; ++u) {
             const int t = u * WARP + lane;
-            const int jj = t >> 2, q = (t & 3) * 4;
+            const int jj = t / QPC, q = (t % QPC) * 4;
             const int i = chunk * CH + q;
             if (i < sm->len[jj])
                 *reinterpret_cast<float4 *>(dst + p.out_off(o, warp_chain0 + jj, sm->start[jj]) + i) =

@@ -14,19 +14,26 @@ void note_launch();
 bool prof_on();
 void prof_mark(int kind, cudaStream_t s, bool start);
 
+// Warps per block of a one-thread-per-chain launch: the spread of batch_shape for
+// small batches; for batches of at least two warps per SM, the largest block (up to
+// 4 warps) whose resident warps (shared memory and registers permitting) hold the
+// whole batch in one wave, else the one with the most resident warps. Occupancy
+// answers are cached per kernel.
+Shape chains_shape(long long warps, const void *kern, size_t per_warp);
+
 template <class P, int RING>
 tv_status launch_chains(const P &p, long long nchains, float2 *rec, float *crec, float2 *spill,
                         tvk::WsHeader *hdr, cudaStream_t s, int kind)
 {
     const long long warps = (nchains + tvk::WARP - 1) / tvk::WARP;
     if (warps == 0) return TV_OK;
-    const Shape sh = batch_shape(warps, sm_count_current());
     const size_t per_warp = sizeof(tvk::WarpSmem<P, RING>);
     auto kern = tvk::chain_batch_kernel<P, RING>;
     tv_status st = check_cuda(
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * per_warp)),
         "cudaFuncSetAttribute");
     if (st != TV_OK) return st;
+    const Shape sh = chains_shape(warps, (const void *)kern, per_warp);
     const bool prof = prof_on();
     if (prof) prof_mark(kind, s, true);
     kern<<<(unsigned)sh.blocks, sh.wpb * tvk::WARP, sh.wpb * per_warp, s>>>(p, rec, crec, spill, hdr);
