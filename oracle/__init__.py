@@ -8,6 +8,7 @@ from .oracle import (  # noqa: F401
     build,
     chain_solve,
     chain_solve_batch,
+    chain_solve_general,
     chain_vjp,
     rof_primal,
     tv2d_pd,

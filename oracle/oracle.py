@@ -42,6 +42,7 @@ def _load():
                                             _I64]
             lib.tvo_chain_solve_batch.argtypes = [_D, _D, ctypes.c_double, _I64, ctypes.c_int64,
                                                   _D, ctypes.c_int, _I64]
+            lib.tvo_chain_solve_general_batch.argtypes = [_D, _D, _D, _D, _I64, ctypes.c_int64, _D]
             lib.tvo_chain_vjp.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, _D, _D]
             lib.tvo_rof_primal.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D,
                                            ctypes.c_double, _D]
@@ -102,6 +103,25 @@ def chain_solve_batch(c, offsets, w=None, lam=0.0, nthreads=None, return_max_len
     if st != 0:
         raise RuntimeError(f"oracle batch solve failed: {st}")
     return (x, int(m.value)) if return_max_len else x
+
+
+def chain_solve_general(a, b, wlo, whi, offsets=None):
+    """General convex chains of Sec. 4 / 4.1 (Algorithm 2): unaries a_i x^2/2 - b_i x
+    (a_i > 0), pairwise w^-_i d (d < 0) / w^+_i d (d >= 0) on d = x_{i+1} - x_i. Arrays
+    of one entry per node (wlo/whi at a chain's last node unused); ``offsets`` CSR
+    (default: one chain)."""
+    a, b, wlo, whi = (_f64(v) for v in (a, b, wlo, whi))
+    n = b.size
+    if offsets is None:
+        offsets = np.array([0, n], dtype=np.int64)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    x = np.empty(n, dtype=np.float64)
+    st = _load().tvo_chain_solve_general_batch(_p(a), _p(b), _p(wlo), _p(whi),
+                                               offsets.ctypes.data_as(_I64), offsets.size - 1,
+                                               _p(x))
+    if st != 0:
+        raise ValueError(f"oracle general chain solve failed ({st})")
+    return x
 
 
 def chain_vjp(x, g, fuse_tol=1e-9, with_w=False):

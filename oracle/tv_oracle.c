@@ -193,6 +193,171 @@ int tvo_chain_solve(int64_t n, const double *c, const double *w, double lam, dou
     return TVO_OK;
 }
 
+/* ---------------- the general convex chain (Sec. 4, Sec. 4.1) ----------------
+ *
+ * Unaries f_i(x) = a_i x^2 / 2 - b_i x with a_i > 0 (Sec. 4.1), pairwise terms on
+ * d = x_{i+1} - x_i: f_i(d) = w^-_i d for d < 0 and w^+_i d for d >= 0, with
+ * w^-_i <= w^+_i (Sec. 4). Algorithm 2: m^_i(z) = m_{i-1,i}(z) + a_i z - b_i
+ * (transformation (a)), m_{i,i+1} = clip_[w^-_i, w^+_i](m^_i) (transformation (b)),
+ * lambda^-_i and lambda^+_i where m^_i reaches w^-_i and w^+_i; the root edge has
+ * w^- = w^+ = 0. The stored slope s_p has true slope s_p + abar_i with
+ * abar_i = sum_{k<=i} a_k (Sec. 4.1). TV-l2 is a_i = 1, b_i = c_i, w^-_i = -w_i,
+ * w^+_i = w_i.
+ */
+static int64_t chain_general_core(int64_t n, const double *a, const double *b, const double *wlo,
+                                  const double *whi, double *x, double *lo, double *hi, tvo_bp *D)
+{
+    if (n <= 0) return 0;
+    if (n == 1) {
+        x[0] = b[0] / a[0];
+        if (lo) lo[0] = x[0];
+        if (hi) hi[0] = x[0];
+        return 0;
+    }
+    double *lam_minus = (double *)malloc(sizeof(double) * (size_t)n);
+    double *lam_plus = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!lam_minus || !lam_plus) {
+        free(lam_minus);
+        free(lam_plus);
+        return -1;
+    }
+    /* Node 0: m^_0(z) = a_0 z - b_0. */
+    double abar = a[0];
+    int64_t front = n, back = n + 1;
+    D[front].lam = (b[0] + wlo[0]) / a[0];
+    D[front].s = a[0] - abar; /* true slope a_0 between the two breakpoints */
+    D[back].lam = (b[0] + whi[0]) / a[0];
+    D[back].s = -abar;        /* true slope 0: the clipped flat right end */
+    lam_minus[0] = D[front].lam;
+    lam_plus[0] = D[back].lam;
+    int64_t max_len = 2;
+    double wl_prev = wlo[0], wh_prev = whi[0];
+
+    for (int64_t i = 1; i < n; ++i) {
+        const double ai = a[i], bi = b[i];
+        abar += ai;
+        const double wl = (i < n - 1) ? wlo[i] : 0.0; /* root edge */
+        const double wh = (i < n - 1) ? whi[i] : 0.0;
+
+        /* Left scan: forward recursion from the first breakpoint, where the incoming
+         * message has its left value w^-_{i-1}. */
+        int64_t p = front;
+        double v = wl_prev + ai * D[p].lam - bi;
+        int64_t last_popped;
+        double lm, lm_s;
+        if (v >= wl) {
+            /* lambda^- on the left end segment, true slope a_i */
+            last_popped = front - 1;
+            lm = D[p].lam + (wl - v) / ai;
+            lm_s = ai - abar;
+        } else {
+            while (p < back) {
+                double vq = v + (D[p].s + abar) * (D[p + 1].lam - D[p].lam);
+                if (vq < wl) {
+                    ++p;
+                    v = vq;
+                } else {
+                    break;
+                }
+            }
+            last_popped = p;
+            lm = D[p].lam + (wl - v) / (D[p].s + abar);
+            lm_s = D[p].s;
+        }
+
+        /* Right scan over the breakpoints kept by the left scan: backward recursion
+         * from the last breakpoint, where the incoming message has its right value
+         * w^+_{i-1}. */
+        double hp;
+        int64_t new_back_last;
+        if (back > last_popped) {
+            int64_t q = back;
+            double vr = wh_prev + ai * D[q].lam - bi;
+            if (vr <= wh) {
+                /* lambda^+ on the right end segment, true slope a_i */
+                hp = D[q].lam + (wh - vr) / ai;
+                new_back_last = back;
+            } else {
+                for (;;) {
+                    if (q - 1 > last_popped) {
+                        double slope = D[q - 1].s + abar;
+                        double vprev = vr - slope * (D[q].lam - D[q - 1].lam);
+                        if (vprev > wh) {
+                            --q;
+                            vr = vprev;
+                            continue;
+                        }
+                        hp = D[q].lam - (vr - wh) / slope;
+                    } else {
+                        hp = D[q].lam - (vr - wh) / (lm_s + abar);
+                    }
+                    break;
+                }
+                new_back_last = q - 1;
+            }
+        } else {
+            hp = lm + (wh - wl) / (lm_s + abar);
+            new_back_last = last_popped;
+        }
+
+        front = last_popped;
+        D[front].lam = lm;
+        D[front].s = lm_s;
+        back = (new_back_last > front ? new_back_last : front) + 1;
+        D[back].lam = hp;
+        D[back].s = -abar;
+        if (back - front + 1 > max_len) max_len = back - front + 1;
+        lam_minus[i] = lm;
+        lam_plus[i] = hp;
+        wl_prev = wl;
+        wh_prev = wh;
+    }
+
+    x[n - 1] = 0.5 * (lam_minus[n - 1] + lam_plus[n - 1]);
+    for (int64_t i = n - 2; i >= 0; --i) {
+        double v = x[i + 1];
+        if (v < lam_minus[i]) v = lam_minus[i];
+        if (v > lam_plus[i]) v = lam_plus[i];
+        x[i] = v;
+    }
+    if (lo) memcpy(lo, lam_minus, sizeof(double) * (size_t)n);
+    if (hi) memcpy(hi, lam_plus, sizeof(double) * (size_t)n);
+    free(lam_minus);
+    free(lam_plus);
+    return max_len;
+}
+
+/* General chains in a CSR batch (one thread; a, b, wlo, whi laid out like x, the
+ * entries at a chain's last node of wlo/whi unused). */
+int tvo_chain_solve_general_batch(const double *a, const double *b, const double *wlo,
+                                  const double *whi, const int64_t *offsets, int64_t num_chains,
+                                  double *x)
+{
+    if (num_chains < 0 || !offsets) return TVO_ERR_INVALID;
+    int64_t nmax = 0;
+    for (int64_t k = 0; k < num_chains; ++k) {
+        const int64_t len = offsets[k + 1] - offsets[k];
+        if (len < 0) return TVO_ERR_INVALID;
+        if (len > nmax) nmax = len;
+    }
+    tvo_bp *D = (tvo_bp *)malloc(sizeof(tvo_bp) * (size_t)(2 * nmax + 4));
+    if (!D) return TVO_ERR_NOMEM;
+    for (int64_t k = 0; k < num_chains; ++k) {
+        const int64_t o = offsets[k], len = offsets[k + 1] - offsets[k];
+        for (int64_t i = 0; i < len; ++i)
+            if (!(a[o + i] > 0.0) || (i < len - 1 && !(wlo[o + i] <= whi[o + i]))) {
+                free(D);
+                return TVO_ERR_INVALID;
+            }
+        if (chain_general_core(len, a + o, b + o, wlo + o, whi + o, x + o, NULL, NULL, D) < 0) {
+            free(D);
+            return TVO_ERR_NOMEM;
+        }
+    }
+    free(D);
+    return TVO_OK;
+}
+
 /* ---------------- batches of contiguous chains (CSR offsets), threaded ---------------- */
 
 typedef struct {
