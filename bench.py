@@ -358,6 +358,35 @@ def main():
             del wt
         del ys, xs
 
+    # ---------------- general convex chains (curvature a_i, slopes w^-_i <= w^+_i) ----------
+    GB, GN = 2048, 1024
+    grng = np.random.default_rng(11)
+    ga = grng.uniform(0.5, 2.0, (GB, GN)).astype(np.float32)
+    gb = (ga * np.tile(synth.chain_batch(256, GN, seed0=3000), (GB // 256, 1))).astype(np.float32)
+    gwl = grng.uniform(-0.3, 0.05, (GB, GN)).astype(np.float32)
+    gwh = (gwl + grng.uniform(0.0, 0.4, (GB, GN))).astype(np.float32)
+    gt = [torch.from_numpy(v).to(dev) for v in (ga, gb, gwl, gwh)]
+    gx = torch.empty_like(gt[1])
+    for _ in range(3):
+        _lib.chain_prox_general(gt[1], gt[2], gt[3], a=gt[0], out=gx)
+    gms = []
+    for _ in range(10):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _lib.chain_prox_general(gt[1], gt[2], gt[3], a=gt[0], out=gx)
+        b.record(stream)
+        b.synchronize()
+        gms.append(a.elapsed_time(b))
+    gmed = float(np.median(gms))
+    general = {"value": GB * GN / (gmed * 1e-3) / 1e9, "unit": "Gnode/s", "ms": gmed,
+               "workload": f"{GB} chains x {GN}, a ~ U[0.5,2], b = a * (step signal), "
+                           "w^- ~ U[-0.3,0.05], w^+ = w^- + U[0,0.4]",
+               "bytes_per_node": 20,
+               "GB_per_s": 20.0 * GB * GN / (gmed * 1e-3) / 1e9}
+    del gt, gx
+
     # ---------------- differentiable prox: forward + backward ----------------
     DB, DN = 4096, 1024
     yd = torch.from_numpy(synth.chain_batch(DB, DN, seed0=1000)).to(dev)
@@ -503,6 +532,7 @@ def main():
                                     "traffic": recorded_traffic("chain"),
                                     "bytes_per_node": 8}},
         "chain_prox_sweep": sweep,
+        "general_chain": general,
         "diff_prox": {"value": DB * DN / (dms * 1e-3) / 1e9, "unit": "Gnode/s",
                       "workload": f"{DB} chains x {DN}, lambda 0.15, forward + backward "
                                   "(loss sum c_i x_i, c ~ N(0,1)), L2 flushed",

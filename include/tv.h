@@ -123,6 +123,26 @@ tv_status tv_chain_solve_noalloc(const float *d_y, const float *d_w, float lambd
                                  float *d_x, tv_stream_t stream);
 
 /*
+ * General convex chains: the problem of Sec. 4 with the quadratic unaries of Sec. 4.1,
+ *     x* = argmin_x sum_i (a_i x_i^2 / 2 - b_i x_i) + sum_{i<n} f_i(x_{i+1} - x_i),
+ *     f_i(d) = wlo_i * d for d < 0 and whi_i * d for d >= 0,
+ * with a_i > 0 and wlo_i <= whi_i (TV-l2 is a = 1, b = y, wlo = -w, whi = w; whi > 0 > wlo
+ * penalises jumps up and down differently; wlo = whi adds a linear term).
+ *   d_a        per-node curvature, or NULL for a_i = 1
+ *   d_b, d_wlo, d_whi   per-node arrays laid out like d_y of tv_chain_solve (the entries
+ *              of wlo/whi at a chain's last node are not read)
+ *   d_offsets, num_chains, max_len, d_x, workspace (tv_chain_workspace_size): as for
+ *              tv_chain_solve
+ * Every batch runs one warp per chain (rooted at the middle node for chains of 64 nodes
+ * or more). Values are not validated on the device: a_i <= 0 or wlo_i > whi_i give
+ * undefined results (never an out-of-bounds access).
+ */
+tv_status tv_chain_solve_general(const float *d_a, const float *d_b, const float *d_wlo,
+                                 const float *d_whi, const int64_t *d_offsets, int64_t num_chains,
+                                 int64_t max_len, float *d_x, void *d_workspace,
+                                 size_t workspace_bytes, tv_stream_t stream);
+
+/*
  * Backward of the chain prox (vector-Jacobian product), for a differentiable TV
  * layer. From the optimality conditions of eq. 1D-ROF, on every maximal run S of
  * equal values of the solution x ("segment"), x_S = mean(y_S) + (u_r - u_{l-1})/|S|

@@ -60,6 +60,7 @@ SIGNATURES = {
     "tv2d_batched_last_mode": (ctypes.c_int, []),
     "tv_set_batched_graph": (ctypes.c_int, [ctypes.c_int]),
     "tv_set_coop_max_chains": (ctypes.c_int, [_i64]),
+    "tv_chain_solve_general": (ctypes.c_int, [_p, _p, _p, _p, _p, _i64, _i64, _p, _p, _sz, _p]),
     "tv_set_coop_split": (ctypes.c_int, [ctypes.c_int]),
     "tv_net_conv3x3": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       _p, _p, ctypes.c_int, ctypes.c_int, _p, _p, _p]),
@@ -174,6 +175,31 @@ def chain_prox(y, w=None, lam: float = 0.0, offsets=None, max_len: int | None = 
     wsb = ws if ws is not None else workspace(nbytes, y.device, "chain")
     _check(lib.tv_chain_solve(_ptr(y), _ptr(w), float(lam), offp, num_chains, max_len, _ptr(x),
                               _ptr(wsb), wsb.numel(), _stream(y.device)))
+    return x
+
+
+def chain_prox_general(b, wlo, whi, a=None, offsets=None, max_len: int | None = None, out=None,
+                       ws=None):
+    """General convex chains: argmin sum (a_i x_i^2/2 - b_i x_i) + sum f_i(x_{i+1} - x_i) with
+    f_i(d) = wlo_i d (d < 0), whi_i d (d >= 0). ``b``, ``wlo``, ``whi`` (and ``a``, default 1)
+    are (num_chains, n) or flat with CSR ``offsets`` (int64 CUDA tensor) and ``max_len``."""
+    lib = load()
+    _require_cuda(b, wlo, whi, a)
+    if offsets is None:
+        if b.dim() != 2:
+            raise ValueError("b must be (num_chains, n) when offsets is None")
+        num_chains, n = b.shape
+        max_len = n
+    else:
+        if max_len is None:
+            raise ValueError("max_len is required with offsets")
+        num_chains = offsets.numel() - 1
+    x = torch.empty_like(b) if out is None else out
+    nbytes = lib.tv_chain_workspace_size(num_chains, max_len)
+    wsb = ws if ws is not None else workspace(nbytes, b.device, "chain")
+    _check(lib.tv_chain_solve_general(_ptr(a), _ptr(b), _ptr(wlo), _ptr(whi), _ptr(offsets),
+                                      num_chains, max_len, _ptr(x), _ptr(wsb), wsb.numel(),
+                                      _stream(b.device)))
     return x
 
 

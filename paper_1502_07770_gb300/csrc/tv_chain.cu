@@ -424,6 +424,79 @@ struct CoopColsP {
     __device__ void finish_empty() const {}
 };
 
+// ---- general convex chains (Sec. 4, Sec. 4.1), one warp per chain ----
+struct GenRowsP {
+    static constexpr bool CREC = false;
+    struct Raw {
+        float a, b, wl, wh;
+    };
+    struct Acc {};
+
+    const float *a, *b, *wlo, *whi;
+    const int64_t *offsets;
+    long long nchains;
+    int maxlen;
+    float *x;
+    long long off0;
+
+    __device__ bool resolve()
+    {
+        off0 = offsets ? (long long)offsets[0] : 0;
+        return true;
+    }
+    __device__ long long num_chains() const { return nchains; }
+    __device__ int max_len() const { return maxlen; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        if (offsets) {
+            const long long lo = offsets[k], hi = offsets[k + 1];
+            if (lo < off0 || hi < lo || hi - lo > maxlen || hi - off0 > (k + 1) * (long long)maxlen)
+                return false;
+            start = lo;
+            n = (int)(hi - lo);
+        } else {
+            start = k * (long long)maxlen;
+            n = maxlen;
+        }
+        return true;
+    }
+    __device__ void fetch(long long, long long start, int n, int i, Raw &r) const
+    {
+        const bool in = i < n, e = i < n - 1;
+        r.a = in ? (a ? a[start + i] : 1.f) : 1.f;
+        r.b = in ? b[start + i] : 0.f;
+        r.wl = e ? wlo[start + i] : 0.f;
+        r.wh = e ? whi[start + i] : 0.f;
+    }
+    __device__ void unary_g(long long, long long, int, int, const Raw &r, float &ai, float &bi,
+                            float &wl, float &wh, Acc &) const
+    {
+        ai = r.a;
+        bi = r.b;
+        wl = r.wl;
+        wh = r.wh;
+    }
+    __device__ void unary_g_direct(int i, int n, long long, long long start, float &ai, float &bi,
+                                   float &wl, float &wh) const
+    {
+        ai = a ? a[start + i] : 1.f;
+        bi = b[start + i];
+        wl = (i < n - 1) ? wlo[start + i] : 0.f;
+        wh = (i < n - 1) ? whi[start + i] : 0.f;
+    }
+    __device__ void emit(long long, long long start, int i, float xv, float) const
+    {
+        x[start + i] = xv;
+    }
+    __device__ long long spill_off(long long k, long long start) const
+    {
+        return 2 * (start - off0) + 2 * k;
+    }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &, int) const {}
+    __device__ void finish_empty() const {}
+};
+
 template <class P>
 tv_status launch_batch(const P &p, long long nchains, float2 *rec, float *crec, float2 *spill,
                        WsHeader *hdr, cudaStream_t s)
@@ -523,6 +596,51 @@ size_t tv_chain_workspace_size(int64_t num_chains, int64_t max_len)
     if (num_chains < 0 || max_len < 0) return 0;
     const long long warps = (num_chains + WARP - 1) / WARP;
     return carve_chain_ws(nullptr, warps, max_len, 2 * num_chains * max_len + 2 * num_chains).bytes;
+}
+
+tv_status tv_chain_solve_general(const float *d_a, const float *d_b, const float *d_wlo,
+                                 const float *d_whi, const int64_t *d_offsets, int64_t num_chains,
+                                 int64_t max_len, float *d_x, void *d_workspace,
+                                 size_t workspace_bytes, tv_stream_t stream)
+{
+    clear_error();
+    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 30)) {
+        set_error("tv_chain_solve_general: num_chains and max_len must be >= 0 (max_len <= 2^30)");
+        return TV_ERR_INVALID;
+    }
+    if (num_chains == 0) return TV_OK;
+    if (!d_b || !d_wlo || !d_whi || !d_x || !d_workspace) {
+        set_error("tv_chain_solve_general: b, wlo, whi, x and workspace must not be NULL");
+        return TV_ERR_INVALID;
+    }
+    const void *ins[4] = {d_a, d_b, d_wlo, d_whi};
+    if (!d_offsets) {
+        const size_t bytes = (size_t)num_chains * (size_t)max_len * sizeof(float);
+        for (const void *q : ins)
+            if (overlaps(d_x, bytes, q, bytes)) {
+                set_error("tv_chain_solve_general: x must not overlap the inputs");
+                return TV_ERR_INVALID;
+            }
+    } else {
+        for (const void *q : ins)
+            if (q == d_x) {
+                set_error("tv_chain_solve_general: x must not alias the inputs");
+                return TV_ERR_INVALID;
+            }
+    }
+    const long long warps = (num_chains + WARP - 1) / WARP;
+    const long long total = (long long)num_chains * max_len;
+    ChainWs ws = carve_chain_ws(d_workspace, warps, max_len, 2 * total + 2 * num_chains);
+    if (workspace_bytes < ws.bytes) {
+        set_error("tv_chain_solve_general: workspace of %zu bytes, %zu needed", workspace_bytes,
+                  ws.bytes);
+        return TV_ERR_NOMEM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
+    if (st != TV_OK) return st;
+    GenRowsP p{d_a, d_b, d_wlo, d_whi, d_offsets, num_chains, (int)max_len, d_x, 0};
+    return launch_coop(p, num_chains, (int)max_len, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_CHAIN);
 }
 
 tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,

@@ -18,6 +18,8 @@
 // A message of more than 32 breakpoints is finished from global memory by lane 0
 // with the sequential update of tv_dp.cuh (two-ended array of 2n+2 entries).
 #pragma once
+#include <type_traits>
+
 #include "tv_dp.cuh"
 
 namespace tvk {
@@ -115,34 +117,38 @@ __device__ __forceinline__ float seg_frac(float num, float den)
     return fminf(fmaxf(__fdividef(num, den), 0.f), 1.f);
 }
 
+// General form (Sec. 4, Sec. 4.1): unary a_i x^2/2 - b_i x, pairwise slopes w^-_i <= w^+_i.
+// m^_i = m_{i-1,i} + a_i z - b_i; the message is clipped to [w^-_i, w^+_i]; the end pieces
+// of m^_i have slope a_i. `wl_prev` is w^-_{i-1} (the message's value left of its first
+// breakpoint). TV-l2 is a_i = 1, b_i = c_i, w^-_i = -w_i, w^+_i = w_i.
 template <int G>
-__device__ __forceinline__ void coop_update(float &lam, float &V, float &T, int &size,
-                                            float &lam0, float &w_prev, float ci, float wi,
-                                            int sl, int seg_shift, bool active, bool &ovf,
-                                            float &lm, float &hp)
+__device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, int &size,
+                                              float &lam0, float &wl_prev, float ai, float bi,
+                                              float wl, float wh, int sl, int seg_shift,
+                                              bool active, bool &ovf, float &lm, float &hp)
 {
     const bool valid = sl < size;
     const bool last = sl == size - 1;
-    const float S = T + 1.f;              // slope of m^_i right of this breakpoint
-    const float v = V + lam - ci;         // m^_i at this breakpoint
-    const float v0 = lam0 - ci - w_prev;  // m^_i at the first breakpoint
+    const float S = T + ai;                    // slope of m^_i right of this breakpoint
+    const float v = fmaf(ai, lam, V) - bi;     // m^_i at this breakpoint
+    const float v0 = fmaf(ai, lam0, wl_prev) - bi;  // m^_i at the first breakpoint
     const float lam_n = __shfl_down_sync(FULL, lam, 1, G);
-    float candL = fmaxf(lam + __fdividef(-wi - v, S), lam);
-    float candR = fmaxf(lam + __fdividef(wi - v, S), lam);
+    float candL = fmaxf(lam + __fdividef(wl - v, S), lam);
+    float candR = fmaxf(lam + __fdividef(wh - v, S), lam);
     if (!last) {
         candL = fminf(candL, lam_n);
         candR = fminf(candR, lam_n);
     }
     int ell, kl;
     if constexpr (G == WARP) {
-        ell = min((int)__reduce_min_sync(FULL, (unsigned)((valid && v >= -wi) ? sl : WARP)), size);
-        kl = __reduce_max_sync(FULL, (valid && v <= wi) ? sl : -1);
+        ell = min((int)__reduce_min_sync(FULL, (unsigned)((valid && v >= wl) ? sl : WARP)), size);
+        kl = __reduce_max_sync(FULL, (valid && v <= wh) ? sl : -1);
     } else {
         // one warp reduction per half and side: the other half contributes the
         // neutral element, each lane keeps its own half's result
         const bool lo_half = seg_shift == 0;
-        const unsigned ge = (valid && v >= -wi) ? (unsigned)sl : (unsigned)G;
-        const int le = (valid && v <= wi) ? sl : -1;
+        const unsigned ge = (valid && v >= wl) ? (unsigned)sl : (unsigned)G;
+        const int le = (valid && v <= wh) ? sl : -1;
         const unsigned ell0 = __reduce_min_sync(FULL, lo_half ? ge : (unsigned)G);
         const unsigned ell1 = __reduce_min_sync(FULL, lo_half ? (unsigned)G : ge);
         const int kl0 = __reduce_max_sync(FULL, lo_half ? le : -1);
@@ -155,27 +161,40 @@ __device__ __forceinline__ void coop_update(float &lam, float &V, float &T, int 
     ovf = ovf || (active && K + 2 > G);
     // lambda^- on the piece right of the last breakpoint removed on the left,
     // lambda^+ on the piece right of the last one kept; with none, on the left end
-    // piece (slope 1)
+    // piece (slope a_i)
     const int il = (ell - 1) & (G - 1);
     const float gl = __shfl_sync(FULL, candL, il, G);
     const float Sl = __shfl_sync(FULL, S, il, G);
     const float gr = __shfl_sync(FULL, candR, keep_last & (G - 1), G);
-    lm = (ell == 0) ? lam0 - (v0 + wi) : gl;
-    hp = (keep_last < 0) ? lam0 + (wi - v0) : gr;
-    // new message m_{i,i+1}: lambda^- (value -w_i, the slope of m^_i there), the kept
-    // breakpoints with their values and slopes, lambda^+ (value +w_i, flat beyond)
+    lm = (ell == 0) ? lam0 + (wl - v0) / ai : gl;
+    hp = (keep_last < 0) ? lam0 + (wh - v0) / ai : gr;
+    // new message m_{i,i+1}: lambda^- (value w^-_i, the slope of m^_i there), the kept
+    // breakpoints with their values and slopes, lambda^+ (value w^+_i, flat beyond)
     const int src = (sl - 1 + ell) & (G - 1);
     const float nl = __shfl_sync(FULL, lam, src, G);
     const float nv = __shfl_sync(FULL, v, src, G);
     const float nS = __shfl_sync(FULL, S, src, G);
     if (active) {
         lam = (sl == 0) ? lm : ((sl == K + 1) ? hp : nl);
-        V = (sl == 0) ? -wi : ((sl == K + 1) ? wi : nv);
-        T = (sl == 0) ? ((ell == 0) ? 1.f : Sl) : ((sl == K + 1) ? 0.f : nS);
+        V = (sl == 0) ? wl : ((sl == K + 1) ? wh : nv);
+        T = (sl == 0) ? ((ell == 0) ? ai : Sl) : ((sl == K + 1) ? 0.f : nS);
         size = K + 2;
         lam0 = lm;
-        w_prev = wi;
+        wl_prev = wl;
     }
+}
+
+// TV-l2 form: a_i = 1, b_i = c_i, [w^-_i, w^+_i] = [-w_i, w_i]; `w_prev` is w_{i-1}.
+template <int G>
+__device__ __forceinline__ void coop_update(float &lam, float &V, float &T, int &size,
+                                            float &lam0, float &w_prev, float ci, float wi,
+                                            int sl, int seg_shift, bool active, bool &ovf,
+                                            float &lm, float &hp)
+{
+    float wl_prev = -w_prev;
+    coop_update_g<G>(lam, V, T, size, lam0, wl_prev, 1.f, ci, -wi, wi, sl, seg_shift, active, ovf,
+                     lm, hp);
+    if (active) w_prev = wi;
 }
 
 // Start of a message at the first node of a walk: m_{0,1} = clip(z - c_0, -w_0, w_0).
@@ -364,10 +383,10 @@ __device__ __forceinline__ float msg_eval(const PairMsg &m, float z)
     return fmaf(t, m.val[hi] - m.val[lo], m.val[lo]);
 }
 
-// Root of h(z) = z - c + mL'(z) + mR'(z), computed by one warp: lane l evaluates h at
+// Root of h(z) = a z - b + mL'(z) + mR'(z), computed by one warp: lane l evaluates h at
 // breakpoint l of each message; the largest point with h <= 0 and the smallest with
 // h > 0 are neighbours among all kinks, and h is linear between them.
-__device__ __forceinline__ float pair_root(const PairXchg &xc, float c, int lane)
+__device__ __forceinline__ float pair_root(const PairXchg &xc, float a, float b, int lane)
 {
     float lo_z = -INFINITY, lo_h = 0.f, hi_z = INFINITY, hi_h = 0.f;
 #pragma unroll
@@ -375,7 +394,7 @@ __device__ __forceinline__ float pair_root(const PairXchg &xc, float c, int lane
         const PairMsg &own = xc.m[side], &oth = xc.m[1 - side];
         if (lane < own.size) {
             const float z = own.lam[lane];
-            const float h = (z - c) + own.val[lane] + msg_eval(oth, z);
+            const float h = fmaf(a, z, -b) + own.val[lane] + msg_eval(oth, z);
             if (h <= 0.f) {
                 if (z > lo_z) {
                     lo_z = z;
@@ -402,9 +421,9 @@ __device__ __forceinline__ float pair_root(const PairXchg &xc, float c, int lane
     }
     const PairMsg &L = xc.m[0], &R = xc.m[1];
     if (lo_z == -INFINITY)  // left of every kink: both messages at their left values
-        return fminf(c - L.val[0] - R.val[0], hi_z);
+        return fminf((b - L.val[0] - R.val[0]) / a, hi_z);
     if (hi_z == INFINITY)  // right of every kink
-        return fmaxf(c - L.val[L.size - 1] - R.val[R.size - 1], lo_z);
+        return fmaxf((b - L.val[L.size - 1] - R.val[R.size - 1]) / a, lo_z);
     return fminf(fmaxf(fmaf(-lo_h, __fdividef(hi_z - lo_z, hi_h - lo_h), lo_z), lo_z), hi_z);
 }
 
@@ -506,7 +525,7 @@ __device__ void coop_solve_chain_split(const P &p, typename P::Acc &acc, long lo
         return;
     }
     if (role == 0) {
-        const float xs = pair_root(xc, c_s, lane);
+        const float xs = pair_root(xc, 1.f, c_s, lane);
         if (lane == 0) xc.xs = xs;
         __syncwarp();
     }
@@ -674,7 +693,7 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
     if (sl == 0) mine.size = size;
     __syncwarp();
     const float cs_all = __shfl_sync(FULL, c_s, 0);
-    const float xs = pair_root(xc, cs_all, lane);
+    const float xs = pair_root(xc, 1.f, cs_all, lane);
     if (lane == 0) {
         float cc = 0.f;
         if constexpr (P::CREC) cc = cs_all;
@@ -711,6 +730,278 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
             if constexpr (P::CREC) cc = crecp[i];
             p.emit(k, start, i, xv, cc);
         }
+        x_next = __shfl_sync(FULL, xv, 0, SEG);
+    }
+}
+
+// ------------------------------------------------------------------------------
+// General convex chains (Sec. 4, Sec. 4.1): policies with unary_g give, per node,
+// a_i > 0, b_i and the pairwise slopes [w^-_i, w^+_i] of edge (i, i+1).
+template <class P, class = void>
+struct has_unary_g : std::false_type {};
+template <class P>
+struct has_unary_g<P, std::void_t<decltype(&P::unary_g)>> : std::true_type {};
+
+// Overflow path of the general chain: lane 0, the two-ended array of Sec. 4.1 (2n+2
+// entries (lambda, s), true slope s + abar_i, abar_i = sum a_k) in global memory.
+template <class P>
+__device__ void solve_chain_general_lane0(const P &p, long long k, long long start, int n,
+                                          float2 *D, float2 *rec)
+{
+    float a, b, wl, wh;
+    p.unary_g_direct(0, n, k, start, a, b, wl, wh);
+    if (n == 1) {
+        p.emit(k, start, 0, b / a, 0.f);
+        return;
+    }
+    float abar = a;
+    int front = n, back = n + 1;
+    D[front] = make_float2((b + wl) / a, 0.f);
+    D[back] = make_float2((b + wh) / a, -abar);
+    rec[0] = make_float2(D[front].x, D[back].x);
+    float wl_prev = wl, wh_prev = wh, xlast = 0.f;
+    for (int i = 1; i < n; ++i) {
+        p.unary_g_direct(i, n, k, start, a, b, wl, wh);
+        abar += a;
+        int pp = front;
+        float v = fmaf(a, D[pp].x, wl_prev) - b;
+        int last_popped;
+        float lm, lm_s;
+        if (v >= wl) {
+            last_popped = front - 1;
+            lm = D[pp].x + (wl - v) / a;
+            lm_s = a - abar;
+        } else {
+            while (pp < back) {
+                const float vq = v + (D[pp].y + abar) * (D[pp + 1].x - D[pp].x);
+                if (!(vq < wl)) break;
+                ++pp;
+                v = vq;
+            }
+            last_popped = pp;
+            lm = D[pp].x + (wl - v) / (D[pp].y + abar);
+            lm_s = D[pp].y;
+        }
+        float hp;
+        int new_back_last;
+        if (back > last_popped) {
+            int q = back;
+            float vr = fmaf(a, D[q].x, wh_prev) - b;
+            if (vr <= wh) {
+                hp = D[q].x + (wh - vr) / a;
+                new_back_last = back;
+            } else {
+                for (;;) {
+                    if (q - 1 > last_popped) {
+                        const float slope = D[q - 1].y + abar;
+                        const float vprev = vr - slope * (D[q].x - D[q - 1].x);
+                        if (vprev > wh) {
+                            --q;
+                            vr = vprev;
+                            continue;
+                        }
+                        hp = D[q].x - (vr - wh) / slope;
+                    } else {
+                        hp = D[q].x - (vr - wh) / (lm_s + abar);
+                    }
+                    break;
+                }
+                new_back_last = q - 1;
+            }
+        } else {
+            hp = lm + (wh - wl) / (lm_s + abar);
+            new_back_last = last_popped;
+        }
+        front = last_popped;
+        D[front] = make_float2(lm, lm_s);
+        back = (new_back_last > front ? new_back_last : front) + 1;
+        D[back] = make_float2(hp, -abar);
+        if (i == n - 1) xlast = 0.5f * (lm + hp);
+        else rec[i] = make_float2(lm, hp);
+        wl_prev = wl;
+        wh_prev = wh;
+    }
+    float xv = xlast;
+    p.emit(k, start, n - 1, xv, 0.f);
+    for (int i = n - 2; i >= 0; --i) {
+        const float2 r = rec[i];
+        xv = clip_to(xv, r.x, r.y);
+        p.emit(k, start, i, xv, 0.f);
+    }
+}
+
+// One general chain by one warp from one end (any length).
+template <class P>
+__device__ void coop_solve_chain_general(const P &p, typename P::Acc &acc, long long k,
+                                         long long start, int n, int lane, float2 *sm_rec,
+                                         int smem_nodes, float2 *rec_g, float2 *spill,
+                                         WsHeader *hdr)
+{
+    const int max_len = p.max_len();
+    float2 *recp = n <= smem_nodes ? sm_rec : rec_g + k * (long long)max_len;
+    // empty message: the first update produces m_{0,1} = clip(a_0 z - b_0, w^-_0, w^+_0)
+    float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, wl_prev = 0.f, xlast = 0.f;
+    int size = 0;
+    bool ok = true, ovf = false;
+    typename P::Raw raw, raw_next{};
+    p.fetch(k, start, n, lane, raw);
+    const int nblocks = (n + WARP - 1) / WARP;
+    for (int blk = 0; blk < nblocks; ++blk) {
+        const int base = blk * WARP;
+        if (blk + 1 < nblocks) p.fetch(k, start, n, base + WARP + lane, raw_next);
+        float av, bv, wlv, whv;
+        p.unary_g(k, start, n, base + lane, raw, av, bv, wlv, whv, acc);
+        const int cnt = min(WARP, n - base);
+        if (ok) {
+            for (int j = 0; j < cnt; ++j) {
+                const int i = base + j;
+                const float ai = __shfl_sync(FULL, av, j), bi = __shfl_sync(FULL, bv, j);
+                const float wl = (i < n - 1) ? __shfl_sync(FULL, wlv, j) : 0.f;
+                const float wh = (i < n - 1) ? __shfl_sync(FULL, whv, j) : 0.f;
+                float lmv, hpv;
+                coop_update_g<WARP>(lam, V, T, size, lam0, wl_prev, ai, bi, wl, wh, lane, 0, true,
+                                    ovf, lmv, hpv);
+                if (i == n - 1) xlast = (n == 1) ? bi / ai : 0.5f * (lmv + hpv);
+                else if (lane == 0) recp[i] = make_float2(lmv, hpv);
+            }
+            ok = !ovf;
+        }
+        raw = raw_next;
+    }
+    __syncwarp();
+    if (!ok) {
+        if (lane == 0) {
+            atomicAdd(&hdr->overflowed, 1ull);
+            solve_chain_general_lane0(p, k, start, n, spill, rec_g + k * (long long)max_len);
+        }
+        __syncwarp();
+        return;
+    }
+    float x_next = xlast;
+    for (int blk = nblocks - 1; blk >= 0; --blk) {
+        const int i = blk * WARP + lane;
+        float lo = -INFINITY, hi = INFINITY;
+        if (i < n - 1) {
+            const float2 r = recp[i];
+            lo = r.x;
+            hi = r.y;
+        }
+        const float xv = clip_suffix(lo, hi, x_next, lane, min(WARP, n - blk * WARP));
+        if (i < n) p.emit(k, start, i, xv, 0.f);
+        x_next = __shfl_sync(FULL, xv, 0);
+    }
+}
+
+// One general chain of kSplitMinLen nodes or more: rooted at its middle node, the two
+// forward passes in the warp's two 16-lane halves (as coop_solve_chain_halves). The
+// reversed right half sees edge (i-1, i) with the slopes [-w^+_{i-1}, -w^-_{i-1}].
+template <class P>
+__device__ void coop_solve_chain_halves_general(const P &p, typename P::Acc &acc, long long k,
+                                                long long start, int n, int lane, PairXchg &xc,
+                                                float2 *sm_rec, int smem_nodes, float2 *rec_g,
+                                                float2 *spill, WsHeader *hdr)
+{
+    const int max_len = p.max_len();
+    float2 *recp = n <= smem_nodes ? sm_rec : rec_g + k * (long long)max_len;
+    const int s = n / 2;
+    const int half = lane >> 4, sl = lane & (SEG - 1), seg_shift = half * SEG;
+    const int cntw = half == 0 ? s + 1 : n - s;
+    const int cnt_all = (s + 1 > n - s) ? s + 1 : n - s;
+    auto node = [&](int q) { return half == 0 ? q : n - 1 - q; };
+    auto fetch_at = [&](int q, typename P::Raw &r) {
+        p.fetch(k, start, n, q < cntw ? node(q) : n, r);
+    };
+    float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, wl_prev = 0.f, a_s = 1.f, b_s = 0.f;
+    int size = 0;
+    bool ok = true, ovf = false;
+    typename P::Raw raw, raw_next{};
+    fetch_at(sl, raw);
+    const int nblocks = (cnt_all + SEG - 1) / SEG;
+    for (int blk = 0; blk < nblocks; ++blk) {
+        const int base = blk * SEG;
+        if (blk + 1 < nblocks) fetch_at(base + SEG + sl, raw_next);
+        const int q = base + sl;
+        const int i_l = q < cntw ? node(q) : n;
+        float av, bv, wlv, whv;
+        p.unary_g(k, start, n, i_l, raw, av, bv, wlv, whv, acc);
+        // right half: the next position's edge, reversed
+        const float wlr = __shfl_down_sync(FULL, wlv, 1, SEG);
+        const float whr = __shfl_down_sync(FULL, whv, 1, SEG);
+        const float wl_sel = half == 0 ? wlv : -whr;
+        const float wh_sel = half == 0 ? whv : -wlr;
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < SEG; ++j) {
+                const int qq = base + j;
+                const float ai = __shfl_sync(FULL, av, j, SEG);
+                const float bi = __shfl_sync(FULL, bv, j, SEG);
+                float wl = __shfl_sync(FULL, wl_sel, j, SEG);
+                float wh = __shfl_sync(FULL, wh_sel, j, SEG);
+                if (j == SEG - 1) {
+                    float a2, b2, wl2, wh2;
+                    p.unary_g(k, start, n, base + SEG < cntw ? node(base + SEG) : n, raw_next, a2,
+                              b2, wl2, wh2, acc);
+                    const float nl = __shfl_sync(FULL, wl2, 0, SEG);
+                    const float nh = __shfl_sync(FULL, wh2, 0, SEG);
+                    if (half == 1) {
+                        wl = -nh;
+                        wh = -nl;
+                    }
+                }
+                const bool stepping = qq < cntw - 1;
+                if (half == 0 && qq == cntw - 1) {
+                    a_s = ai;
+                    b_s = bi;
+                }
+                float lmv, hpv;
+                coop_update_g<SEG>(lam, V, T, size, lam0, wl_prev, ai, bi, wl, wh, sl, seg_shift,
+                                   stepping, ovf, lmv, hpv);
+                if (stepping && sl == 0) recp[node(qq)] = make_float2(lmv, hpv);
+            }
+            ok = !__any_sync(FULL, ovf);
+        }
+        raw = raw_next;
+    }
+    __syncwarp();
+    if (!ok) {
+        if (lane == 0) {
+            atomicAdd(&hdr->overflowed, 1ull);
+            solve_chain_general_lane0(p, k, start, n, spill, rec_g + k * (long long)max_len);
+        }
+        __syncwarp();
+        return;
+    }
+    PairMsg &mine = xc.m[half];
+    mine.lam[sl] = lam;
+    mine.val[sl] = V;
+    if (sl == 0) mine.size = size;
+    __syncwarp();
+    const float as_all = __shfl_sync(FULL, a_s, 0), bs_all = __shfl_sync(FULL, b_s, 0);
+    const float xs = pair_root(xc, as_all, bs_all, lane);
+    if (lane == 0) p.emit(k, start, s, xs, 0.f);
+    const int nbl_l = (s + SEG - 1) / SEG;
+    const int nbl_r = (n - 1 - s + SEG - 1) / SEG;
+    const int nbb = nbl_l > nbl_r ? nbl_l : nbl_r;
+    float x_next = xs;
+    for (int t = 0; t < nbb; ++t) {
+        int i;
+        bool inb;
+        if (half == 0) {
+            const int blk = nbl_l - 1 - t;
+            i = blk * SEG + sl;
+            inb = blk >= 0 && i < s;
+        } else {
+            i = s + 1 + t * SEG + (SEG - 1 - sl);
+            inb = t < nbl_r && i < n;
+        }
+        float lo = -INFINITY, hi = INFINITY;
+        if (inb) {
+            const float2 r = recp[i];
+            lo = r.x;
+            hi = r.y;
+        }
+        const float xv = clip_suffix16(lo, hi, x_next, sl, inb);
+        if (inb) p.emit(k, start, i, xv, 0.f);
         x_next = __shfl_sync(FULL, xv, 0, SEG);
     }
 }
@@ -795,12 +1086,21 @@ __global__ void __launch_bounds__(256) coop_chain_kernel(P p_in, float2 *rec_g, 
         p.finish_empty();
         return;
     }
-    if (HALVES && n >= kSplitMinLen)
-        coop_solve_chain_halves(p, acc, k, start, n, lane, xch[warp], sm_rec, sm_crec, smem_nodes,
-                                rec_g, crec_g, spill + p.spill_off(k, start), hdr);
-    else
-        coop_solve_chain(p, acc, k, start, n, lane, sm_rec, sm_crec, smem_nodes, rec_g, crec_g,
-                         spill + p.spill_off(k, start), hdr);
+    if constexpr (has_unary_g<P>::value) {
+        if (HALVES && n >= kSplitMinLen)
+            coop_solve_chain_halves_general(p, acc, k, start, n, lane, xch[warp], sm_rec,
+                                            smem_nodes, rec_g, spill + p.spill_off(k, start), hdr);
+        else
+            coop_solve_chain_general(p, acc, k, start, n, lane, sm_rec, smem_nodes, rec_g,
+                                     spill + p.spill_off(k, start), hdr);
+    } else {
+        if (HALVES && n >= kSplitMinLen)
+            coop_solve_chain_halves(p, acc, k, start, n, lane, xch[warp], sm_rec, sm_crec,
+                                    smem_nodes, rec_g, crec_g, spill + p.spill_off(k, start), hdr);
+        else
+            coop_solve_chain(p, acc, k, start, n, lane, sm_rec, sm_crec, smem_nodes, rec_g, crec_g,
+                             spill + p.spill_off(k, start), hdr);
+    }
     p.finish(acc, lane);
 }
 

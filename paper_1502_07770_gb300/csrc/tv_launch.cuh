@@ -56,7 +56,10 @@ tv_status launch_coop(const P &p, long long nchains, int max_len, float2 *rec, f
     if (nchains <= 0) return TV_OK;
     // chains long enough to split: two 16-lane halves in one warp (mode 1) or two
     // warps (mode 2, coop_pair_kernel)
-    const int mode = max_len >= tvk::kSplitMinLen ? coop_split() : 0;
+    int mode = max_len >= tvk::kSplitMinLen ? coop_split() : 0;
+    if constexpr (tvk::has_unary_g<P>::value) {
+        if (mode == 2) mode = 1;  // general chains: one warp per chain
+    }
     const bool pair = mode == 2 && wpb % 2 == 0;
     const int cpb = pair ? wpb / 2 : wpb;  // chains per block
     const long long blocks = (nchains + cpb - 1) / cpb;
@@ -66,8 +69,10 @@ tv_status launch_coop(const P &p, long long nchains, int max_len, float2 *rec, f
                       xchg + cpb * tvk::coop_smem_per_warp<P>(max_len) <= (size_t)200 * 1024;
     const int smem_nodes = fits ? max_len : 0;
     const size_t smem = xchg + cpb * tvk::coop_smem_per_warp<P>(smem_nodes);
-    auto kern = pair ? tvk::coop_pair_kernel<P>
-                     : (mode == 1 ? tvk::coop_chain_kernel<P, true> : tvk::coop_chain_kernel<P, false>);
+    auto kern = mode == 1 ? tvk::coop_chain_kernel<P, true> : tvk::coop_chain_kernel<P, false>;
+    if constexpr (!tvk::has_unary_g<P>::value) {
+        if (pair) kern = tvk::coop_pair_kernel<P>;
+    }
     tv_status st = check_cuda(
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
         "cudaFuncSetAttribute");
