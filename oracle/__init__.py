@@ -11,5 +11,6 @@ from .oracle import (  # noqa: F401
     chain_solve_general,
     chain_vjp,
     rof_primal,
+    tv2d_lagrangian,
     tv2d_pd,
 )

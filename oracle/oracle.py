@@ -43,6 +43,10 @@ def _load():
             lib.tvo_chain_solve_batch.argtypes = [_D, _D, ctypes.c_double, _I64, ctypes.c_int64,
                                                   _D, ctypes.c_int, _I64]
             lib.tvo_chain_solve_general_batch.argtypes = [_D, _D, _D, _D, _I64, ctypes.c_int64, _D]
+            lib.tvo_tv2d_lagrangian.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                 ctypes.c_double, ctypes.c_int, ctypes.c_int, _D,
+                                                 ctypes.POINTER(ctypes.c_int), _D]
             lib.tvo_chain_vjp.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, _D, _D]
             lib.tvo_rof_primal.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D,
                                            ctypes.c_double, _D]
@@ -170,3 +174,25 @@ def tv2d_pd(f, lam=0.0, w_h=None, w_v=None, y0=None, max_iters=1000, tol=1e-4, t
         raise RuntimeError(f"oracle tv2d failed: {st}")
     out = (x, int(it.value), trace[:int(it.value)], st == 0)
     return out + (y,) if return_y else out
+
+
+def tv2d_lagrangian(f, lam=0.0, w_h=None, w_v=None, tau0=100.0, max_iters=500, tol=1e-4,
+                    check_every=5, nthreads=None):
+    """ROF by the symmetric Lagrangian split of Sec. 6 (x_h, x_v, y) with tau_k = tau0 / k.
+
+    Returns ``(x, iters, gap_trace, converged)``; ``gap_trace[k-1]`` is the per-pixel
+    gap after iteration k where it was checked (NaN elsewhere).
+    """
+    lib = _load()
+    f = _f64(f)
+    H, W = f.shape
+    nthreads = nthreads or os.cpu_count() or 1
+    x = np.empty((H, W))
+    trace = np.full(max_iters, np.nan)
+    it = ctypes.c_int(0)
+    st = lib.tvo_tv2d_lagrangian(H, W, _p(f), _p(_f64(w_h)), _p(_f64(w_v)), float(lam),
+                                 float(tau0), int(max_iters), float(tol), int(check_every),
+                                 int(nthreads), _p(x), ctypes.byref(it), _p(trace))
+    if st not in (0, 3):
+        raise RuntimeError(f"oracle tv2d_lagrangian failed: {st}")
+    return x, int(it.value), trace[:int(it.value)], st == 0
