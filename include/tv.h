@@ -248,6 +248,26 @@ tv_status tv2d_denoise_batched(const tv_image_desc *imgs, int n_imgs, int max_it
                                double gap_tol, int *iters_out, double *gap_out,
                                void *d_workspace, size_t workspace_bytes, tv_stream_t stream);
 
+/*
+ * ROF denoising by the symmetric Lagrangian split of Sec. 6 (the form the paper uses
+ * for stereo, here on the convex ROF model): x_h (rows) and x_v (columns) each carry half
+ * of the data term and are coupled by a multiplier y,
+ *     min_{x_h, x_v} max_y TV_h(x_h) + 1/4||x_h - f||^2 + TV_v(x_v) + 1/4||x_v - f||^2 + <x_h - x_v, y>,
+ * with the primal-dual iteration of Sec. 6: tau_k = tau0 / k, sigma_k = 1 / (2 tau_k),
+ * over-relaxation 1; start x_h = x_v = f, y = 0. Every check_every iterations (and at
+ * max_iters) the per-pixel gap (P(xbar) - D(y)) / (H W) is evaluated, xbar = (x_h + x_v)/2,
+ * D the Lagrangian dual (one extra row and column chain batch); the solve stops when it
+ * is <= gap_tol (0: never early). d_x receives xbar. Arguments otherwise as
+ * tv2d_denoise; workspace of tv2d_lagrangian_workspace_size bytes. Returns TV_OK or
+ * TV_ERR_NOT_CONVERGED (x still written); synchronous at every gap check.
+ */
+size_t tv2d_lagrangian_workspace_size(int64_t H, int64_t W);
+tv_status tv2d_denoise_lagrangian(const float *d_img, int64_t H, int64_t W, const float *d_wh,
+                                  const float *d_wv, float lambda, float tau0, int max_iters,
+                                  double gap_tol, int check_every, float *d_x, int *iters_out,
+                                  double *gap_out, void *d_workspace, size_t workspace_bytes,
+                                  tv_stream_t stream);
+
 /* How the calling thread's last tv2d_denoise_batched ran its iterations: 1 as one
  * CUDA graph with a device-side loop condition, 0 replayed from the host (conditional
  * graph nodes unavailable, or disabled), -1 no batched solve yet. */

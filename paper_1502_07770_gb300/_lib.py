@@ -60,6 +60,11 @@ SIGNATURES = {
     "tv2d_batched_last_mode": (ctypes.c_int, []),
     "tv_set_batched_graph": (ctypes.c_int, [ctypes.c_int]),
     "tv_set_coop_max_chains": (ctypes.c_int, [_i64]),
+    "tv2d_lagrangian_workspace_size": (_sz, [_i64, _i64]),
+    "tv2d_denoise_lagrangian": (ctypes.c_int, [_p, _i64, _i64, _p, _p, ctypes.c_float,
+                                               ctypes.c_float, ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_int, _p, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_double), _p, _sz, _p]),
     "tv_chain_solve_general": (ctypes.c_int, [_p, _p, _p, _p, _p, _i64, _i64, _p, _p, _sz, _p]),
     "tv_set_coop_split": (ctypes.c_int, [ctypes.c_int]),
     "tv_net_conv3x3": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -315,6 +320,30 @@ def tv2d_denoise(img, lam: float = 0.1, w_h=None, w_v=None, y0=None, max_iters: 
     st = lib.tv2d_denoise(_ptr(img), H, W, _ptr(w_h), _ptr(w_v), float(lam), _ptr(y0),
                           int(max_iters), float(tol), _ptr(x), ctypes.byref(it),
                           ctypes.byref(gap), _ptr(wsb), wsb.numel(), _stream(img.device))
+    if st not in (TV_OK, TV_ERR_NOT_CONVERGED):
+        _check(st)
+    return x, it.value, gap.value, st == TV_OK
+
+
+def tv2d_denoise_lagrangian(img, lam: float = 0.1, w_h=None, w_v=None, tau0: float = 10.0,
+                            max_iters: int = 500, tol: float = 1e-4, check_every: int = 5,
+                            out=None, ws=None):
+    """ROF by the symmetric Lagrangian split (x_h, x_v, y) of Sec. 6 with tau_k = tau0 / k.
+
+    Returns ``(x, iterations, per-pixel gap, converged)``.
+    """
+    lib = load()
+    _require_cuda(img, w_h, w_v)
+    H, W = img.shape
+    x = torch.empty_like(img) if out is None else out
+    nbytes = lib.tv2d_lagrangian_workspace_size(H, W)
+    wsb = ws if ws is not None else workspace(nbytes, img.device, "lagrangian")
+    it = ctypes.c_int(0)
+    gap = ctypes.c_double(0.0)
+    st = lib.tv2d_denoise_lagrangian(_ptr(img), H, W, _ptr(w_h), _ptr(w_v), float(lam),
+                                     float(tau0), int(max_iters), float(tol), int(check_every),
+                                     _ptr(x), ctypes.byref(it), ctypes.byref(gap), _ptr(wsb),
+                                     wsb.numel(), _stream(img.device))
     if st not in (TV_OK, TV_ERR_NOT_CONVERGED):
         _check(st)
     return x, it.value, gap.value, st == TV_OK

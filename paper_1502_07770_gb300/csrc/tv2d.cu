@@ -4,14 +4,13 @@
 //
 // Per iteration k, two fused kernels run the chain dynamic program of
 // Algorithm 2 / Sec. 4.1 with the proximal arithmetic folded into their loads
-// and stores:
-//   column (dual) phase, one thread per image column:
+// and stores (one warp per chain for up to 2048 chains, else one thread):
+//   column (dual) phase, one chain per image column:
 //       eta = y + sigma_k (x^k + theta_{k-1} (x^k - x^{k-1}))
 //       xhat = argmin TV_v(x) + sigma_k/2 ||x - eta/sigma_k||^2  (chains: c = eta/sigma_k,
 //              w' = w_v/sigma_k)
 //       y <- eta - sigma_k xhat                                   (eq. prox-tv-conj)
-//     and, from the same loads, the terms of the primal-dual gap G_{k-1};
-//   row (primal) phase, one thread per image row:
+//   row (primal) phase, one chain per image row:
 //       x^{k+1} = argmin TV_h(x) + (1+1/tau_k)/2 ||x - (f + (x^k - tau_k y)/tau_k)/(1+1/tau_k)||^2
 //              (chains: c = (tau f + x^k - tau y)/(tau+1), w' = w_h tau/(tau+1)).
 // Step sizes follow the accelerated variant: theta_k = 1/sqrt(1+2 tau_k),
@@ -22,11 +21,10 @@
 // f - D_h^T p_h - D_v^T p_v = x^{k+1} + (x^{k+1} - x^k)/tau_k),
 //   G_k = P(x^{k+1}) - D(p) = 1/2||x^{k+1} - f||^2 + TV(x^{k+1}) - 1/2||f||^2
 //         + 1/2||x^{k+1} + (x^{k+1} - x^k)/tau_k||^2 >= 0.
-// The column phase of iteration k+1 reads exactly x^{k+1}, x^k and f, and has
-// vertical neighbours along its chains and horizontal ones across its lanes, so
-// it accumulates G_k per pixel; the last warp to finish reduces the partials in
-// FP64 (fixed order) and raises the stop flag. Later kernels see the flag and
-// return at once, so a batch of launched iterations costs nothing after it.
+// A gap kernel after each row phase reads x^{k+1}, x^k and f, accumulates G_k per
+// pixel (FP32 over at most 32 pixels per thread, FP64 beyond); its last block sums
+// the block partials in a fixed order and raises the stop flag. Later kernels see
+// the flag and return at once, so a batch of launched iterations costs little after it.
 #include <cuda_runtime.h>
 #include <math.h>
 
