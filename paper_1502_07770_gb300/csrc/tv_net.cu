@@ -87,95 +87,166 @@ __device__ __forceinline__ void load_patch(__nv_bfloat16 *patch, const __nv_bflo
     }
 }
 
-// Output-tile convolution. MODE 0: forward, out = conv + bias, optional ReLU;
-// writes the FP32 pre-activation (if pre_out) and the BF16 activation.
-// MODE 1: backward data: out = conv (weights already flipped/transposed), times
-// the ReLU mask (mask_pre > 0) of the layer below; writes BF16.
+// The same patch with 16-byte asynchronous copies (zero-filled outside the image).
+__device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, bool valid)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_net() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_net()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int C>
+__device__ __forceinline__ void load_patch_async(__nv_bfloat16 *patch, const __nv_bfloat16 *X,
+                                                 int b, int H, int W, int y0, int x0)
+{
+    constexpr int PS = C + 8;
+    constexpr int V = C / 8;
+    for (int t = threadIdx.x; t < PH * PW * V; t += blockDim.x) {
+        const int v = t % V, pix = t / V;
+        const int py = pix / PW, px = pix % PW;
+        const int gy = y0 + py - 1, gx = x0 + px - 1;
+        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const __nv_bfloat16 *src = in ? X + (((long long)b * H + gy) * W + gx) * C + v * 8 : X;
+        cp_async16_zfill(patch + pix * PS + v * 8, src, in);
+    }
+}
+
+// Output-tile convolution, persistent: each block loads the weights once and walks the
+// 8 x 16 output tiles blockIdx.x, +gridDim.x, ..., prefetching the next tile's input
+// patch with asynchronous copies (double buffer) while the tensor cores work on the
+// current one. MODE 0: forward, out = conv + bias, optional ReLU; writes the FP32
+// pre-activation (if pre_out) and the BF16 activation (if act_out). MODE 1: backward
+// data: out = conv (weights already flipped/transposed), times the ReLU mask
+// (mask_pre > 0) of the layer below; writes BF16.
+template <int CIN, int COUT>
+constexpr size_t conv_persist_smem()
+{
+    return sizeof(__nv_bfloat16) * ((size_t)COUT * (9 * CIN + 8) + 2 * (size_t)PH * PW * (CIN + 8));
+}
+
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(NTHR)
-    conv3x3_tile(const __nv_bfloat16 *X, int H, int W, const __nv_bfloat16 *Wt, const float *bias,
-                 int relu, const float *mask_pre, float *pre_out, __nv_bfloat16 *act_out)
+    conv3x3_persist(const __nv_bfloat16 *X, int B, int H, int W, const __nv_bfloat16 *Wt,
+                    const float *bias, int relu, const float *mask_pre, float *pre_out,
+                    __nv_bfloat16 *act_out)
 {
     constexpr int PS = CIN + 8;
     constexpr int K = 9 * CIN;
-    constexpr int KS = K + 8;      // padded weight row (bf16)
-    constexpr int NT = COUT / 8;   // n8 tiles
-    __shared__ __align__(16) __nv_bfloat16 patch[PH * PW * PS];
-    __shared__ __align__(16) __nv_bfloat16 wsm[COUT * KS];
-    const int b = blockIdx.z, y0 = blockIdx.y * TH, x0 = blockIdx.x * TW;
+    constexpr int KS = K + 8;
+    constexpr int NT = COUT / 8;
+    constexpr int PATCH = PH * PW * PS;
+    extern __shared__ __align__(16) unsigned char smem_net[];
+    __nv_bfloat16 *wsm = reinterpret_cast<__nv_bfloat16 *>(smem_net);
+    __nv_bfloat16 *pbuf = wsm + COUT * KS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    const int per_img = tiles_x * tiles_y;
+    const long long ntiles = (long long)B * per_img;
+    auto origin = [&](long long tile, int &b, int &y0, int &x0) {
+        b = (int)(tile / per_img);
+        const int rem = (int)(tile - (long long)b * per_img);
+        y0 = (rem / tiles_x) * TH;
+        x0 = (rem % tiles_x) * TW;
+    };
+    long long tile = blockIdx.x;
+    if (tile < ntiles) {
+        int b, y0, x0;
+        origin(tile, b, y0, x0);
+        load_patch_async<CIN>(pbuf, X, b, H, W, y0, x0);
+    }
+    cp_async_commit_net();
     for (int t = threadIdx.x; t < COUT * (K / 8); t += blockDim.x) {
         const int n = t / (K / 8), v = t % (K / 8);
         *reinterpret_cast<uint4 *>(wsm + n * KS + v * 8) =
             *reinterpret_cast<const uint4 *>(Wt + (long long)n * K + v * 8);
     }
-    load_patch<CIN>(patch, X, b, H, W, y0, x0);
-    __syncthreads();
-
-    float acc[2][NT][4];
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int j = 0; j < NT; ++j) acc[m][j][0] = acc[m][j][1] = acc[m][j][2] = acc[m][j][3] = 0.f;
-    // warp w owns tile rows 2w and 2w+1 (16 pixels each = one m16 tile each)
-    const int arow = lane & 15;            // A row = pixel column within the tile row
-    const int acol = (lane >> 4) * 8;      // A k offset (channels) 0 or 8
-    const int brow = lane & 7;             // B row = output channel within an n8 tile
+    const int arow = lane & 15;
+    const int acol = (lane >> 4) * 8;
+    const int brow = lane & 7;
     const int bcol = ((lane >> 3) & 1) * 8;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3;
-#pragma unroll
-        for (int c0 = 0; c0 < CIN; c0 += 16) {
-            const int k0 = tap * CIN + c0;
-            unsigned bf[NT][2];
-#pragma unroll
-            for (int j = 0; j < NT; ++j)
-                ldsm_x2(smem_u32(wsm + (j * 8 + brow) * KS + k0 + bcol), bf[j][0], bf[j][1]);
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const int py = warp * 2 + m + ky, px = arow + kx;
-                unsigned a0, a1, a2, a3;
-                ldsm_x4(smem_u32(patch + (py * PW + px) * PS + c0 + acol), a0, a1, a2, a3);
-#pragma unroll
-                for (int j = 0; j < NT; ++j) mma_bf16(acc[m][j], a0, a1, a2, a3, bf[j][0], bf[j][1]);
-            }
-        }
-    }
-    // epilogue: C fragment rows = pixels (groupID, groupID + 8), cols = channels
     const int g = lane >> 2, tq = lane & 3;
+    int buf = 0;
+    for (; tile < ntiles; tile += gridDim.x) {
+        const long long next = tile + gridDim.x;
+        if (next < ntiles) {
+            int b, y0, x0;
+            origin(next, b, y0, x0);
+            load_patch_async<CIN>(pbuf + (buf ^ 1) * PATCH, X, b, H, W, y0, x0);
+        }
+        cp_async_commit_net();
+        cp_async_wait_net<1>();
+        __syncthreads();
+        const __nv_bfloat16 *patch = pbuf + buf * PATCH;
+        float acc[2][NT][4];
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        const int y = y0 + warp * 2 + m;
+        for (int m = 0; m < 2; ++m)
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int x = x0 + g + half * 8;
-            if (y >= H || x >= W) continue;
-            const long long base = (((long long)b * H + y) * W + x) * COUT;
+            for (int j = 0; j < NT; ++j) acc[m][j][0] = acc[m][j][1] = acc[m][j][2] = acc[m][j][3] = 0.f;
 #pragma unroll
-            for (int j = 0; j < NT; ++j) {
-                const int co = j * 8 + tq * 2;
-                float v0 = acc[m][j][half * 2 + 0], v1 = acc[m][j][half * 2 + 1];
-                if (MODE == 0) {
-                    if (bias) {
-                        v0 += bias[co];
-                        v1 += bias[co + 1];
-                    }
-                    if (pre_out) *reinterpret_cast<float2 *>(pre_out + base + co) = make_float2(v0, v1);
-                    if (relu) {
-                        v0 = fmaxf(v0, 0.f);
-                        v1 = fmaxf(v1, 0.f);
-                    }
-                } else {
-                    const float2 mp = *reinterpret_cast<const float2 *>(mask_pre + base + co);
-                    v0 = mp.x > 0.f ? v0 : 0.f;
-                    v1 = mp.y > 0.f ? v1 : 0.f;
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+            for (int c0 = 0; c0 < CIN; c0 += 16) {
+                const int k0 = tap * CIN + c0;
+                unsigned bf[NT][2];
+#pragma unroll
+                for (int j = 0; j < NT; ++j)
+                    ldsm_x2(smem_u32(wsm + (j * 8 + brow) * KS + k0 + bcol), bf[j][0], bf[j][1]);
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int py = warp * 2 + m + ky, px = arow + kx;
+                    unsigned a0, a1, a2, a3;
+                    ldsm_x4(smem_u32(patch + (py * PW + px) * PS + c0 + acol), a0, a1, a2, a3);
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) mma_bf16(acc[m][j], a0, a1, a2, a3, bf[j][0], bf[j][1]);
                 }
-                if (act_out)
-                    *reinterpret_cast<__nv_bfloat162 *>(act_out + base + co) = __floats2bfloat162_rn(v0, v1);
             }
         }
+        int b, y0, x0;
+        origin(tile, b, y0, x0);
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int y = y0 + warp * 2 + m;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int x = x0 + g + half * 8;
+                if (y >= H || x >= W) continue;
+                const long long base = (((long long)b * H + y) * W + x) * COUT;
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                    const int co = j * 8 + tq * 2;
+                    float v0 = acc[m][j][half * 2 + 0], v1 = acc[m][j][half * 2 + 1];
+                    if (MODE == 0) {
+                        if (bias) {
+                            v0 += bias[co];
+                            v1 += bias[co + 1];
+                        }
+                        if (pre_out) *reinterpret_cast<float2 *>(pre_out + base + co) = make_float2(v0, v1);
+                        if (relu) {
+                            v0 = fmaxf(v0, 0.f);
+                            v1 = fmaxf(v1, 0.f);
+                        }
+                    } else {
+                        const float2 mp = *reinterpret_cast<const float2 *>(mask_pre + base + co);
+                        v0 = mp.x > 0.f ? v0 : 0.f;
+                        v1 = mp.y > 0.f ? v1 : 0.f;
+                    }
+                    if (act_out)
+                        *reinterpret_cast<__nv_bfloat162 *>(act_out + base + co) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+        __syncthreads();  // every warp is done with this buffer before it is refilled
+        buf ^= 1;
     }
+    cp_async_wait_net<0>();
 }
 
 // Partial sums of dW[co][tap][ci] = sum over pixels p of dY[p][co] * X[p + tap][ci]
@@ -312,9 +383,25 @@ tv_status launch_conv(const __nv_bfloat16 *X, int B, int H, int W, const __nv_bf
                       const float *bias, int relu, const float *mask_pre, float *pre_out,
                       __nv_bfloat16 *act_out, cudaStream_t s)
 {
-    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, B);
-    conv3x3_tile<CIN, COUT, MODE><<<grid, NTHR, 0, s>>>(X, H, W, Wt, bias, relu, mask_pre, pre_out,
-                                                         act_out);
+    auto kern = conv3x3_persist<CIN, COUT, MODE>;
+    constexpr size_t smem = conv_persist_smem<CIN, COUT>();
+    static int per_sm = 0;  // resident blocks per SM (occupancy, computed once per kernel)
+    if (per_sm == 0) {
+        tv_status st0 = check_cuda(
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "cudaFuncSetAttribute");
+        if (st0 != TV_OK) return st0;
+        int b = 0;
+        st0 = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NTHR, smem),
+                         "occupancy");
+        if (st0 != TV_OK) return st0;
+        per_sm = b < 1 ? 1 : b;
+    }
+    const long long ntiles = (long long)B * ((W + TW - 1) / TW) * ((H + TH - 1) / TH);
+    long long blocks = (long long)per_sm * sm_count_current();
+    if (blocks > ntiles) blocks = ntiles;
+    kern<<<(unsigned)blocks, NTHR, smem, s>>>(X, B, H, W, Wt, bias, relu, mask_pre, pre_out,
+                                                act_out);
     tv_status st = check_cuda(cudaGetLastError(), "conv launch");
     if (st == TV_OK) note_launch();
     return st;
