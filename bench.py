@@ -178,6 +178,18 @@ def cpu_baseline(f, seconds):
                       f"{threads} threads, {el:.1f} s"}
 
 
+def max_over_ranks(value, device, world):
+    """The largest of each rank's value (the job's time is its slowest rank's); the value
+    itself with one rank. Uses the initialised default process group."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     """The oracle arm: the FP64 CPU oracle on the same workload, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -271,10 +283,7 @@ def main():
     _lib.profile_enable(False)
     clk = clocks.stop()
     ms_step = float(np.sum(step_ms)) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, dev, world)
 
     # ---------------- end to end through host buffers ----------------
     h_in = torch.from_numpy(f_np).pin_memory()
@@ -292,10 +301,7 @@ def main():
         if it >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = float(np.mean(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(e2e, dev, world)
 
     # ---------------- batched chain prox (Gnode/s) ----------------
     base = synth.chain_batch(256, CHAIN_N, seed0=1000)
