@@ -680,11 +680,10 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
     }
     __syncwarp();
     if (!ok) {
-        if (lane == 0) {
-            atomicAdd(&hdr->overflowed, 1ull);
-            solve_chain_global_lane0(p, k, start, n, spill, rec_g + k * (long long)max_len, crecp);
-        }
-        __syncwarp();
+        // a half outgrew 16 breakpoints: solve the chain from one end with all 32 lanes
+        // (which itself falls back to lane 0 beyond 32)
+        coop_solve_chain(p, acc, k, start, n, lane, sm_rec, sm_crec, smem_nodes, rec_g, crec_g,
+                         spill, hdr);
         return;
     }
     PairMsg &mine = xc.m[half];
@@ -964,11 +963,8 @@ __device__ void coop_solve_chain_halves_general(const P &p, typename P::Acc &acc
     }
     __syncwarp();
     if (!ok) {
-        if (lane == 0) {
-            atomicAdd(&hdr->overflowed, 1ull);
-            solve_chain_general_lane0(p, k, start, n, spill, rec_g + k * (long long)max_len);
-        }
-        __syncwarp();
+        // a half outgrew 16 breakpoints: the whole warp from one end (then lane 0)
+        coop_solve_chain_general(p, acc, k, start, n, lane, sm_rec, smem_nodes, rec_g, spill, hdr);
         return;
     }
     PairMsg &mine = xc.m[half];

@@ -224,3 +224,17 @@ def test_thread_kernel_closed_forms(thread_path):
     yk = synth.chain_batch(32, 1024, seed0=21)
     for k in range(32):
         assert pins.kkt_residual(yk[k], 0.15, x[k]) < 2e-3
+
+
+def test_half_overflow_falls_back_to_the_whole_warp():
+    """A chain whose left half needs ~22 breakpoints: more than a 16-lane half holds, fewer
+    than the 32 lanes of the whole warp, which solves it without the lane-0 path."""
+    n = 80
+    base = np.concatenate([(-np.arange(40) / 40.0), np.random.default_rng(0).uniform(0, 1, 40)])
+    y = np.tile(base.astype(np.float32), (16, 1))
+    w = np.tile(np.concatenate([np.full(40, 2.5), np.full(40, 0.05)]).astype(np.float32), (16, 1))
+    ws = _lib.workspace(_lib.load().tv_chain_workspace_size(16, n), DEV, "half-overflow")
+    x = _lib.chain_prox(_gpu(y), _gpu(w), ws=ws).cpu().numpy()
+    assert _lib.workspace_status(ws)[1] == 0  # never reached the lane-0 path
+    xr = oracle.chain_solve_batch(y.ravel(), np.arange(17) * n, w=w.ravel()).reshape(y.shape)
+    assert np.abs(x - xr).max() <= TOL
