@@ -47,6 +47,7 @@ def _load():
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, _D,
                                                  ctypes.POINTER(ctypes.c_int), _D]
+            lib.tvo_chain_solve_pq_batch.argtypes = [_D, _D, _D, _D, _D, _I64, ctypes.c_int64, _D]
             lib.tvo_chain_vjp.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, _D, _D]
             lib.tvo_rof_primal.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D,
                                            ctypes.c_double, _D]
@@ -196,3 +197,20 @@ def tv2d_lagrangian(f, lam=0.0, w_h=None, w_v=None, tau0=100.0, max_iters=500, t
     if st not in (0, 3):
         raise RuntimeError(f"oracle tv2d_lagrangian failed: {st}")
     return x, int(it.value), trace[:int(it.value)], st == 0
+
+
+def chain_solve_pq(a, b, alpha, f, w, offsets=None):
+    """Chains with piecewise-quadratic unaries a_i x^2/2 - b_i x + alpha_i |x - f_i| and TV
+    weights w (Sec. 4.2): one entry per node (w at a chain's last node unused); CSR
+    ``offsets`` (default: one chain)."""
+    a, b, alpha, f, w = (_f64(v) for v in (a, b, alpha, f, w))
+    n = b.size
+    if offsets is None:
+        offsets = np.array([0, n], dtype=np.int64)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    x = np.empty(n, dtype=np.float64)
+    st = _load().tvo_chain_solve_pq_batch(_p(a), _p(b), _p(alpha), _p(f), _p(w),
+                                          offsets.ctypes.data_as(_I64), offsets.size - 1, _p(x))
+    if st != 0:
+        raise ValueError(f"oracle piecewise-quadratic chain solve failed ({st})")
+    return x

@@ -781,3 +781,144 @@ int tvo_tv2d_lagrangian(int H, int W, const double *f, const double *wh, const d
     if (st != TVO_OK) return st;
     return done ? TVO_OK : TVO_NOT_CONVERGED;
 }
+
+
+/* ---------------- piecewise-quadratic unaries on a chain (Sec. 4.2) ----------------
+ *
+ * x* = argmin sum_i (a_i x_i^2/2 - b_i x_i + alpha_i |x_i - f_i|) + sum_{i<n} w_i |x_{i+1} - x_i|,
+ * a_i > 0, alpha_i >= 0, w_i >= 0: the convex chain of Algorithm 2 whose unary derivatives
+ * g_i(z) = a_i z - b_i + alpha_i sign(z - f_i) are piecewise linear with a jump of
+ * 2 alpha_i at f_i (the piecewise-quadratic unaries of Sec. 4.2). The message (a
+ * derivative) is stored explicitly, obviously rather than fast: sorted breakpoints
+ * lam[0..t-1] and the linear function A_p z + B_p of every piece p = 0..t (piece p lies
+ * between lam[p-1] and lam[p], with lam[-1] = -inf and lam[t] = +inf); values jump up at
+ * breakpoints. The message into node 0 is 0 (one piece, A = B = 0). At node i: add g_i
+ * to every piece, inserting f_i as a breakpoint; clip to [-w_i, w_i]:
+ *   lambda^- = sup{z : m^_i(z) < -w_i},  lambda^+ = inf{z : m^_i(z) > w_i},
+ * the new message is -w_i left of lambda^-, m^_i between, +w_i right of lambda^+; the last
+ * node has w = 0 and x_{n-1} = lambda^- = lambda^+. Backward: x_i = clip(x_{i+1}, lambda^-_i,
+ * lambda^+_i) (Algorithm 2).
+ */
+typedef struct {
+    int64_t t;     /* number of breakpoints */
+    double *lam;   /* breakpoints */
+    double *A, *B; /* pieces 0..t */
+} tvo_pwl;
+
+/* m^ = m + g: a z - b on every piece, -alpha left of f and +alpha right of it. */
+static void pq_add(tvo_pwl *h, double a, double b, double alpha, double f)
+{
+    int64_t pos = 0; /* pieces 0..pos lie left of f, pos+1..t right of it */
+    while (pos < h->t && h->lam[pos] < f) ++pos;
+    if (!(pos < h->t && h->lam[pos] == f)) {
+        for (int64_t q = h->t; q > pos; --q) h->lam[q] = h->lam[q - 1];
+        for (int64_t q = h->t + 1; q > pos; --q) {
+            h->A[q] = h->A[q - 1];
+            h->B[q] = h->B[q - 1];
+        }
+        h->lam[pos] = f;
+        h->t += 1;
+    }
+    for (int64_t p = 0; p <= h->t; ++p) {
+        h->A[p] += a;
+        h->B[p] += -b + (p <= pos ? -alpha : alpha);
+    }
+}
+
+/* Clip to [wlo, whi]; returns lambda^-, lambda^+. `o` is scratch of the same capacity. */
+static void pq_clip(tvo_pwl *h, double wlo, double whi, double *lm, double *hp, tvo_pwl *o)
+{
+    const int64_t t = h->t;
+    int64_t pl = t, pr = 0;
+    double l = 0.0, r = 0.0;
+    for (int64_t p = 0; p <= t; ++p) {
+        const double end = (p < t) ? h->A[p] * h->lam[p] + h->B[p] : INFINITY;
+        if (end >= wlo) { /* the crossing is in piece p, or at the jump into it */
+            const double z = (wlo - h->B[p]) / h->A[p];
+            l = (p > 0 && z < h->lam[p - 1]) ? h->lam[p - 1] : z;
+            pl = p;
+            break;
+        }
+    }
+    for (int64_t p = t; p >= 0; --p) {
+        const double start = (p > 0) ? h->A[p] * h->lam[p - 1] + h->B[p] : -INFINITY;
+        if (start <= whi) { /* the crossing is in piece p, or at the jump out of it */
+            const double z = (whi - h->B[p]) / h->A[p];
+            r = (p < t && z > h->lam[p]) ? h->lam[p] : z;
+            pr = p;
+            break;
+        }
+    }
+    *lm = l;
+    *hp = r;
+    /* breakpoints lambda^-, lam[pl..pr-1], lambda^+; pieces wlo, pl..pr, whi */
+    int64_t nt = 0;
+    o->lam[nt++] = l;
+    o->A[0] = 0.0;
+    o->B[0] = wlo;
+    for (int64_t p = pl; p <= pr; ++p) {
+        if (p > pl) o->lam[nt++] = h->lam[p - 1];
+        o->A[nt] = h->A[p];
+        o->B[nt] = h->B[p];
+    }
+    if (pl > pr) { /* one jump of m^ crosses both levels: lambda^- = lambda^+, a zero-length
+                      piece between them at the lower level */
+        o->A[nt] = 0.0;
+        o->B[nt] = wlo;
+    }
+    o->lam[nt++] = r;
+    o->A[nt] = 0.0;
+    o->B[nt] = whi;
+    o->t = nt;
+    /* swap the buffers */
+    tvo_pwl tmp = *h;
+    *h = *o;
+    *o = tmp;
+}
+
+static int chain_pq_core(int64_t n, const double *a, const double *b, const double *alpha,
+                         const double *f, const double *w, double *x)
+{
+    if (n <= 0) return TVO_OK;
+    const int64_t cap = 3 * n + 8;
+    double *buf = (double *)malloc(sizeof(double) * (size_t)(6 * cap + 2 * n));
+    if (!buf) return TVO_ERR_NOMEM;
+    tvo_pwl h = {0, buf, buf + cap, buf + 2 * cap};
+    tvo_pwl o = {0, buf + 3 * cap, buf + 4 * cap, buf + 5 * cap};
+    double *lo = buf + 6 * cap, *hi = lo + n;
+    h.A[0] = 0.0;
+    h.B[0] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        pq_add(&h, a[i], b[i], alpha[i], f[i]);
+        const double wi = (i < n - 1) ? w[i] : 0.0;
+        pq_clip(&h, -wi, wi, &lo[i], &hi[i], &o);
+    }
+    x[n - 1] = 0.5 * (lo[n - 1] + hi[n - 1]);
+    for (int64_t i = n - 2; i >= 0; --i) {
+        double v = x[i + 1];
+        if (v < lo[i]) v = lo[i];
+        if (v > hi[i]) v = hi[i];
+        x[i] = v;
+    }
+    free(buf);
+    return TVO_OK;
+}
+
+/* Chains with piecewise-quadratic unaries in a CSR batch (one thread); w at a chain's
+ * last node unused. */
+int tvo_chain_solve_pq_batch(const double *a, const double *b, const double *alpha,
+                             const double *f, const double *w, const int64_t *offsets,
+                             int64_t num_chains, double *x)
+{
+    if (num_chains < 0 || !offsets) return TVO_ERR_INVALID;
+    for (int64_t k = 0; k < num_chains; ++k) {
+        const int64_t o = offsets[k], len = offsets[k + 1] - offsets[k];
+        if (len < 0) return TVO_ERR_INVALID;
+        for (int64_t i = 0; i < len; ++i)
+            if (!(a[o + i] > 0.0) || !(alpha[o + i] >= 0.0) || (i < len - 1 && !(w[o + i] >= 0.0)))
+                return TVO_ERR_INVALID;
+        const int st = chain_pq_core(len, a + o, b + o, alpha + o, f + o, w + o, x + o);
+        if (st != TVO_OK) return st;
+    }
+    return TVO_OK;
+}
