@@ -143,6 +143,26 @@ tv_status tv_chain_solve_general(const float *d_a, const float *d_b, const float
                                  size_t workspace_bytes, tv_stream_t stream);
 
 /*
+ * Chains with piecewise-quadratic unaries (Sec. 4.2):
+ *     x* = argmin_x sum_i (a_i x_i^2 / 2 - b_i x_i + alpha_i |x_i - f_i|) + sum_{i<n} w_i |x_{i+1} - x_i|,
+ * a_i > 0, alpha_i >= 0, w_i >= 0. This is the row proximal map of TV-l1 denoising
+ * (alpha = 1, a = 1/tau, b = xi/tau). One warp per chain; messages of more than 32
+ * breakpoints are finished by one thread from the workspace.
+ *   d_a        per-node curvature, or NULL for a_i = 1
+ *   d_b, d_f   per-node arrays laid out like d_y of tv_chain_solve
+ *   d_alpha    per-node l1 weights, or NULL: every node has `alpha`
+ *   d_w        per-node edge weights (entry at a chain's last node unused), or NULL: `lambda`
+ *   d_offsets, num_chains, max_len, d_x: as for tv_chain_solve
+ *   workspace  tv_chain_pq_workspace_size(num_chains, max_len) bytes
+ */
+size_t tv_chain_pq_workspace_size(int64_t num_chains, int64_t max_len);
+tv_status tv_chain_solve_pq(const float *d_a, const float *d_b, const float *d_alpha, float alpha,
+                            const float *d_f, const float *d_w, float lambda,
+                            const int64_t *d_offsets, int64_t num_chains, int64_t max_len,
+                            float *d_x, void *d_workspace, size_t workspace_bytes,
+                            tv_stream_t stream);
+
+/*
  * Backward of the chain prox (vector-Jacobian product), for a differentiable TV
  * layer. From the optimality conditions of eq. 1D-ROF, on every maximal run S of
  * equal values of the solution x ("segment"), x_S = mean(y_S) + (u_r - u_{l-1})/|S|

@@ -60,6 +60,9 @@ SIGNATURES = {
     "tv2d_batched_last_mode": (ctypes.c_int, []),
     "tv_set_batched_graph": (ctypes.c_int, [ctypes.c_int]),
     "tv_set_coop_max_chains": (ctypes.c_int, [_i64]),
+    "tv_chain_pq_workspace_size": (_sz, [_i64, _i64]),
+    "tv_chain_solve_pq": (ctypes.c_int, [_p, _p, _p, ctypes.c_float, _p, _p, ctypes.c_float, _p,
+                                         _i64, _i64, _p, _p, _sz, _p]),
     "tv2d_lagrangian_workspace_size": (_sz, [_i64, _i64]),
     "tv2d_denoise_lagrangian": (ctypes.c_int, [_p, _i64, _i64, _p, _p, ctypes.c_float,
                                                ctypes.c_float, ctypes.c_int, ctypes.c_double,
@@ -205,6 +208,33 @@ def chain_prox_general(b, wlo, whi, a=None, offsets=None, max_len: int | None = 
     _check(lib.tv_chain_solve_general(_ptr(a), _ptr(b), _ptr(wlo), _ptr(whi), _ptr(offsets),
                                       num_chains, max_len, _ptr(x), _ptr(wsb), wsb.numel(),
                                       _stream(b.device)))
+    return x
+
+
+def chain_prox_pq(b, f, a=None, alpha=1.0, w=None, lam: float = 0.0, offsets=None,
+                  max_len: int | None = None, out=None, ws=None):
+    """Chains with piecewise-quadratic unaries: argmin sum (a_i x_i^2/2 - b_i x_i +
+    alpha_i |x_i - f_i|) + sum w_i |x_{i+1} - x_i|. ``alpha`` and ``w`` are tensors or
+    scalars (``lam`` when ``w`` is None); layouts as :func:`chain_prox_general`."""
+    lib = load()
+    alpha_t = alpha if torch.is_tensor(alpha) else None
+    _require_cuda(b, f, a, alpha_t, w)
+    if offsets is None:
+        if b.dim() != 2:
+            raise ValueError("b must be (num_chains, n) when offsets is None")
+        num_chains, n = b.shape
+        max_len = n
+    else:
+        if max_len is None:
+            raise ValueError("max_len is required with offsets")
+        num_chains = offsets.numel() - 1
+    x = torch.empty_like(b) if out is None else out
+    nbytes = lib.tv_chain_pq_workspace_size(num_chains, max_len)
+    wsb = ws if ws is not None else workspace(nbytes, b.device, "pq")
+    _check(lib.tv_chain_solve_pq(_ptr(a), _ptr(b), _ptr(alpha_t),
+                                 0.0 if alpha_t is not None else float(alpha), _ptr(f), _ptr(w),
+                                 float(lam), _ptr(offsets), num_chains, max_len, _ptr(x),
+                                 _ptr(wsb), wsb.numel(), _stream(b.device)))
     return x
 
 

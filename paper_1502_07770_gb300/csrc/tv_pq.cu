@@ -1,0 +1,394 @@
+// Chains with piecewise-quadratic unaries (Sec. 4.2):
+//     x* = argmin_x sum_i (a_i x_i^2 / 2 - b_i x_i + alpha_i |x_i - f_i|) + sum_{i<n} w_i |x_{i+1} - x_i|,
+// the convex chain of Algorithm 2 whose unary derivatives g_i(z) = a_i z - b_i +
+// alpha_i sign(z - f_i) are piecewise linear with a jump of 2 alpha_i at f_i. It is the
+// row proximal map of TV-l1 denoising (Sec. 6): alpha = 1, a = 1/tau, b = xi/tau.
+//
+// One warp per chain. The message (a derivative) is held in registers, one breakpoint
+// per lane: its position lambda_k, the message's left and right limits L_k <= R_k there
+// (a jump where they differ) and its slope S_k on the piece to the right (0 right of the
+// last breakpoint); left of the first breakpoint it is constant at its left bound. Per
+// node: f_i is inserted (a ballot finds its place, one shuffle opens the slot), z - ... is
+// added to every limit (a_i lambda_k - b_i, -alpha_i left of f_i and +alpha_i right of it,
+// the jump 2 alpha_i at f_i), a_i to every slope; then the clip to [-w_i, w_i] finds
+//   lambda^- = sup{z : m^_i(z) < -w_i},  lambda^+ = inf{z : m^_i(z) > w_i}
+// either inside a piece (every lane computes its piece's crossings) or at a jump.
+// Backward: x_i = clip(x_{i+1}, lambda^-_i, lambda^+_i), 32 clips composed per step.
+// A message of more than 32 breakpoints is finished by lane 0 from global memory.
+#include <cuda_runtime.h>
+
+#include "tv_launch.cuh"
+
+using namespace tvk;
+using namespace tvh;
+
+namespace {
+
+struct PqState {
+    float lam, L, R, S;  // this lane's breakpoint
+    int size;
+    float lam0, L0;      // the first breakpoint and its left limit (every lane)
+    float wlo_p;         // the message's value left of its first breakpoint
+};
+
+// One node: returns the clip points; sets ovf (sticky) if more than 32 breakpoints
+// would be needed (the state is then meaningless).
+__device__ __forceinline__ void pq_update(PqState &s, float a, float b, float al, float f,
+                                          float wlo, float whi, int lane, bool &ovf, float &lm,
+                                          float &hp)
+{
+    bool valid = lane < s.size;
+    // ---- insert f (unless a breakpoint is already there) ----
+    const unsigned below = __ballot_sync(FULL, valid && s.lam < f);
+    const int ins = __popc(below);
+    const float lam_at = __shfl_sync(FULL, s.lam, ins & 31);
+    const bool exists = ins < s.size && lam_at == f;
+    if (!exists) {
+        if (s.size + 1 > WARP) ovf = true;
+        const int src = (ins - 1) & 31;
+        const float pl = __shfl_sync(FULL, s.lam, src), pR = __shfl_sync(FULL, s.R, src),
+                    pS = __shfl_sync(FULL, s.S, src);
+        float mval, Sn;
+        if (ins == 0) {
+            mval = s.size > 0 ? s.wlo_p : 0.f;  // the message's flat left end (0 before node 0)
+            Sn = 0.f;
+        } else {
+            mval = fmaf(pS, f - pl, pR);
+            Sn = pS;
+        }
+        const float ul = __shfl_up_sync(FULL, s.lam, 1), uL = __shfl_up_sync(FULL, s.L, 1),
+                    uR = __shfl_up_sync(FULL, s.R, 1), uS = __shfl_up_sync(FULL, s.S, 1);
+        if (lane == ins) {
+            s.lam = f;
+            s.L = mval;
+            s.R = mval;
+            s.S = Sn;
+        } else if (lane > ins) {
+            s.lam = ul;
+            s.L = uL;
+            s.R = uR;
+            s.S = uS;
+        }
+        s.size += 1;
+        valid = lane < s.size;
+    }
+    // ---- transformation (a): + a z - b - alpha left of f, + alpha right of it ----
+    {
+        const float lin = fmaf(a, s.lam, -b);
+        const float dl = (lane <= ins) ? -al : al;
+        const float dr = (lane < ins) ? -al : al;
+        s.L += lin + dl;
+        s.R += lin + dr;
+        s.S += a;
+    }
+    const float lam_n = __shfl_down_sync(FULL, s.lam, 1);
+    const bool last = lane == s.size - 1;
+    // crossings of wlo and whi on the piece right of this breakpoint (the last piece has
+    // slope a), clamped to the piece
+    float cL = fmaxf(s.lam + __fdividef(wlo - s.R, s.S), s.lam);
+    float cR = fmaxf(s.lam + __fdividef(whi - s.R, s.S), s.lam);
+    if (!last) {
+        cL = fminf(cL, lam_n);
+        cR = fminf(cR, lam_n);
+    }
+    const int ell = min((int)__reduce_min_sync(FULL, (unsigned)((valid && s.R >= wlo) ? lane : WARP)),
+                        s.size);
+    const int kl = __reduce_max_sync(FULL, (valid && s.L <= whi) ? lane : -1);
+    const float L0 = __shfl_sync(FULL, s.L, 0), lam0 = __shfl_sync(FULL, s.lam, 0);
+    const float Le = __shfl_sync(FULL, s.L, ell & 31), Re = __shfl_sync(FULL, s.R, ell & 31),
+                lame = __shfl_sync(FULL, s.lam, ell & 31), Se = __shfl_sync(FULL, s.S, ell & 31);
+    const float cLm = __shfl_sync(FULL, cL, (ell - 1) & 31), Sm = __shfl_sync(FULL, s.S, (ell - 1) & 31);
+    const float Lk = __shfl_sync(FULL, s.L, kl & 31), Rk = __shfl_sync(FULL, s.R, kl & 31),
+                lamk = __shfl_sync(FULL, s.lam, kl & 31), cRk = __shfl_sync(FULL, cR, kl & 31);
+    const bool jumpL = ell < s.size && Le < wlo;
+    const bool jumpR = kl >= 0 && Rk > whi;
+    const bool both = jumpL && jumpR && ell == kl;
+    float Sl;
+    if (jumpL) {
+        lm = lame;
+        Sl = Se;
+    } else if (ell == 0) {
+        lm = fminf(lam0 + (wlo - L0) / a, lam0);  // on the left end piece (slope a)
+        Sl = a;
+    } else {
+        lm = cLm;
+        Sl = Sm;
+    }
+    if (jumpR) hp = lamk;
+    else if (kl < 0) hp = fminf(lam0 + (whi - L0) / a, lam0);
+    else hp = cRk;
+    const int k0 = ell + (jumpL ? 1 : 0), k1 = kl - (jumpR ? 1 : 0);
+    const int K = k1 >= k0 ? k1 - k0 + 1 : 0;
+    if (K + 2 > WARP) ovf = true;
+    const float lmR = jumpL ? fminf(Re, whi) : wlo;
+    const float hpL = jumpR ? (both ? fminf(Re, whi) : fmaxf(Lk, wlo)) : whi;
+    const int src = (lane - 1 + k0) & 31;
+    const float nl = __shfl_sync(FULL, s.lam, src), nL = __shfl_sync(FULL, s.L, src),
+                nR = __shfl_sync(FULL, s.R, src), nS = __shfl_sync(FULL, s.S, src);
+    if (lane == 0) {
+        s.lam = lm;
+        s.L = wlo;
+        s.R = lmR;
+        s.S = both ? 0.f : Sl;
+    } else if (lane == K + 1) {
+        s.lam = hp;
+        s.L = hpL;
+        s.R = whi;
+        s.S = 0.f;
+    } else {
+        s.lam = nl;
+        s.L = nL;
+        s.R = nR;
+        s.S = nS;
+    }
+    s.size = K + 2;
+    s.wlo_p = wlo;
+}
+
+// Overflow path: lane 0, the same update on a global array of (lambda, L, R, S) entries
+// (4 * (3n + 4) floats), sequential and O(size) per node.
+struct PqEntry {
+    float lam, L, R, S;
+};
+
+__device__ void pq_lane0(int n, const float *a, const float *b, const float *al, const float *f,
+                         const float *w, float alpha, float lam, float *x, PqEntry *E,
+                         PqEntry *Etmp, float2 *rec)
+{
+    int size = 0;
+    float wlo_p = 0.f;
+    for (int i = 0; i < n; ++i) {
+        const float ai = a ? a[i] : 1.f, bi = b[i], ali = al ? al[i] : alpha, fi = f[i];
+        const float wi = (i < n - 1) ? (w ? w[i] : lam) : 0.f;
+        const float wlo = -wi, whi = wi;
+        int ins = 0;
+        while (ins < size && E[ins].lam < fi) ++ins;
+        const bool exists = ins < size && E[ins].lam == fi;
+        if (!exists) {
+            float mval = 0.f, Sn = 0.f;
+            if (ins == 0) mval = size > 0 ? wlo_p : 0.f;
+            else {
+                mval = fmaf(E[ins - 1].S, fi - E[ins - 1].lam, E[ins - 1].R);
+                Sn = E[ins - 1].S;
+            }
+            for (int q = size; q > ins; --q) E[q] = E[q - 1];
+            E[ins] = PqEntry{fi, mval, mval, Sn};
+            ++size;
+        }
+        for (int k = 0; k < size; ++k) {
+            const float lin = fmaf(ai, E[k].lam, -bi);
+            E[k].L += lin + (k <= ins ? -ali : ali);
+            E[k].R += lin + (k < ins ? -ali : ali);
+            E[k].S += ai;
+        }
+        int ell = size, kl = -1;
+        for (int k = 0; k < size; ++k)
+            if (E[k].R >= wlo) {
+                ell = k;
+                break;
+            }
+        for (int k = size - 1; k >= 0; --k)
+            if (E[k].L <= whi) {
+                kl = k;
+                break;
+            }
+        auto cross = [&](int k, float lev) {
+            float z = fmaxf(E[k].lam + (lev - E[k].R) / E[k].S, E[k].lam);
+            if (k < size - 1) z = fminf(z, E[k + 1].lam);
+            return z;
+        };
+        const bool jumpL = ell < size && E[ell].L < wlo;
+        const bool jumpR = kl >= 0 && E[kl].R > whi;
+        const bool both = jumpL && jumpR && ell == kl;
+        float lm, hp, Sl;
+        if (jumpL) {
+            lm = E[ell].lam;
+            Sl = E[ell].S;
+        } else if (ell == 0) {
+            lm = fminf(E[0].lam + (wlo - E[0].L) / ai, E[0].lam);
+            Sl = ai;
+        } else {
+            lm = cross(ell - 1, wlo);
+            Sl = E[ell - 1].S;
+        }
+        if (jumpR) hp = E[kl].lam;
+        else if (kl < 0) hp = fminf(E[0].lam + (whi - E[0].L) / ai, E[0].lam);
+        else hp = cross(kl, whi);
+        const int k0 = ell + (jumpL ? 1 : 0), k1 = kl - (jumpR ? 1 : 0);
+        int nt = 0;
+        Etmp[nt++] = PqEntry{lm, wlo, jumpL ? fminf(E[ell].R, whi) : wlo, both ? 0.f : Sl};
+        for (int k = k0; k <= k1; ++k) Etmp[nt++] = E[k];
+        Etmp[nt++] = PqEntry{hp, jumpR ? (both ? fminf(E[ell].R, whi) : fmaxf(E[kl].L, wlo)) : whi,
+                             whi, 0.f};
+        for (int q = 0; q < nt; ++q) E[q] = Etmp[q];
+        size = nt;
+        wlo_p = wlo;
+        rec[i] = make_float2(lm, hp);
+    }
+    float xv = 0.5f * (rec[n - 1].x + rec[n - 1].y);
+    x[n - 1] = xv;
+    for (int i = n - 2; i >= 0; --i) {
+        xv = clip_to(xv, rec[i].x, rec[i].y);
+        x[i] = xv;
+    }
+}
+
+struct PqArgs {
+    const float *a, *b, *al, *f, *w;
+    float alpha, lam;  // used where al / w are NULL
+    const int64_t *offsets;
+    long long nchains;
+    int maxlen;
+    float *x;
+    float2 *rec;    // records: chain k at k * maxlen
+    PqEntry *ent;   // overflow entries: chain k at k * 2 * (3 maxlen + 4)
+};
+
+constexpr int kPqWarps = 4;
+
+__global__ void __launch_bounds__(kPqWarps * WARP) pq_chain_kernel(PqArgs p, WsHeader *hdr)
+{
+    const int lane = threadIdx.x & (WARP - 1);
+    const long long k = (long long)blockIdx.x * kPqWarps + threadIdx.x / WARP;
+    if (k >= p.nchains) return;
+    long long start = k * (long long)p.maxlen;
+    int n = p.maxlen;
+    if (p.offsets) {
+        const long long off0 = p.offsets[0], lo = p.offsets[k], hi = p.offsets[k + 1];
+        if (lo < off0 || hi < lo || hi - lo > p.maxlen) {
+            if (lane == 0) atomicOr(&hdr->status, ERR_BAD_CHAIN);
+            return;
+        }
+        start = lo;
+        n = (int)(hi - lo);
+    }
+    if (n == 0) return;
+    float2 *rec = p.rec + k * (long long)p.maxlen;
+    const float *a = p.a ? p.a + start : nullptr;
+    const float *b = p.b + start, *f = p.f + start;
+    const float *al = p.al ? p.al + start : nullptr;
+    const float *w = p.w ? p.w + start : nullptr;
+    PqState s{0.f, 0.f, 0.f, 0.f, 0, 0.f, 0.f, 0.f};
+    bool ovf = false;
+    float xlast = 0.f;
+    const int nblocks = (n + WARP - 1) / WARP;
+    for (int blk = 0; blk < nblocks && !ovf; ++blk) {
+        const int i_l = blk * WARP + lane;
+        const bool in = i_l < n;
+        const float av = (in && a) ? a[i_l] : 1.f, bv = in ? b[i_l] : 0.f,
+                    alv = in ? (al ? al[i_l] : p.alpha) : 0.f, fv = in ? f[i_l] : 0.f,
+                    wv = (i_l < n - 1) ? (w ? w[i_l] : p.lam) : 0.f;
+        const int cnt = min(WARP, n - blk * WARP);
+        for (int j = 0; j < cnt; ++j) {
+            const int i = blk * WARP + j;
+            const float ai = __shfl_sync(FULL, av, j), bi = __shfl_sync(FULL, bv, j),
+                        ali = __shfl_sync(FULL, alv, j), fi = __shfl_sync(FULL, fv, j),
+                        wi = __shfl_sync(FULL, wv, j);
+            float lm, hp;
+            pq_update(s, ai, bi, ali, fi, -wi, wi, lane, ovf, lm, hp);
+            if (i == n - 1) xlast = 0.5f * (lm + hp);
+            else if (lane == 0) rec[i] = make_float2(lm, hp);
+        }
+        ovf = __any_sync(FULL, ovf);
+    }
+    __syncwarp();
+    if (ovf) {
+        if (lane == 0) {
+            atomicAdd(&hdr->overflowed, 1ull);
+            PqEntry *E = p.ent + k * 2LL * (3LL * p.maxlen + 4);
+            pq_lane0(n, a, b, al, f, w, p.alpha, p.lam, p.x + start, E, E + (3LL * p.maxlen + 4),
+                     rec);
+        }
+        return;
+    }
+    float x_next = xlast;
+    for (int blk = nblocks - 1; blk >= 0; --blk) {
+        const int i = blk * WARP + lane;
+        float lo = -INFINITY, hi = INFINITY;
+        if (i < n - 1) {
+            const float2 r = rec[i];
+            lo = r.x;
+            hi = r.y;
+        }
+        const float xv = clip_suffix(lo, hi, x_next, lane, min(WARP, n - blk * WARP));
+        if (i < n) p.x[start + i] = xv;
+        x_next = __shfl_sync(FULL, xv, 0);
+    }
+}
+
+struct PqWs {
+    WsHeader *hdr;
+    float2 *rec;
+    PqEntry *ent;
+    size_t bytes;
+};
+
+PqWs carve_pq(void *base, long long nchains, long long maxlen)
+{
+    Carver cv(base);
+    PqWs o;
+    o.hdr = cv.take<WsHeader>(1);
+    o.rec = cv.take<float2>((size_t)(nchains * maxlen));
+    o.ent = cv.take<PqEntry>((size_t)(nchains * 2 * (3 * maxlen + 4)));
+    o.bytes = align_up(cv.used, 256);
+    return o;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tv_chain_pq_workspace_size(int64_t num_chains, int64_t max_len)
+{
+    if (num_chains < 0 || max_len < 0) return 0;
+    return carve_pq(nullptr, num_chains, max_len).bytes;
+}
+
+tv_status tv_chain_solve_pq(const float *d_a, const float *d_b, const float *d_alpha, float alpha,
+                            const float *d_f, const float *d_w, float lambda,
+                            const int64_t *d_offsets, int64_t num_chains, int64_t max_len,
+                            float *d_x, void *d_workspace, size_t workspace_bytes,
+                            tv_stream_t stream)
+{
+    clear_error();
+    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 28)) {
+        set_error("tv_chain_solve_pq: num_chains and max_len must be >= 0 (max_len <= 2^28)");
+        return TV_ERR_INVALID;
+    }
+    if (num_chains == 0) return TV_OK;
+    if (!d_b || !d_f || !d_x || !d_workspace) {
+        set_error("tv_chain_solve_pq: b, f, x and workspace must not be NULL");
+        return TV_ERR_INVALID;
+    }
+    if ((!d_alpha && !(alpha >= 0.f && alpha < INFINITY)) ||
+        (!d_w && !(lambda >= 0.f && lambda < INFINITY))) {
+        set_error("tv_chain_solve_pq: alpha and lambda must be finite and >= 0");
+        return TV_ERR_INVALID;
+    }
+    const void *ins[5] = {d_a, d_b, d_alpha, d_f, d_w};
+    for (const void *q : ins)
+        if (q && q == d_x) {
+            set_error("tv_chain_solve_pq: x must not alias the inputs");
+            return TV_ERR_INVALID;
+        }
+    PqWs ws = carve_pq(d_workspace, num_chains, max_len);
+    if (workspace_bytes < ws.bytes) {
+        set_error("tv_chain_solve_pq: workspace of %zu bytes, %zu needed", workspace_bytes, ws.bytes);
+        return TV_ERR_NOMEM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
+    if (st != TV_OK) return st;
+    PqArgs p{d_a, d_b, d_alpha, d_f, d_w, alpha, lambda, d_offsets, num_chains, (int)max_len,
+             d_x, ws.rec, ws.ent};
+    const long long blocks = (num_chains + kPqWarps - 1) / kPqWarps;
+    const bool prof = prof_on();
+    if (prof) prof_mark(PK_CHAIN, s, true);
+    pq_chain_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, ws.hdr);
+    st = check_cuda(cudaGetLastError(), "piecewise-quadratic chain launch");
+    if (st == TV_OK) note_launch();
+    if (prof) prof_mark(PK_CHAIN, s, false);
+    return st;
+}
+
+}  // extern "C"
