@@ -12,6 +12,7 @@ from .oracle import (  # noqa: F401
     chain_solve_pq,
     chain_vjp,
     rof_primal,
+    tv2d_l1,
     tv2d_lagrangian,
     tv2d_pd,
 )

@@ -48,6 +48,8 @@ def _load():
                                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, _D,
                                                  ctypes.POINTER(ctypes.c_int), _D]
             lib.tvo_chain_solve_pq_batch.argtypes = [_D, _D, _D, _D, _D, _I64, ctypes.c_int64, _D]
+            lib.tvo_tv2d_l1.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D]
             lib.tvo_chain_vjp.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, _D, _D]
             lib.tvo_rof_primal.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D,
                                            ctypes.c_double, _D]
@@ -214,3 +216,19 @@ def chain_solve_pq(a, b, alpha, f, w, offsets=None):
     if st != 0:
         raise ValueError(f"oracle piecewise-quadratic chain solve failed ({st})")
     return x
+
+
+def tv2d_l1(f, lam=0.0, w_h=None, w_v=None, tau=1.0, iters=100, nthreads=None):
+    """TV-l1 denoising, min TV(x) + ||x - f||_1, by the primal-dual iteration with row
+    chains of piecewise-quadratic unaries and column chains (constant steps, tau sigma = 1).
+    Returns ``(x, energies)``; ``energies[k]`` is TV(x^{k+1}) + ||x^{k+1} - f||_1."""
+    lib = _load()
+    f = _f64(f)
+    H, W = f.shape
+    x = np.empty((H, W))
+    e = np.empty(iters)
+    st = lib.tvo_tv2d_l1(H, W, _p(f), _p(_f64(w_h)), _p(_f64(w_v)), float(lam), float(tau),
+                         int(iters), int(nthreads or os.cpu_count() or 1), _p(x), _p(e))
+    if st != 0:
+        raise RuntimeError(f"oracle tv2d_l1 failed: {st}")
+    return x, e

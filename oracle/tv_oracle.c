@@ -922,3 +922,75 @@ int tvo_chain_solve_pq_batch(const double *a, const double *b, const double *alp
     }
     return TVO_OK;
 }
+
+
+/* ---------------- TV-l1 denoising (Sec. 6) ----------------
+ *
+ * min_x TV_h(x) + TV_v(x) + sum_i |x_i - f_i|, as the saddle-point problem
+ *   min_x max_y <x, y> + TV_h(x) + ||x - f||_1 - TV_v^*(y)
+ * with the primal-dual iteration of eq. pd at constant steps (tau sigma = 1, theta = 1;
+ * the model is not strongly convex):
+ *   c = y^k / sigma + xbar^k,  y^{k+1} = sigma (c - argmin TV_v(z) + sigma/2 ||z - c||^2)
+ *        (column chains, eq. prox-tv-conj)
+ *   x^{k+1} = argmin TV_h(x) + ||x - f||_1 + 1/(2 tau) ||x - (x^k - tau y^{k+1})||^2
+ *        (row chains with piecewise-quadratic unaries, eq. prox-pq; scaled by tau:
+ *         a = 1, b = xi, alpha = tau, weights tau w_h)
+ *   xbar^{k+1} = 2 x^{k+1} - x^k.
+ * Start x^0 = xbar^0 = f, y^0 = 0. energy[k] = TV(x^{k+1}) + ||x^{k+1} - f||_1.
+ */
+static double l1_energy(int H, int W, const double *f, const double *wh, const double *wv,
+                        double lam, const double *x)
+{
+    double s = tv_h_of(H, W, wh, lam, x) + tv_v_of(H, W, wv, lam, x);
+    for (int64_t i = 0; i < (int64_t)H * W; ++i) s += fabs(x[i] - f[i]);
+    return s;
+}
+
+int tvo_tv2d_l1(int H, int W, const double *f, const double *wh, const double *wv, double lam,
+                double tau, int max_iters, int nthreads, double *x_out, double *energy)
+{
+    if (H < 1 || W < 1 || !f || !x_out || max_iters < 1 || !(tau > 0.0)) return TVO_ERR_INVALID;
+    const int64_t N = (int64_t)H * W;
+    const double sigma = 1.0 / tau;
+    double *x = x_out;
+    double *xb = (double *)malloc(sizeof(double) * (size_t)N);
+    double *y = (double *)calloc((size_t)N, sizeof(double));
+    double *c = (double *)malloc(sizeof(double) * (size_t)N);
+    double *xh = (double *)malloc(sizeof(double) * (size_t)N);
+    double *xn = (double *)malloc(sizeof(double) * (size_t)N);
+    double *ones = (double *)malloc(sizeof(double) * (size_t)W);
+    double *alw = (double *)malloc(sizeof(double) * (size_t)W);
+    double *ww = (double *)malloc(sizeof(double) * (size_t)W);
+    if (!xb || !y || !c || !xh || !xn || !ones || !alw || !ww) {
+        free(xb); free(y); free(c); free(xh); free(xn); free(ones); free(alw); free(ww);
+        return TVO_ERR_NOMEM;
+    }
+    memcpy(x, f, sizeof(double) * (size_t)N);
+    memcpy(xb, f, sizeof(double) * (size_t)N);
+    for (int q = 0; q < W; ++q) {
+        ones[q] = 1.0;
+        alw[q] = tau;
+    }
+    int st = TVO_OK;
+    for (int k = 0; k < max_iters && st == TVO_OK; ++k) {
+        for (int64_t i = 0; i < N; ++i) c[i] = y[i] / sigma + xb[i];
+        st = col_prox(H, W, c, wv, lam, sigma, xh, nthreads);
+        if (st != TVO_OK) break;
+        for (int64_t i = 0; i < N; ++i) y[i] = sigma * (c[i] - xh[i]);
+        for (int64_t i = 0; i < N; ++i) c[i] = x[i] - tau * y[i]; /* xi */
+        for (int r = 0; r < H && st == TVO_OK; ++r) {
+            for (int q = 0; q + 1 < W; ++q) ww[q] = tau * (wh ? wh[(int64_t)r * (W - 1) + q] : lam);
+            ww[W - 1] = 0.0;
+            st = chain_pq_core(W, ones, c + (int64_t)r * W, alw, f + (int64_t)r * W, ww,
+                               xn + (int64_t)r * W);
+        }
+        if (st != TVO_OK) break;
+        for (int64_t i = 0; i < N; ++i) {
+            xb[i] = 2.0 * xn[i] - x[i];
+            x[i] = xn[i];
+        }
+        if (energy) energy[k] = l1_energy(H, W, f, wh, wv, lam, x);
+    }
+    free(xb); free(y); free(c); free(xh); free(xn); free(ones); free(alw); free(ww);
+    return st;
+}
