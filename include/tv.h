@@ -288,6 +288,29 @@ tv_status tv2d_denoise_lagrangian(const float *d_img, int64_t H, int64_t W, cons
                                   double *gap_out, void *d_workspace, size_t workspace_bytes,
                                   tv_stream_t stream);
 
+/*
+ * 2D TV-l1 denoising (Sec. 6):  x* = argmin_x TV_h(x) + TV_v(x) + sum_p |x_p - f_p|,
+ * weights as tv2d_denoise. Solved as the saddle point min_x max_y <x, y> + TV_h(x) +
+ * ||x - f||_1 - TV_v^*(y) by the primal-dual iteration of eq. pd at constant steps
+ * tau, sigma = 1/tau, theta = 1 (the model is not strongly convex), from x^0 = f, y^0 = 0:
+ *   dual step    column chains (eq. prox-tv-conj) on c = y / sigma + xbar;
+ *   primal step  row chains with piecewise-quadratic unaries (tv_chain_solve_pq) on
+ *                xi = x - tau y, scaled by tau (a = 1, b = xi, alpha = tau, w = tau w_h);
+ *   xbar = 2 x^{k+1} - x^k.
+ * After every check_every-th iteration (and the last) the energy E = TV(x) + ||x - f||_1
+ * is summed on the device (FP64, fixed order) and read back; the solve stops when two
+ * consecutive checks differ by at most tol * E (tol = 0: run max_iters). tau in (0, inf);
+ * 0.3 suits images with values in [0, 1]. d_x receives x^k; *iters_out the iterations
+ * run; *energy_out the last energy (either may be NULL). Workspace of
+ * tv2d_l1_workspace_size bytes. Returns TV_OK, or TV_ERR_NOT_CONVERGED when tol > 0 and
+ * max_iters ran out (x still written); synchronous at every check.
+ */
+size_t tv2d_l1_workspace_size(int64_t H, int64_t W);
+tv_status tv2d_denoise_l1(const float *d_img, int64_t H, int64_t W, const float *d_wh,
+                          const float *d_wv, float lambda, float tau, int max_iters, double tol,
+                          int check_every, float *d_x, int *iters_out, double *energy_out,
+                          void *d_workspace, size_t workspace_bytes, tv_stream_t stream);
+
 /* How the calling thread's last tv2d_denoise_batched ran its iterations: 1 as one
  * CUDA graph with a device-side loop condition, 0 replayed from the host (conditional
  * graph nodes unavailable, or disabled), -1 no batched solve yet. */

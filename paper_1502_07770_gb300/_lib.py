@@ -68,6 +68,11 @@ SIGNATURES = {
                                                ctypes.c_float, ctypes.c_int, ctypes.c_double,
                                                ctypes.c_int, _p, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_double), _p, _sz, _p]),
+    "tv2d_l1_workspace_size": (_sz, [_i64, _i64]),
+    "tv2d_denoise_l1": (ctypes.c_int, [_p, _i64, _i64, _p, _p, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_int, _p,
+                                       ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_double), _p, _sz, _p]),
     "tv_chain_solve_general": (ctypes.c_int, [_p, _p, _p, _p, _p, _i64, _i64, _p, _p, _sz, _p]),
     "tv_set_coop_split": (ctypes.c_int, [ctypes.c_int]),
     "tv_net_conv3x3": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -377,6 +382,32 @@ def tv2d_denoise_lagrangian(img, lam: float = 0.1, w_h=None, w_v=None, tau0: flo
     if st not in (TV_OK, TV_ERR_NOT_CONVERGED):
         _check(st)
     return x, it.value, gap.value, st == TV_OK
+
+
+def tv2d_denoise_l1(img, lam: float = 0.1, w_h=None, w_v=None, tau: float = 0.3,
+                    max_iters: int = 300, tol: float = 0.0, check_every: int = 10, out=None,
+                    ws=None):
+    """TV-l1 denoising min TV(x) + ||x - f||_1 (Sec. 6) by eq. pd at constant steps tau,
+    1/tau: column chains for the dual, piecewise-quadratic row chains for the primal.
+
+    Returns ``(x, iterations, energy, converged)``; with ``tol = 0`` exactly
+    ``max_iters`` iterations run and ``converged`` is True.
+    """
+    lib = load()
+    _require_cuda(img, w_h, w_v)
+    H, W = img.shape
+    x = torch.empty_like(img) if out is None else out
+    nbytes = lib.tv2d_l1_workspace_size(H, W)
+    wsb = ws if ws is not None else workspace(nbytes, img.device, "l1")
+    it = ctypes.c_int(0)
+    en = ctypes.c_double(0.0)
+    st = lib.tv2d_denoise_l1(_ptr(img), H, W, _ptr(w_h), _ptr(w_v), float(lam), float(tau),
+                             int(max_iters), float(tol), int(check_every), _ptr(x),
+                             ctypes.byref(it), ctypes.byref(en), _ptr(wsb), wsb.numel(),
+                             _stream(img.device))
+    if st not in (TV_OK, TV_ERR_NOT_CONVERGED):
+        _check(st)
+    return x, it.value, en.value, st == TV_OK
 
 
 def tv2d_denoise_batched(images, lams, w_hs=None, w_vs=None, y0s=None, max_iters: int = 200,

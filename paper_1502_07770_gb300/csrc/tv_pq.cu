@@ -152,14 +152,14 @@ struct PqEntry {
 };
 
 __device__ void pq_lane0(int n, const float *a, const float *b, const float *al, const float *f,
-                         const float *w, float alpha, float lam, float *x, PqEntry *E,
-                         PqEntry *Etmp, float2 *rec)
+                         const float *w, float wscale, float alpha, float lam, float *x,
+                         PqEntry *E, PqEntry *Etmp, float2 *rec)
 {
     int size = 0;
     float wlo_p = 0.f;
     for (int i = 0; i < n; ++i) {
         const float ai = a ? a[i] : 1.f, bi = b[i], ali = al ? al[i] : alpha, fi = f[i];
-        const float wi = (i < n - 1) ? (w ? w[i] : lam) : 0.f;
+        const float wi = (i < n - 1) ? (w ? w[i] * wscale : lam) : 0.f;
         const float wlo = -wi, whi = wi;
         int ins = 0;
         while (ins < size && E[ins].lam < fi) ++ins;
@@ -236,6 +236,8 @@ __device__ void pq_lane0(int n, const float *a, const float *b, const float *al,
 struct PqArgs {
     const float *a, *b, *al, *f, *w;
     float alpha, lam;  // used where al / w are NULL
+    float wscale;      // multiplies every edge weight
+    long long w_stride;  // > 0: chain k's weights at w + k * w_stride (image rows), else w + start
     const int64_t *offsets;
     long long nchains;
     int maxlen;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kPqWarps * WARP) pq_chain_kernel(PqArgs p, WsH
     const float *a = p.a ? p.a + start : nullptr;
     const float *b = p.b + start, *f = p.f + start;
     const float *al = p.al ? p.al + start : nullptr;
-    const float *w = p.w ? p.w + start : nullptr;
+    const float *w = p.w ? p.w + (p.w_stride > 0 ? k * p.w_stride : start) : nullptr;
     PqState s{0.f, 0.f, 0.f, 0.f, 0, 0.f, 0.f, 0.f};
     bool ovf = false;
     float xlast = 0.f;
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(kPqWarps * WARP) pq_chain_kernel(PqArgs p, WsH
         const bool in = i_l < n;
         const float av = (in && a) ? a[i_l] : 1.f, bv = in ? b[i_l] : 0.f,
                     alv = in ? (al ? al[i_l] : p.alpha) : 0.f, fv = in ? f[i_l] : 0.f,
-                    wv = (i_l < n - 1) ? (w ? w[i_l] : p.lam) : 0.f;
+                    wv = (i_l < n - 1) ? (w ? w[i_l] * p.wscale : p.lam) : 0.f;
         const int cnt = min(WARP, n - blk * WARP);
         for (int j = 0; j < cnt; ++j) {
             const int i = blk * WARP + j;
@@ -296,8 +298,8 @@ __global__ void __launch_bounds__(kPqWarps * WARP) pq_chain_kernel(PqArgs p, WsH
         if (lane == 0) {
             atomicAdd(&hdr->overflowed, 1ull);
             PqEntry *E = p.ent + k * 2LL * (3LL * p.maxlen + 4);
-            pq_lane0(n, a, b, al, f, w, p.alpha, p.lam, p.x + start, E, E + (3LL * p.maxlen + 4),
-                     rec);
+            pq_lane0(n, a, b, al, f, w, p.wscale, p.alpha, p.lam, p.x + start, E,
+                     E + (3LL * p.maxlen + 4), rec);
         }
         return;
     }
@@ -333,6 +335,196 @@ PqWs carve_pq(void *base, long long nchains, long long maxlen)
     o.bytes = align_up(cv.used, 256);
     return o;
 }
+
+// ------------------------------------------------------------- TV-l1 in 2D --
+// min_x TV_h(x) + TV_v(x) + ||x - f||_1 as min_x max_y <x, y> + TV_h(x) + ||x - f||_1 -
+// TV_v^*(y) (Sec. 6), by the primal-dual iteration of eq. pd at constant steps
+// (tau sigma = 1, theta = 1): the dual step is the column chains of eq. prox-tv-conj,
+// the primal step the row chains with piecewise-quadratic unaries of eq. prox-pq
+// (scaled by tau: a = 1, b = x - tau y, alpha = tau, weights tau w_h).
+
+// Column (dual) phase, one warp per column: c = y / sigma + xbar, weights w_v / sigma,
+// y <- sigma (c - xhat).
+template <bool HAS_W>
+struct L1ColsP {
+    static constexpr bool CREC = true;
+    struct Raw {
+        float xb, y, w;
+    };
+    struct Acc {};
+    const float *xbar, *wv;
+    float *y;
+    float lam;
+    long long H, W;
+    float sigma, inv_sigma;
+
+    __device__ bool resolve() { return true; }
+    __device__ long long num_chains() const { return W; }
+    __device__ int max_len() const { return (int)H; }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        start = k;
+        n = (int)H;
+        return true;
+    }
+    __device__ void fetch(long long col, long long, int n, int i, Raw &r) const
+    {
+        const bool in = i < n;
+        const long long o = (long long)i * W + col;
+        r.xb = in ? xbar[o] : 0.f;
+        r.y = in ? y[o] : 0.f;
+        r.w = HAS_W ? ((i < n - 1) ? wv[o] : 0.f) : lam;
+    }
+    __device__ void unary(long long, long long, int, int, const Raw &r, float &c, float &w,
+                          Acc &) const
+    {
+        c = r.y * inv_sigma + r.xb;
+        w = r.w * inv_sigma;
+    }
+    __device__ void unary_direct(int i, int n, long long col, long long, float &c, float &w) const
+    {
+        (void)c;  // from the forward-pass record
+        const float wvv = (HAS_W && i < n - 1) ? wv[(long long)i * W + col] : lam;
+        w = (i < n - 1) ? wvv * inv_sigma : 0.f;
+    }
+    __device__ void emit(long long col, long long, int i, float xhat, float c) const
+    {
+        y[(long long)i * W + col] = sigma * (c - xhat);
+    }
+    __device__ void emit_direct(int i, long long col, long long start, float xhat, float c) const
+    {
+        emit(col, start, i, xhat, c);
+    }
+    __device__ long long spill_off(long long col, long long) const { return col * (2 * H + 2); }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &, int) const {}
+    __device__ void finish_empty() const {}
+};
+
+__global__ void l1_xi(long long N, const float *x, const float *y, float tau, float *xi)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
+         q += (long long)gridDim.x * blockDim.x)
+        xi[q] = x[q] - tau * y[q];
+}
+
+// xbar = 2 x_new - x; x = x_new
+__global__ void l1_relax(long long N, const float *xn, float *x, float *xbar)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
+         q += (long long)gridDim.x * blockDim.x) {
+        const float v = xn[q];
+        xbar[q] = v + (v - x[q]);
+        x[q] = v;
+    }
+}
+
+constexpr int kL1Threads = 256;
+
+// TV(x) + ||x - f||_1: FP32 over at most 32 pixels per thread, FP64 beyond; the last
+// block sums the block partials in a fixed order into *energy.
+__global__ void __launch_bounds__(kL1Threads)
+    l1_energy_kernel(const float *f, const float *wh, const float *wv, float lam, long long H,
+                     long long W, const float *x, double *partials, unsigned *ticket,
+                     double *energy)
+{
+    __shared__ double red[kL1Threads];
+    __shared__ bool last;
+    const long long N = H * W;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long dr = stride / W, dc = stride - dr * W;
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long r = q / W, c = q - r * W;
+    double acc = 0.0;
+    float part = 0.f;
+    int cnt = 0;
+    for (; q < N; q += stride) {
+        const float xv = x[q];
+        float t = fabsf(xv - f[q]);
+        if (c + 1 < W) t += (wh ? wh[r * (W - 1) + c] : lam) * fabsf(x[q + 1] - xv);
+        if (r + 1 < H) t += (wv ? wv[q] : lam) * fabsf(x[q + W] - xv);
+        part += t;
+        if (++cnt == 32) {
+            acc += (double)part;
+            part = 0.f;
+            cnt = 0;
+        }
+        c += dc;
+        r += dr;
+        if (c >= W) {
+            c -= W;
+            ++r;
+        }
+    }
+    acc += (double)part;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = kL1Threads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double b = 0.0;
+    for (unsigned bq = threadIdx.x; bq < gridDim.x; bq += blockDim.x) b += __ldcg(partials + bq);
+    red[threadIdx.x] = b;
+    __syncthreads();
+    for (int h = kL1Threads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *energy = red[0];
+        *ticket = 0;
+    }
+}
+
+struct L1Ws {
+    WsHeader *hdr;
+    double *energy, *partials;
+    unsigned *ticket;
+    float *xbar, *y, *xi, *xn, *crec;
+    float2 *rec, *spill;
+    PqWs pq;
+    size_t bytes;
+};
+
+int l1_blocks(long long N)
+{
+    long long b = (N + kL1Threads * 8 - 1) / (kL1Threads * 8);
+    const long long cap = 4LL * sm_count_current();
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+L1Ws carve_l1(void *base, long long H, long long W)
+{
+    Carver cv(base);
+    L1Ws o;
+    const long long N = H * W;
+    o.hdr = cv.take<WsHeader>(1);
+    o.energy = cv.take<double>(1);
+    o.ticket = cv.take<unsigned>(1);
+    o.partials = cv.take<double>((size_t)l1_blocks(N));
+    o.xbar = cv.take<float>((size_t)N);
+    o.y = cv.take<float>((size_t)N);
+    o.xi = cv.take<float>((size_t)N);
+    o.xn = cv.take<float>((size_t)N);
+    o.crec = cv.take<float>((size_t)N);
+    o.rec = cv.take<float2>((size_t)N);
+    o.spill = cv.take<float2>((size_t)(W * (2 * H + 2)));
+    char *pq_base = cv.take<char>(carve_pq(nullptr, H, W).bytes);
+    o.pq = carve_pq(base ? pq_base : nullptr, H, W);
+    o.bytes = align_up(cv.used, 256);
+    return o;
+}
+
+int ew_blocks_pq(long long n) { return (int)std::min<long long>((n + 255) / 256, 8LL * sm_count_current()); }
 
 }  // namespace
 
@@ -379,8 +571,8 @@ tv_status tv_chain_solve_pq(const float *d_a, const float *d_b, const float *d_a
     cudaStream_t s = (cudaStream_t)stream;
     tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
     if (st != TV_OK) return st;
-    PqArgs p{d_a, d_b, d_alpha, d_f, d_w, alpha, lambda, d_offsets, num_chains, (int)max_len,
-             d_x, ws.rec, ws.ent};
+    PqArgs p{d_a, d_b, d_alpha, d_f, d_w, alpha, lambda, 1.f, 0, d_offsets, num_chains,
+             (int)max_len, d_x, ws.rec, ws.ent};
     const long long blocks = (num_chains + kPqWarps - 1) / kPqWarps;
     const bool prof = prof_on();
     if (prof) prof_mark(PK_CHAIN, s, true);
@@ -389,6 +581,115 @@ tv_status tv_chain_solve_pq(const float *d_a, const float *d_b, const float *d_a
     if (st == TV_OK) note_launch();
     if (prof) prof_mark(PK_CHAIN, s, false);
     return st;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+size_t tv2d_l1_workspace_size(int64_t H, int64_t W)
+{
+    if (H < 1 || W < 1) return 0;
+    return carve_l1(nullptr, H, W).bytes;
+}
+
+tv_status tv2d_denoise_l1(const float *d_img, int64_t H, int64_t W, const float *d_wh,
+                          const float *d_wv, float lambda, float tau, int max_iters, double tol,
+                          int check_every, float *d_x, int *iters_out, double *energy_out,
+                          void *d_workspace, size_t workspace_bytes, tv_stream_t stream)
+{
+    clear_error();
+    if (H < 1 || W < 1 || H > (1LL << 28) || W > (1LL << 28) || max_iters < 1 ||
+        check_every < 1 || !(tau > 0.f && tau < INFINITY)) {
+        set_error("tv2d_denoise_l1: need H, W >= 1, max_iters >= 1, check_every >= 1 and a "
+                  "finite tau > 0");
+        return TV_ERR_INVALID;
+    }
+    if (!d_img || !d_x || !d_workspace) {
+        set_error("tv2d_denoise_l1: img, x and workspace must not be NULL");
+        return TV_ERR_INVALID;
+    }
+    if (!(tol >= 0.0 && tol < INFINITY) ||
+        ((!d_wh || !d_wv) && !(lambda >= 0.f && lambda < INFINITY))) {
+        set_error("tv2d_denoise_l1: tol and lambda must be finite and >= 0");
+        return TV_ERR_INVALID;
+    }
+    const long long N = H * W;
+    const size_t npx = (size_t)N * sizeof(float);
+    {
+        const char *a = (const char *)d_x, *b = (const char *)d_img;
+        if (a < b + npx && b < a + npx) {
+            set_error("tv2d_denoise_l1: x must not overlap the image");
+            return TV_ERR_INVALID;
+        }
+    }
+    L1Ws ws = carve_l1(d_workspace, H, W);
+    if (workspace_bytes < ws.bytes) {
+        set_error("tv2d_denoise_l1: workspace of %zu bytes, %zu needed", workspace_bytes, ws.bytes);
+        return TV_ERR_NOMEM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    tv_status st;
+    if ((st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset")) != TV_OK ||
+        (st = check_cuda(cudaMemsetAsync(ws.pq.hdr, 0, sizeof(WsHeader), s), "memset")) != TV_OK ||
+        (st = check_cuda(cudaMemsetAsync(ws.ticket, 0, sizeof(unsigned), s), "memset")) != TV_OK ||
+        (st = check_cuda(cudaMemcpyAsync(d_x, d_img, npx, cudaMemcpyDeviceToDevice, s), "copy")) !=
+            TV_OK ||
+        (st = check_cuda(cudaMemcpyAsync(ws.xbar, d_img, npx, cudaMemcpyDeviceToDevice, s), "copy")) !=
+            TV_OK ||
+        (st = check_cuda(cudaMemsetAsync(ws.y, 0, npx, s), "memset")) != TV_OK)
+        return st;
+    const float sigma = 1.f / tau;
+    const int eb = l1_blocks(N);
+    double e_prev = NAN, e = NAN;
+    int k = 0;
+    bool done = false;
+    while (k < max_iters) {
+        // dual step: column chains
+        if (d_wv) {
+            L1ColsP<true> p{ws.xbar, d_wv, ws.y, lambda, H, W, sigma, 1.f / sigma};
+            st = launch_coop(p, W, (int)H, ws.rec, ws.crec, ws.spill, ws.hdr, s, PK_COL);
+        } else {
+            L1ColsP<false> p{ws.xbar, d_wv, ws.y, lambda, H, W, sigma, 1.f / sigma};
+            st = launch_coop(p, W, (int)H, ws.rec, ws.crec, ws.spill, ws.hdr, s, PK_COL);
+        }
+        if (st != TV_OK) return st;
+        l1_xi<<<ew_blocks_pq(N), 256, 0, s>>>(N, d_x, ws.y, tau, ws.xi);
+        if ((st = check_cuda(cudaGetLastError(), "xi")) != TV_OK) return st;
+        note_launch();
+        // primal step: row chains with piecewise-quadratic unaries (scaled by tau)
+        PqArgs p{nullptr, ws.xi, nullptr, d_img, d_wh, tau, tau * lambda, tau,
+                 d_wh ? (long long)(W - 1) : 0, nullptr, H, (int)W, ws.xn, ws.pq.rec, ws.pq.ent};
+        const long long blocks = (H + kPqWarps - 1) / kPqWarps;
+        const bool prof = prof_on();
+        if (prof) prof_mark(PK_ROW, s, true);
+        pq_chain_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, ws.pq.hdr);
+        if ((st = check_cuda(cudaGetLastError(), "row chains")) != TV_OK) return st;
+        note_launch();
+        if (prof) prof_mark(PK_ROW, s, false);
+        l1_relax<<<ew_blocks_pq(N), 256, 0, s>>>(N, ws.xn, d_x, ws.xbar);
+        if ((st = check_cuda(cudaGetLastError(), "relax")) != TV_OK) return st;
+        note_launch();
+        ++k;
+        if (k % check_every == 0 || k == max_iters) {
+            l1_energy_kernel<<<eb, kL1Threads, 0, s>>>(d_img, d_wh, d_wv, lambda, H, W, d_x,
+                                                       ws.partials, ws.ticket, ws.energy);
+            if ((st = check_cuda(cudaGetLastError(), "energy")) != TV_OK) return st;
+            note_launch();
+            st = check_cuda(cudaMemcpyAsync(&e, ws.energy, sizeof(double), cudaMemcpyDeviceToHost, s),
+                            "read energy");
+            if (st == TV_OK) st = check_cuda(cudaStreamSynchronize(s), "synchronize");
+            if (st != TV_OK) return st;
+            if (tol > 0.0 && e_prev == e_prev && fabs(e_prev - e) <= tol * fabs(e)) {
+                done = true;
+                break;
+            }
+            e_prev = e;
+        }
+    }
+    if (iters_out) *iters_out = k;
+    if (energy_out) *energy_out = e;
+    return (done || tol == 0.0) ? TV_OK : TV_ERR_NOT_CONVERGED;
 }
 
 }  // extern "C"

@@ -94,6 +94,17 @@ def shapes_image(H: int, W: int, seed: int, n_shapes: int = 200, noise: float = 
     return img.astype(np.float32), noisy.astype(np.float32)
 
 
+def salt_pepper_image(H: int, W: int, seed: int, frac: float = 0.15) -> np.ndarray:
+    """The noisy shapes image (``n_shapes`` = max(4, H W / 400)) with a fraction ``frac``
+    of its pixels replaced by 0 or 1 (impulse noise, the input TV-l1 denoising suits).
+    float32 (H, W)."""
+    f = shapes_image(H, W, seed, n_shapes=max(4, H * W // 400))[1]
+    rng = _rng(seed)
+    m = rng.uniform(size=f.shape) < frac
+    f[m] = rng.integers(0, 2, int(m.sum()))
+    return f.astype(np.float32)
+
+
 def edge_aware_weights(f: np.ndarray, lam: float, scale: float = 0.2):
     """Per-edge weights ``lam * exp(-|f_i - f_j| / scale)`` of a float32 image.
 
