@@ -300,8 +300,9 @@ tv_status tv2d_denoise_lagrangian(const float *d_img, int64_t H, int64_t W, cons
  * After every check_every-th iteration (and the last) the energy E = TV(x) + ||x - f||_1
  * is summed on the device (FP64, fixed order) and read back; the solve stops when two
  * consecutive checks differ by at most tol * E (tol = 0: run max_iters). tau in (0, inf);
- * 0.3 suits images with values in [0, 1]. d_x receives x^k; *iters_out the iterations
- * run; *energy_out the last energy (either may be NULL). Workspace of
+ * 0.1 suits images with values in [0, 1] and lambda near 0.5. d_x receives x^k;
+ * *iters_out the iterations run; *energy_out the last energy (either may be NULL).
+ * Workspace of
  * tv2d_l1_workspace_size bytes. Returns TV_OK, or TV_ERR_NOT_CONVERGED when tol > 0 and
  * max_iters ran out (x still written); synchronous at every check.
  */

@@ -384,7 +384,7 @@ def tv2d_denoise_lagrangian(img, lam: float = 0.1, w_h=None, w_v=None, tau0: flo
     return x, it.value, gap.value, st == TV_OK
 
 
-def tv2d_denoise_l1(img, lam: float = 0.1, w_h=None, w_v=None, tau: float = 0.3,
+def tv2d_denoise_l1(img, lam: float = 0.55, w_h=None, w_v=None, tau: float = 0.1,
                     max_iters: int = 300, tol: float = 0.0, check_every: int = 10, out=None,
                     ws=None):
     """TV-l1 denoising min TV(x) + ||x - f||_1 (Sec. 6) by eq. pd at constant steps tau,

@@ -2,7 +2,8 @@
 //     x* = argmin_x sum_i (a_i x_i^2 / 2 - b_i x_i + alpha_i |x_i - f_i|) + sum_{i<n} w_i |x_{i+1} - x_i|,
 // the convex chain of Algorithm 2 whose unary derivatives g_i(z) = a_i z - b_i +
 // alpha_i sign(z - f_i) are piecewise linear with a jump of 2 alpha_i at f_i. It is the
-// row proximal map of TV-l1 denoising (Sec. 6): alpha = 1, a = 1/tau, b = xi/tau.
+// row proximal map of TV-l1 denoising (Sec. 6): alpha = 1, a = 1/tau, b = xi/tau, or,
+// multiplied through by tau, a = 1, b = xi, alpha = tau (the form tv2d_denoise_l1 uses).
 //
 // One warp per chain. The message (a derivative) is held in registers, one breakpoint
 // per lane: its position lambda_k, the message's left and right limits L_k <= R_k there

@@ -94,9 +94,10 @@ def shapes_image(H: int, W: int, seed: int, n_shapes: int = 200, noise: float = 
     return img.astype(np.float32), noisy.astype(np.float32)
 
 
-def salt_pepper_image(H: int, W: int, seed: int, frac: float = 0.15) -> np.ndarray:
+def salt_pepper_image(H: int, W: int, seed: int, frac: float = 0.25) -> np.ndarray:
     """The noisy shapes image (``n_shapes`` = max(4, H W / 400)) with a fraction ``frac``
-    of its pixels replaced by 0 or 1 (impulse noise, the input TV-l1 denoising suits).
+    of its pixels replaced by 0 or 1 (impulse noise; 25 % is the degradation of the
+    TV-l1 experiment of Sec. 6).
     float32 (H, W)."""
     f = shapes_image(H, W, seed, n_shapes=max(4, H * W // 400))[1]
     rng = _rng(seed)
