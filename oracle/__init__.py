@@ -9,6 +9,7 @@ from .oracle import (  # noqa: F401
     chain_solve,
     chain_solve_batch,
     chain_solve_general,
+    chain_solve_nonconvex,
     chain_solve_pq,
     chain_vjp,
     rof_primal,

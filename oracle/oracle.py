@@ -50,6 +50,8 @@ def _load():
             lib.tvo_chain_solve_pq_batch.argtypes = [_D, _D, _D, _D, _D, _I64, ctypes.c_int64, _D]
             lib.tvo_tv2d_l1.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D]
+            lib.tvo_chain_solve_nonconvex_batch.argtypes = [_I64, _D, _D, _D, _D, _D, _D, _I64,
+                                                            ctypes.c_int64, _D, _D]
             lib.tvo_chain_vjp.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, _D, _D]
             lib.tvo_rof_primal.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D,
                                            ctypes.c_double, _D]
@@ -231,4 +233,44 @@ def tv2d_l1(f, lam=0.0, w_h=None, w_v=None, tau=1.0, iters=100, nthreads=None):
                          int(iters), int(nthreads or os.cpu_count() or 1), _p(x), _p(e))
     if st != 0:
         raise RuntimeError(f"oracle tv2d_l1 failed: {st}")
+    return x, e
+
+
+def chain_solve_nonconvex(unaries, w, C=None, offsets=None):
+    """Chains with continuous piecewise-linear unaries and truncated TV (Sec. 3):
+    min sum_i f_i(x_i) + sum_{i<n} min(w_i |x_{i+1} - x_i|, C_i).
+
+    ``unaries``: one ``(lam, val, s_left, s_right)`` per node (breakpoints, values there,
+    end slopes; s_left <= 0 <= s_right), or a tuple ``(uo, ul, uv, sl, sr)`` of CSR arrays.
+    ``w``, ``C``: per node (edge to the next node; the last entry of a chain unused); C
+    None or inf entries for plain TV. Returns ``(x, energies)`` with one optimum energy per
+    chain."""
+    if isinstance(unaries, tuple) and len(unaries) == 5:
+        uo, ul, uv, sl, sr = unaries
+        uo = np.ascontiguousarray(uo, dtype=np.int64)
+        ul, uv, sl, sr = (_f64(a) for a in (ul, uv, sl, sr))
+    else:
+        lens = [len(u[0]) for u in unaries]
+        uo = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        ul = _f64(np.concatenate([np.asarray(u[0], dtype=np.float64) for u in unaries]) if lens else [])
+        uv = _f64(np.concatenate([np.asarray(u[1], dtype=np.float64) for u in unaries]) if lens else [])
+        sl = _f64([u[2] for u in unaries])
+        sr = _f64([u[3] for u in unaries])
+    n = uo.size - 1
+    w = _f64(w)
+    C = np.full(n, np.inf) if C is None else _f64(C)
+    if offsets is None:
+        offsets = np.array([0, n], dtype=np.int64)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    x = np.empty(n, dtype=np.float64)
+    e = np.empty(offsets.size - 1, dtype=np.float64)
+    if ul.size == 0:
+        ul = np.zeros(1)
+        uv = np.zeros(1)
+    st = _load().tvo_chain_solve_nonconvex_batch(uo.ctypes.data_as(_I64), _p(ul), _p(uv), _p(sl),
+                                                 _p(sr), _p(w), _p(C),
+                                                 offsets.ctypes.data_as(_I64), offsets.size - 1,
+                                                 _p(x), _p(e))
+    if st != 0:
+        raise ValueError(f"oracle non-convex chain solve failed ({st})")
     return x, e

@@ -994,3 +994,390 @@ int tvo_tv2d_l1(int H, int W, const double *f, const double *wh, const double *w
     free(xb); free(y); free(c); free(xh); free(xn); free(ones); free(alw); free(ww);
     return st;
 }
+
+
+/* ---------------- non-convex chains: truncated TV, piecewise-linear unaries (Sec. 3) ----------------
+ *
+ * x* in argmin_x sum_i f_i(x_i) + sum_{i<n} min(w_i |x_{i+1} - x_i|, C_i),
+ * f_i continuous piecewise linear (any shape, bounded below), w_i >= 0, C_i >= 0 (C_i = +inf:
+ * plain TV). DP on the chain (eq. Message:update): M^_0 = f_0; M_{i,i+1} = M^_i (x) f_{i,i+1}
+ * (min-convolution); M^_{i+1} = f_{i+1} + M_{i,i+1}. Messages are piecewise linear and are
+ * stored as the paper's sequence (s_0, lambda_1, s_1, ..., lambda_t, s_t) together with the
+ * value at lambda_1 (the sequence alone fixes a message up to a constant; the value is kept so
+ * that the optimum energy can be read off). The min-convolution with min(w|z|, C) is taken as
+ * three consecutive ones (Prop. ConsecutiveMinConvolution) with
+ *   f^1(z) = w z for z >= 0 (+inf left of 0)   -- Algorithm 1,
+ *   f^2(z) = w |z| for z <= 0 (+inf right of 0) -- Algorithm 1 on the reversed function,
+ *   f^3(z) = C for z != 0, 0 at 0               -- min(h, min h + C).
+ * Backward: x_{n-1} minimises M^_{n-1}; x_i = pi_{i,i+1}(x_{i+1}), pi taken from its definition
+ * as an argmin of M^_i(z) + min(w_i |x_{i+1} - z|, C_i) over z (the minimum of this piecewise-
+ * linear function lies at a breakpoint of M^_i, at x_{i+1}, or at x_{i+1} -+ C_i / w_i; the
+ * first minimum in that order is taken), for which every M^_i is kept.
+ */
+typedef struct {
+    int64_t t;     /* breakpoints lam[0..t-1], non-decreasing */
+    double s0;     /* slope left of lam[0] */
+    double *lam;
+    double *s;     /* s[p]: slope right of lam[p] */
+    double v0;     /* value at lam[0] (t > 0), or the constant (t = 0) */
+    int64_t cap;
+} tvo_plf;
+
+static int plf_reserve(tvo_plf *h, int64_t cap)
+{
+    if (cap <= h->cap) return TVO_OK;
+    double *l = (double *)realloc(h->lam, sizeof(double) * (size_t)cap);
+    if (!l) return TVO_ERR_NOMEM;
+    h->lam = l;
+    double *s = (double *)realloc(h->s, sizeof(double) * (size_t)cap);
+    if (!s) return TVO_ERR_NOMEM;
+    h->s = s;
+    h->cap = cap;
+    return TVO_OK;
+}
+
+static void plf_free(tvo_plf *h)
+{
+    free(h->lam);
+    free(h->s);
+    h->lam = h->s = NULL;
+    h->cap = h->t = 0;
+}
+
+/* values at the breakpoints */
+static void plf_values(const tvo_plf *h, double *v)
+{
+    if (h->t == 0) return;
+    v[0] = h->v0;
+    for (int64_t p = 1; p < h->t; ++p) v[p] = v[p - 1] + h->s[p - 1] * (h->lam[p] - h->lam[p - 1]);
+}
+
+static double plf_eval(const tvo_plf *h, double z)
+{
+    if (h->t == 0) return h->v0;
+    if (z <= h->lam[0]) return h->v0 + h->s0 * (z - h->lam[0]);
+    double v = h->v0;
+    int64_t p = 0;
+    while (p + 1 < h->t && h->lam[p + 1] <= z) {
+        v += h->s[p] * (h->lam[p + 1] - h->lam[p]);
+        ++p;
+    }
+    return v + h->s[p] * (z - h->lam[p]);
+}
+
+static int plf_push(tvo_plf *o, double lam, double s)
+{
+    if (o->t == o->cap && plf_reserve(o, o->cap ? 2 * o->cap : 16) != TVO_OK) return TVO_ERR_NOMEM;
+    o->lam[o->t] = lam;
+    o->s[o->t] = s;
+    o->t += 1;
+    return TVO_OK;
+}
+
+/* eq. Message:update:a on a chain: o = h + f, breakpoints merged, slopes added. */
+static int plf_sum(const tvo_plf *h, const tvo_plf *f, tvo_plf *o)
+{
+    o->t = 0;
+    o->s0 = h->s0 + f->s0;
+    int64_t i = 0, j = 0;
+    while (i < h->t || j < f->t) {
+        double z;
+        if (j >= f->t || (i < h->t && h->lam[i] <= f->lam[j])) z = h->lam[i];
+        else z = f->lam[j];
+        while (i < h->t && h->lam[i] == z) ++i;
+        while (j < f->t && f->lam[j] == z) ++j;
+        /* slopes right of z: of the last breakpoint at or left of z in each, else s0 */
+        const double sh = i > 0 ? h->s[i - 1] : h->s0;
+        const double sf = j > 0 ? f->s[j - 1] : f->s0;
+        if (plf_push(o, z, sh + sf) != TVO_OK) return TVO_ERR_NOMEM;
+    }
+    o->v0 = o->t ? plf_eval(h, o->lam[0]) + plf_eval(f, o->lam[0]) : h->v0 + f->v0;
+    return TVO_OK;
+}
+
+/* h^rev(z) = h(-z): the sequence reversed and negated. */
+static int plf_rev(const tvo_plf *h, tvo_plf *o)
+{
+    if (plf_reserve(o, h->t + 1) != TVO_OK) return TVO_ERR_NOMEM;
+    o->t = h->t;
+    if (h->t == 0) {
+        o->s0 = -h->s0;
+        o->v0 = h->v0;
+        return TVO_OK;
+    }
+    o->s0 = -h->s[h->t - 1];
+    for (int64_t k = 0; k < h->t; ++k) {
+        o->lam[k] = -h->lam[h->t - 1 - k];
+        o->s[k] = k + 1 < h->t ? -h->s[h->t - 2 - k] : -h->s0;
+    }
+    o->v0 = plf_eval(h, h->lam[h->t - 1]);
+    return TVO_OK;
+}
+
+/* Algorithm 1: o = h (x) f^1 with f^1(z) = w z for z >= 0, +inf for z < 0 (h bounded below,
+ * so s_0 <= 0 <= w). `v` is scratch of h->t values. */
+static int plf_mc1(const tvo_plf *h, double w, tvo_plf *o, double *v)
+{
+    o->t = 0;
+    o->s0 = h->s0;
+    o->v0 = h->v0;
+    const int64_t t = h->t;
+    if (t == 0) return TVO_OK;
+    plf_values(h, v);
+    int64_t p = 0;
+    while (p < t) {
+        if (plf_push(o, h->lam[p], h->s[p] < w ? h->s[p] : w) != TVO_OK) return TVO_ERR_NOMEM;
+        if (h->s[p] >= w) {
+            /* hbar(z) = w (z - lam_p) + h(lam_p); the smallest q in p+2..t (q = t is the
+             * right end, far out on the last segment) with h(lam_q) < hbar(lam_q) */
+            int64_t q = p + 2;
+            for (; q < t; ++q)
+                if (v[q] < w * (h->lam[q] - h->lam[p]) + v[p]) break;
+            if (q >= t && !(h->s[t - 1] < w)) return TVO_OK; /* [lam_p, +inf] maps to lam_p */
+            if (q > t) q = t;
+            /* h = hbar on the segment right of lam_{q-1} (slope s_{q-1} < w) */
+            const double l0 = h->lam[q - 1];
+            const double gap = v[q - 1] - (w * (l0 - h->lam[p]) + v[p]); /* >= 0 */
+            const double z = l0 + gap / (w - h->s[q - 1]);
+            if (plf_push(o, z, h->s[q - 1]) != TVO_OK) return TVO_ERR_NOMEM;
+            p = q;
+        } else {
+            ++p;
+        }
+    }
+    return TVO_OK;
+}
+
+/* o = h (x) f^3 = min(h, min h + C), C >= 0 finite; h bounded below. Drops breakpoints
+ * whose two slopes agree. `v` is scratch of h->t values. */
+static int plf_mc3(const tvo_plf *h, double C, tvo_plf *o, double *v)
+{
+    o->t = 0;
+    if (h->t == 0) {
+        o->s0 = h->s0;
+        o->v0 = h->v0;
+        return TVO_OK;
+    }
+    plf_values(h, v);
+    double m = v[0];
+    for (int64_t p = 1; p < h->t; ++p) m = v[p] < m ? v[p] : m;
+    const double cap = m + C;
+    /* the points (z, value) of min(h, cap), in order, then slopes between them */
+    int64_t np = 0, npcap = 2 * h->t + 2;
+    double *pz = (double *)malloc(sizeof(double) * (size_t)npcap);
+    double *pv = (double *)malloc(sizeof(double) * (size_t)npcap);
+    if (!pz || !pv) {
+        free(pz);
+        free(pv);
+        return TVO_ERR_NOMEM;
+    }
+    /* left end: h rises to the left with slope -s0 >= 0 */
+    double sl = h->s0;
+    if (v[0] >= cap) sl = 0.0;
+    else if (h->s0 < 0.0) {
+        pz[np] = h->lam[0] + (cap - v[0]) / h->s0;
+        pv[np++] = cap;
+        sl = 0.0;
+    }
+    for (int64_t p = 0; p < h->t; ++p) {
+        pz[np] = h->lam[p];
+        pv[np++] = v[p] < cap ? v[p] : cap;
+        if (p + 1 < h->t) {
+            const double a = v[p] - cap, b = v[p + 1] - cap;
+            if ((a < 0.0 && b > 0.0) || (a > 0.0 && b < 0.0)) {
+                pz[np] = h->lam[p] + (h->lam[p + 1] - h->lam[p]) * (a / (a - b));
+                pv[np++] = cap;
+            }
+        }
+    }
+    const int64_t last = h->t - 1;
+    double sr = h->s[last];
+    if (v[last] >= cap) sr = 0.0;
+    else if (h->s[last] > 0.0) {
+        pz[np] = h->lam[last] + (cap - v[last]) / h->s[last];
+        pv[np++] = cap;
+        sr = 0.0;
+    }
+    o->s0 = sl;
+    o->v0 = pv[0];
+    for (int64_t k = 0; k < np; ++k) {
+        const double s = k + 1 < np ? (pz[k + 1] > pz[k] ? (pv[k + 1] - pv[k]) / (pz[k + 1] - pz[k])
+                                                         : 0.0)
+                                    : sr;
+        const double s_left = o->t ? o->s[o->t - 1] : sl;
+        if (k > 0 && k + 1 < np && s == s_left) continue; /* no change of slope */
+        if (o->t == 0) o->v0 = pv[k];
+        if (plf_push(o, pz[k], s) != TVO_OK) {
+            free(pz);
+            free(pv);
+            return TVO_ERR_NOMEM;
+        }
+    }
+    free(pz);
+    free(pv);
+    return TVO_OK;
+}
+
+/* the objective of the backward step at z */
+static double nc_back_obj(const tvo_plf *h, double z, double xn, double w, double C)
+{
+    double d = w * fabs(xn - z);
+    if (d > C) d = C;
+    return plf_eval(h, z) + d;
+}
+
+/*
+ * One chain of n nodes. Unary i: breakpoints ul[uo[i]..uo[i+1]), values uv there, slopes
+ * sl[i] (left end) and sr[i] (right end). w[i], C[i]: edge (i, i+1) (entries at i = n-1
+ * unused; C = INFINITY for plain TV). x: n outputs; *energy: the optimum.
+ */
+static int chain_nonconvex_core(int64_t n, const int64_t *uo, const double *ul, const double *uv,
+                                const double *sl, const double *sr, const double *w,
+                                const double *C, double *x, double *energy)
+{
+    if (n <= 0) {
+        *energy = 0.0;
+        return TVO_OK;
+    }
+    tvo_plf *Mh = (tvo_plf *)calloc((size_t)n, sizeof(tvo_plf)); /* M^_i, kept */
+    tvo_plf f = {0}, a = {0}, b = {0};
+    double *v = NULL;
+    int64_t vcap = 0;
+    int st = TVO_OK;
+    if (!Mh) return TVO_ERR_NOMEM;
+    for (int64_t i = 0; i < n && st == TVO_OK; ++i) {
+        /* f_i as a sequence */
+        const int64_t t = uo[i + 1] - uo[i];
+        st = plf_reserve(&f, t + 1);
+        if (st != TVO_OK) break;
+        f.t = t;
+        if (t == 0) {
+            /* bounded below and linear: a constant */
+            f.s0 = 0.0;
+            f.v0 = 0.0;
+        } else {
+            f.s0 = sl[i];
+            f.v0 = uv[uo[i]];
+            for (int64_t p = 0; p < t; ++p) {
+                f.lam[p] = ul[uo[i] + p];
+                f.s[p] = p + 1 < t ? (ul[uo[i] + p + 1] > ul[uo[i] + p]
+                                          ? (uv[uo[i] + p + 1] - uv[uo[i] + p]) /
+                                                (ul[uo[i] + p + 1] - ul[uo[i] + p])
+                                          : 0.0)
+                                   : sr[i];
+            }
+        }
+        if (i == 0) {
+            st = plf_reserve(&Mh[0], t + 1);
+            if (st != TVO_OK) break;
+            Mh[0].t = f.t;
+            Mh[0].s0 = f.s0;
+            Mh[0].v0 = f.v0;
+            memcpy(Mh[0].lam, f.lam, sizeof(double) * (size_t)t);
+            memcpy(Mh[0].s, f.s, sizeof(double) * (size_t)t);
+        } else {
+            st = plf_sum(&b, &f, &Mh[i]); /* b holds M_{i-1,i} */
+            if (st != TVO_OK) break;
+        }
+        if (i == n - 1) break;
+        /* M_{i,i+1} = ((M^_i (x) f^1) (x) f^2) (x) f^3 */
+        const tvo_plf *h = &Mh[i];
+        const int64_t need = 2 * h->t + 4;
+        if (need > vcap) {
+            double *nv = (double *)realloc(v, sizeof(double) * (size_t)need);
+            if (!nv) {
+                st = TVO_ERR_NOMEM;
+                break;
+            }
+            v = nv;
+            vcap = need;
+        }
+        if ((st = plf_mc1(h, w[i], &a, v)) != TVO_OK) break;       /* (x) f^1 */
+        if ((st = plf_rev(&a, &b)) != TVO_OK) break;
+        if ((st = plf_mc1(&b, w[i], &a, v)) != TVO_OK) break;      /* (x) f^2 via reversal */
+        if ((st = plf_rev(&a, &b)) != TVO_OK) break;
+        if (isfinite(C[i])) {
+            if (2 * b.t + 4 > vcap) {
+                double *nv = (double *)realloc(v, sizeof(double) * (size_t)(2 * b.t + 4));
+                if (!nv) {
+                    st = TVO_ERR_NOMEM;
+                    break;
+                }
+                v = nv;
+                vcap = 2 * b.t + 4;
+            }
+            if ((st = plf_mc3(&b, C[i], &a, v)) != TVO_OK) break;  /* (x) f^3 */
+            if ((st = plf_reserve(&b, a.t + 1)) != TVO_OK) break;
+            b.t = a.t;
+            b.s0 = a.s0;
+            b.v0 = a.v0;
+            memcpy(b.lam, a.lam, sizeof(double) * (size_t)a.t);
+            memcpy(b.s, a.s, sizeof(double) * (size_t)a.t);
+        }
+    }
+    if (st == TVO_OK) {
+        /* x_{n-1}: the first minimiser of M^_{n-1} among its breakpoints */
+        const tvo_plf *h = &Mh[n - 1];
+        double best = h->v0, bz = h->t ? h->lam[0] : 0.0, val = h->v0;
+        for (int64_t p = 1; p < h->t; ++p) {
+            val += h->s[p - 1] * (h->lam[p] - h->lam[p - 1]);
+            if (val < best) {
+                best = val;
+                bz = h->lam[p];
+            }
+        }
+        x[n - 1] = bz;
+        *energy = best;
+        for (int64_t i = n - 2; i >= 0; --i) {
+            const tvo_plf *g = &Mh[i];
+            const double xn = x[i + 1];
+            double bzz = xn, bo = nc_back_obj(g, xn, xn, w[i], C[i]);
+            for (int64_t p = 0; p < g->t; ++p) {
+                const double o = nc_back_obj(g, g->lam[p], xn, w[i], C[i]);
+                if (o < bo) {
+                    bo = o;
+                    bzz = g->lam[p];
+                }
+            }
+            if (isfinite(C[i]) && w[i] > 0.0) {
+                const double r = C[i] / w[i];
+                const double zc[2] = {xn - r, xn + r};
+                for (int k = 0; k < 2; ++k) {
+                    const double o = nc_back_obj(g, zc[k], xn, w[i], C[i]);
+                    if (o < bo) {
+                        bo = o;
+                        bzz = zc[k];
+                    }
+                }
+            }
+            x[i] = bzz;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) plf_free(&Mh[i]);
+    free(Mh);
+    plf_free(&f);
+    plf_free(&a);
+    plf_free(&b);
+    free(v);
+    return st;
+}
+
+/* Batch of contiguous chains (CSR offsets over nodes). uo: node -> breakpoint offsets
+ * (N + 1 entries, absolute). energy: one per chain. */
+int tvo_chain_solve_nonconvex_batch(const int64_t *uo, const double *ul, const double *uv,
+                                    const double *sl, const double *sr, const double *w,
+                                    const double *C, const int64_t *offsets, int64_t nchains,
+                                    double *x, double *energy)
+{
+    if (!uo || !offsets || !x || !energy || nchains < 0) return TVO_ERR_INVALID;
+    for (int64_t k = 0; k < nchains; ++k) {
+        const int64_t o = offsets[k], len = offsets[k + 1] - o;
+        if (len < 0) return TVO_ERR_INVALID;
+        for (int64_t i = 0; i < len; ++i)
+            if (uo[o + i + 1] < uo[o + i]) return TVO_ERR_INVALID;
+        const int st = chain_nonconvex_core(len, uo + o, ul, uv, sl + o, sr + o, w + o, C + o,
+                                            x + o, &energy[k]);
+        if (st != TVO_OK) return st;
+    }
+    return TVO_OK;
+}
