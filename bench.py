@@ -82,10 +82,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+# the sources each recorded kernel is built from (its translation unit and the
+# shared headers): a change to any of them voids that kernel's recorded traffic
+KERNEL_SOURCES = {
+    "tv2d": ["tv2d.cu", "tv2d_common.cuh", "tv_coop.cuh", "tv_dp.cuh", "tv_launch.cuh", "tv_host.h"],
+    "chain": ["tv_chain.cu", "tv_coop.cuh", "tv_dp.cuh", "tv_launch.cuh", "tv_host.h"],
+    "pq": ["tv_pq.cu", "tv_coop.cuh", "tv_dp.cuh", "tv_launch.cuh", "tv_host.h"],
+}
+
+
+def kernel_source_hash(group):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1502_07770_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES[group]:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -93,11 +102,12 @@ def kernel_source_hash():
 
 def recorded_traffic(kind):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
+    the current sources of that kernel; else None."""
+    group = kind.split("_")[0]
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             t = json.load(fh)
-        if t.get("kernel_source_hash") == kernel_source_hash():
+        if t.get("source_hash", {}).get(group) == kernel_source_hash(group):
             return t.get(kind)
     except Exception:
         pass
@@ -495,7 +505,21 @@ def main():
         b.synchronize()
         if rep >= args.warmup:
             l1_ms.append(a.elapsed_time(b))
+    _lib.profile_enable(True)
+    _lib.profile_read("col")
+    _lib.profile_read("row")
+    _lib.tv2d_denoise_l1(f1, lam=0.55, tau=0.1, max_iters=L1_ITERS, tol=0.0,
+                         check_every=L1_ITERS, out=x)
+    torch.cuda.synchronize(dev)
+    l1c, l1r = _lib.profile_read("col"), _lib.profile_read("row")
+    _lib.profile_enable(False)
+    pq_ms = l1r[0] / max(l1r[1], 1)
+    pq_achieved = 12.0 * H * W / (pq_ms * 1e-3) / 1e9  # read xi, f; write x
     tv_l1 = {"ms": float(np.median(l1_ms)), "iterations": r1[1],
+             "col_kernel_ms": l1c[0] / max(l1c[1], 1), "row_kernel_ms": pq_ms,
+             "row_roofline": {"bound": "hbm", "kernel": "pq_chain_kernel", "achieved": pq_achieved,
+                              "peak": hbm, "unit": "GB/s", "frac": pq_achieved / hbm,
+                              "traffic": recorded_traffic("pq_row"), "bytes_per_pixel": 12},
              "ms_per_iteration": float(np.median(l1_ms)) / L1_ITERS, "energy": r1[2],
              "tau": 0.1, "workload": f"{H}x{W} shapes image with 25% salt-and-pepper pixels, "
                                      "lambda 0.55, 100 iterations of eq. pd (column chains + "

@@ -6,6 +6,7 @@
     python -m paper_1502_07770_gb300.profile_cases net      [--reps R]   # warm-start inference 1024x1024
     python -m paper_1502_07770_gb300.profile_cases train    [--reps R]   # one training step, 8 x 512x512
     python -m paper_1502_07770_gb300.profile_cases batched  [--reps R]   # 16 uneven images, host-replayed loop
+    python -m paper_1502_07770_gb300.profile_cases l1       [--reps R]   # TV-l1 1024x1024, 10 iterations
 
 Each case runs its workload R times (after one untimed call) and prints one line. The
 batched case forbids the conditional-graph loop so that every kernel is an ordinary
@@ -23,7 +24,7 @@ from . import _lib, learned, synth
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["tv2d", "chain", "backward", "net", "train", "batched"])
+    ap.add_argument("case", choices=["tv2d", "chain", "backward", "net", "train", "batched", "l1"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--chains", type=int, default=32768)
     ap.add_argument("--len", type=int, default=1024)
@@ -51,6 +52,10 @@ def main(argv=None):
             fs, lams, ys = learned.make_dataset(range(10000, 10008), H=512, W=512, device=dev,
                                                 tol=1e-4, max_iters=50)
             run = lambda: net.train_step(fs, lams, ys)
+    elif a.case == "l1":
+        f = torch.from_numpy(synth.salt_pepper_image(1024, 1024, seed=7)).to(dev)
+        run = lambda: _lib.tv2d_denoise_l1(f, lam=0.55, tau=0.1, max_iters=10, tol=0.0,
+                                           check_every=10)
     else:
         _lib.set_batched_graph(False)
         sizes, lams = synth.uneven_image_sizes(16, seed=100)
