@@ -43,7 +43,8 @@ typedef enum {
     TV_ERR_CUDA = 2,           /* a CUDA runtime call or launch failed */
     TV_ERR_NOT_CONVERGED = 3,  /* tv2d_denoise stopped at max_iters above gap_tol */
     TV_ERR_TIMEOUT = 4,        /* reserved: a bounded device wait gave up */
-    TV_ERR_NOMEM = 5           /* the workspace is smaller than the size query asked for */
+    TV_ERR_NOMEM = 5,          /* the workspace is smaller than the size query asked for */
+    TV_ERR_CAPACITY = 6        /* a message outgrew max_breakpoints (tv_chain_solve_nonconvex) */
 } tv_status;
 
 typedef void *tv_stream_t; /* cudaStream_t */
@@ -163,6 +164,47 @@ tv_status tv_chain_solve_pq(const float *d_a, const float *d_b, const float *d_a
                             tv_stream_t stream);
 
 /*
+ * Non-convex chains (Sec. 3): continuous piecewise-linear unaries and truncated TV,
+ *     x* in argmin_x sum_i f_i(x_i) + sum_{i<n} min(w_i |x_{i+1} - x_i|, C_i),
+ * solved exactly (up to FP32 rounding) by dynamic programming on the chain (eq.
+ * Message:update) with piecewise-linear messages; the min-convolution with min(w|.|, C)
+ * is taken as the three consecutive ones of Prop. ConsecutiveMinConvolution (Algorithm 1,
+ * its mirror image, and the truncation). One warp per chain; messages of up to
+ * max_breakpoints points in shared memory; every M^_i kept in the workspace for the
+ * backward pass. A minimiser need not be unique: x is one of them.
+ *   unaries    either CSR: d_uoff (num_nodes + 1 absolute offsets, non-decreasing), d_ulam
+ *              (strictly increasing breakpoints per node) and d_uval (values there); or a
+ *              grid (d_uoff = d_ulam = NULL): breakpoints 0, 1, ..., grid_len - 1 and values
+ *              d_uval[i * grid_len + l] (a cost volume). A node with no breakpoint is 0.
+ *   d_sl, d_sr per-node slopes of the unaries left of the first and right of the last
+ *              breakpoint (NULL: the scalars sl <= 0 and sr >= 0 for every node)
+ *   d_w, d_C   per-node edge weight and truncation of the edge to the next node (entry at
+ *              a chain's last node unused), or NULL: the scalars w >= 0 and C >= 0 (C =
+ *              INFINITY: plain TV)
+ *   d_offsets, num_chains, max_len: as for tv_chain_solve (NULL offsets: num_chains
+ *              chains of max_len nodes, num_nodes = num_chains * max_len)
+ *   max_breakpoints  points a message may hold (1..4096; a node's breakpoint count plus
+ *              the incoming message's must fit)
+ *   d_x        num_nodes outputs; d_energy: num_chains optimum energies (FP64 sum of FP32
+ *              message minima)
+ *   workspace  tv_chain_nonconvex_workspace_size(num_nodes, num_chains, max_len,
+ *              max_breakpoints) bytes (num_chains * max_len * max_breakpoints * 8 + ...).
+ * A chain whose message outgrows max_breakpoints gets NaN in x and energy and the
+ * workspace error word reports TV_ERR_CAPACITY (tv_workspace_status). Unaries must be
+ * bounded below (sl <= 0 <= sr); other values give undefined results, never an
+ * out-of-bounds access. Asynchronous on `stream`.
+ */
+size_t tv_chain_nonconvex_workspace_size(int64_t num_nodes, int64_t num_chains, int64_t max_len,
+                                         int max_breakpoints);
+tv_status tv_chain_solve_nonconvex(const int64_t *d_uoff, const float *d_ulam,
+                                   const float *d_uval, int grid_len, const float *d_sl,
+                                   const float *d_sr, float sl, float sr, const float *d_w,
+                                   float w, const float *d_C, float C, const int64_t *d_offsets,
+                                   int64_t num_nodes, int64_t num_chains, int64_t max_len,
+                                   int max_breakpoints, float *d_x, double *d_energy,
+                                   void *d_workspace, size_t workspace_bytes, tv_stream_t stream);
+
+/*
  * Backward of the chain prox (vector-Jacobian product), for a differentiable TV
  * layer. From the optimality conditions of eq. 1D-ROF, on every maximal run S of
  * equal values of the solution x ("segment"), x_S = mean(y_S) + (u_r - u_{l-1})/|S|
@@ -201,8 +243,9 @@ tv_status tv_chain_solve_columns(const float *d_y, const float *d_w, float lambd
 
 /*
  * Read back and clear the device-side error word of a workspace used by the chain
- * calls above (synchronises `stream`). *d_status_out receives TV_OK or
- * TV_ERR_INVALID (a chain longer than max_len, or decreasing offsets). When
+ * calls above (synchronises `stream`). *d_status_out receives TV_OK,
+ * TV_ERR_INVALID (a chain longer than max_len, or decreasing offsets) or
+ * TV_ERR_CAPACITY (tv_chain_solve_nonconvex: a message outgrew max_breakpoints). When
  * overflowed != NULL it receives how many chains outgrew on-chip message storage
  * and were finished from the workspace reserve (a performance counter).
  */

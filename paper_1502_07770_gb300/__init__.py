@@ -10,8 +10,8 @@ The CUDA binding is imported lazily so that ``synth`` (input generators) can
 be used without a GPU.
 """
 _LIB_NAMES = ("chain_prox", "chain_prox_columns", "chain_prox_backward", "chain_prox_diff",
-              "chain_prox_general", "chain_prox_pq", "ChainProxFn", "tv2d_denoise",
-              "tv2d_denoise_batched", "tv2d_denoise_lagrangian", "tv2d_denoise_l1",
+              "chain_prox_general", "chain_prox_pq", "chain_prox_nonconvex", "ChainProxFn",
+              "tv2d_denoise", "tv2d_denoise_batched", "tv2d_denoise_lagrangian", "tv2d_denoise_l1",
               "workspace_status")
 __all__ = list(_LIB_NAMES) + ["synth", "autotune"]
 

@@ -18,7 +18,8 @@ import torch
 
 from . import build as _build
 
-TV_OK, TV_ERR_INVALID, TV_ERR_CUDA, TV_ERR_NOT_CONVERGED, TV_ERR_TIMEOUT, TV_ERR_NOMEM = range(6)
+(TV_OK, TV_ERR_INVALID, TV_ERR_CUDA, TV_ERR_NOT_CONVERGED, TV_ERR_TIMEOUT, TV_ERR_NOMEM,
+ TV_ERR_CAPACITY) = range(7)
 
 _lock = threading.Lock()
 _lib = None
@@ -61,6 +62,11 @@ SIGNATURES = {
     "tv_set_batched_graph": (ctypes.c_int, [ctypes.c_int]),
     "tv_set_coop_max_chains": (ctypes.c_int, [_i64]),
     "tv_chain_pq_workspace_size": (_sz, [_i64, _i64]),
+    "tv_chain_nonconvex_workspace_size": (_sz, [_i64, _i64, _i64, ctypes.c_int]),
+    "tv_chain_solve_nonconvex": (ctypes.c_int, [_p, _p, _p, ctypes.c_int, _p, _p, ctypes.c_float,
+                                                ctypes.c_float, _p, ctypes.c_float, _p,
+                                                ctypes.c_float, _p, _i64, _i64, _i64,
+                                                ctypes.c_int, _p, _p, _p, _sz, _p]),
     "tv_chain_solve_pq": (ctypes.c_int, [_p, _p, _p, ctypes.c_float, _p, _p, ctypes.c_float, _p,
                                          _i64, _i64, _p, _p, _sz, _p]),
     "tv2d_lagrangian_workspace_size": (_sz, [_i64, _i64]),
@@ -241,6 +247,56 @@ def chain_prox_pq(b, f, a=None, alpha=1.0, w=None, lam: float = 0.0, offsets=Non
                                  float(lam), _ptr(offsets), num_chains, max_len, _ptr(x),
                                  _ptr(wsb), wsb.numel(), _stream(b.device)))
     return x
+
+
+def chain_prox_nonconvex(uval, uoff=None, ulam=None, sl=-1.0, sr=1.0, w=0.0, C=float("inf"),
+                         offsets=None, max_len: int | None = None, max_breakpoints: int = 512,
+                         out=None, energy=None, ws=None):
+    """Non-convex chains (Sec. 3): argmin sum_i f_i(x_i) + sum_i min(w_i |x_{i+1} - x_i|, C_i)
+    with continuous piecewise-linear unaries f_i.
+
+    Unaries: a cost volume ``uval`` of shape (num_chains, n, L) or (num_nodes, L) with
+    breakpoints 0..L-1 (``uoff`` None), or CSR ``uoff`` (num_nodes + 1, int64), ``ulam``,
+    ``uval`` (flat). ``sl``/``sr`` (end slopes), ``w`` and ``C`` are per-node tensors or
+    scalars. Chains: ``offsets`` (CSR over nodes, with ``max_len``) or, without offsets,
+    the (num_chains, n) layout of a grid ``uval`` (CSR: one chain). Returns
+    ``(x, energy)``: x per node, the optimum energy per chain (float64)."""
+    lib = load()
+    _require_cuda(*[v for v in (uval, ulam, sl, sr, w, C) if torch.is_tensor(v)])
+    for v in (uoff, offsets):
+        if v is not None and (not v.is_cuda or v.dtype != torch.int64 or not v.is_contiguous()):
+            raise ValueError("uoff and offsets must be contiguous int64 CUDA tensors")
+    dev = uval.device
+    if uoff is None:
+        L = uval.shape[-1]
+        num_nodes = uval.numel() // L
+        if offsets is None:
+            if uval.dim() != 3:
+                raise ValueError("uval must be (num_chains, n, L) when offsets is None")
+            num_chains, max_len = uval.shape[0], uval.shape[1]
+    else:
+        L = 0
+        num_nodes = uoff.numel() - 1
+        if offsets is None:
+            num_chains, max_len = 1, num_nodes
+    if offsets is not None:
+        if max_len is None:
+            raise ValueError("max_len is required with offsets")
+        num_chains = offsets.numel() - 1
+    x = torch.empty(num_nodes, dtype=torch.float32, device=dev) if out is None else out
+    e = torch.empty(num_chains, dtype=torch.float64, device=dev) if energy is None else energy
+    nbytes = lib.tv_chain_nonconvex_workspace_size(num_nodes, num_chains, max_len,
+                                                   int(max_breakpoints))
+    wsb = ws if ws is not None else workspace(nbytes, dev, "nonconvex")
+    tens = lambda v: v if torch.is_tensor(v) else None
+    scal = lambda v: 0.0 if torch.is_tensor(v) else float(v)
+    _check(lib.tv_chain_solve_nonconvex(_ptr(uoff), _ptr(ulam), _ptr(uval), int(L),
+                                        _ptr(tens(sl)), _ptr(tens(sr)), scal(sl), scal(sr),
+                                        _ptr(tens(w)), scal(w), _ptr(tens(C)), scal(C),
+                                        _ptr(offsets), num_nodes, num_chains, max_len,
+                                        int(max_breakpoints), _ptr(x), _ptr(e), _ptr(wsb),
+                                        wsb.numel(), _stream(dev)))
+    return x, e
 
 
 def chain_prox_columns(y, w=None, lam: float = 0.0, out=None, ws=None):

@@ -15,7 +15,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtv.so")
 SOURCES = ["tv_chain.cu", "tv2d.cu", "tv2d_batched.cu", "tv2d_lagrangian.cu", "tv_grad.cu",
-           "tv_net.cu", "tv_pq.cu"]
+           "tv_net.cu", "tv_pq.cu", "tv_nonconvex.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-diag-suppress", "177",
          "-I", INCLUDE]

@@ -772,7 +772,9 @@ tv_status tv_workspace_status(void *d_workspace, tv_stream_t stream, int *status
                               "read header");
     if (st == TV_OK) st = check_cuda(cudaStreamSynchronize(s), "synchronize");
     if (st != TV_OK) return st;
-    *status_out = (h.status & ERR_BAD_CHAIN) ? TV_ERR_INVALID : TV_OK;
+    *status_out = (h.status & ERR_BAD_CHAIN)  ? TV_ERR_INVALID
+                  : (h.status & ERR_CAPACITY) ? TV_ERR_CAPACITY
+                                              : TV_OK;
     if (overflowed) *overflowed = (int64_t)h.overflowed;
     return check_cuda(cudaMemsetAsync(d_workspace, 0, sizeof(WsHeader), s), "clear header");
 }

@@ -59,6 +59,7 @@ constexpr int QPC = CH / 4;  // 16-byte quads per chain and chunk
 
 // Device error word bits (workspace header).
 constexpr int ERR_BAD_CHAIN = 1;
+constexpr int ERR_CAPACITY = 2;  // a message outgrew its storage (chain left NaN)
 
 struct WsHeader {
     int status;              // ERR_* bits, sticky until read

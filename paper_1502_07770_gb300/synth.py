@@ -106,6 +106,52 @@ def salt_pepper_image(H: int, W: int, seed: int, frac: float = 0.25) -> np.ndarr
     return f.astype(np.float32)
 
 
+def stereo_cost_volume(H: int, W: int, L: int, seed: int, slope: float = 0.25,
+                       trunc: float = 1.0, noise: float = 0.3,
+                       outliers: float = 0.1) -> tuple[np.ndarray, np.ndarray]:
+    """A synthetic matching-cost volume standing in for a stereo data term (Sec. 6):
+    a disparity map of random slanted planes on rectangles and ellipses (levels in
+    [0, L-1]), and per pixel the non-convex cost c(d) = min(slope |d - d*|, trunc) +
+    U[0, noise] at the integer disparities d = 0..L-1, plus, at a fraction ``outliers`` of
+    the pixels, a false minimum of depth 0.5 at a uniform disparity. Returns
+    ``(cost (H, W, L) float32, d* (H, W) float32)``."""
+    rng = _rng(seed)
+    d = np.full((H, W), 0.5 * (L - 1))
+    rr = np.arange(H, dtype=np.float64)[:, None]
+    cc = np.arange(W, dtype=np.float64)[None, :]
+    for _ in range(max(4, H * W // 4000)):
+        level = rng.uniform(0.0, L - 1.0)
+        gy, gx = rng.uniform(-0.05, 0.05, 2)
+        cy, cx = rng.uniform(0.0, H), rng.uniform(0.0, W)
+        hh, hw = 0.5 * rng.uniform(H / 16.0, H / 3.0), 0.5 * rng.uniform(W / 16.0, W / 3.0)
+        rect = rng.uniform() < 0.5
+        y0, y1 = int(max(0, np.floor(cy - hh))), int(min(H, np.ceil(cy + hh) + 1))
+        x0, x1 = int(max(0, np.floor(cx - hw))), int(min(W, np.ceil(cx + hw) + 1))
+        if y1 <= y0 or x1 <= x0:
+            continue
+        ry, rx = rr[y0:y1] - cy, cc[:, x0:x1] - cx
+        if rect:
+            m = (np.abs(ry) <= hh) & (np.abs(rx) <= hw)
+        else:
+            m = ry ** 2 / hh ** 2 + rx ** 2 / hw ** 2 <= 1.0
+        sub = d[y0:y1, x0:x1]
+        sub[m] = (level + gy * ry + gx * rx)[m]
+    d = np.clip(d, 0.0, L - 1.0)
+    cost = np.empty((H, W, L), dtype=np.float32)
+    out = rng.uniform(size=(H, W)) < outliers
+    fd = rng.integers(0, L, size=(H, W))
+    lab = np.arange(L, dtype=np.float32)[None, :]
+    d32 = d.astype(np.float32)
+    for r in range(H):  # row by row, in FP32, to bound the temporaries
+        c = np.minimum(np.float32(slope) * np.abs(lab - d32[r, :, None]), np.float32(trunc))
+        c += np.float32(noise) * rng.random((W, L), dtype=np.float32)
+        o = np.flatnonzero(out[r])
+        if o.size:
+            c[o] -= np.maximum(0.0, 0.5 - slope * np.abs(lab - fd[r, o, None])).astype(np.float32)
+        cost[r] = c
+    return cost, d.astype(np.float32)
+
+
 def edge_aware_weights(f: np.ndarray, lam: float, scale: float = 0.2):
     """Per-edge weights ``lam * exp(-|f_i - f_j| / scale)`` of a float32 image.
 
