@@ -525,6 +525,38 @@ def main():
                                      "lambda 0.55, 100 iterations of eq. pd (column chains + "
                                      "piecewise-quadratic row chains)"}
 
+    # ---------------- non-convex chains (Sec. 3) on a stereo-sized cost volume ----------------
+    NC_H, NC_W, NC_L = 1000, 1482, 126
+    nc_cost = torch.from_numpy(synth.stereo_cost_volume(NC_H, NC_W, NC_L, seed=0)[0]).to(dev)
+    nc_x = torch.empty(NC_H * NC_W, dtype=torch.float32, device=dev)
+    nc_e = torch.empty(NC_H, dtype=torch.float64, device=dev)
+    nc_ms = []
+    for rep in range(args.warmup + max(3, args.steps // 10)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _lib.chain_prox_nonconvex(nc_cost, sl=-1.0, sr=1.0, w=0.1, C=0.8, max_breakpoints=512,
+                                  out=nc_x, energy=nc_e)
+        b.record(stream)
+        b.synchronize()
+        if rep >= args.warmup:
+            nc_ms.append(a.elapsed_time(b))
+    nc_status, _ = _lib.workspace_status(_lib.workspace(1, dev, "nonconvex"))
+    ncm = float(np.median(nc_ms))
+    nc_nodes = NC_H * NC_W
+    nc_bytes = nc_nodes * (NC_L * 4 + 4)  # read the node's costs, write x
+    nc_achieved = nc_bytes / (ncm * 1e-3) / 1e9
+    nonconvex = {"ms": ncm, "value": nc_nodes / (ncm * 1e-3) / 1e9, "unit": "Gnode/s",
+                 "status": int(nc_status), "max_breakpoints": 512,
+                 "roofline": {"bound": "hbm", "kernel": "nc_chain_kernel", "achieved": nc_achieved,
+                              "peak": hbm, "unit": "GB/s", "frac": nc_achieved / hbm,
+                              "bytes_per_node": NC_L * 4 + 4,
+                              "note": "latency-bound: one warp per chain, 1000 chains"},
+                 "workload": f"{NC_H} chains x {NC_W} nodes, cost volume of {NC_L} disparities "
+                             "(truncated-linear cost + noise + 10% false minima), w 0.1, C 0.8, "
+                             "the size of the paper's stereo pair"}
+    del nc_cost
+
     # ---------------- learned dual warm start (stored network) ----------------
     from paper_1502_07770_gb300 import learned
     net = learned.load_weights(dev)
@@ -619,6 +651,7 @@ def main():
                                 "edge-aware weights lambda*exp(-|df|/0.2), to per-pixel gap 1e-4"},
         "lagrangian_split": lagrangian,
         "tv_l1": tv_l1,
+        "nonconvex_chain": nonconvex,
         "learned_warm_start": {
             "heldout_512": {k: lsum[k] for k in ("images", "iters_zero", "iters_warm", "ms_zero",
                                                   "ms_warm", "fallbacks", "all_converged")},

@@ -81,6 +81,7 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_double), _p, _sz, _p]),
     "tv_chain_solve_general": (ctypes.c_int, [_p, _p, _p, _p, _p, _i64, _i64, _p, _p, _sz, _p]),
     "tv_set_coop_split": (ctypes.c_int, [ctypes.c_int]),
+    "tv_set_thread_split": (ctypes.c_int, [ctypes.c_int]),
     "tv_net_conv3x3": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       _p, _p, ctypes.c_int, ctypes.c_int, _p, _p, _p]),
     "tv_net_conv3x3_backward_data": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -517,6 +518,12 @@ def set_coop_split(mode: int):
     """0: one warp per chain from one end; 1: two 16-lane halves from the middle (default);
     2: two warps from the middle."""
     _check(load().tv_set_coop_split(int(mode)))
+
+
+def set_thread_split(on: bool):
+    """Middle-rooted chains (two threads per chain) in the one-thread-per-chain path of
+    ``chain_prox`` (True, the default) or one thread per chain from one end (False)."""
+    _check(load().tv_set_thread_split(1 if on else 0))
 
 
 def set_coop_max_chains(n: int):

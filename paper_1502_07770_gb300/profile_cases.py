@@ -7,6 +7,7 @@
     python -m paper_1502_07770_gb300.profile_cases train    [--reps R]   # one training step, 8 x 512x512
     python -m paper_1502_07770_gb300.profile_cases batched  [--reps R]   # 16 uneven images, host-replayed loop
     python -m paper_1502_07770_gb300.profile_cases l1       [--reps R]   # TV-l1 1024x1024, 10 iterations
+    python -m paper_1502_07770_gb300.profile_cases nonconvex [--reps R] [--chains B]  # B x 1482 x 126 cost volume
 
 Each case runs its workload R times (after one untimed call) and prints one line. The
 batched case forbids the conditional-graph loop so that every kernel is an ordinary
@@ -24,9 +25,10 @@ from . import _lib, learned, synth
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["tv2d", "chain", "backward", "net", "train", "batched", "l1"])
+    ap.add_argument("case", choices=["tv2d", "chain", "backward", "net", "train", "batched", "l1", "nonconvex"])
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--chains", type=int, default=32768)
+    ap.add_argument("--chains", type=int, default=None,
+                    help="chains (chain case, default 32768) or rows (nonconvex, default 1000)")
     ap.add_argument("--len", type=int, default=1024)
     a = ap.parse_args(argv)
     dev = torch.device("cuda:0")
@@ -35,7 +37,7 @@ def main(argv=None):
         run = lambda: _lib.tv2d_denoise(f, lam=0.1, max_iters=200, tol=1e-4)
     elif a.case == "chain":
         base = synth.chain_batch(256, a.len, seed0=1000)
-        y = torch.from_numpy(np.tile(base, (max(1, a.chains // 256), 1))).to(dev)
+        y = torch.from_numpy(np.tile(base, (max(1, (a.chains or 32768) // 256), 1))).to(dev)
         x = torch.empty_like(y)
         run = lambda: _lib.chain_prox(y, lam=0.15, out=x)
     elif a.case == "backward":
@@ -56,6 +58,11 @@ def main(argv=None):
         f = torch.from_numpy(synth.salt_pepper_image(1024, 1024, seed=7)).to(dev)
         run = lambda: _lib.tv2d_denoise_l1(f, lam=0.55, tau=0.1, max_iters=10, tol=0.0,
                                            check_every=10)
+    elif a.case == "nonconvex":
+        rows = a.chains or 1000
+        vol = torch.from_numpy(synth.stereo_cost_volume(rows, 1482, 126, seed=0)[0]).to(dev)
+        run = lambda: _lib.chain_prox_nonconvex(vol, sl=-1.0, sr=1.0, w=0.1, C=0.8,
+                                                max_breakpoints=512)
     else:
         _lib.set_batched_graph(False)
         sizes, lams = synth.uneven_image_sizes(16, seed=100)
