@@ -169,9 +169,10 @@ tv_status tv_chain_solve_pq(const float *d_a, const float *d_b, const float *d_a
  * solved exactly (up to FP32 rounding) by dynamic programming on the chain (eq.
  * Message:update) with piecewise-linear messages; the min-convolution with min(w|.|, C)
  * is taken as the three consecutive ones of Prop. ConsecutiveMinConvolution (Algorithm 1,
- * its mirror image, and the truncation). One warp per chain; messages of up to
- * max_breakpoints points in shared memory; every M^_i kept in the workspace for the
- * backward pass. A minimiser need not be unique: x is one of them.
+ * its mirror image, and the truncation). Each chain is rooted at its middle node and its
+ * two halves run on two warps; messages of up to max_breakpoints points in shared
+ * memory; every M^_i kept in the workspace for the backward pass. A minimiser need not
+ * be unique: x is one of them.
  *   unaries    either CSR: d_uoff (num_nodes + 1 absolute offsets, non-decreasing), d_ulam
  *              (strictly increasing breakpoints per node) and d_uval (values there); or a
  *              grid (d_uoff = d_ulam = NULL): breakpoints 0, 1, ..., grid_len - 1 and values
@@ -188,7 +189,8 @@ tv_status tv_chain_solve_pq(const float *d_a, const float *d_b, const float *d_a
  *   d_x        num_nodes outputs; d_energy: num_chains optimum energies (FP64 sum of FP32
  *              message minima)
  *   workspace  tv_chain_nonconvex_workspace_size(num_nodes, num_chains, max_len,
- *              max_breakpoints) bytes (num_chains * max_len * max_breakpoints * 8 + ...).
+ *              max_breakpoints) bytes (num_chains * (max_len + 1) * max_breakpoints * 8
+ *              + ...).
  * A chain whose message outgrows max_breakpoints gets NaN in x and energy and the
  * workspace error word reports TV_ERR_CAPACITY (tv_workspace_status). Unaries must be
  * bounded below (sl <= 0 <= sr); other values give undefined results, never an

@@ -7,7 +7,8 @@
 // with f^1 (Algorithm 1), with f^2 (Algorithm 1 on the mirrored function) and with f^3
 // (min(h, min h + C)).
 //
-// One warp per chain. A message is a list of breakpoints (lambda_p, h(lambda_p)) in shared
+// Two warps per chain, one per half of a chain rooted at its middle node (see
+// nc_chain_kernel). A message is a list of breakpoints (lambda_p, h(lambda_p)) in shared
 // memory plus the slopes of its two ends; each lane owns a contiguous chunk of the list.
 //  - sum: the two sorted lists are merged by merge-path partitioning (one binary search
 //    per lane, then a sequential merge of the lane's output chunk), every point taking
@@ -21,9 +22,10 @@
 // Values are kept relative to the minimum of M^_i (the minimum is the same after every
 // min-convolution, since each f^k >= 0 with f^k(0) = 0); the minima are summed in FP64 into
 // the chain's optimum energy. Every M^_i goes to the workspace; the backward pass takes
-// x_{n-1} in argmin M^_{n-1} and x_i = pi_i(x_{i+1}) from the definition of pi as an argmin
-// of M^_i(z) + min(w_i |x_{i+1} - z|, C_i) over z, evaluated at every breakpoint of M^_i
-// and at x_{i+1}, x_{i+1} - C_i/w_i, x_{i+1} + C_i/w_i (the first minimum in that order).
+// the root's x in argmin M^_root and, outwards, x_i = pi_i(x_j) (j the neighbour on the
+// root side) from the definition of pi as an argmin of M^_i(z) + min(w |x_j - z|, C) over
+// z, evaluated at every breakpoint of M^_i and at x_j, x_j - C/w, x_j + C/w (the first
+// minimum in that order).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,7 +40,8 @@ namespace {
 constexpr int kNcMaxWarps = 4;
 
 // warps per block: as many as fit three message buffers each in ~220 KB of shared memory
-int nc_warps(int T) { return std::max(1, std::min(kNcMaxWarps, (220 * 1024) / (24 * T))); }
+// (at least the two warps of one chain: 2 * 24 * 4096 bytes fit)
+int nc_warps(int T) { return std::max(2, std::min(kNcMaxWarps, (220 * 1024) / (24 * T))); }
 
 struct NcArgs {
     const int64_t *uoff;  // node -> first breakpoint (N + 1 entries), or NULL: grid unaries
@@ -54,7 +57,7 @@ struct NcArgs {
     int T;                // breakpoints a message may hold
     float *x;
     double *energy;
-    float2 *arena;        // chain k's M^_i at k * maxlen * T
+    float2 *arena;        // chain k's M^_i at k * (maxlen + 1) * T, half 1 from ceil(maxlen/2) * T
     int2 *meta;           // per node: (offset in the chain's arena, count)
     float2 *tails;        // per node: end slopes of M^_i
 };
@@ -347,64 +350,97 @@ __device__ float nc_argmin(const float2 *H, int t, float sl, float sr, bool pair
     return b.z;
 }
 
+// What the two warps of a chain tell each other at the root (shared memory).
+struct NcPairXchg {
+    double esum[2];   // each half's sum of message minima
+    int ta[2], mi[2];  // each half's final message: count, buffer
+    float sl[2], sr[2], cA[2];
+    int bad[2];
+};
+
+__device__ __forceinline__ void pair_bar(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// Two warps per chain, rooted at node mid = n/2 (Algorithm 2 may take any root): warp 0
+// of the pair runs the forward pass over nodes 0..mid-1, warp 1 over nodes n-1..mid+1
+// (the pairwise terms are symmetric, so the update is the same), each ending with the
+// message into the root; after a pair barrier both warps form M^_mid = f_mid + M_L + M_R
+// from the two messages and take the same x_mid in argmin M^_mid, then each clips its own
+// half outwards. Shared memory per warp: three message buffers of T points.
 __global__ void __launch_bounds__(kNcMaxWarps * WARP) nc_chain_kernel(NcArgs p, WsHeader *hdr)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & (WARP - 1);
     const int warp = threadIdx.x / WARP;
-    const long long k = (long long)blockIdx.x * (blockDim.x / WARP) + warp;
-    if (k >= p.nchains) return;
+    const int role = warp & 1;
+    const int pair = warp >> 1;
+    const int pairs = blockDim.x / (2 * WARP);
+    const long long k = (long long)blockIdx.x * pairs + pair;
+    const int T = p.T;
+    NcPairXchg *xs = reinterpret_cast<NcPairXchg *>(smem_raw) + pair;
+    float2 *buf0 = reinterpret_cast<float2 *>(smem_raw + ((pairs * sizeof(NcPairXchg) + 15) & ~(size_t)15));
+    auto Pw = [&](int w, int b) { return buf0 + ((size_t)w * 3 + b) * T; };
+    auto P = [&](int b) { return Pw(warp, b); };
+    if (k >= p.nchains) return;  // both warps of the pair
     long long start = k * (long long)p.maxlen;
     int n = p.maxlen;
     if (p.offsets) {
         const long long off0 = p.offsets[0], lo = p.offsets[k], hi = p.offsets[k + 1];
         if (lo < off0 || hi < lo || hi - lo > p.maxlen || hi > p.nnodes) {
-            if (lane == 0) atomicOr(&hdr->status, ERR_BAD_CHAIN);
+            if (lane == 0 && role == 0) atomicOr(&hdr->status, ERR_BAD_CHAIN);
             return;
         }
         start = lo;
         n = (int)(hi - lo);
     }
     if (n == 0) {
-        if (lane == 0) p.energy[k] = 0.0;
+        if (lane == 0 && role == 0) p.energy[k] = 0.0;
         return;
     }
-    const int T = p.T;
-    float2 *buf = reinterpret_cast<float2 *>(smem_raw) + (size_t)warp * 3 * T;
-    auto P = [&](int b) { return buf + (size_t)b * T; };
-    float2 *arena = p.arena + k * (long long)p.maxlen * T;
-    // the message into node i: list in buffer mi (0 or 1), tails, constant when empty;
-    // buffer 2 holds M^_i
+    const int mid = n >> 1;
+    const int cnt = role == 0 ? mid : n - 1 - mid;
+    const long long half_cap = (long long)((p.maxlen + 1) / 2) * T;
+    float2 *arena = p.arena + k * (long long)(p.maxlen + 1) * T + role * half_cap;
+    // node of step j and the node on the root side of its edge
+    auto node_of = [&](int j) { return role == 0 ? j : n - 1 - j; };
+    auto edge_of = [&](int i) { return role == 0 ? i : i - 1; };  // index of w / C of the edge
+
+    auto load_unary = [&](long long node, float2 *F, int &tf, float &slF, float &srF) -> bool {
+        if (p.uoff) {
+            const long long u0 = p.uoff[node], u1 = p.uoff[node + 1];
+            tf = (int)max(0LL, u1 - u0);
+            if (tf > T) return false;
+            for (int q = lane; q < tf; q += WARP) F[q] = make_float2(p.ulam[u0 + q], p.uval[u0 + q]);
+        } else {
+            tf = p.grid_len;
+            if (tf > T) return false;
+            for (int q = lane; q < tf; q += WARP)
+                F[q] = make_float2((float)q, p.uval[node * (long long)p.grid_len + q]);
+        }
+        slF = p.sl ? p.sl[node] : p.sl_s;
+        srF = p.sr ? p.sr[node] : p.sr_s;
+        if (tf == 0) slF = srF = 0.f;
+        return true;
+    };
+
+    // ---------------- forward pass over this warp's half ----------------
     int mi = 0, ta = 0;
     float slA = 0.f, srA = 0.f, cA = 0.f;
     double energy = 0.0;
     unsigned aoff = 0;
     bool bad = false;
-    for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < cnt; ++j) {
+        const int i = node_of(j);
         const long long node = start + i;
-        // unary f_i into the free buffer
         const int fi = 1 - mi;
         float2 *F = P(fi);
         int tf;
-        if (p.uoff) {
-            const long long u0 = p.uoff[node], u1 = p.uoff[node + 1];
-            tf = (int)max(0LL, u1 - u0);
-            if (tf <= T)
-                for (int q = lane; q < tf; q += WARP) F[q] = make_float2(p.ulam[u0 + q], p.uval[u0 + q]);
-        } else {
-            tf = p.grid_len;
-            if (tf <= T)
-                for (int q = lane; q < tf; q += WARP)
-                    F[q] = make_float2((float)q, p.uval[node * (long long)p.grid_len + q]);
-        }
-        float slF = p.sl ? p.sl[node] : p.sl_s, srF = p.sr ? p.sr[node] : p.sr_s;
-        if (tf == 0) slF = srF = 0.f;
-        if (ta + tf > T || (long long)aoff + ta + tf > (long long)p.maxlen * T) {
+        float slF, srF;
+        if (!load_unary(node, F, tf, slF, srF) || ta + tf > T ||
+            (long long)aoff + ta + tf > half_cap) {
             bad = true;
             break;
         }
         __syncwarp();
-        // M^_i = f_i + M_{i-1,i}
         float2 *Mh = P(2);
         const int th = ta + tf;
         const float m = nc_merge(P(mi), ta, slA, srA, cA, F, tf, slF, srF, Mh, lane);
@@ -415,16 +451,9 @@ __global__ void __launch_bounds__(kNcMaxWarps * WARP) nc_chain_kernel(NcArgs p, 
             p.meta[node] = make_int2((int)aoff, th);
             p.tails[node] = make_float2(slH, srH);
         }
-        if (i == n - 1) {
-            // record M^_{n-1} (relative) for the backward pass
-            for (int q = lane; q < th; q += WARP) {
-                const float2 e = Mh[q];
-                arena[aoff + q] = make_float2(e.x, e.y - m);
-            }
-            break;
-        }
-        const float wi = p.w ? p.w[node] : p.w_s;
-        const float Ci = p.C ? p.C[node] : p.C_s;
+        const int e = edge_of(i);
+        const float wi = p.w ? p.w[start + e] : p.w_s;
+        const float Ci = p.C ? p.C[start + e] : p.C_s;
         // (x) f^1 into F's buffer (free now), recording M^_i; (x) f^2 into mi's buffer
         float s1l, s1r, s2l, s2r;
         const int t1 = nc_mc12<false>(Mh, th, slH, srH, m, wi, F, arena + aoff, lane, s1l, s1r);
@@ -455,27 +484,83 @@ __global__ void __launch_bounds__(kNcMaxWarps * WARP) nc_chain_kernel(NcArgs p, 
         __syncwarp();
     }
     bad = __any_sync(FULL, bad);
-    if (bad) {
-        if (lane == 0) {
-            atomicOr(&hdr->status, ERR_CAPACITY);
-            p.energy[k] = NAN;
+    if (lane == 0) {
+        xs->esum[role] = energy;
+        xs->ta[role] = ta;
+        xs->mi[role] = mi;
+        xs->sl[role] = slA;
+        xs->sr[role] = srA;
+        xs->cA[role] = cA;
+        xs->bad[role] = bad ? 1 : 0;
+    }
+    pair_bar(1 + pair);
+
+    // ---------------- root: M^_mid = M_L + M_R + f_mid, both warps alike ----------------
+    const bool any_bad = xs->bad[0] || xs->bad[1];
+    float xmid = 0.f;
+    bool root_bad = any_bad;
+    int tr = 0;
+    float slr = 0.f, srr = 0.f, mr = 0.f;
+    if (!any_bad) {
+        const int tL = xs->ta[0], tR = xs->ta[1];
+        const float2 *ML = Pw(2 * pair, xs->mi[0]), *MR = Pw(2 * pair + 1, xs->mi[1]);
+        const int other = 1 - xs->mi[role];  // my free message buffer
+        if (tL + tR > T) {
+            root_bad = true;
+        } else {
+            nc_merge(ML, tL, xs->sl[0], xs->sr[0], xs->cA[0], MR, tR, xs->sl[1], xs->sr[1], P(2),
+                     lane);
         }
-        for (int i = lane; i < n; i += WARP) p.x[start + i] = NAN;
+        int tf = 0;
+        float slF = 0.f, srF = 0.f;
+        if (!root_bad && !load_unary(start + mid, P(other), tf, slF, srF)) root_bad = true;
+        if (!root_bad && tL + tR + tf > T) root_bad = true;
+        __syncwarp();
+        // both warps have read both messages before either overwrites its own
+        pair_bar(1 + pair);
+        if (!root_bad) {
+            const float cLR = (tL + tR == 0) ? xs->cA[0] + xs->cA[1] : 0.f;
+            const float slLR = xs->sl[0] + xs->sl[1], srLR = xs->sr[0] + xs->sr[1];
+            float2 *R = P(xs->mi[role]);
+            mr = nc_merge(P(2), tL + tR, slLR, srLR, cLR, P(other), tf, slF, srF, R, lane);
+            tr = tL + tR + tf;
+            slr = slLR + slF;
+            srr = srLR + srF;
+            __syncwarp();
+            xmid = nc_argmin(R, tr, slr, srr, false, 0.f, 0.f, 0.f, lane);
+        }
+    } else {
+        pair_bar(1 + pair);
+    }
+    if (root_bad) {
+        if (role == 0) {
+            if (lane == 0) {
+                atomicOr(&hdr->status, ERR_CAPACITY);
+                p.energy[k] = NAN;
+            }
+            for (int i = lane; i < n; i += WARP) p.x[start + i] = NAN;
+        }
         return;
     }
-    if (lane == 0) p.energy[k] = energy;
+    if (role == 0) {
+        if (lane == 0) {
+            p.energy[k] = xs->esum[0] + xs->esum[1] + (double)mr;
+            p.x[start + mid] = xmid;
+        }
+    }
     __syncwarp();
     __threadfence_block();
-    // backward
-    float xn = 0.f;
-    for (int i = n - 1; i >= 0; --i) {
+    // ---------------- backward: clip this half outwards from the root ----------------
+    float xn = xmid;
+    for (int j = cnt - 1; j >= 0; --j) {
+        const int i = node_of(j);
         const long long node = start + i;
         const int2 mt = p.meta[node];
         const float2 tl = p.tails[node];
-        const bool pair = i < n - 1;
-        const float wi = pair ? (p.w ? p.w[node] : p.w_s) : 0.f;
-        const float Ci = pair ? (p.C ? p.C[node] : p.C_s) : 0.f;
-        const float xi = nc_argmin(arena + mt.x, mt.y, tl.x, tl.y, pair, xn, wi, Ci, lane);
+        const int e = edge_of(i);
+        const float wi = p.w ? p.w[start + e] : p.w_s;
+        const float Ci = p.C ? p.C[start + e] : p.C_s;
+        const float xi = nc_argmin(arena + mt.x, mt.y, tl.x, tl.y, true, xn, wi, Ci, lane);
         if (lane == 0) p.x[node] = xi;
         xn = xi;
     }
@@ -496,7 +581,7 @@ NcWs carve_nc(void *base, long long nodes, long long nchains, long long maxlen, 
     o.hdr = cv.take<WsHeader>(1);
     o.meta = cv.take<int2>((size_t)nodes);
     o.tails = cv.take<float2>((size_t)nodes);
-    o.arena = cv.take<float2>((size_t)(nchains * maxlen * (long long)T));
+    o.arena = cv.take<float2>((size_t)(nchains * (maxlen + 1) * (long long)T));
     o.bytes = align_up(cv.used, 256);
     return o;
 }
@@ -563,13 +648,15 @@ tv_status tv_chain_solve_nonconvex(const int64_t *d_uoff, const float *d_ulam,
     NcArgs p{d_uoff, d_ulam, d_uval, grid_len, d_sl, d_sr, sl, sr, d_w, d_C, w, C, d_offsets,
              num_chains, num_nodes, (int)max_len, max_breakpoints, d_x, d_energy, ws.arena,
              ws.meta, ws.tails};
-    const int wpb = nc_warps(max_breakpoints);
-    const size_t smem = (size_t)wpb * 3 * max_breakpoints * sizeof(float2);
+    const int pairs = std::max(1, nc_warps(max_breakpoints) / 2);
+    const int wpb = 2 * pairs;
+    const size_t smem = ((pairs * sizeof(NcPairXchg) + 15) & ~(size_t)15) +
+                        (size_t)wpb * 3 * max_breakpoints * sizeof(float2);
     st = check_cuda(cudaFuncSetAttribute(nc_chain_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                     "cudaFuncSetAttribute");
     if (st != TV_OK) return st;
-    const long long blocks = (num_chains + wpb - 1) / wpb;
+    const long long blocks = (num_chains + pairs - 1) / pairs;
     const bool prof = prof_on();
     if (prof) prof_mark(PK_CHAIN, s, true);
     nc_chain_kernel<<<(unsigned)blocks, wpb * WARP, smem, s>>>(p, ws.hdr);

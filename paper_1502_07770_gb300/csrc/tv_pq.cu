@@ -25,6 +25,20 @@ using namespace tvh;
 
 namespace {
 
+__device__ __forceinline__ float warp_min_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_max_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
 struct PqState {
     float lam, L, R, S;  // this lane's breakpoint
     int size;
@@ -319,6 +333,216 @@ __global__ void __launch_bounds__(kPqWarps * WARP) pq_chain_kernel(PqArgs p, WsH
     }
 }
 
+// ------------------------------------------------------ middle-rooted pairs --
+// Two warps per chain, rooted at node mid = n/2 (Algorithm 2 allows any root): warp 0 of
+// a pair runs pq_update over nodes 0..mid-1, warp 1 over nodes n-1..mid+1 (the pairwise
+// terms are symmetric, so the update is the same), each ending with the message into the
+// root. After a pair barrier both warps read the two messages from shared memory and find
+// the same root x_mid, the zero of
+//     g(z) = a z - b + alpha sign(z - f) + m_L(z) + m_R(z)
+// (non-decreasing, piecewise linear with jumps): every breakpoint of either message and
+// f are candidates; the first candidate c1 with g(c1+) >= 0 is the root if g(c1-) <= 0,
+// else the root lies on the linear piece between c1 and the candidate c0 before it.
+// Each warp then clips its half outwards (Algorithm 2, backward).
+struct PqMsg {
+    float lam[WARP], L[WARP], R[WARP], S[WARP];
+    int size, ovf;
+};
+
+__device__ __forceinline__ void pq_pair_bar(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// value of message M just left (m_lo) and right (m_hi) of z, and its slope right of z
+__device__ __forceinline__ void pq_msg_at(const PqMsg &M, float z, float &m_lo, float &m_hi,
+                                          float &slope)
+{
+    const int t = M.size;
+    if (t == 0) {
+        m_lo = m_hi = slope = 0.f;
+        return;
+    }
+    // e = entries with lam <= z, j = entries with lam < z
+    int e = 0, j = 0;
+    for (int q = 0; q < t; ++q) {
+        e += M.lam[q] <= z;
+        j += M.lam[q] < z;
+    }
+    if (e == 0) {
+        m_hi = M.L[0];
+        slope = 0.f;
+    } else {
+        const int q = e - 1;
+        m_hi = M.lam[q] == z ? M.R[q] : fmaf(M.S[q], z - M.lam[q], M.R[q]);
+        slope = M.S[q];
+    }
+    if (j < t && M.lam[j] == z) m_lo = M.L[j];
+    else if (j == 0) m_lo = M.L[0];
+    else m_lo = fmaf(M.S[j - 1], z - M.lam[j - 1], M.R[j - 1]);
+}
+
+__device__ float pq_root(const PqMsg &ML, const PqMsg &MR, float a, float b, float al, float f,
+                         int lane)
+{
+    float cand[3];
+    int nc = 0;
+    if (lane < ML.size) cand[nc++] = ML.lam[lane];
+    if (lane < MR.size) cand[nc++] = MR.lam[lane];
+    if (lane == 0) cand[nc++] = f;
+    float gm[3], gp[3], sp[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        gm[q] = gp[q] = sp[q] = 0.f;
+        if (q < nc) {
+            const float c = cand[q];
+            float l1, h1, s1, l2, h2, s2;
+            pq_msg_at(ML, c, l1, h1, s1);
+            pq_msg_at(MR, c, l2, h2, s2);
+            const float lin = fmaf(a, c, -b);
+            gm[q] = lin + (c <= f ? -al : al) + l1 + l2;
+            gp[q] = lin + (c < f ? -al : al) + h1 + h2;
+            sp[q] = a + s1 + s2;
+        }
+    }
+    float c1 = INFINITY;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        if (q < nc && gp[q] >= 0.f) c1 = fminf(c1, cand[q]);
+    c1 = warp_min_f(c1);
+    const float lEndL = ML.size ? ML.L[0] : 0.f, lEndR = MR.size ? MR.L[0] : 0.f;
+    if (!(c1 < INFINITY)) {
+        // right of every candidate: both messages at their right ends
+        const float rL = ML.size ? ML.R[ML.size - 1] : 0.f, rR = MR.size ? MR.R[MR.size - 1] : 0.f;
+        return (b - al - rL - rR) / a;
+    }
+    float g1m = -INFINITY, c0 = -INFINITY;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        if (q < nc && cand[q] == c1) g1m = fmaxf(g1m, gm[q]);
+        if (q < nc && cand[q] < c1) c0 = fmaxf(c0, cand[q]);
+    }
+    g1m = warp_max_f(g1m);
+    if (g1m <= 0.f) return c1;  // a jump of g (or an exact zero) at c1
+    c0 = warp_max_f(c0);
+    if (!(c0 > -INFINITY)) {
+        // left of every candidate: both messages at their left ends, the unary at -alpha
+        return fminf((b + al - lEndL - lEndR) / a, c1);
+    }
+    float g0 = -INFINITY, s0 = -INFINITY;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        if (q < nc && cand[q] == c0) {
+            g0 = fmaxf(g0, gp[q]);
+            s0 = fmaxf(s0, sp[q]);
+        }
+    g0 = warp_max_f(g0);
+    s0 = warp_max_f(s0);
+    const float z = c0 - g0 / s0;
+    return fminf(fmaxf(z, c0), c1);
+}
+
+__global__ void __launch_bounds__(kPqWarps * WARP) pq_pair_kernel(PqArgs p, WsHeader *hdr)
+{
+    __shared__ PqMsg msg[kPqWarps];
+    const int lane = threadIdx.x & (WARP - 1);
+    const int warp = threadIdx.x / WARP;
+    const int role = warp & 1, pair = warp >> 1;
+    const long long k = (long long)blockIdx.x * (kPqWarps / 2) + pair;
+    if (k >= p.nchains) return;  // both warps of the pair
+    long long start = k * (long long)p.maxlen;
+    int n = p.maxlen;
+    if (p.offsets) {
+        const long long off0 = p.offsets[0], lo = p.offsets[k], hi = p.offsets[k + 1];
+        if (lo < off0 || hi < lo || hi - lo > p.maxlen) {
+            if (lane == 0 && role == 0) atomicOr(&hdr->status, ERR_BAD_CHAIN);
+            return;
+        }
+        start = lo;
+        n = (int)(hi - lo);
+    }
+    if (n == 0) return;
+    const int mid = n >> 1;
+    const int cnt = role == 0 ? mid : n - 1 - mid;
+    auto node_of = [&](int j) { return role == 0 ? j : n - 1 - j; };
+    float2 *rec = p.rec + k * (long long)p.maxlen;
+    const float *a = p.a ? p.a + start : nullptr;
+    const float *b = p.b + start, *f = p.f + start;
+    const float *al = p.al ? p.al + start : nullptr;
+    const float *w = p.w ? p.w + (p.w_stride > 0 ? k * p.w_stride : start) : nullptr;
+    PqState s{0.f, 0.f, 0.f, 0.f, 0, 0.f, 0.f, 0.f};
+    bool ovf = false;
+    const int nblocks = (cnt + WARP - 1) / WARP;
+    for (int blk = 0; blk < nblocks && !ovf; ++blk) {
+        const int j_l = blk * WARP + lane;
+        const bool in = j_l < cnt;
+        const int i_l = in ? node_of(j_l) : 0;
+        const int e_l = role == 0 ? i_l : i_l - 1;  // the edge towards the root
+        const float av = (in && a) ? a[i_l] : 1.f, bv = in ? b[i_l] : 0.f,
+                    alv = in ? (al ? al[i_l] : p.alpha) : 0.f, fv = in ? f[i_l] : 0.f,
+                    wv = in ? (w ? w[e_l] * p.wscale : p.lam) : 0.f;
+        const int c = min(WARP, cnt - blk * WARP);
+        for (int jj = 0; jj < c; ++jj) {
+            const float ai = __shfl_sync(FULL, av, jj), bi = __shfl_sync(FULL, bv, jj),
+                        ali = __shfl_sync(FULL, alv, jj), fi = __shfl_sync(FULL, fv, jj),
+                        wi = __shfl_sync(FULL, wv, jj);
+            const int i = __shfl_sync(FULL, i_l, jj);
+            float lm, hp;
+            pq_update(s, ai, bi, ali, fi, -wi, wi, lane, ovf, lm, hp);
+            if (lane == 0) rec[i] = make_float2(lm, hp);
+        }
+        ovf = __any_sync(FULL, ovf);
+    }
+    PqMsg &mine = msg[warp];
+    mine.lam[lane] = s.lam;
+    mine.L[lane] = s.L;
+    mine.R[lane] = s.R;
+    mine.S[lane] = s.S;
+    if (lane == 0) {
+        mine.size = cnt > 0 ? s.size : 0;
+        mine.ovf = ovf ? 1 : 0;
+    }
+    pq_pair_bar(1 + pair);
+    const PqMsg &ML = msg[2 * pair], &MR = msg[2 * pair + 1];
+    if (ML.ovf || MR.ovf) {
+        if (role == 0 && lane == 0) {
+            atomicAdd(&hdr->overflowed, 1ull);
+            PqEntry *E = p.ent + k * 2LL * (3LL * p.maxlen + 4);
+            pq_lane0(n, a, b, al, f, w, p.wscale, p.alpha, p.lam, p.x + start, E,
+                     E + (3LL * p.maxlen + 4), rec);
+        }
+        return;
+    }
+    const float am = a ? a[mid] : 1.f, alm = al ? al[mid] : p.alpha;
+    const float xm = pq_root(ML, MR, am, b[mid], alm, f[mid], lane);
+    if (role == 0 && lane == 0) p.x[start + mid] = xm;
+    // backward over this half, outwards from the root, in processing order
+    float x_next = xm;
+    for (int blk = nblocks - 1; blk >= 0; --blk) {
+        const int j = blk * WARP + lane;
+        float lo = -INFINITY, hi = INFINITY;
+        if (j < cnt) {
+            const float2 r = rec[node_of(j)];
+            lo = r.x;
+            hi = r.y;
+        }
+        const float xv = clip_suffix(lo, hi, x_next, lane, min(WARP, cnt - blk * WARP));
+        if (j < cnt) p.x[start + node_of(j)] = xv;
+        x_next = __shfl_sync(FULL, xv, 0);
+    }
+}
+
+// chains of 64 nodes or more: two warps per chain from the middle node; shorter ones one
+// warp per chain from one end
+void launch_pq(const PqArgs &p, long long nchains, long long max_len, WsHeader *hdr,
+               cudaStream_t s)
+{
+    if (max_len >= 64) {
+        const long long blocks = (nchains + kPqWarps / 2 - 1) / (kPqWarps / 2);
+        pq_pair_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
+    } else {
+        const long long blocks = (nchains + kPqWarps - 1) / kPqWarps;
+        pq_chain_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
+    }
+}
+
 struct PqWs {
     WsHeader *hdr;
     float2 *rec;
@@ -574,10 +798,9 @@ tv_status tv_chain_solve_pq(const float *d_a, const float *d_b, const float *d_a
     if (st != TV_OK) return st;
     PqArgs p{d_a, d_b, d_alpha, d_f, d_w, alpha, lambda, 1.f, 0, d_offsets, num_chains,
              (int)max_len, d_x, ws.rec, ws.ent};
-    const long long blocks = (num_chains + kPqWarps - 1) / kPqWarps;
     const bool prof = prof_on();
     if (prof) prof_mark(PK_CHAIN, s, true);
-    pq_chain_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, ws.hdr);
+    launch_pq(p, num_chains, max_len, ws.hdr, s);
     st = check_cuda(cudaGetLastError(), "piecewise-quadratic chain launch");
     if (st == TV_OK) note_launch();
     if (prof) prof_mark(PK_CHAIN, s, false);
@@ -661,10 +884,9 @@ tv_status tv2d_denoise_l1(const float *d_img, int64_t H, int64_t W, const float 
         // primal step: row chains with piecewise-quadratic unaries (scaled by tau)
         PqArgs p{nullptr, ws.xi, nullptr, d_img, d_wh, tau, tau * lambda, tau,
                  d_wh ? (long long)(W - 1) : 0, nullptr, H, (int)W, ws.xn, ws.pq.rec, ws.pq.ent};
-        const long long blocks = (H + kPqWarps - 1) / kPqWarps;
         const bool prof = prof_on();
         if (prof) prof_mark(PK_ROW, s, true);
-        pq_chain_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, ws.pq.hdr);
+        launch_pq(p, H, W, ws.pq.hdr, s);
         if ((st = check_cuda(cudaGetLastError(), "row chains")) != TV_OK) return st;
         note_launch();
         if (prof) prof_mark(PK_ROW, s, false);
