@@ -383,10 +383,11 @@ tv_status tv_set_coop_max_chains(int64_t max_chains);
  * solution up to FP32 rounding. */
 tv_status tv_set_coop_split(int mode);
 /* How tv_chain_solve runs chains of 64 nodes or more when its batch runs one thread per
- * chain and has at most 8 warps' worth of chains per SM: 1 (the default) rooted at the
- * middle node, each half by its own thread and the root solved from both halves'
- * messages (Algorithm 2 allows any root); 0 by one thread from one end (as larger
- * batches always are). Both give the same solution up to FP32 rounding. */
+ * chain: 1 (the default) rooted at the middle node, each half by its own thread (messages
+ * of up to 16 breakpoints on chip) and the root solved from both halves' messages
+ * (Algorithm 2 allows any root); 0 by one thread from one end (messages of up to 32
+ * breakpoints on chip). Longer messages are finished from the workspace either way. Both
+ * give the same solution up to FP32 rounding. */
 tv_status tv_set_thread_split(int on);
 
 /* ------------------------------------------ learned dual warm start (net) ---- */

@@ -518,6 +518,9 @@ tv_status launch_batch(const P &p, long long nchains, float2 *rec, float *crec, 
 // A chain whose half outgrows the ring is re-solved whole by its left lane from the
 // workspace (Sec. 4.1 two-ended array).
 constexpr int HW = WARP / 2;  // chains per warp
+// ring entries per half: 16 keep every warp of a full batch resident (27 per SM at
+// 65536 chains); longer messages take the workspace path
+constexpr int kRingHalf = 16;
 
 template <bool HAS_W>
 struct alignas(16) HalfSmem {
@@ -525,7 +528,7 @@ struct alignas(16) HalfSmem {
     union {
         struct {
             float in[NIN][2][WARP * RP];
-            float2 ring[kRing][WARP];
+            float2 ring[kRingHalf][WARP];
         } f;
         struct {
             float2 rec[2][CH][WARP];
@@ -600,8 +603,8 @@ __device__ void half_fallback(const ChainRowsP<HAS_W> &p, long long start, int n
 // Root of z - c + m_L(z) + m_R(z): each message is -w left of its first breakpoint,
 // +w right of its last, with slope s_p + abar right of breakpoint p (abar = the half's
 // node count); an empty half contributes 0.
-__device__ __forceinline__ float half_root(const RingStore<kRing> &SL, int FL, int BL, float aL,
-                                           float wL, const RingStore<kRing> &SR, int FR, int BR,
+__device__ __forceinline__ float half_root(const RingStore<kRingHalf> &SL, int FL, int BL, float aL,
+                                           float wL, const RingStore<kRingHalf> &SR, int FR, int BR,
                                            float aR, float wR, float c)
 {
     const bool hasL = BL >= FL, hasR = BR >= FR;
@@ -614,7 +617,7 @@ __device__ __forceinline__ float half_root(const RingStore<kRing> &SL, int FL, i
     if (!(zc < INFINITY)) return c;  // no message at all
     float hc = zc - c - wL - wR;      // h at the first breakpoint (slope 1 to its left)
     float slope = 1.f;                // slope of h on the segment ending at zc
-    for (int it = 0; it < 2 * kRing + 4; ++it) {
+    for (int it = 0; it < 2 * kRingHalf + 4; ++it) {
         if (hc >= 0.f) return zc - hc / slope;
         // pass the breakpoint(s) at zc; the slopes right of it come from the last
         // breakpoint passed in each half
@@ -634,7 +637,7 @@ __device__ __forceinline__ float half_root(const RingStore<kRing> &SL, int FL, i
         hc = fmaf(slope, zn - zc, hc);
         zc = zn;
     }
-    return zc - hc / slope;  // not reached: at most 2 (kRing + 1) breakpoints
+    return zc - hc / slope;  // not reached: at most 2 (kRingHalf + 1) breakpoints
 }
 
 template <bool HAS_W>
@@ -669,7 +672,7 @@ __global__ void __launch_bounds__(128) chain_halves_kernel(ChainRowsP<HAS_W> p, 
     for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(FULL, cmax, o));
     __syncwarp();
     float2 *rec_w = rec + wg * (long long)halfmax * WARP;
-    RingStore<kRing> S{(unsigned)__cvta_generic_to_shared(&sm->u.f.ring[0][lane])};
+    RingStore<kRingHalf> S{(unsigned)__cvta_generic_to_shared(&sm->u.f.ring[0][lane])};
     DPState d;
     d.F = 0;
     d.B = -1;
@@ -702,7 +705,7 @@ __global__ void __launch_bounds__(128) chain_halves_kernel(ChainRowsP<HAS_W> p, 
                     if (j == 0) {
                         dp_first(d, S, 0, c, w, lm, hp);
                     } else {
-                        alive = dp_step(d, S, kRing, c, w, (float)(j + 1), lm, hp);
+                        alive = dp_step(d, S, kRingHalf, c, w, (float)(j + 1), lm, hp);
                     }
                     if (alive) rec_w[(long long)j * WARP + lane] = make_float2(lm, hp);
                 }
@@ -722,7 +725,7 @@ __global__ void __launch_bounds__(128) chain_halves_kernel(ChainRowsP<HAS_W> p, 
     const bool ok = __shfl_sync(FULL, (int)(alive && aliveR), lane & (HW - 1)) != 0;
     float xroot = 0.f;
     if (left && n > 0 && ok) {
-        const RingStore<kRing> SR{S.base + HW * 8};  // lane + 16's ring
+        const RingStore<kRingHalf> SR{S.base + HW * 8};  // lane + 16's ring
         const float c = p.y[start + mid];
         xroot = half_root(S, cnt > 0 ? d.F : 0, cnt > 0 ? d.B : -1, (float)cnt, d.w_prev, SR,
                           cntR > 0 ? FR : 0, cntR > 0 ? BR : -1, (float)cntR, wR, c);
@@ -1006,11 +1009,9 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
         CoopRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x, 0};
         return launch_coop(p, num_chains, (int)max_len, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_CHAIN);
     }
-    // two threads per chain where a thread per chain leaves the SMs short of warps (at
-    // most 8 per SM): there the halves' extra warps hide latency; fuller batches are
-    // issue-bound and run one thread per chain
-    const bool halves = g_thread_split.load() != 0 && max_len >= kHalvesMinLen &&
-                        warps <= 8LL * sm_count_current();
+    // chains of 64 nodes or more: two threads per chain (twice the warps, half the steps
+    // each, and a 16-entry ring that keeps every warp of a full batch resident)
+    const bool halves = g_thread_split.load() != 0 && max_len >= kHalvesMinLen;
     if (d_w) {
         ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,
                            vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0};
