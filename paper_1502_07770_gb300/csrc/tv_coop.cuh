@@ -139,23 +139,16 @@ __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, in
         candL = fminf(candL, lam_n);
         candR = fminf(candR, lam_n);
     }
-    int ell, kl;
-    if constexpr (G == WARP) {
-        ell = min((int)__reduce_min_sync(FULL, (unsigned)((valid && v >= wl) ? sl : WARP)), size);
-        kl = __reduce_max_sync(FULL, (valid && v <= wh) ? sl : -1);
-    } else {
-        // one warp reduction per half and side: the other half contributes the
-        // neutral element, each lane keeps its own half's result
-        const bool lo_half = seg_shift == 0;
-        const unsigned ge = (valid && v >= wl) ? (unsigned)sl : (unsigned)G;
-        const int le = (valid && v <= wh) ? sl : -1;
-        const unsigned ell0 = __reduce_min_sync(FULL, lo_half ? ge : (unsigned)G);
-        const unsigned ell1 = __reduce_min_sync(FULL, lo_half ? (unsigned)G : ge);
-        const int kl0 = __reduce_max_sync(FULL, lo_half ? le : -1);
-        const int kl1 = __reduce_max_sync(FULL, lo_half ? -1 : le);
-        ell = min((int)(lo_half ? ell0 : ell1), size);
-        kl = lo_half ? kl0 : kl1;
+    // first lane with v >= w^- and last lane with v <= w^+: one vote each, then the
+    // lowest / highest set bit of this segment's bits
+    unsigned bge = __ballot_sync(FULL, valid && v >= wl);
+    unsigned ble = __ballot_sync(FULL, valid && v <= wh);
+    if constexpr (G != WARP) {
+        bge = (bge >> seg_shift) & ((1u << G) - 1u);
+        ble = (ble >> seg_shift) & ((1u << G) - 1u);
     }
+    const int ell = min(bge ? __ffs(bge) - 1 : G, size);
+    const int kl = ble ? 31 - __clz(ble) : -1;
     const int keep_last = kl > ell - 1 ? kl : ell - 1;  // last kept breakpoint (-1: none)
     const int K = keep_last - ell + 1;
     ovf = ovf || (active && K + 2 > G);

@@ -106,9 +106,10 @@ __device__ __forceinline__ void pq_update(PqState &s, float a, float b, float al
         cL = fminf(cL, lam_n);
         cR = fminf(cR, lam_n);
     }
-    const int ell = min((int)__reduce_min_sync(FULL, (unsigned)((valid && s.R >= wlo) ? lane : WARP)),
-                        s.size);
-    const int kl = __reduce_max_sync(FULL, (valid && s.L <= whi) ? lane : -1);
+    const unsigned bge = __ballot_sync(FULL, valid && s.R >= wlo);
+    const unsigned ble = __ballot_sync(FULL, valid && s.L <= whi);
+    const int ell = min(bge ? __ffs(bge) - 1 : WARP, s.size);
+    const int kl = ble ? 31 - __clz(ble) : -1;
     const float L0 = __shfl_sync(FULL, s.L, 0), lam0 = __shfl_sync(FULL, s.lam, 0);
     const float Le = __shfl_sync(FULL, s.L, ell & 31), Re = __shfl_sync(FULL, s.R, ell & 31),
                 lame = __shfl_sync(FULL, s.lam, ell & 31), Se = __shfl_sync(FULL, s.S, ell & 31);
