@@ -133,8 +133,9 @@ __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, in
     const float v = fmaf(ai, lam, V) - bi;     // m^_i at this breakpoint
     const float v0 = fmaf(ai, lam0, wl_prev) - bi;  // m^_i at the first breakpoint
     const float lam_n = __shfl_down_sync(FULL, lam, 1, G);
-    float candL = fmaxf(lam + __fdividef(wl - v, S), lam);
-    float candR = fmaxf(lam + __fdividef(wh - v, S), lam);
+    const float rS = __fdividef(1.f, S);  // one reciprocal for both crossings
+    float candL = fmaxf(fmaf(wl - v, rS, lam), lam);
+    float candR = fmaxf(fmaf(wh - v, rS, lam), lam);
     if (!last) {
         candL = fminf(candL, lam_n);
         candR = fminf(candR, lam_n);
@@ -155,15 +156,15 @@ __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, in
     // lambda^- on the piece right of the last breakpoint removed on the left,
     // lambda^+ on the piece right of the last one kept; with none, on the left end
     // piece (slope a_i)
-    const int il = (ell - 1) & (G - 1);
-    const float gl = __shfl_sync(FULL, candL, il, G);
-    const float Sl = __shfl_sync(FULL, S, il, G);
-    const float gr = __shfl_sync(FULL, candR, keep_last & (G - 1), G);
+    // source lanes are taken modulo the segment width by the shuffles themselves
+    const float gl = __shfl_sync(FULL, candL, ell - 1, G);
+    const float Sl = __shfl_sync(FULL, S, ell - 1, G);
+    const float gr = __shfl_sync(FULL, candR, keep_last, G);
     lm = (ell == 0) ? lam0 + (wl - v0) / ai : gl;
     hp = (keep_last < 0) ? lam0 + (wh - v0) / ai : gr;
     // new message m_{i,i+1}: lambda^- (value w^-_i, the slope of m^_i there), the kept
     // breakpoints with their values and slopes, lambda^+ (value w^+_i, flat beyond)
-    const int src = (sl - 1 + ell) & (G - 1);
+    const int src = sl - 1 + ell;
     const float nl = __shfl_sync(FULL, lam, src, G);
     const float nv = __shfl_sync(FULL, v, src, G);
     const float nS = __shfl_sync(FULL, S, src, G);
