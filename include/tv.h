@@ -399,6 +399,15 @@ tv_status tv_set_thread_split(int on);
  * biases, pre-activations and gradients FP32. Convolutions are 3x3, stride 1, zero
  * padding 1 (cross-correlation), computed on BF16 tensor cores with FP32 accumulate.
  */
+/* Which tensor-core path the forward convolutions take: 0 (the default) mma.sync
+ * m16n8k16 (persistent blocks, 8 x 16 pixel tiles); 1 tcgen05.mma with TMEM accumulators
+ * (128-pixel row tiles, two accumulators so that a tile's MMAs overlap the previous
+ * tile's epilogue, one issuing thread per block). Both accumulate the same BF16 products
+ * in FP32, in a different order. With 16 or 32 output channels each tcgen05 MMA is only
+ * 128 x 32 x 16 and the forward pass of the network is faster on mma.sync (0.38 against
+ * 0.53 ms at 1024 x 1024). The backward kernels always use mma.sync. */
+tv_status tv_net_set_tensor_path(int mode);
+
 /* y = conv(x) + bias (bias may be NULL), optionally ReLU'd into act_out (BF16, may be
  * NULL); pre_out (FP32, may be NULL) receives the value before the ReLU; at least one of
  * the two outputs is given. All tensor pointers 16-byte aligned; B <= 65535. */

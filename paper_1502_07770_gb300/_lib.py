@@ -82,6 +82,7 @@ SIGNATURES = {
     "tv_chain_solve_general": (ctypes.c_int, [_p, _p, _p, _p, _p, _i64, _i64, _p, _p, _sz, _p]),
     "tv_set_coop_split": (ctypes.c_int, [ctypes.c_int]),
     "tv_set_thread_split": (ctypes.c_int, [ctypes.c_int]),
+    "tv_net_set_tensor_path": (ctypes.c_int, [ctypes.c_int]),
     "tv_net_conv3x3": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       _p, _p, ctypes.c_int, ctypes.c_int, _p, _p, _p]),
     "tv_net_conv3x3_backward_data": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -524,6 +525,12 @@ def set_thread_split(on: bool):
     """Middle-rooted chains (two threads per chain) in the one-thread-per-chain path of
     ``chain_prox`` (True, the default) or one thread per chain from one end (False)."""
     _check(load().tv_set_thread_split(1 if on else 0))
+
+
+def set_net_tensor_path(mode: int):
+    """Forward convolutions of the warm-start network on mma.sync (0, the default) or on
+    tcgen05 with TMEM accumulators (1)."""
+    _check(load().tv_net_set_tensor_path(int(mode)))
 
 
 def set_coop_max_chains(n: int):

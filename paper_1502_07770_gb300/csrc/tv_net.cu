@@ -12,6 +12,7 @@
 // Each block of the two pixel-major kernels computes an 8 x 16 pixel tile for all
 // output channels from a zero-padded 10 x 18 input patch in shared memory; A and B
 // fragments are read with ldmatrix from rows padded by 16 bytes (conflict-free).
+#include <atomic>
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -391,6 +392,10 @@ tv_status launch_conv(const __nv_bfloat16 *X, int B, int H, int W, const __nv_bf
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
             "cudaFuncSetAttribute");
         if (st0 != TV_OK) return st0;
+        st0 = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              (int)cudaSharedmemCarveoutMaxShared),
+                         "cudaFuncSetAttribute");
+        if (st0 != TV_OK) return st0;
         int b = 0;
         st0 = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NTHR, smem),
                          "occupancy");
@@ -558,6 +563,291 @@ __global__ void flip_weights(const __nv_bfloat16 *Wt, int cin, int cout, __nv_bf
 
 int ew_blocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 8LL * sm_count_current()); }
 
+// ------------------------------------------- forward on tcgen05 (TMEM accumulators) --
+// The forward convolution as tcgen05.mma instructions: one block computes 128
+// consecutive output pixels of one image row (M = 128, N = COUT, K = 9 * CIN) into a
+// TMEM accumulator of COUT FP32 columns. Operands are in shared memory in the
+// canonical K-major layout without swizzle (8-row x 16-byte core matrices):
+//   A: the three input rows y-1, y, y+1 over pixels x0-1 .. x0+128 (zero outside the
+//      image), one region of 130 pixels x 16 bytes per 8-channel group; the operand of
+//      tap (dy, dx) is the row-dy region started dx+1 pixels in (16 bytes per pixel),
+//      so the nine taps need no copies;
+//   B: the weights of every tap, [tap][8-channel group][COUT][8], loaded once per block.
+// One thread issues the 9 * CIN / 16 MMAs and commits them to an mbarrier; the four
+// warps then read their 32 TMEM lanes (pixels) with tcgen05.ld, add the bias, apply the
+// ReLU and store. Blocks are persistent over the tiles.
+constexpr int TC_M = 128;           // pixels per tile
+constexpr int TC_P = TC_M + 2;      // staged pixels per row
+constexpr int TC_REG = TC_P * 16;   // bytes of one (row, 8-channel group) region
+constexpr unsigned kTcSpin = 1u << 26;  // mbarrier polls before a wait gives up
+
+__device__ unsigned g_tc_timeouts;  // waits that gave up (their tiles are not written)
+
+template <int CIN, int COUT>
+constexpr size_t conv_tc_smem()
+{
+    return 1024 + (size_t)2 * 3 * (CIN / 8) * TC_REG + (size_t)9 * COUT * CIN * 2 + 64;  // + 2 mbarriers
+}
+
+__device__ __forceinline__ uint64_t tc_desc(unsigned saddr, unsigned lbo, unsigned sbo)
+{
+    // start >> 4 (bits 0-13), leading-dimension byte offset >> 4 (16-29), stride byte
+    // offset >> 4 (32-45), descriptor version 1 (46-47), no swizzle (61-63 = 0)
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned phase)
+{
+    for (unsigned it = 0; it < kTcSpin; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int N>
+__device__ __forceinline__ void tc_ld(unsigned taddr, float (&v)[N])
+{
+    static_assert(N == 16 || N == 32, "tcgen05.ld of 16 or 32 columns");
+    uint32_t r[N];
+    if constexpr (N == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+            "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+              "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+              "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+              "=r"(r[31])
+            : "r"(taddr));
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+            "%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(NTHR)
+    conv3x3_tc(const __nv_bfloat16 *X, int B, int H, int W, const __nv_bfloat16 *Wt,
+               const float *bias, int relu, float *pre_out, __nv_bfloat16 *act_out)
+{
+    constexpr int KG = CIN / 8;
+    constexpr int ABYTES = 3 * KG * TC_REG;
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    unsigned char *abuf = smem_tc;                 // two A buffers
+    unsigned char *bbuf = abuf + 2 * ABYTES;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(bbuf + 9 * COUT * CIN * 2);  // two
+    unsigned *tslot = reinterpret_cast<unsigned *>(mbar + 2);
+    const unsigned a_s = smem_u32(abuf), b_s = smem_u32(bbuf), mb_s = smem_u32(mbar);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = (W + TC_M - 1) / TC_M;
+    const long long ntiles = (long long)B * H * tiles_x;
+
+    // the three input rows of a tile (zero outside the image) into buffer `nb`
+    auto stage = [&](long long tile, int nb) {
+        const int tx = (int)(tile % tiles_x);
+        const long long row = tile / tiles_x;  // b * H + y
+        const int y = (int)(row % H), b = (int)(row / H);
+        const int x0 = tx * TC_M;
+        unsigned char *dst = abuf + nb * ABYTES;
+        for (int t = tid; t < 3 * KG * TC_P; t += NTHR) {
+            const int pix = t % TC_P, g = (t / TC_P) % KG, dyi = t / (TC_P * KG);
+            const int gy = y + dyi - 1, gx = x0 + pix - 1;
+            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const __nv_bfloat16 *src = in ? X + (((long long)b * H + gy) * W + gx) * CIN + g * 8 : X;
+            cp_async16_zfill(dst + (dyi * KG + g) * TC_REG + pix * 16, src, in);
+        }
+    };
+    constexpr uint32_t idesc = tc_idesc(TC_M, COUT);
+    // the 9 * CIN / 16 MMAs of a tile from A buffer `nb` into accumulator `acc_col`
+    auto issue = [&](int nb, unsigned tmem_acc, unsigned mbar_addr) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const unsigned a0 = a_s + nb * ABYTES;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dyi = tap / 3, dxi = tap % 3;
+#pragma unroll
+            for (int ks = 0; ks < KG / 2; ++ks) {
+                const uint64_t ad = tc_desc(a0 + (dyi * KG + 2 * ks) * TC_REG + dxi * 16, TC_REG, 128);
+                const uint64_t bd = tc_desc(b_s + (tap * KG + 2 * ks) * COUT * 16, COUT * 16, 128);
+                const unsigned acc = (tap | ks) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_acc),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar_addr)
+            : "memory");
+    };
+
+    long long tile = blockIdx.x;
+    if (tile < ntiles) stage(tile, 0);
+    cp_async_commit_net();
+    // weights: [tap][group][co][8 channels]; bias in registers
+    for (int t = tid; t < 9 * KG * COUT; t += NTHR) {
+        const int co = t % COUT, g = (t / COUT) % KG, tap = t / (COUT * KG);
+        *reinterpret_cast<uint4 *>(bbuf + ((tap * KG + g) * COUT + co) * 16) =
+            *reinterpret_cast<const uint4 *>(Wt + ((long long)co * 9 + tap) * CIN + g * 8);
+    }
+    float bv[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) bv[c] = bias ? bias[c] : 0.f;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_s) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_s + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        // two accumulators of 32 columns: the MMAs of a tile overlap the previous tile's epilogue
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(
+                         smem_u32(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tslot;
+
+    unsigned phase[2] = {0u, 0u};
+    long long prev = -1;  // the tile whose accumulator awaits its epilogue
+    int i = 0;
+    bool bad = false;
+    auto epilogue = [&](long long t, int slot) {
+        float v[COUT];
+        tc_ld<COUT>(tmem + (unsigned)(slot * 32) + ((unsigned)(warp * 32) << 16), v);
+        const int tx = (int)(t % tiles_x);
+        const long long row = t / tiles_x;
+        const int x = tx * TC_M + warp * 32 + lane;
+        if (x < W) {
+            const long long base = (row * W + x) * COUT;
+#pragma unroll
+            for (int c = 0; c < COUT; c += 4) {
+                float4 q = make_float4(v[c] + bv[c], v[c + 1] + bv[c + 1], v[c + 2] + bv[c + 2],
+                                       v[c + 3] + bv[c + 3]);
+                if (pre_out) *reinterpret_cast<float4 *>(pre_out + base + c) = q;
+                if (relu) {
+                    q.x = fmaxf(q.x, 0.f);
+                    q.y = fmaxf(q.y, 0.f);
+                    q.z = fmaxf(q.z, 0.f);
+                    q.w = fmaxf(q.w, 0.f);
+                }
+                if (act_out) {
+                    const __nv_bfloat162 lo = __floats2bfloat162_rn(q.x, q.y);
+                    const __nv_bfloat162 hi = __floats2bfloat162_rn(q.z, q.w);
+                    uint2 u;
+                    u.x = *reinterpret_cast<const unsigned *>(&lo);
+                    u.y = *reinterpret_cast<const unsigned *>(&hi);
+                    *reinterpret_cast<uint2 *>(act_out + base + c) = u;
+                }
+            }
+        }
+    };
+    for (; tile < ntiles; tile += gridDim.x, ++i) {
+        const int cur = i & 1;
+        cp_async_wait_net<0>();  // this tile's rows
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) issue(cur, tmem + (unsigned)(cur * 32), mb_s + 8u * cur);
+        if (prev >= 0) {
+            // the previous tile's MMAs: done before its rows' buffer is refilled
+            const bool ok = tc_wait(mb_s + 8u * (cur ^ 1), phase[cur ^ 1]);
+            phase[cur ^ 1] ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                bad = true;
+                break;
+            }
+        }
+        const long long next = tile + gridDim.x;
+        if (next < ntiles) stage(next, cur ^ 1);
+        cp_async_commit_net();
+        if (prev >= 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            epilogue(prev, cur ^ 1);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        prev = tile;
+    }
+    if (!bad && prev >= 0) {
+        const int slot = (i - 1) & 1;
+        const bool ok = tc_wait(mb_s + 8u * slot, phase[slot]);
+        if (__syncthreads_or(!ok)) {
+            bad = true;
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            epilogue(prev, slot);
+        }
+    }
+    if (bad && tid == 0) atomicAdd(&g_tc_timeouts, 1u);
+    cp_async_wait_net<0>();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem) : "memory");
+}
+
+static std::atomic<int> g_net_tc{0};  // mma.sync by default: faster for N = 16/32 (see tv.h)
+
+template <int CIN, int COUT>
+tv_status launch_conv_tc(const __nv_bfloat16 *X, int B, int H, int W, const __nv_bfloat16 *Wt,
+                         const float *bias, int relu, float *pre_out, __nv_bfloat16 *act_out,
+                         cudaStream_t s)
+{
+    auto kern = conv3x3_tc<CIN, COUT>;
+    constexpr size_t smem = conv_tc_smem<CIN, COUT>();
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        tv_status st0 = check_cuda(
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "cudaFuncSetAttribute");
+        if (st0 != TV_OK) return st0;
+        // the whole unified memory as shared memory, so that several blocks fit per SM
+        st0 = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              (int)cudaSharedmemCarveoutMaxShared),
+                         "cudaFuncSetAttribute");
+        if (st0 != TV_OK) return st0;
+        // blocks per SM from the shared memory (the occupancy query does not see that
+        // a block holds only 64 of the 512 TMEM columns); at most 4, 256 columns
+        const int b = (int)((227 * 1024) / (smem + 1024));
+        per_sm = b < 1 ? 1 : (b > 4 ? 4 : b);
+    }
+    const long long ntiles = (long long)B * H * ((W + TC_M - 1) / TC_M);
+    long long blocks = (long long)per_sm * sm_count_current();
+    if (blocks > ntiles) blocks = ntiles;
+    kern<<<(unsigned)blocks, NTHR, smem, s>>>(X, B, H, W, Wt, bias, relu, pre_out, act_out);
+    tv_status st = check_cuda(cudaGetLastError(), "conv launch");
+    if (st == TV_OK) note_launch();
+    return st;
+}
+
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 // grid.y = ceil(H / TH) and grid.z = B are limited to 65535
@@ -576,6 +866,17 @@ __global__ void cast_bf16(const float *a, long long n, __nv_bfloat16 *out)
 }  // namespace
 
 extern "C" {
+
+tv_status tv_net_set_tensor_path(int mode)
+{
+    clear_error();
+    if (mode < 0 || mode > 1) {
+        set_error("tv_net_set_tensor_path: 0 (mma.sync) or 1 (tcgen05)");
+        return TV_ERR_INVALID;
+    }
+    g_net_tc.store(mode);
+    return TV_OK;
+}
 
 tv_status tv_net_conv3x3(const void *d_x, int B, int H, int W, int cin, const void *d_w,
                          const float *d_bias, int cout, int relu, float *d_pre_out,
@@ -596,6 +897,12 @@ tv_status tv_net_conv3x3(const void *d_x, int B, int H, int W, int cin, const vo
     auto X = static_cast<const __nv_bfloat16 *>(d_x);
     auto Wt = static_cast<const __nv_bfloat16 *>(d_w);
     auto A = static_cast<__nv_bfloat16 *>(d_act_out);
+    if (g_net_tc.load() != 0) {
+        if (cin == 16 && cout == 32) return launch_conv_tc<16, 32>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+        if (cin == 32 && cout == 32) return launch_conv_tc<32, 32>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+        if (cin == 32 && cout == 16) return launch_conv_tc<32, 16>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+        return launch_conv_tc<16, 16>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+    }
     if (cin == 16 && cout == 32) return launch_conv<16, 32, 0>(X, B, H, W, Wt, d_bias, relu, nullptr, d_pre_out, A, s);
     if (cin == 32 && cout == 32) return launch_conv<32, 32, 0>(X, B, H, W, Wt, d_bias, relu, nullptr, d_pre_out, A, s);
     if (cin == 32 && cout == 16) return launch_conv<32, 16, 0>(X, B, H, W, Wt, d_bias, relu, nullptr, d_pre_out, A, s);

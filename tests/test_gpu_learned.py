@@ -68,6 +68,35 @@ def test_conv_forward(cin, cout):
 
 
 @pytest.mark.parametrize("cin,cout", PAIRS)
+@pytest.mark.parametrize("shape", [(2, 13, 37), (1, 7, 300), (3, 2, 128)])
+def test_conv_forward_tensor_paths(cin, cout, shape):
+    """The tcgen05 forward (128-pixel row tiles, TMEM accumulators) and the mma.sync
+    forward against the FP64 reference, on rows of one, several and partial tiles."""
+    lib = _lib.load()
+    b_, h_, w_ = shape
+    x = _bf16((b_, h_, w_, cin), 11)
+    w = _bf16((cout, 3, 3, cin), 12, scale=0.2)
+    b = torch.randn(cout, generator=torch.Generator().manual_seed(13)).to(DEV)
+    want = ref.conv3x3(_np(x), _np(w), b.cpu().numpy().astype(np.float64)).numpy()
+    tol = 2e-5 * max(1.0, np.abs(want).max())
+    outs = []
+    try:
+        for mode in (1, 0):
+            _lib.set_net_tensor_path(mode)
+            pre = torch.full((b_, h_, w_, cout), float("nan"), device=DEV)
+            act = torch.empty(b_, h_, w_, cout, dtype=torch.bfloat16, device=DEV)
+            _lib._check(lib.tv_net_conv3x3(_vp(x), b_, h_, w_, cin, _vp(w), _vp(b), cout, 1,
+                                           _vp(pre), _vp(act), _stream()))
+            got = pre.cpu().numpy()
+            np.testing.assert_allclose(got, want, rtol=0, atol=tol)
+            _bf16_close(_np(act), np.maximum(want, 0.0), atol=1e-4)
+            outs.append(got)
+    finally:
+        _lib.set_net_tensor_path(0)
+    np.testing.assert_allclose(outs[0], outs[1], rtol=0, atol=tol)
+
+
+@pytest.mark.parametrize("cin,cout", PAIRS)
 def test_conv_backward_data_and_weight(cin, cout):
     lib = _lib.load()
     x = _bf16((B, H, W, cin), 4)
