@@ -382,12 +382,13 @@ tv_status tv_set_coop_max_chains(int64_t max_chains);
  * allows any root); 2 rooted at its middle node by two warps. All give the same
  * solution up to FP32 rounding. */
 tv_status tv_set_coop_split(int mode);
-/* How tv_chain_solve runs chains of 64 nodes or more when its batch runs one thread per
- * chain: 1 (the default) rooted at the middle node, each half by its own thread (messages
- * of up to 16 breakpoints on chip) and the root solved from both halves' messages
- * (Algorithm 2 allows any root); 0 by one thread from one end (messages of up to 32
- * breakpoints on chip). Longer messages are finished from the workspace either way. Both
- * give the same solution up to FP32 rounding. */
+/* How batches that run one thread per chain (tv_chain_solve with chains of 64 nodes or
+ * more, and the thread path of tv2d_denoise_batched) solve a chain: 1 (the default)
+ * rooted at the middle node, each half by its own thread (messages of up to 16
+ * breakpoints on chip) and the root solved from both halves' messages (Algorithm 2
+ * allows any root); 0 by one thread from one end (messages of up to 32 breakpoints on
+ * chip). Longer messages are finished from the workspace either way. Both give the same
+ * solution up to FP32 rounding. Read when a batched solve is planned. */
 tv_status tv_set_thread_split(int on);
 
 /* ------------------------------------------ learned dual warm start (net) ---- */

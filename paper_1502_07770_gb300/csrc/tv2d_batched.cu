@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "tv2d_common.cuh"
+#include "tv_halves.cuh"
 #include "tv_launch.cuh"
 
 using namespace tvk;
@@ -243,6 +244,7 @@ struct BRowsTP {
     const BGroup *groups;
     long long nslots;
     int maxlen;
+    int cpw_log;  // log2 of the chains per warp (5: one thread per chain, 4: per half)
     const Tv2dParams *prm;
     const float2 *spill_base;
     // bound per warp
@@ -259,7 +261,7 @@ struct BRowsTP {
     __device__ int max_len() const { return maxlen; }
     __device__ bool bind_warp(long long wc0)
     {
-        const BGroup g = groups[wc0 / WARP];
+        const BGroup g = groups[wc0 >> cpw_log];
         const BState &s = st[g.img];
         if (PHASE != 0 && s.done) return false;
         im = imgs + g.img;
@@ -281,12 +283,12 @@ struct BRowsTP {
         return true;
     }
     __device__ long long rec_slot(long long, int) const { return rec0; }
-    __device__ int row_of(long long k) const { return r0 + (int)(k & (WARP - 1)); }
+    __device__ int row_of(long long k) const { return r0 + (int)(k & ((1 << cpw_log) - 1)); }
     __device__ bool chain(long long k, long long &start, int &n) const
     {
         start = 0;
         n = 0;
-        if ((int)(k & (WARP - 1)) < cnt) {
+        if ((int)(k & ((1 << cpw_log) - 1)) < cnt) {
             start = (long long)row_of(k) * im->W;
             n = im->W;
         }
@@ -360,6 +362,7 @@ struct BRowsTP {
 struct BColsTP {
     static constexpr bool COLS = true;
     static constexpr int NIN = 4;  // x^k, x^{k-1}, y, w_v
+    static constexpr int WI = 3;   // the weights input
     static constexpr bool NEIGH = false;
     static constexpr bool CREC = true;
     static constexpr int NOUT = 0;
@@ -369,6 +372,7 @@ struct BColsTP {
     const BGroup *groups;
     long long nslots;
     int maxlen;
+    int cpw_log;  // log2 of the chains per warp (5: one thread per chain, 4: per half)
     const Tv2dParams *prm;
     const float2 *spill_base;
     // bound per warp
@@ -384,7 +388,7 @@ struct BColsTP {
     __device__ int max_len() const { return maxlen; }
     __device__ bool bind_warp(long long wc0)
     {
-        const BGroup g = groups[wc0 / WARP];
+        const BGroup g = groups[wc0 >> cpw_log];
         const BState &s = st[g.img];
         if (s.done) return false;
         im = imgs + g.img;
@@ -407,7 +411,7 @@ struct BColsTP {
     {
         start = 0;
         n = 0;
-        const int l = (int)(k & (WARP - 1));
+        const int l = (int)(k & ((1 << cpw_log) - 1));
         if (l < cnt) {
             start = c0 + l;  // the column
             n = im->H;
@@ -441,8 +445,14 @@ struct BColsTP {
     __device__ long long out_off(int, long long, long long) const { return 0; }
     __device__ void emit_cols(int i, long long k, float xhat, float c) const
     {
-        const int l = (int)(k & (WARP - 1));
+        const int l = (int)(k & ((1 << cpw_log) - 1));
         if (l < cnt) im->y[(long long)i * im->W + c0 + l] = sigma * (c - xhat);
+    }
+    // c_i of column `col` from global memory (the overflow path of the halves kernel)
+    __device__ float c_direct(int i, long long, long long col) const
+    {
+        const long long o = (long long)i * im->W + col;
+        return im->y[o] * inv_sigma + (xk[o] + theta * (xk[o] - xkm1[o]));
     }
     __device__ void emit_direct(int i, long long, long long col, float xhat, float c) const
     {
@@ -550,6 +560,7 @@ struct Plan {
     std::vector<ChainRef> cols, rows;
     std::vector<BGroup> rgroups, cgroups;  // one-thread-per-chain groups
     bool thread_rows = false, thread_cols = false;
+    bool halves = false;  // thread-per-chain batches run a thread per chain half
     std::vector<GapTile> tiles;
     std::vector<int> ntiles, tile0;
     int max_h = 0, max_w = 0;
@@ -585,11 +596,14 @@ BatchedWs carve_batched(void *base, const tv_image_desc *d, int n, int max_iters
         ncols += d[m].W;
         nrows += d[m].H;
         ntiles += (d[m].H * d[m].W + kGapTilePixels - 1) / kGapTilePixels;
+        // groups of 32 chains (a thread per chain) or of 16 (a thread per chain half):
+        // room for either layout of the records
         const long long rg = (d[m].H + WARP - 1) / WARP, cg = (d[m].W + WARP - 1) / WARP;
-        nrg += rg;
-        ncg += cg;
-        rrec += rg * WARP * d[m].W;
-        crec += cg * WARP * d[m].H;
+        const long long rg2 = (d[m].H + HW - 1) / HW, cg2 = (d[m].W + HW - 1) / HW;
+        nrg += rg2;
+        ncg += cg2;
+        rrec += std::max(rg * WARP * d[m].W, rg2 * WARP * ((d[m].W + 1) / 2));
+        crec += std::max(cg * WARP * d[m].H, cg2 * WARP * ((d[m].H + 1) / 2));
     }
     o.imgs = cv.take<BImg>((size_t)n);
     o.st = cv.take<BState>((size_t)n);
@@ -644,18 +658,22 @@ void build_plan(const tv_image_desc *d, int n, Plan &plan)
         for (int r = 0; r < d[m].H; ++r) plan.rows.push_back(ChainRef{m, r});
     plan.rgroups.clear();
     plan.cgroups.clear();
+    // a thread per chain half (16 chains per warp, ceil(len / 2) record rows) or a
+    // thread per chain (32 chains per warp, len record rows)
+    plan.halves = thread_split() != 0;
+    const int G = plan.halves ? HW : WARP;
     long long rrec = 0, crec = 0;
     for (int m : by_w)
-        for (long long r = 0; r < d[m].H; r += WARP) {
+        for (long long r = 0; r < d[m].H; r += G) {
             plan.rgroups.push_back(
-                BGroup{m, (int)r, (int)std::min<long long>(WARP, d[m].H - r), 0, rrec});
-            rrec += (long long)WARP * d[m].W;
+                BGroup{m, (int)r, (int)std::min<long long>(G, d[m].H - r), 0, rrec});
+            rrec += (long long)WARP * (plan.halves ? (d[m].W + 1) / 2 : d[m].W);
         }
     for (int m : by_h)
-        for (long long c = 0; c < d[m].W; c += WARP) {
+        for (long long c = 0; c < d[m].W; c += G) {
             plan.cgroups.push_back(
-                BGroup{m, (int)c, (int)std::min<long long>(WARP, d[m].W - c), 0, crec});
-            crec += (long long)WARP * d[m].H;
+                BGroup{m, (int)c, (int)std::min<long long>(G, d[m].W - c), 0, crec});
+            crec += (long long)WARP * (plan.halves ? (d[m].H + 1) / 2 : d[m].H);
         }
     // batches larger than the warp-per-chain limit run one thread per chain
     plan.thread_rows = (long long)plan.rows.size() > coop_max_chains();
@@ -726,6 +744,8 @@ tv_status launch_phase(const BatchedWs &ws, const Plan &plan, const ChainRef *ch
     return check_cuda(cudaGetLastError(), "batched phase launch");
 }
 
+constexpr int kBRingHalf = 16;  // ring entries per chain half
+
 template <class P>
 P thread_policy(const BatchedWs &ws, const Plan &plan, bool cols)
 {
@@ -733,7 +753,8 @@ P thread_policy(const BatchedWs &ws, const Plan &plan, bool cols)
     p.imgs = ws.imgs;
     p.st = ws.st;
     p.groups = cols ? ws.cgroups : ws.rgroups;
-    p.nslots = (long long)(cols ? plan.cgroups.size() : plan.rgroups.size()) * WARP;
+    p.cpw_log = plan.halves ? 4 : 5;
+    p.nslots = (long long)(cols ? plan.cgroups.size() : plan.rgroups.size()) << p.cpw_log;
     p.maxlen = cols ? plan.max_h : plan.max_w;
     p.prm = ws.prm;
     p.spill_base = plan.imgs[0].spill;
@@ -743,9 +764,14 @@ P thread_policy(const BatchedWs &ws, const Plan &plan, bool cols)
 template <class P>
 tv_status prepare_thread()
 {
-    return check_cuda(cudaFuncSetAttribute(chain_batch_kernel<P, kBRing>,
+    tv_status st = check_cuda(cudaFuncSetAttribute(chain_batch_kernel<P, kBRing>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(4 * sizeof(WarpSmem<P, kBRing>))),
+                              "cudaFuncSetAttribute");
+    if (st != TV_OK) return st;
+    return check_cuda(cudaFuncSetAttribute(chain_halves_kernel<P, kBRingHalf>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(4 * sizeof(WarpSmem<P, kBRing>))),
+                                           (int)(4 * sizeof(HalfSmem<P, kBRingHalf>))),
                       "cudaFuncSetAttribute");
 }
 
@@ -753,6 +779,14 @@ template <class P>
 tv_status launch_thread(const BatchedWs &ws, const Plan &plan, bool cols, cudaStream_t s)
 {
     const P p = thread_policy<P>(ws, plan, cols);
+    if (plan.halves) {
+        const Shape sh = chains_shape(p.nslots / HW, (const void *)chain_halves_kernel<P, kBRingHalf>,
+                                      sizeof(HalfSmem<P, kBRingHalf>));
+        chain_halves_kernel<P, kBRingHalf><<<(unsigned)sh.blocks, sh.wpb * WARP,
+                                             sh.wpb * sizeof(HalfSmem<P, kBRingHalf>), s>>>(
+            p, ws.trec, ws.tcrec, const_cast<float2 *>(p.spill_base), ws.hdr, 0);
+        return check_cuda(cudaGetLastError(), "batched thread-per-half launch");
+    }
     const Shape sh = chains_shape(p.nslots / WARP, (const void *)chain_batch_kernel<P, kBRing>,
                                   sizeof(WarpSmem<P, kBRing>));
     chain_batch_kernel<P, kBRing><<<(unsigned)sh.blocks, sh.wpb * WARP,

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <vector>
 
+#include "tv_halves.cuh"
 #include "tv_launch.cuh"
 
 namespace tvh {
@@ -59,6 +60,8 @@ static std::atomic<long long> g_coop_max{kCoopMaxChainsDefault};
 long long coop_max_chains() { return g_coop_max.load(); }
 static std::atomic<int> g_coop_split{1};
 int coop_split() { return g_coop_split.load(); }
+static std::atomic<int> g_thread_split{1};
+int thread_split() { return g_thread_split.load(); }
 bool prof_on() { return g_prof_on; }
 
 void prof_mark(int kind, cudaStream_t s, bool start)
@@ -161,6 +164,7 @@ template <bool HAS_W>
 struct ChainRowsP {
     static constexpr bool COLS = false;
     static constexpr int NIN = HAS_W ? 2 : 1;
+    static constexpr int WI = HAS_W ? 1 : -1;  // the weights input
     static constexpr bool NEIGH = false;
     static constexpr bool CREC = false;
     static constexpr int NOUT = 1;
@@ -505,285 +509,11 @@ tv_status launch_batch(const P &p, long long nchains, float2 *rec, float *crec, 
 }
 
 // ----------------------------------------------- middle-rooted thread chains --
-// One thread per chain half (Algorithm 2 may take any node as the root): the chain of
-// contiguous chain k is rooted at node mid = n/2; lane l < 16 of a warp runs the
-// forward pass of chain (warp's first + l) over nodes 0..mid-1, lane l + 16 runs it
-// over nodes n-1 down to mid+1 (the same update: the pairwise terms are symmetric).
-// Each half ends with the message into the root; the left lane then solves
-//     z - c_mid + m_L(z) + m_R(z) = 0
-// by one merged walk over both halves' breakpoint sequences (the partner's ring is in
-// the same shared memory), and both lanes clip their halves outwards from x_mid
-// (Algorithm 2, backward). Twice the warps of one thread per chain, each with half
-// the steps: the update is latency-bound, so more warps per scheduler hide more.
-// A chain whose half outgrows the ring is re-solved whole by its left lane from the
-// workspace (Sec. 4.1 two-ended array).
-constexpr int HW = WARP / 2;  // chains per warp
-// ring entries per half: 16 keep every warp of a full batch resident (27 per SM at
-// 65536 chains); longer messages take the workspace path
+// tv_halves.cuh: one thread per chain half. A 16-entry ring per half keeps every warp
+// of a full batch resident (27 per SM at 65536 chains); longer messages take the
+// workspace path.
 constexpr int kRingHalf = 16;
 
-template <bool HAS_W>
-struct alignas(16) HalfSmem {
-    static constexpr int NIN = HAS_W ? 2 : 1;
-    union {
-        struct {
-            float in[NIN][2][WARP * RP];
-            float2 ring[kRingHalf][WARP];
-        } f;
-        struct {
-            float2 rec[2][CH][WARP];
-            float out[WARP * RP];
-        } b;
-    } u;
-    long long start[WARP];
-    int n[WARP];
-    int cnt[WARP];
-};
-
-// node of step j of lane l's half (left: j; right: n-1-j)
-__device__ __forceinline__ int half_node(int lane, int n, int j)
-{
-    return lane < HW ? j : n - 1 - j;
-}
-
-template <bool HAS_W>
-__device__ __forceinline__ void half_fill(const ChainRowsP<HAS_W> &p, HalfSmem<HAS_W> *sm, int b,
-                                          int chunk, int lane)
-{
-#pragma unroll 4
-    for (int u = 0; u < CH; ++u) {
-        const int t = u * WARP + lane;
-        const int lt = t / CH, jj = t % CH;
-        const int j = chunk * CH + jj;
-        if (j < sm->cnt[lt]) {
-            const int i = half_node(lt, sm->n[lt], j);
-            cp_async4(&sm->u.f.in[0][b][lt * RP + jj], p.y + sm->start[lt] + i);
-            if constexpr (HAS_W)  // the edge from node i towards the root
-                cp_async4(&sm->u.f.in[1][b][lt * RP + jj],
-                          p.w + sm->start[lt] + (lt < HW ? i : i - 1));
-        }
-    }
-}
-
-// The whole chain by one thread, from node 0 (overflow path). Records at rec16[i * HW].
-template <bool HAS_W>
-__device__ void half_fallback(const ChainRowsP<HAS_W> &p, long long start, int n, float2 *spill,
-                              float2 *rec16)
-{
-    LinearStore S{spill};
-    DPState d;
-    float lm = 0.f, hp = 0.f;
-    float xlast = 0.f;
-    for (int i = 0; i < n; ++i) {
-        const float c = p.y[start + i];
-        float w = 0.f;
-        if (i < n - 1) w = HAS_W ? p.w[start + i] : p.lam;
-        if (i == 0) {
-            if (n == 1) {
-                xlast = c;
-                break;
-            }
-            dp_first(d, S, n, c, w, lm, hp);
-        } else {
-            dp_step(d, S, 2 * n + 2, c, w, (float)(i + 1), lm, hp);
-        }
-        if (i == n - 1) xlast = 0.5f * (lm + hp);
-        else rec16[(long long)i * HW] = make_float2(lm, hp);
-    }
-    float xv = xlast;
-    for (int i = n - 1; i >= 0; --i) {
-        if (i < n - 1) {
-            const float2 r = rec16[(long long)i * HW];
-            xv = clip_to(xv, r.x, r.y);
-        }
-        p.x[start + i] = xv;
-    }
-}
-
-// Root of z - c + m_L(z) + m_R(z): each message is -w left of its first breakpoint,
-// +w right of its last, with slope s_p + abar right of breakpoint p (abar = the half's
-// node count); an empty half contributes 0.
-__device__ __forceinline__ float half_root(const RingStore<kRingHalf> &SL, int FL, int BL, float aL,
-                                           float wL, const RingStore<kRingHalf> &SR, int FR, int BR,
-                                           float aR, float wR, float c)
-{
-    const bool hasL = BL >= FL, hasR = BR >= FR;
-    if (!hasL) wL = 0.f;
-    if (!hasR) wR = 0.f;
-    int pL = FL, pR = FR;
-    float2 eL = hasL ? SL.ld(pL) : make_float2(INFINITY, 0.f);
-    float2 eR = hasR ? SR.ld(pR) : make_float2(INFINITY, 0.f);
-    float zc = fminf(eL.x, eR.x);
-    if (!(zc < INFINITY)) return c;  // no message at all
-    float hc = zc - c - wL - wR;      // h at the first breakpoint (slope 1 to its left)
-    float slope = 1.f;                // slope of h on the segment ending at zc
-    for (int it = 0; it < 2 * kRingHalf + 4; ++it) {
-        if (hc >= 0.f) return zc - hc / slope;
-        // pass the breakpoint(s) at zc; the slopes right of it come from the last
-        // breakpoint passed in each half
-        if (hasL && pL <= BL && eL.x == zc) {
-            ++pL;
-            eL = pL <= BL ? SL.ld(pL) : make_float2(INFINITY, 0.f);
-        }
-        if (hasR && pR <= BR && eR.x == zc) {
-            ++pR;
-            eR = pR <= BR ? SR.ld(pR) : make_float2(INFINITY, 0.f);
-        }
-        const float gL = (hasL && pL > FL) ? SL.ld(pL - 1).y + aL : 0.f;
-        const float gR = (hasR && pR > FR) ? SR.ld(pR - 1).y + aR : 0.f;
-        slope = 1.f + gL + gR;
-        const float zn = fminf(eL.x, eR.x);
-        if (!(zn < INFINITY)) return zc - hc / slope;
-        hc = fmaf(slope, zn - zc, hc);
-        zc = zn;
-    }
-    return zc - hc / slope;  // not reached: at most 2 (kRingHalf + 1) breakpoints
-}
-
-template <bool HAS_W>
-__global__ void __launch_bounds__(128) chain_halves_kernel(ChainRowsP<HAS_W> p, float2 *rec,
-                                                           float2 *spill, WsHeader *hdr,
-                                                           int halfmax)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    p.resolve();
-    const int lane = threadIdx.x & (WARP - 1);
-    const int warp = threadIdx.x / WARP;
-    const int wpb = blockDim.x / WARP;
-    HalfSmem<HAS_W> *sm = reinterpret_cast<HalfSmem<HAS_W> *>(smem_raw) + warp;
-    const long long wg = (long long)blockIdx.x * wpb + warp;
-    const long long k = wg * HW + (lane & (HW - 1));
-    const bool left = lane < HW;
-    long long start = 0;
-    int n = 0;
-    if (k < p.num_chains()) {
-        if (!p.chain(k, start, n)) {
-            if (left) atomicOr(&hdr->status, ERR_BAD_CHAIN);
-            n = 0;
-        }
-    }
-    const int mid = n >> 1;
-    const int cnt = n == 0 ? 0 : (left ? mid : n - 1 - mid);
-    sm->start[lane] = start;
-    sm->n[lane] = n;
-    sm->cnt[lane] = cnt;
-    int cmax = cnt;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(FULL, cmax, o));
-    __syncwarp();
-    float2 *rec_w = rec + wg * (long long)halfmax * WARP;
-    RingStore<kRingHalf> S{(unsigned)__cvta_generic_to_shared(&sm->u.f.ring[0][lane])};
-    DPState d;
-    d.F = 0;
-    d.B = -1;
-    d.w_prev = 0.f;
-    bool alive = true;
-    const int nchunks = (cmax + CH - 1) / CH;
-
-    // ---------------- forward pass over each half ----------------
-    if (nchunks > 0) {
-        half_fill(p, sm, 0, 0, lane);
-        cp_async_commit();
-    }
-    int b = 0;
-    for (int ch = 0; ch < nchunks; ++ch) {
-        if (ch + 1 < nchunks) half_fill(p, sm, b ^ 1, ch + 1, lane);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncwarp();
-#pragma unroll 1
-        for (int j4 = 0; j4 < CH; j4 += 4) {
-            const float4 qc = *reinterpret_cast<const float4 *>(&sm->u.f.in[0][b][lane * RP + j4]);
-            float4 qw = make_float4(p.lam, p.lam, p.lam, p.lam);
-            if constexpr (HAS_W) qw = *reinterpret_cast<const float4 *>(&sm->u.f.in[1][b][lane * RP + j4]);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int j = ch * CH + j4 + e;
-                if (j < cnt && alive) {
-                    const float c = pick4(qc, e), w = pick4(qw, e);
-                    float lm, hp;
-                    if (j == 0) {
-                        dp_first(d, S, 0, c, w, lm, hp);
-                    } else {
-                        alive = dp_step(d, S, kRingHalf, c, w, (float)(j + 1), lm, hp);
-                    }
-                    if (alive) rec_w[(long long)j * WARP + lane] = make_float2(lm, hp);
-                }
-            }
-        }
-        __syncwarp();
-        b ^= 1;
-    }
-    cp_async_wait<0>();
-    __syncwarp();
-
-    // ---------------- root ----------------
-    const int FR = __shfl_down_sync(FULL, d.F, HW), BR = __shfl_down_sync(FULL, d.B, HW);
-    const float wR = __shfl_down_sync(FULL, d.w_prev, HW);
-    const int cntR = __shfl_down_sync(FULL, cnt, HW);
-    const bool aliveR = __shfl_down_sync(FULL, (int)alive, HW) != 0;
-    const bool ok = __shfl_sync(FULL, (int)(alive && aliveR), lane & (HW - 1)) != 0;
-    float xroot = 0.f;
-    if (left && n > 0 && ok) {
-        const RingStore<kRingHalf> SR{S.base + HW * 8};  // lane + 16's ring
-        const float c = p.y[start + mid];
-        xroot = half_root(S, cnt > 0 ? d.F : 0, cnt > 0 ? d.B : -1, (float)cnt, d.w_prev, SR,
-                          cntR > 0 ? FR : 0, cntR > 0 ? BR : -1, (float)cntR, wR, c);
-        p.x[start + mid] = xroot;
-    }
-    xroot = __shfl_sync(FULL, xroot, lane & (HW - 1));
-    __threadfence_block();
-    __syncwarp();
-
-    // ---------------- backward pass, outwards from the root ----------------
-    const int cnt_eff = ok ? cnt : 0;
-    sm->cnt[lane] = cnt_eff;
-    float xv = xroot;
-    auto load_recs = [&](int buf, int ch) {
-#pragma unroll 4
-        for (int u = 0; u < CH; ++u) {
-            const int j = ch * CH + u;
-            if (j < cnt_eff)
-                cp_async8(&sm->u.b.rec[buf][u][lane], rec_w + (long long)j * WARP + lane);
-        }
-    };
-    b = 0;
-    if (nchunks > 0) load_recs(0, nchunks - 1);
-    cp_async_commit();
-    for (int ch = nchunks - 1; ch >= 0; --ch) {
-        if (ch > 0) load_recs(b ^ 1, ch - 1);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncwarp();
-#pragma unroll 4
-        for (int jj = CH - 1; jj >= 0; --jj) {
-            const int j = ch * CH + jj;
-            if (j < cnt_eff) {
-                const float2 r = sm->u.b.rec[b][jj][lane];
-                xv = clip_to(xv, r.x, r.y);
-                sm->u.b.out[lane * RP + jj] = xv;
-            }
-        }
-        __syncwarp();
-#pragma unroll 4
-        for (int u = 0; u < CH; ++u) {
-            const int t = u * WARP + lane;
-            const int lt = t / CH, jj = t % CH;
-            const int j = ch * CH + jj;
-            if (j < sm->cnt[lt])
-                p.x[sm->start[lt] + half_node(lt, sm->n[lt], j)] = sm->u.b.out[lt * RP + jj];
-        }
-        __syncwarp();
-        b ^= 1;
-    }
-    cp_async_wait<0>();
-    if (left && n > 0 && !ok) {
-        atomicAdd(&hdr->overflowed, 1ull);
-        half_fallback(p, start, n, spill + p.spill_off(k, start), rec_w + lane);
-    }
-}
-
-static std::atomic<int> g_thread_split{1};
 constexpr int kHalvesMinLen = 64;
 
 template <bool HAS_W>
@@ -791,8 +521,8 @@ tv_status launch_halves(const ChainRowsP<HAS_W> &p, long long nchains, int max_l
                         float2 *spill, WsHeader *hdr, cudaStream_t s)
 {
     const long long warps = (nchains + HW - 1) / HW;
-    const size_t per_warp = sizeof(HalfSmem<HAS_W>);
-    auto kern = chain_halves_kernel<HAS_W>;
+    const size_t per_warp = sizeof(HalfSmem<ChainRowsP<HAS_W>, kRingHalf>);
+    auto kern = chain_halves_kernel<ChainRowsP<HAS_W>, kRingHalf>;
     tv_status st = check_cuda(
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * per_warp)),
         "cudaFuncSetAttribute");
@@ -800,7 +530,7 @@ tv_status launch_halves(const ChainRowsP<HAS_W> &p, long long nchains, int max_l
     const Shape sh = chains_shape(warps, (const void *)kern, per_warp);
     const bool prof = prof_on();
     if (prof) prof_mark(PK_CHAIN, s, true);
-    kern<<<(unsigned)sh.blocks, sh.wpb * WARP, sh.wpb * per_warp, s>>>(p, rec, spill, hdr,
+    kern<<<(unsigned)sh.blocks, sh.wpb * WARP, sh.wpb * per_warp, s>>>(p, rec, nullptr, spill, hdr,
                                                                        (max_len + 1) / 2);
     st = check_cuda(cudaGetLastError(), "chain halves kernel launch");
     if (st == TV_OK) note_launch();
@@ -868,7 +598,7 @@ tv_status tv_set_thread_split(int on)
         set_error("tv_set_thread_split: 0 or 1");
         return TV_ERR_INVALID;
     }
-    g_thread_split.store(on);
+    tvh::g_thread_split.store(on);
     return TV_OK;
 }
 
@@ -1011,7 +741,7 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     }
     // chains of 64 nodes or more: two threads per chain (twice the warps, half the steps
     // each, and a 16-entry ring that keeps every warp of a full batch resident)
-    const bool halves = g_thread_split.load() != 0 && max_len >= kHalvesMinLen;
+    const bool halves = thread_split() != 0 && max_len >= kHalvesMinLen;
     if (d_w) {
         ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,
                            vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0};

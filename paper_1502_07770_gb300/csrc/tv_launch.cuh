@@ -48,6 +48,7 @@ tv_status launch_chains(const P &p, long long nchains, float2 *rec, float *crec,
 constexpr int kCoopSmemNodes = 4096;
 
 int coop_split();  // 0 one warp per chain, 1 two halves in one warp, 2 two warps
+int thread_split();  // 1: thread-per-chain batches run a thread per chain half
 
 template <class P>
 tv_status launch_coop(const P &p, long long nchains, int max_len, float2 *rec, float *crec,
