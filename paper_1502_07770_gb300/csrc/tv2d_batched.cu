@@ -493,6 +493,7 @@ __global__ void __launch_bounds__(kBGapThreads)
         const long long dr = stride / W, dc = stride - dr * W;
         long long q = t.first + threadIdx.x;
         long long r = q / W, c = q - r * W;
+#pragma unroll 4
         for (; q < t.first + t.count; q += stride) {
             const float xv = x1[q], fv = im->f[q];
             const float z = xv + (xv - x0[q]) * inv_tau;
@@ -584,7 +585,7 @@ struct BatchedWs {
     size_t bytes;
 };
 
-constexpr long long kGapTilePixels = 1 << 16;
+constexpr long long kGapTilePixels = 1 << 14;  // 64 pixels per thread: enough blocks in flight
 
 // Lays out the workspace (base may be NULL to size it) and fills the image table.
 BatchedWs carve_batched(void *base, const tv_image_desc *d, int n, int max_iters, Plan &plan)
