@@ -94,7 +94,7 @@ tv_status launch_coop(const P &p, long long nchains, int max_len, float2 *rec, f
 // Batches of fewer chains than this run one warp per chain (the update of one
 // chain is then latency-bound, and a warp shortens its critical path); larger
 // batches run one thread per chain.
-constexpr long long kCoopMaxChainsDefault = 2048;
+constexpr long long kCoopMaxChainsDefault = 4096;
 long long coop_max_chains();  // tunable, see tv_set_coop_max_chains
 
 }  // namespace tvh
