@@ -18,6 +18,8 @@
 // A message of more than 32 breakpoints is finished by lane 0 from global memory.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "tv_launch.cuh"
 
 using namespace tvk;
@@ -161,6 +163,123 @@ __device__ __forceinline__ void pq_update(PqState &s, float a, float b, float al
     s.wlo_p = wlo;
 }
 
+// The same update on a segment of G lanes (G = 16: two chain halves per warp, each
+// segment one half; sl the lane in the segment, seg_shift its first lane). Every lane
+// executes every shuffle; a segment whose half has no node at this step passes
+// active = false and keeps its state.
+template <int G>
+__device__ __forceinline__ void pq_update_seg(PqState &s, float a, float b, float al, float f,
+                                              float wlo, float whi, int sl, int seg_shift,
+                                              bool active, bool &ovf, float &lm, float &hp)
+{
+    auto seg = [&](unsigned bal) { return (bal >> seg_shift) & ((1u << G) - 1u); };
+    bool valid = sl < s.size;
+    // ---- insert f (unless a breakpoint is already there) ----
+    const int ins = __popc(seg(__ballot_sync(FULL, valid && s.lam < f)));
+    const float lam_at = __shfl_sync(FULL, s.lam, ins, G);
+    const bool exists = ins < s.size && lam_at == f;
+    const float pl = __shfl_sync(FULL, s.lam, ins - 1, G), pR = __shfl_sync(FULL, s.R, ins - 1, G),
+                pS = __shfl_sync(FULL, s.S, ins - 1, G);
+    const float ul = __shfl_up_sync(FULL, s.lam, 1, G), uL = __shfl_up_sync(FULL, s.L, 1, G),
+                uR = __shfl_up_sync(FULL, s.R, 1, G), uS = __shfl_up_sync(FULL, s.S, 1, G);
+    if (active && !exists) {
+        if (s.size + 1 > G) ovf = true;
+        float mval, Sn;
+        if (ins == 0) {
+            mval = s.size > 0 ? s.wlo_p : 0.f;  // the message's flat left end (0 before node 0)
+            Sn = 0.f;
+        } else {
+            mval = fmaf(pS, f - pl, pR);
+            Sn = pS;
+        }
+        if (sl == ins) {
+            s.lam = f;
+            s.L = mval;
+            s.R = mval;
+            s.S = Sn;
+        } else if (sl > ins) {
+            s.lam = ul;
+            s.L = uL;
+            s.R = uR;
+            s.S = uS;
+        }
+        s.size += 1;
+        valid = sl < s.size;
+    }
+    // ---- transformation (a): + a z - b - alpha left of f, + alpha right of it ----
+    if (active) {
+        const float lin = fmaf(a, s.lam, -b);
+        const float dl = (sl <= ins) ? -al : al;
+        const float dr = (sl < ins) ? -al : al;
+        s.L += lin + dl;
+        s.R += lin + dr;
+        s.S += a;
+    }
+    const float lam_n = __shfl_down_sync(FULL, s.lam, 1, G);
+    const bool last = sl == s.size - 1;
+    float cL = fmaxf(s.lam + __fdividef(wlo - s.R, s.S), s.lam);
+    float cR = fmaxf(s.lam + __fdividef(whi - s.R, s.S), s.lam);
+    if (!last) {
+        cL = fminf(cL, lam_n);
+        cR = fminf(cR, lam_n);
+    }
+    const unsigned bge = seg(__ballot_sync(FULL, valid && s.R >= wlo));
+    const unsigned ble = seg(__ballot_sync(FULL, valid && s.L <= whi));
+    const int ell = min(bge ? __ffs(bge) - 1 : G, s.size);
+    const int kl = ble ? 31 - __clz(ble) : -1;
+    const float L0 = __shfl_sync(FULL, s.L, 0, G), lam0 = __shfl_sync(FULL, s.lam, 0, G);
+    const float Le = __shfl_sync(FULL, s.L, ell, G), Re = __shfl_sync(FULL, s.R, ell, G),
+                lame = __shfl_sync(FULL, s.lam, ell, G), Se = __shfl_sync(FULL, s.S, ell, G);
+    const float cLm = __shfl_sync(FULL, cL, ell - 1, G), Sm = __shfl_sync(FULL, s.S, ell - 1, G);
+    const float Lk = __shfl_sync(FULL, s.L, kl, G), Rk = __shfl_sync(FULL, s.R, kl, G),
+                lamk = __shfl_sync(FULL, s.lam, kl, G), cRk = __shfl_sync(FULL, cR, kl, G);
+    const bool jumpL = ell < s.size && Le < wlo;
+    const bool jumpR = kl >= 0 && Rk > whi;
+    const bool both = jumpL && jumpR && ell == kl;
+    float Sl;
+    if (jumpL) {
+        lm = lame;
+        Sl = Se;
+    } else if (ell == 0) {
+        lm = fminf(lam0 + (wlo - L0) / a, lam0);  // on the left end piece (slope a)
+        Sl = a;
+    } else {
+        lm = cLm;
+        Sl = Sm;
+    }
+    if (jumpR) hp = lamk;
+    else if (kl < 0) hp = fminf(lam0 + (whi - L0) / a, lam0);
+    else hp = cRk;
+    const int k0 = ell + (jumpL ? 1 : 0), k1 = kl - (jumpR ? 1 : 0);
+    const int K = k1 >= k0 ? k1 - k0 + 1 : 0;
+    if (active && K + 2 > G) ovf = true;
+    const float lmR = jumpL ? fminf(Re, whi) : wlo;
+    const float hpL = jumpR ? (both ? fminf(Re, whi) : fmaxf(Lk, wlo)) : whi;
+    const int src = sl - 1 + k0;
+    const float nl = __shfl_sync(FULL, s.lam, src, G), nL = __shfl_sync(FULL, s.L, src, G),
+                nR = __shfl_sync(FULL, s.R, src, G), nS = __shfl_sync(FULL, s.S, src, G);
+    if (active) {
+        if (sl == 0) {
+            s.lam = lm;
+            s.L = wlo;
+            s.R = lmR;
+            s.S = both ? 0.f : Sl;
+        } else if (sl == K + 1) {
+            s.lam = hp;
+            s.L = hpL;
+            s.R = whi;
+            s.S = 0.f;
+        } else {
+            s.lam = nl;
+            s.L = nL;
+            s.R = nR;
+            s.S = nS;
+        }
+        s.size = K + 2;
+        s.wlo_p = wlo;
+    }
+}
+
 // Overflow path: lane 0, the same update on a global array of (lambda, L, R, S) entries
 // (4 * (3n + 4) floats), sequential and O(size) per node.
 struct PqEntry {
@@ -264,23 +383,11 @@ struct PqArgs {
 
 constexpr int kPqWarps = 4;
 
-__global__ void __launch_bounds__(kPqWarps * WARP) pq_chain_kernel(PqArgs p, WsHeader *hdr)
+// Chain k (first node `start`, n nodes) by the calling warp from node 0: the 32-lane
+// update, records, backward clips; lane 0 from the workspace past 32 breakpoints.
+__device__ void pq_solve_warp(const PqArgs &p, long long k, long long start, int n, int lane,
+                              WsHeader *hdr)
 {
-    const int lane = threadIdx.x & (WARP - 1);
-    const long long k = (long long)blockIdx.x * kPqWarps + threadIdx.x / WARP;
-    if (k >= p.nchains) return;
-    long long start = k * (long long)p.maxlen;
-    int n = p.maxlen;
-    if (p.offsets) {
-        const long long off0 = p.offsets[0], lo = p.offsets[k], hi = p.offsets[k + 1];
-        if (lo < off0 || hi < lo || hi - lo > p.maxlen) {
-            if (lane == 0) atomicOr(&hdr->status, ERR_BAD_CHAIN);
-            return;
-        }
-        start = lo;
-        n = (int)(hi - lo);
-    }
-    if (n == 0) return;
     float2 *rec = p.rec + k * (long long)p.maxlen;
     const float *a = p.a ? p.a + start : nullptr;
     const float *b = p.b + start, *f = p.f + start;
@@ -334,23 +441,46 @@ __global__ void __launch_bounds__(kPqWarps * WARP) pq_chain_kernel(PqArgs p, WsH
     }
 }
 
-// ------------------------------------------------------ middle-rooted pairs --
-// Two warps per chain, rooted at node mid = n/2 (Algorithm 2 allows any root): warp 0 of
-// a pair runs pq_update over nodes 0..mid-1, warp 1 over nodes n-1..mid+1 (the pairwise
-// terms are symmetric, so the update is the same), each ending with the message into the
-// root. After a pair barrier both warps read the two messages from shared memory and find
-// the same root x_mid, the zero of
+// chain offsets: chain k's first node and length (false: malformed, flagged)
+__device__ __forceinline__ bool pq_chain_of(const PqArgs &p, long long k, int lane, WsHeader *hdr,
+                                            long long &start, int &n)
+{
+    start = k * (long long)p.maxlen;
+    n = p.maxlen;
+    if (p.offsets) {
+        const long long off0 = p.offsets[0], lo = p.offsets[k], hi = p.offsets[k + 1];
+        if (lo < off0 || hi < lo || hi - lo > p.maxlen) {
+            if (lane == 0) atomicOr(&hdr->status, ERR_BAD_CHAIN);
+            return false;
+        }
+        start = lo;
+        n = (int)(hi - lo);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kPqWarps * WARP) pq_chain_kernel(PqArgs p, WsHeader *hdr)
+{
+    const int lane = threadIdx.x & (WARP - 1);
+    const long long k = (long long)blockIdx.x * kPqWarps + threadIdx.x / WARP;
+    if (k >= p.nchains) return;
+    long long start;
+    int n;
+    if (!pq_chain_of(p, k, lane, hdr, start, n) || n == 0) return;
+    pq_solve_warp(p, k, start, n, lane, hdr);
+}
+
+// ------------------------------------------------------ middle-rooted chains --
+// Rooted at node mid = n/2 (Algorithm 2 allows any root), a chain's two halves each end
+// with the message into the root; the root x_mid is the zero of
 //     g(z) = a z - b + alpha sign(z - f) + m_L(z) + m_R(z)
 // (non-decreasing, piecewise linear with jumps): every breakpoint of either message and
 // f are candidates; the first candidate c1 with g(c1+) >= 0 is the root if g(c1-) <= 0,
 // else the root lies on the linear piece between c1 and the candidate c0 before it.
-// Each warp then clips its half outwards (Algorithm 2, backward).
 struct PqMsg {
     float lam[WARP], L[WARP], R[WARP], S[WARP];
     int size, ovf;
 };
-
-__device__ __forceinline__ void pq_pair_bar(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
 
 // value of message M just left (m_lo) and right (m_hi) of z, and its slope right of z
 __device__ __forceinline__ void pq_msg_at(const PqMsg &M, float z, float &m_lo, float &m_hi,
@@ -440,29 +570,28 @@ __device__ float pq_root(const PqMsg &ML, const PqMsg &MR, float a, float b, flo
     return fminf(fmaxf(z, c0), c1);
 }
 
-__global__ void __launch_bounds__(kPqWarps * WARP) pq_pair_kernel(PqArgs p, WsHeader *hdr)
+// ----------------------------------------------------- middle-rooted halves --
+// One warp per chain, rooted at node mid = n/2: lanes 0-15 run pq_update_seg<16> over
+// nodes 0..mid-1, lanes 16-31 over nodes n-1..mid+1, both in the same instructions;
+// the two messages into the root (at most 16 breakpoints each) go to shared memory and
+// the whole warp finds the root (pq_root), then each segment clips its
+// half outwards. A half that outgrows 16 breakpoints sends the chain to the one-warp
+// solve from node 0 (32 breakpoints, then lane 0 from the workspace).
+__global__ void __launch_bounds__(kPqWarps * WARP) pq_halves_kernel(PqArgs p, WsHeader *hdr)
 {
-    __shared__ PqMsg msg[kPqWarps];
+    __shared__ PqMsg msg[kPqWarps][2];
     const int lane = threadIdx.x & (WARP - 1);
     const int warp = threadIdx.x / WARP;
-    const int role = warp & 1, pair = warp >> 1;
-    const long long k = (long long)blockIdx.x * (kPqWarps / 2) + pair;
-    if (k >= p.nchains) return;  // both warps of the pair
-    long long start = k * (long long)p.maxlen;
-    int n = p.maxlen;
-    if (p.offsets) {
-        const long long off0 = p.offsets[0], lo = p.offsets[k], hi = p.offsets[k + 1];
-        if (lo < off0 || hi < lo || hi - lo > p.maxlen) {
-            if (lane == 0 && role == 0) atomicOr(&hdr->status, ERR_BAD_CHAIN);
-            return;
-        }
-        start = lo;
-        n = (int)(hi - lo);
-    }
-    if (n == 0) return;
+    const long long k = (long long)blockIdx.x * kPqWarps + warp;
+    if (k >= p.nchains) return;
+    long long start;
+    int n;
+    if (!pq_chain_of(p, k, lane, hdr, start, n) || n == 0) return;
     const int mid = n >> 1;
-    const int cnt = role == 0 ? mid : n - 1 - mid;
-    auto node_of = [&](int j) { return role == 0 ? j : n - 1 - j; };
+    const int seg = lane >> 4, sl = lane & 15, seg_shift = seg * 16;
+    const int cnt = seg == 0 ? mid : n - 1 - mid;
+    const int cmax = max(mid, n - 1 - mid);
+    auto node_of = [&](int j) { return seg == 0 ? j : n - 1 - j; };
     float2 *rec = p.rec + k * (long long)p.maxlen;
     const float *a = p.a ? p.a + start : nullptr;
     const float *b = p.b + start, *f = p.f + start;
@@ -470,74 +599,71 @@ __global__ void __launch_bounds__(kPqWarps * WARP) pq_pair_kernel(PqArgs p, WsHe
     const float *w = p.w ? p.w + (p.w_stride > 0 ? k * p.w_stride : start) : nullptr;
     PqState s{0.f, 0.f, 0.f, 0.f, 0, 0.f, 0.f, 0.f};
     bool ovf = false;
-    const int nblocks = (cnt + WARP - 1) / WARP;
+    const int nblocks = (cmax + 15) / 16;
     for (int blk = 0; blk < nblocks && !ovf; ++blk) {
-        const int j_l = blk * WARP + lane;
+        const int j_l = blk * 16 + sl;
         const bool in = j_l < cnt;
         const int i_l = in ? node_of(j_l) : 0;
-        const int e_l = role == 0 ? i_l : i_l - 1;  // the edge towards the root
+        const int e_l = seg == 0 ? i_l : i_l - 1;  // the edge towards the root
         const float av = (in && a) ? a[i_l] : 1.f, bv = in ? b[i_l] : 0.f,
                     alv = in ? (al ? al[i_l] : p.alpha) : 0.f, fv = in ? f[i_l] : 0.f,
                     wv = in ? (w ? w[e_l] * p.wscale : p.lam) : 0.f;
-        const int c = min(WARP, cnt - blk * WARP);
-        for (int jj = 0; jj < c; ++jj) {
-            const float ai = __shfl_sync(FULL, av, jj), bi = __shfl_sync(FULL, bv, jj),
-                        ali = __shfl_sync(FULL, alv, jj), fi = __shfl_sync(FULL, fv, jj),
-                        wi = __shfl_sync(FULL, wv, jj);
-            const int i = __shfl_sync(FULL, i_l, jj);
+        const int c16 = min(16, cmax - blk * 16);
+        for (int jj = 0; jj < c16; ++jj) {
+            const float ai = __shfl_sync(FULL, av, jj, 16), bi = __shfl_sync(FULL, bv, jj, 16),
+                        ali = __shfl_sync(FULL, alv, jj, 16), fi = __shfl_sync(FULL, fv, jj, 16),
+                        wi = __shfl_sync(FULL, wv, jj, 16);
+            const int i = __shfl_sync(FULL, i_l, jj, 16);
+            const bool active = blk * 16 + jj < cnt;
             float lm, hp;
-            pq_update(s, ai, bi, ali, fi, -wi, wi, lane, ovf, lm, hp);
-            if (lane == 0) rec[i] = make_float2(lm, hp);
+            pq_update_seg<16>(s, ai, bi, ali, fi, -wi, wi, sl, seg_shift, active, ovf, lm, hp);
+            if (active && sl == 0) rec[i] = make_float2(lm, hp);
         }
         ovf = __any_sync(FULL, ovf);
     }
-    PqMsg &mine = msg[warp];
-    mine.lam[lane] = s.lam;
-    mine.L[lane] = s.L;
-    mine.R[lane] = s.R;
-    mine.S[lane] = s.S;
-    if (lane == 0) {
-        mine.size = cnt > 0 ? s.size : 0;
-        mine.ovf = ovf ? 1 : 0;
-    }
-    pq_pair_bar(1 + pair);
-    const PqMsg &ML = msg[2 * pair], &MR = msg[2 * pair + 1];
-    if (ML.ovf || MR.ovf) {
-        if (role == 0 && lane == 0) {
-            atomicAdd(&hdr->overflowed, 1ull);
-            PqEntry *E = p.ent + k * 2LL * (3LL * p.maxlen + 4);
-            pq_lane0(n, a, b, al, f, w, p.wscale, p.alpha, p.lam, p.x + start, E,
-                     E + (3LL * p.maxlen + 4), rec);
-        }
+    if (ovf) {
+        // a half outgrew 16 breakpoints: the whole chain by the warp from node 0
+        pq_solve_warp(p, k, start, n, lane, hdr);
         return;
     }
+    PqMsg &mine = msg[warp][seg];
+    mine.lam[sl] = s.lam;
+    mine.L[sl] = s.L;
+    mine.R[sl] = s.R;
+    mine.S[sl] = s.S;
+    if (sl == 0) {
+        mine.size = cnt > 0 ? s.size : 0;
+        mine.ovf = 0;
+    }
+    __syncwarp();
     const float am = a ? a[mid] : 1.f, alm = al ? al[mid] : p.alpha;
-    const float xm = pq_root(ML, MR, am, b[mid], alm, f[mid], lane);
-    if (role == 0 && lane == 0) p.x[start + mid] = xm;
-    // backward over this half, outwards from the root, in processing order
+    const float xm = pq_root(msg[warp][0], msg[warp][1], am, b[mid], alm, f[mid], lane);
+    if (lane == 0) p.x[start + mid] = xm;
+    // backward over each half, outwards from the root, in processing order
     float x_next = xm;
     for (int blk = nblocks - 1; blk >= 0; --blk) {
-        const int j = blk * WARP + lane;
+        const int j = blk * 16 + sl;
+        const bool inb = j < cnt;
         float lo = -INFINITY, hi = INFINITY;
-        if (j < cnt) {
+        if (inb) {
             const float2 r = rec[node_of(j)];
             lo = r.x;
             hi = r.y;
         }
-        const float xv = clip_suffix(lo, hi, x_next, lane, min(WARP, cnt - blk * WARP));
-        if (j < cnt) p.x[start + node_of(j)] = xv;
-        x_next = __shfl_sync(FULL, xv, 0);
+        const float xv = clip_suffix16(lo, hi, x_next, sl, inb);
+        if (inb) p.x[start + node_of(j)] = xv;
+        x_next = __shfl_sync(FULL, xv, 0, 16);
     }
 }
 
-// chains of 64 nodes or more: two warps per chain from the middle node; shorter ones one
-// warp per chain from one end
+// chains of 64 nodes or more: rooted at the middle node, the halves on two 16-lane
+// segments of one warp; shorter ones one warp per chain from one end
 void launch_pq(const PqArgs &p, long long nchains, long long max_len, WsHeader *hdr,
                cudaStream_t s)
 {
     if (max_len >= 64) {
-        const long long blocks = (nchains + kPqWarps / 2 - 1) / (kPqWarps / 2);
-        pq_pair_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
+        const long long blocks = (nchains + kPqWarps - 1) / kPqWarps;
+        pq_halves_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
     } else {
         const long long blocks = (nchains + kPqWarps - 1) / kPqWarps;
         pq_chain_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
