@@ -49,15 +49,40 @@ __device__ __forceinline__ int half_node(int lane, int n, int j)
     return lane < HW ? j : n - 1 - j;
 }
 
+// Row inputs in bit a of `vmask` (16-byte aligned rows of a multiple of 4 nodes) are
+// copied by each lane for its own half: the chunk's CH nodes as CH/4 16-byte pieces, in
+// memory order. A left half's steps ascend with the nodes, so step jj of the chunk sits at
+// tile position jj; a right half's descend, so step jj sits at CH-1-jj. Pieces that would
+// leave the chain are copied node by node.
 template <class P, int RING>
 __device__ __forceinline__ void half_fill(const P &p, HalfSmem<P, RING> *sm, int b, int chunk,
-                                          int lane, long long wc0)
+                                          int lane, long long wc0, unsigned vmask, long long k,
+                                          long long start, int n, int cnt)
 {
 #pragma unroll
     for (int a = 0; a < P::NIN; ++a) {
         const float *src = p.in_ptr(a);
         if (src == nullptr) continue;
         float *tile = sm->u.f.in[a][b];
+        if (!P::COLS && ((vmask >> a) & 1u)) {
+            if (chunk * CH < cnt) {
+                const float *row = src + p.in_off(a, k, start);
+                const int lim = p.in_lim(a, n);
+#pragma unroll
+                for (int h = 0; h < CH / 4; ++h) {
+                    const int lo = lane < HW ? chunk * CH + 4 * h : n - CH - chunk * CH + 4 * h;
+                    if (lo >= 0 && lo + 3 < lim) {
+                        cp_async16(&tile[lane * RP + 4 * h], row + lo);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (lo + e >= 0 && lo + e < lim)
+                                cp_async4(&tile[lane * RP + 4 * h + e], row + lo + e);
+                    }
+                }
+            }
+            continue;
+        }
         if constexpr (P::COLS) {
             // node j of every lane's column: 16 left lanes and 16 right lanes each read
             // 16 neighbouring columns of one node row
@@ -203,6 +228,19 @@ __global__ void __launch_bounds__(128) chain_halves_kernel(P p_in, float2 *rec, 
     }
     const int mid = n >> 1;
     const int cnt = n == 0 ? 0 : (left ? mid : n - 1 - mid);  // update steps of this half
+    // row inputs and outputs moved 16 bytes at a time by each lane for its own half
+    // (edge weights excepted: a right half reads them one node off the 4-node grid)
+    unsigned vmask = 0;
+    bool vout = false;
+    if constexpr (!P::COLS) {
+#pragma unroll
+        for (int a = 0; a < P::NIN; ++a)
+            if (a != P::WI && p.in_vec(a)) vmask |= 1u << a;
+        vout = p.out_vec();
+    }
+    // both staging layouts are shared across the warp's lanes: keep them warp-uniform
+    vmask = __reduce_and_sync(FULL, vmask);
+    vout = __all_sync(FULL, vout);
     sm->start[lane] = start;
     sm->n[lane] = n;
     sm->cnt[lane] = cnt;
@@ -225,27 +263,30 @@ __global__ void __launch_bounds__(128) chain_halves_kernel(P p_in, float2 *rec, 
     const int nchunks = (cmax + CH - 1) / CH;
 
     // ---------------- forward pass over each half ----------------
-    if (nchunks > 0) half_fill(p, sm, 0, 0, lane, wc0);
+    if (nchunks > 0) half_fill(p, sm, 0, 0, lane, wc0, vmask, k, start, n, cnt);
     cp_async_commit();
     int b = 0;
     for (int ch = 0; ch < nchunks; ++ch) {
-        if (ch + 1 < nchunks) half_fill(p, sm, b ^ 1, ch + 1, lane, wc0);
+        if (ch + 1 < nchunks) half_fill(p, sm, b ^ 1, ch + 1, lane, wc0, vmask, k, start, n, cnt);
         cp_async_commit();
         cp_async_wait<1>();
         __syncwarp();
 #pragma unroll 1
         for (int j4 = 0; j4 < CH; j4 += 4) {
             float4 q[P::NIN];
+            const unsigned rv = left ? 0u : vmask;  // inputs whose steps run backwards in the tile
 #pragma unroll
             for (int a = 0; a < P::NIN; ++a)
-                q[a] = *reinterpret_cast<const float4 *>(&sm->u.f.in[a][b][lane * RP + j4]);
+                q[a] = *reinterpret_cast<const float4 *>(
+                    &sm->u.f.in[a][b][lane * RP + (((rv >> a) & 1u) ? CH - 4 - j4 : j4)]);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = ch * CH + j4 + e;
                 if (j < cnt && alive) {
                     float v[P::NIN];
 #pragma unroll
-                    for (int a = 0; a < P::NIN; ++a) v[a] = pick4(q[a], e);
+                    for (int a = 0; a < P::NIN; ++a)
+                        v[a] = ((rv >> a) & 1u) ? pick4(q[a], 3 - e) : pick4(q[a], e);
                     const int i = half_node(lane, n, j);
                     float c, w;
                     p.unary(v, 0.f, j, i, i + 2, k, c, w, acc);
@@ -307,34 +348,74 @@ __global__ void __launch_bounds__(128) chain_halves_kernel(P p_in, float2 *rec, 
         cp_async_commit();
         cp_async_wait<1>();
         __syncwarp();
-#pragma unroll 4
-        for (int jj = CH - 1; jj >= 0; --jj) {
-            const int j = ch * CH + jj;
-            if (j < cnt_eff) {
-                const float2 r = sm->u.b.rec[b][jj][lane];
-                xv = clip_to(xv, r.x, r.y);
-                if constexpr (P::COLS) {
-                    float cc = 0.f;
-                    if constexpr (P::CREC) cc = sm->u.b.crec[b][jj][lane];
-                    p.emit_cols(half_node(lane, n, j), k, xv, cc);
-                } else {
-                    sm->u.b.out[lane * RP + jj] = xv;
+        bool stored = false;
+        if constexpr (!P::COLS) {
+            if (vout) {
+                // each lane stores its own half: 4 steps in registers, then the group's 4
+                // nodes (lowest first) with one 16-byte store, or node by node when the
+                // group holds steps beyond the half
+#pragma unroll
+                for (int g = CH / 4 - 1; g >= 0; --g) {
+                    float xs[4];
+#pragma unroll
+                    for (int e = 3; e >= 0; --e) {
+                        const int jj = 4 * g + e;
+                        xs[e] = 0.f;
+                        if (ch * CH + jj < cnt_eff) {
+                            const float2 r = sm->u.b.rec[b][jj][lane];
+                            xv = clip_to(xv, r.x, r.y);
+                            xs[e] = xv;
+                        }
+                    }
+                    const int j0 = ch * CH + 4 * g;
+                    const int lo = left ? j0 : n - 4 - j0;
+#pragma unroll
+                    for (int o = 0; o < P::NOUT; ++o) {
+                        float *dst = p.out_ptr(o) + p.out_off(o, k, start);
+                        if (j0 + 3 < cnt_eff) {
+                            *reinterpret_cast<float4 *>(dst + lo) =
+                                left ? make_float4(xs[0], xs[1], xs[2], xs[3])
+                                     : make_float4(xs[3], xs[2], xs[1], xs[0]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (j0 + e < cnt_eff) dst[left ? lo + e : lo + 3 - e] = xs[e];
+                        }
+                    }
                 }
+                stored = true;
             }
         }
-        if constexpr (!P::COLS) {
-            __syncwarp();
-#pragma unroll
-            for (int o = 0; o < P::NOUT; ++o) {
-                float *dst = p.out_ptr(o);
+        if (!stored) {
 #pragma unroll 4
-                for (int u = 0; u < CH; ++u) {
-                    const int t = u * WARP + lane;
-                    const int lt = t / CH, jj = t % CH;
-                    const int j = ch * CH + jj;
-                    if (j < sm->cnt[lt])
-                        dst[p.out_off(o, wc0 + (lt & (HW - 1)), sm->start[lt]) +
-                            half_node(lt, sm->n[lt], j)] = sm->u.b.out[lt * RP + jj];
+            for (int jj = CH - 1; jj >= 0; --jj) {
+                const int j = ch * CH + jj;
+                if (j < cnt_eff) {
+                    const float2 r = sm->u.b.rec[b][jj][lane];
+                    xv = clip_to(xv, r.x, r.y);
+                    if constexpr (P::COLS) {
+                        float cc = 0.f;
+                        if constexpr (P::CREC) cc = sm->u.b.crec[b][jj][lane];
+                        p.emit_cols(half_node(lane, n, j), k, xv, cc);
+                    } else {
+                        sm->u.b.out[lane * RP + jj] = xv;
+                    }
+                }
+            }
+            if constexpr (!P::COLS) {
+                __syncwarp();
+#pragma unroll
+                for (int o = 0; o < P::NOUT; ++o) {
+                    float *dst = p.out_ptr(o);
+#pragma unroll 4
+                    for (int u = 0; u < CH; ++u) {
+                        const int t = u * WARP + lane;
+                        const int lt = t / CH, jj = t % CH;
+                        const int j = ch * CH + jj;
+                        if (j < sm->cnt[lt])
+                            dst[p.out_off(o, wc0 + (lt & (HW - 1)), sm->start[lt]) +
+                                half_node(lt, sm->n[lt], j)] = sm->u.b.out[lt * RP + jj];
+                    }
                 }
             }
         }

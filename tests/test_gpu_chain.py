@@ -217,6 +217,33 @@ def test_thread_kernel_ragged_long_and_overflow(thread_path):
     assert np.abs(x - xr).max() <= TOL
 
 
+def test_thread_kernel_aligned_rows_stay_in_bounds(thread_path):
+    """Uniform chains whose arrays are 16-byte aligned with a length a multiple of 4 are
+    staged and stored 16 bytes at a time per half. The lengths here end a half inside a
+    4-node group or an 8-node chunk. The output sits in a larger buffer whose guard
+    entries must stay NaN. A pointer one float off the 16-byte grid takes the
+    node-by-node path."""
+    rng = np.random.default_rng(8)
+    for n in (64, 68, 72, 100, 132, 260):
+        B = 40
+        y = synth.chain_batch(B, n, seed0=n)
+        w = rng.uniform(0.0, 0.4, size=y.shape).astype(np.float32)
+        for weights in (None, w):
+            xr = oracle.chain_solve_batch(y.ravel(), np.arange(B + 1) * n,
+                                          w=None if weights is None else weights.ravel(),
+                                          lam=0.15).reshape(y.shape)
+            buf = torch.full((B * n + 8,), float("nan"), device=DEV)
+            out = buf[4:4 + B * n].view(B, n)
+            _lib.chain_prox(_gpu(y), None if weights is None else _gpu(weights), lam=0.15, out=out)
+            g = buf.cpu().numpy()
+            assert np.isnan(g[:4]).all() and np.isnan(g[4 + B * n:]).all(), n
+            assert np.abs(g[4:4 + B * n].reshape(B, n) - xr).max() <= TOL, n
+            yo = torch.empty(B * n + 1, device=DEV)[1:].view(B, n)
+            yo.copy_(_gpu(y))
+            xo = _lib.chain_prox(yo, None if weights is None else _gpu(weights), lam=0.15)
+            assert np.abs(xo.cpu().numpy() - xr).max() <= TOL, n
+
+
 def test_thread_kernel_closed_forms(thread_path):
     y = synth.chain_batch(64, 300, seed0=9)
     np.testing.assert_allclose(_rows(y, lam=0.0), y, atol=1e-6)
