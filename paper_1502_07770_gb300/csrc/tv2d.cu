@@ -326,6 +326,7 @@ struct ColPhaseP {
 template <bool HAS_WH>
 struct CoopInitRowsP {
     static constexpr bool CREC = false;
+    static constexpr bool UNIFORM_W = !HAS_WH;  // one weight (a scaled lambda) per chain
     struct Raw {
         float f, y, w;
     };
@@ -382,6 +383,7 @@ struct CoopInitRowsP {
 template <bool HAS_WH>
 struct CoopRowPhaseP {
     static constexpr bool CREC = false;
+    static constexpr bool UNIFORM_W = !HAS_WH;  // one weight (a scaled lambda) per chain
     struct Raw {
         float f, x, y, w;
     };
@@ -461,6 +463,7 @@ struct CoopRowPhaseP {
 template <bool HAS_WV>
 struct CoopColPhaseP {
     static constexpr bool CREC = true;
+    static constexpr bool UNIFORM_W = !HAS_WV;  // one weight (a scaled lambda) per chain
     struct Raw {
         float x, xp, y, wv;
     };

@@ -28,6 +28,7 @@ namespace {
 template <bool HAS_W, int MODE>
 struct LagRowsP {
     static constexpr bool CREC = false;
+    static constexpr bool UNIFORM_W = !HAS_W;  // one weight (a scaled lambda) per chain
     struct Raw {
         float f, x, y, w;
     };
@@ -98,6 +99,7 @@ struct LagRowsP {
 template <bool HAS_W, int MODE>
 struct LagColsP {
     static constexpr bool CREC = false;
+    static constexpr bool UNIFORM_W = !HAS_W;  // one weight (a scaled lambda) per chain
     struct Raw {
         float f, x, y, w;
     };

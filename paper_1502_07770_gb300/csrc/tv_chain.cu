@@ -304,6 +304,7 @@ struct ChainColsP {
 template <bool HAS_W>
 struct CoopRowsP {
     static constexpr bool CREC = false;
+    static constexpr bool UNIFORM_W = !HAS_W;  // one weight (a scaled lambda) per chain
     struct Raw {
         float y, w;
     };
@@ -377,6 +378,7 @@ struct CoopRowsP {
 template <bool HAS_W>
 struct CoopColsP {
     static constexpr bool CREC = false;
+    static constexpr bool UNIFORM_W = !HAS_W;  // one weight (a scaled lambda) per chain
     struct Raw {
         float y, w;
     };

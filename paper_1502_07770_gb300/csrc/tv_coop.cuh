@@ -121,7 +121,8 @@ __device__ __forceinline__ float seg_frac(float num, float den)
 // m^_i = m_{i-1,i} + a_i z - b_i; the message is clipped to [w^-_i, w^+_i]; the end pieces
 // of m^_i have slope a_i. `wl_prev` is w^-_{i-1} (the message's value left of its first
 // breakpoint). TV-l2 is a_i = 1, b_i = c_i, w^-_i = -w_i, w^+_i = w_i.
-template <int G>
+// ALWAYS: every lane of the group updates (compile-time `active`).
+template <int G, bool ALWAYS = false>
 __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, int &size,
                                               float &lam0, float &wl_prev, float ai, float bi,
                                               float wl, float wh, int sl, int seg_shift,
@@ -152,26 +153,26 @@ __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, in
     const int kl = ble ? 31 - __clz(ble) : -1;
     const int keep_last = kl > ell - 1 ? kl : ell - 1;  // last kept breakpoint (-1: none)
     const int K = keep_last - ell + 1;
-    ovf = ovf || (active && K + 2 > G);
+    ovf = ovf || ((ALWAYS || active) && K + 2 > G);
     // lambda^- on the piece right of the last breakpoint removed on the left,
     // lambda^+ on the piece right of the last one kept; with none, on the left end
     // piece (slope a_i)
     // source lanes are taken modulo the segment width by the shuffles themselves
     const float gl = __shfl_sync(FULL, candL, ell - 1, G);
-    const float Sl = __shfl_sync(FULL, S, ell - 1, G);
     const float gr = __shfl_sync(FULL, candR, keep_last, G);
     lm = (ell == 0) ? lam0 + (wl - v0) / ai : gl;
     hp = (keep_last < 0) ? lam0 + (wh - v0) / ai : gr;
     // new message m_{i,i+1}: lambda^- (value w^-_i, the slope of m^_i there), the kept
-    // breakpoints with their values and slopes, lambda^+ (value w^+_i, flat beyond)
+    // breakpoints with their values and slopes, lambda^+ (value w^+_i, flat beyond);
+    // lane 0's source is breakpoint ell-1, so its nS is the slope right of lambda^-
     const int src = sl - 1 + ell;
     const float nl = __shfl_sync(FULL, lam, src, G);
     const float nv = __shfl_sync(FULL, v, src, G);
     const float nS = __shfl_sync(FULL, S, src, G);
-    if (active) {
+    if (ALWAYS || active) {
         lam = (sl == 0) ? lm : ((sl == K + 1) ? hp : nl);
         V = (sl == 0) ? wl : ((sl == K + 1) ? wh : nv);
-        T = (sl == 0) ? ((ell == 0) ? ai : Sl) : ((sl == K + 1) ? 0.f : nS);
+        T = (sl == 0 && ell == 0) ? ai : ((sl == K + 1) ? 0.f : nS);
         size = K + 2;
         lam0 = lm;
         wl_prev = wl;
@@ -179,16 +180,16 @@ __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, in
 }
 
 // TV-l2 form: a_i = 1, b_i = c_i, [w^-_i, w^+_i] = [-w_i, w_i]; `w_prev` is w_{i-1}.
-template <int G>
+template <int G, bool ALWAYS = false>
 __device__ __forceinline__ void coop_update(float &lam, float &V, float &T, int &size,
                                             float &lam0, float &w_prev, float ci, float wi,
                                             int sl, int seg_shift, bool active, bool &ovf,
                                             float &lm, float &hp)
 {
     float wl_prev = -w_prev;
-    coop_update_g<G>(lam, V, T, size, lam0, wl_prev, 1.f, ci, -wi, wi, sl, seg_shift, active, ovf,
-                     lm, hp);
-    if (active) w_prev = wi;
+    coop_update_g<G, ALWAYS>(lam, V, T, size, lam0, wl_prev, 1.f, ci, -wi, wi, sl, seg_shift,
+                             active, ovf, lm, hp);
+    if (ALWAYS || active) w_prev = wi;
 }
 
 // Start of a message at the first node of a walk: m_{0,1} = clip(z - c_0, -w_0, w_0).
@@ -603,6 +604,51 @@ __device__ __forceinline__ float clip_suffix16(float lo, float hi, float x_next,
     return clip_to(x_next, lo, hi);
 }
 
+// Policies whose edge weights are one value for the whole chain (a scaled lambda) say
+// so with `static constexpr bool UNIFORM_W = true`: the halves then take each step's
+// weight from their own lane instead of a shuffle.
+template <class P, class = void>
+struct coop_uniform_w : std::false_type {};
+template <class P>
+struct coop_uniform_w<P, std::enable_if_t<P::UNIFORM_W>> : std::true_type {};
+
+// 16 update steps of both halves (positions base..base+15). FB: every step of the block
+// is an update in both halves (no root step, no tail). UW: one weight for the chain.
+template <bool FB, bool UW, class P>
+__device__ __forceinline__ void coop_halves_block(
+    const P &p, typename P::Acc &acc, long long k, long long start, int n, int base, int cntw,
+    int half, int sl, int seg_shift, float cv, float wv, float wsel,
+    const typename P::Raw &raw_next, float2 *rec_b, int rec_dir, float &lam, float &V, float &T,
+    int &size, float &lam0, float &w_prev, float &c_s, bool &ovf)
+{
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) {
+        const int qq = base + j;
+        const float ci = __shfl_sync(FULL, cv, j, SEG);
+        float wi = wv;
+        if constexpr (!UW) {
+            wi = __shfl_sync(FULL, wsel, j, SEG);
+            if (j == SEG - 1) {
+                // the right half's last step takes the weight staged with the next block
+                float c2, w2;
+                const int qn = base + SEG;
+                p.unary(k, start, n, qn < cntw ? (half == 0 ? qn : n - 1 - qn) : n, raw_next, c2,
+                        w2, acc);
+                const float w_nb = __shfl_sync(FULL, w2, 0, SEG);
+                if (half == 1) wi = w_nb;
+            }
+        }
+        const bool stepping = FB || qq < cntw - 1;
+        if constexpr (!FB) {
+            if (half == 0 && qq == cntw - 1) c_s = ci;
+        }
+        float lmv, hpv;
+        coop_update<SEG, FB>(lam, V, T, size, lam0, w_prev, ci, wi, sl, seg_shift, stepping, ovf,
+                             lmv, hpv);
+        if (stepping && sl == 0) rec_b[j * rec_dir] = make_float2(lmv, hpv);
+    }
+}
+
 template <class P>
 __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long long k,
                                         long long start, int n, int lane, PairXchg &xc,
@@ -632,6 +678,8 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
     bool ok = true, ovf = false;
     typename P::Raw raw, raw_next{};
     fetch_at(sl, raw);
+    constexpr bool UW = coop_uniform_w<P>::value;
+    const int cnt_lo = (s + 1 < n - s) ? s + 1 : n - s;  // the shorter half's positions
     const int nblocks = (cnt_all + SEG - 1) / SEG;
     for (int blk = 0; blk < nblocks; ++blk) {
         const int base = blk * SEG;
@@ -646,28 +694,23 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
         // the right half steps node i with the weight of edge (i-1, i): that of the
         // next position (the next lane; for the segment's last lane, the first
         // position of the next block, read when the last step needs it)
-        const float wr = __shfl_down_sync(FULL, wv, 1, SEG);
-        const float wsel = half == 0 ? wv : wr;
+        float wsel = wv;
+        if constexpr (!UW) {
+            const float wr = __shfl_down_sync(FULL, wv, 1, SEG);
+            wsel = half == 0 ? wv : wr;
+        }
+        // records of this block's steps: node base + j (left half), n-1-base-j (right)
+        float2 *rec_b = recp + (half == 0 ? base : n - 1 - base);
+        const int rec_dir = half == 0 ? 1 : -1;
         if (ok) {
-#pragma unroll
-            for (int j = 0; j < SEG; ++j) {
-                const int qq = base + j;
-                const float ci = __shfl_sync(FULL, cv, j, SEG);
-                float wi = __shfl_sync(FULL, wsel, j, SEG);
-                if (j == SEG - 1) {
-                    float c2, w2;
-                    p.unary(k, start, n, base + SEG < cntw ? node(base + SEG) : n, raw_next, c2,
-                            w2, acc);
-                    const float w_nb = __shfl_sync(FULL, w2, 0, SEG);
-                    if (half == 1) wi = w_nb;
-                }
-                const bool stepping = qq < cntw - 1;
-                if (half == 0 && qq == cntw - 1) c_s = ci;
-                float lmv, hpv;
-                coop_update<SEG>(lam, V, T, size, lam0, w_prev, ci, wi, sl, seg_shift, stepping,
-                                 ovf, lmv, hpv);
-                if (stepping && sl == 0) recp[node(qq)] = make_float2(lmv, hpv);
-            }
+            if (base + SEG < cnt_lo)
+                coop_halves_block<true, UW>(p, acc, k, start, n, base, cntw, half, sl, seg_shift,
+                                            cv, wv, wsel, raw_next, rec_b, rec_dir, lam, V, T, size,
+                                            lam0, w_prev, c_s, ovf);
+            else
+                coop_halves_block<false, UW>(p, acc, k, start, n, base, cntw, half, sl, seg_shift,
+                                             cv, wv, wsel, raw_next, rec_b, rec_dir, lam, V, T,
+                                             size, lam0, w_prev, c_s, ovf);
             ok = !__any_sync(FULL, ovf);
         }
         raw = raw_next;
@@ -1043,9 +1086,11 @@ __global__ void __launch_bounds__(256) coop_pair_kernel(P p_in, float2 *rec_g, f
 
 // One warp per chain; with HALVES, chains of kSplitMinLen nodes or more are rooted
 // at their middle node and solved as two 16-lane halves. Shared memory: (HALVES)
-// one PairXchg per warp, then the warps' records (and c records).
+// one PairXchg per warp, then the warps' records (and c records). Launched with at
+// most 256 threads; no launch bound, which on this target would cap the update at 64
+// registers and spill it.
 template <class P, bool HALVES>
-__global__ void __launch_bounds__(256) coop_chain_kernel(P p_in, float2 *rec_g, float *crec_g,
+__global__ void coop_chain_kernel(P p_in, float2 *rec_g, float *crec_g,
                                                          float2 *spill, WsHeader *hdr,
                                                          int smem_nodes)
 {

@@ -700,6 +700,7 @@ PqWs carve_pq(void *base, long long nchains, long long maxlen)
 template <bool HAS_W>
 struct L1ColsP {
     static constexpr bool CREC = true;
+    static constexpr bool UNIFORM_W = !HAS_W;  // one weight (a scaled lambda) per chain
     struct Raw {
         float xb, y, w;
     };
