@@ -149,8 +149,9 @@ __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, in
         bge = (bge >> seg_shift) & ((1u << G) - 1u);
         ble = (ble >> seg_shift) & ((1u << G) - 1u);
     }
-    const int ell = min(bge ? __ffs(bge) - 1 : G, size);
-    const int kl = ble ? 31 - __clz(ble) : -1;
+    // (trailing zeros of an empty vote are 32, so ell is then size; 31 - clz(0) is -1)
+    const int ell = min(__clz(__brev(bge)), size);
+    const int kl = 31 - __clz(ble);
     const int keep_last = kl > ell - 1 ? kl : ell - 1;  // last kept breakpoint (-1: none)
     const int K = keep_last - ell + 1;
     ovf = ovf || ((ALWAYS || active) && K + 2 > G);
@@ -618,8 +619,8 @@ template <bool FB, bool UW, class P>
 __device__ __forceinline__ void coop_halves_block(
     const P &p, typename P::Acc &acc, long long k, long long start, int n, int base, int cntw,
     int half, int sl, int seg_shift, float cv, float wv, float wsel,
-    const typename P::Raw &raw_next, float2 *rec_b, int rec_dir, float &lam, float &V, float &T,
-    int &size, float &lam0, float &w_prev, float &c_s, bool &ovf)
+    const typename P::Raw &raw_next, float2 *rec_b, float &lam, float &V, float &T, int &size,
+    float &lam0, float &w_prev, float &c_s, bool &ovf)
 {
 #pragma unroll
     for (int j = 0; j < SEG; ++j) {
@@ -645,7 +646,7 @@ __device__ __forceinline__ void coop_halves_block(
         float lmv, hpv;
         coop_update<SEG, FB>(lam, V, T, size, lam0, w_prev, ci, wi, sl, seg_shift, stepping, ovf,
                              lmv, hpv);
-        if (stepping && sl == 0) rec_b[j * rec_dir] = make_float2(lmv, hpv);
+        if (stepping && sl == 0) rec_b[j] = make_float2(lmv, hpv);
     }
 }
 
@@ -699,18 +700,19 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
             const float wr = __shfl_down_sync(FULL, wv, 1, SEG);
             wsel = half == 0 ? wv : wr;
         }
-        // records of this block's steps: node base + j (left half), n-1-base-j (right)
-        float2 *rec_b = recp + (half == 0 ? base : n - 1 - base);
-        const int rec_dir = half == 0 ? 1 : -1;
+        // records of this block's steps at slots base + j: the left half's are its nodes,
+        // the right half's are mirrored (node i at slot n + s - i, from s + 1 up), so that
+        // both halves store forwards from one pointer
+        float2 *rec_b = recp + (half == 0 ? base : s + 1 + base);
         if (ok) {
             if (base + SEG < cnt_lo)
                 coop_halves_block<true, UW>(p, acc, k, start, n, base, cntw, half, sl, seg_shift,
-                                            cv, wv, wsel, raw_next, rec_b, rec_dir, lam, V, T, size,
-                                            lam0, w_prev, c_s, ovf);
+                                            cv, wv, wsel, raw_next, rec_b, lam, V, T, size, lam0,
+                                            w_prev, c_s, ovf);
             else
                 coop_halves_block<false, UW>(p, acc, k, start, n, base, cntw, half, sl, seg_shift,
-                                             cv, wv, wsel, raw_next, rec_b, rec_dir, lam, V, T,
-                                             size, lam0, w_prev, c_s, ovf);
+                                             cv, wv, wsel, raw_next, rec_b, lam, V, T, size, lam0,
+                                             w_prev, c_s, ovf);
             ok = !__any_sync(FULL, ovf);
         }
         raw = raw_next;
@@ -756,7 +758,7 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
         }
         float lo = -INFINITY, hi = INFINITY;
         if (inb) {
-            const float2 r = recp[i];
+            const float2 r = recp[half == 0 ? i : n + s - i];  // right half: mirrored slots
             lo = r.x;
             hi = r.y;
         }
