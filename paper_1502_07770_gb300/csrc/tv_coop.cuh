@@ -124,7 +124,7 @@ __device__ __forceinline__ float seg_frac(float num, float den)
 // ALWAYS: every lane of the group updates (compile-time `active`).
 template <int G, bool ALWAYS = false>
 __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, int &size,
-                                              float &lam0, float &wl_prev, float ai, float bi,
+                                              float &wl_prev, float ai, float bi,
                                               float wl, float wh, int sl, int seg_shift,
                                               bool active, bool &ovf, float &lm, float &hp)
 {
@@ -132,7 +132,6 @@ __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, in
     const bool last = sl == size - 1;
     const float S = T + ai;                    // slope of m^_i right of this breakpoint
     const float v = fmaf(ai, lam, V) - bi;     // m^_i at this breakpoint
-    const float v0 = fmaf(ai, lam0, wl_prev) - bi;  // m^_i at the first breakpoint
     const float lam_n = __shfl_down_sync(FULL, lam, 1, G);
     const float rS = __fdividef(1.f, S);  // one reciprocal for both crossings
     float candL = fmaxf(fmaf(wl - v, rS, lam), lam);
@@ -145,24 +144,26 @@ __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, in
     // lowest / highest set bit of this segment's bits
     unsigned bge = __ballot_sync(FULL, valid && v >= wl);
     unsigned ble = __ballot_sync(FULL, valid && v <= wh);
-    if constexpr (G != WARP) {
-        bge = (bge >> seg_shift) & ((1u << G) - 1u);
-        ble = (ble >> seg_shift) & ((1u << G) - 1u);
-    }
-    // (trailing zeros of an empty vote are 32, so ell is then size; 31 - clz(0) is -1)
+    // (trailing zeros of an empty vote are 32, so ell is then size. Bits of the segment
+    // above only count when none of this segment's is set, and then ell = size <= G too;
+    // the highest set bit is taken among this segment's bits, -1 - seg_shift if none,
+    // which keep_last = max(kl, ell - 1) treats as -1.)
+    if constexpr (G != WARP) bge >>= seg_shift;
     const int ell = min(__clz(__brev(bge)), size);
-    const int kl = 31 - __clz(ble);
+    int kl;
+    if constexpr (G != WARP) kl = 31 - seg_shift - __clz(ble & (((1u << G) - 1u) << seg_shift));
+    else kl = 31 - __clz(ble);
     const int keep_last = kl > ell - 1 ? kl : ell - 1;  // last kept breakpoint (-1: none)
     const int K = keep_last - ell + 1;
     ovf = ovf || ((ALWAYS || active) && K + 2 > G);
     // lambda^- on the piece right of the last breakpoint removed on the left,
     // lambda^+ on the piece right of the last one kept; with none, on the left end
-    // piece (slope a_i)
+    // piece, where m^_i = w^-_{i-1} + a_i z - b_i
     // source lanes are taken modulo the segment width by the shuffles themselves
     const float gl = __shfl_sync(FULL, candL, ell - 1, G);
     const float gr = __shfl_sync(FULL, candR, keep_last, G);
-    lm = (ell == 0) ? lam0 + (wl - v0) / ai : gl;
-    hp = (keep_last < 0) ? lam0 + (wh - v0) / ai : gr;
+    lm = (ell == 0) ? (bi + wl - wl_prev) / ai : gl;
+    hp = (keep_last < 0) ? (bi + wh - wl_prev) / ai : gr;
     // new message m_{i,i+1}: lambda^- (value w^-_i, the slope of m^_i there), the kept
     // breakpoints with their values and slopes, lambda^+ (value w^+_i, flat beyond);
     // lane 0's source is breakpoint ell-1, so its nS is the slope right of lambda^-
@@ -175,7 +176,6 @@ __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, in
         V = (sl == 0) ? wl : ((sl == K + 1) ? wh : nv);
         T = (sl == 0 && ell == 0) ? ai : ((sl == K + 1) ? 0.f : nS);
         size = K + 2;
-        lam0 = lm;
         wl_prev = wl;
     }
 }
@@ -183,18 +183,18 @@ __device__ __forceinline__ void coop_update_g(float &lam, float &V, float &T, in
 // TV-l2 form: a_i = 1, b_i = c_i, [w^-_i, w^+_i] = [-w_i, w_i]; `w_prev` is w_{i-1}.
 template <int G, bool ALWAYS = false>
 __device__ __forceinline__ void coop_update(float &lam, float &V, float &T, int &size,
-                                            float &lam0, float &w_prev, float ci, float wi,
+                                            float &w_prev, float ci, float wi,
                                             int sl, int seg_shift, bool active, bool &ovf,
                                             float &lm, float &hp)
 {
     float wl_prev = -w_prev;
-    coop_update_g<G, ALWAYS>(lam, V, T, size, lam0, wl_prev, 1.f, ci, -wi, wi, sl, seg_shift,
+    coop_update_g<G, ALWAYS>(lam, V, T, size, wl_prev, 1.f, ci, -wi, wi, sl, seg_shift,
                              active, ovf, lm, hp);
     if (ALWAYS || active) w_prev = wi;
 }
 
 // Start of a message at the first node of a walk: m_{0,1} = clip(z - c_0, -w_0, w_0).
-__device__ __forceinline__ void coop_first(float &lam, float &V, float &T, int &size, float &lam0,
+__device__ __forceinline__ void coop_first(float &lam, float &V, float &T, int &size,
                                            float &w_prev, float ci, float wi, int sl, float &lm,
                                            float &hp)
 {
@@ -204,7 +204,6 @@ __device__ __forceinline__ void coop_first(float &lam, float &V, float &T, int &
     V = (sl == 0) ? -wi : wi;
     T = (sl == 0) ? 1.f : 0.f;
     size = 2;
-    lam0 = lm;
     w_prev = wi;
 }
 
@@ -235,7 +234,7 @@ __device__ void coop_solve_chain(const P &p, typename P::Acc &acc, long long k, 
     float *crecp = nullptr;
     if constexpr (P::CREC) crecp = in_smem ? sm_crec : crec_g + k * (long long)max_len;
 
-    float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, w_prev = 0.f;
+    float lam = 0.f, V = 0.f, T = 0.f, w_prev = 0.f;
     int size = 0;
     bool ok = true, ovf = false;
     float xlast = 0.f;
@@ -263,9 +262,9 @@ __device__ void coop_solve_chain(const P &p, typename P::Acc &acc, long long k, 
                         xlast = ci;
                         break;
                     }
-                    coop_first(lam, V, T, size, lam0, w_prev, ci, wi, lane, lmv, hpv);
+                    coop_first(lam, V, T, size, w_prev, ci, wi, lane, lmv, hpv);
                 } else {
-                    coop_update<WARP>(lam, V, T, size, lam0, w_prev, ci, wi, lane, 0, true, ovf,
+                    coop_update<WARP>(lam, V, T, size, w_prev, ci, wi, lane, 0, true, ovf,
                                       lmv, hpv);
                 }
                 if (i == n - 1) xlast = 0.5f * (lmv + hpv);
@@ -441,7 +440,7 @@ __device__ void coop_solve_chain_split(const P &p, typename P::Acc &acc, long lo
     if constexpr (P::CREC) crecp = in_smem ? sm_crec : crec_g + k * (long long)max_len;
     const int s = n / 2;
 
-    float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, w_prev = 0.f;
+    float lam = 0.f, V = 0.f, T = 0.f, w_prev = 0.f;
     int size = 0;
     bool ok = true, ovf = false;
     float c_s = 0.f;
@@ -490,9 +489,9 @@ __device__ void coop_solve_chain_split(const P &p, typename P::Acc &acc, long lo
                 const float wi = __shfl_sync(FULL, role == 0 ? wv : wr, j);
                 float lmv, hpv;
                 if (qq == 0)
-                    coop_first(lam, V, T, size, lam0, w_prev, ci, wi, lane, lmv, hpv);
+                    coop_first(lam, V, T, size, w_prev, ci, wi, lane, lmv, hpv);
                 else
-                    coop_update<WARP>(lam, V, T, size, lam0, w_prev, ci, wi, lane, 0, true, ovf,
+                    coop_update<WARP>(lam, V, T, size, w_prev, ci, wi, lane, 0, true, ovf,
                                       lmv, hpv);
                 if (lane == 0) recp[node(qq)] = make_float2(lmv, hpv);
             }
@@ -620,7 +619,7 @@ __device__ __forceinline__ void coop_halves_block(
     const P &p, typename P::Acc &acc, long long k, long long start, int n, int base, int cntw,
     int half, int sl, int seg_shift, float cv, float wv, float wsel,
     const typename P::Raw &raw_next, float2 *rec_b, float &lam, float &V, float &T, int &size,
-    float &lam0, float &w_prev, float &c_s, bool &ovf)
+    float &w_prev, float &c_s, bool &ovf)
 {
 #pragma unroll
     for (int j = 0; j < SEG; ++j) {
@@ -644,7 +643,7 @@ __device__ __forceinline__ void coop_halves_block(
             if (half == 0 && qq == cntw - 1) c_s = ci;
         }
         float lmv, hpv;
-        coop_update<SEG, FB>(lam, V, T, size, lam0, w_prev, ci, wi, sl, seg_shift, stepping, ovf,
+        coop_update<SEG, FB>(lam, V, T, size, w_prev, ci, wi, sl, seg_shift, stepping, ovf,
                              lmv, hpv);
         if (stepping && sl == 0) rec_b[j] = make_float2(lmv, hpv);
     }
@@ -672,9 +671,9 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
         p.fetch(k, start, n, q < cntw ? node(q) : n, r);
     };
 
-    // Message state of this half; the empty message (size 0, lam0 = w_prev = 0) makes
+    // Message state of this half; the empty message (size 0, w_prev = 0) makes
     // the first update produce m_{0,1} = clip(z - c_0, -w_0, w_0) exactly.
-    float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, w_prev = 0.f, c_s = 0.f;
+    float lam = 0.f, V = 0.f, T = 0.f, w_prev = 0.f, c_s = 0.f;
     int size = 0;
     bool ok = true, ovf = false;
     typename P::Raw raw, raw_next{};
@@ -707,12 +706,12 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
         if (ok) {
             if (base + SEG < cnt_lo)
                 coop_halves_block<true, UW>(p, acc, k, start, n, base, cntw, half, sl, seg_shift,
-                                            cv, wv, wsel, raw_next, rec_b, lam, V, T, size, lam0,
-                                            w_prev, c_s, ovf);
+                                            cv, wv, wsel, raw_next, rec_b, lam, V, T, size, w_prev,
+                                            c_s, ovf);
             else
                 coop_halves_block<false, UW>(p, acc, k, start, n, base, cntw, half, sl, seg_shift,
-                                             cv, wv, wsel, raw_next, rec_b, lam, V, T, size, lam0,
-                                             w_prev, c_s, ovf);
+                                             cv, wv, wsel, raw_next, rec_b, lam, V, T, size, w_prev,
+                                             c_s, ovf);
             ok = !__any_sync(FULL, ovf);
         }
         raw = raw_next;
@@ -878,7 +877,7 @@ __device__ void coop_solve_chain_general(const P &p, typename P::Acc &acc, long 
     const int max_len = p.max_len();
     float2 *recp = n <= smem_nodes ? sm_rec : rec_g + k * (long long)max_len;
     // empty message: the first update produces m_{0,1} = clip(a_0 z - b_0, w^-_0, w^+_0)
-    float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, wl_prev = 0.f, xlast = 0.f;
+    float lam = 0.f, V = 0.f, T = 0.f, wl_prev = 0.f, xlast = 0.f;
     int size = 0;
     bool ok = true, ovf = false;
     typename P::Raw raw, raw_next{};
@@ -897,7 +896,7 @@ __device__ void coop_solve_chain_general(const P &p, typename P::Acc &acc, long 
                 const float wl = (i < n - 1) ? __shfl_sync(FULL, wlv, j) : 0.f;
                 const float wh = (i < n - 1) ? __shfl_sync(FULL, whv, j) : 0.f;
                 float lmv, hpv;
-                coop_update_g<WARP>(lam, V, T, size, lam0, wl_prev, ai, bi, wl, wh, lane, 0, true,
+                coop_update_g<WARP>(lam, V, T, size, wl_prev, ai, bi, wl, wh, lane, 0, true,
                                     ovf, lmv, hpv);
                 if (i == n - 1) xlast = (n == 1) ? bi / ai : 0.5f * (lmv + hpv);
                 else if (lane == 0) recp[i] = make_float2(lmv, hpv);
@@ -949,7 +948,7 @@ __device__ void coop_solve_chain_halves_general(const P &p, typename P::Acc &acc
     auto fetch_at = [&](int q, typename P::Raw &r) {
         p.fetch(k, start, n, q < cntw ? node(q) : n, r);
     };
-    float lam = 0.f, V = 0.f, T = 0.f, lam0 = 0.f, wl_prev = 0.f, a_s = 1.f, b_s = 0.f;
+    float lam = 0.f, V = 0.f, T = 0.f, wl_prev = 0.f, a_s = 1.f, b_s = 0.f;
     int size = 0;
     bool ok = true, ovf = false;
     typename P::Raw raw, raw_next{};
@@ -992,7 +991,7 @@ __device__ void coop_solve_chain_halves_general(const P &p, typename P::Acc &acc
                     b_s = bi;
                 }
                 float lmv, hpv;
-                coop_update_g<SEG>(lam, V, T, size, lam0, wl_prev, ai, bi, wl, wh, sl, seg_shift,
+                coop_update_g<SEG>(lam, V, T, size, wl_prev, ai, bi, wl, wh, sl, seg_shift,
                                    stepping, ovf, lmv, hpv);
                 if (stepping && sl == 0) recp[node(qq)] = make_float2(lmv, hpv);
             }
