@@ -390,6 +390,13 @@ tv_status tv_set_coop_split(int mode);
  * chip). Longer messages are finished from the workspace either way. Both give the same
  * solution up to FP32 rounding. Read when a batched solve is planned. */
 tv_status tv_set_thread_split(int on);
+/* Whether tv2d_denoise launches the kernels of its iterations with a programmatic
+ * dependency on the previous kernel of the stream: 1 (the default) lets each kernel
+ * become resident while its predecessor finishes, and the kernel waits in hardware for
+ * that predecessor's completion and memory before it reads anything; 0 launches them
+ * in plain stream order. The results are identical either way; only the gaps between
+ * kernels differ. Read at each call. */
+tv_status tv_set_programmatic_launch(int on);
 
 /* ------------------------------------------ learned dual warm start (net) ---- */
 /*

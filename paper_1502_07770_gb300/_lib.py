@@ -82,6 +82,7 @@ SIGNATURES = {
     "tv_chain_solve_general": (ctypes.c_int, [_p, _p, _p, _p, _p, _i64, _i64, _p, _p, _sz, _p]),
     "tv_set_coop_split": (ctypes.c_int, [ctypes.c_int]),
     "tv_set_thread_split": (ctypes.c_int, [ctypes.c_int]),
+    "tv_set_programmatic_launch": (ctypes.c_int, [ctypes.c_int]),
     "tv_net_set_tensor_path": (ctypes.c_int, [ctypes.c_int]),
     "tv_net_conv3x3": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       _p, _p, ctypes.c_int, ctypes.c_int, _p, _p, _p]),
@@ -525,6 +526,12 @@ def set_thread_split(on: bool):
     """Middle-rooted chains (two threads per chain) in the one-thread-per-chain path of
     ``chain_prox`` (True, the default) or one thread per chain from one end (False)."""
     _check(load().tv_set_thread_split(1 if on else 0))
+
+
+def set_programmatic_launch(on: bool):
+    """Launch the 2D solver's kernels with a programmatic dependency on their
+    predecessor (the default) or in plain stream order; results are identical."""
+    _check(load().tv_set_programmatic_launch(int(bool(on))))
 
 
 def set_net_tensor_path(mode: int):

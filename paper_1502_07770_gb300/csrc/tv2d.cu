@@ -550,6 +550,7 @@ __global__ void __launch_bounds__(kGapThreads)
 {
     __shared__ double red[kGapThreads];
     __shared__ bool last;
+    pdl_enter();
     if (st->done) return;
     const int kp1 = st->k;  // x^{k+1} is the newest iterate
     if (kp1 < 1) return;
@@ -723,10 +724,11 @@ tv_status launch_gap(const float *img, const float *wh, const float *wv, float l
                      long long W, float *x0, const Tv2dWs &ws, cudaStream_t s)
 {
     const int blocks = gap_blocks(H, W);
-    tv2d_gap_kernel<<<blocks, kGapThreads, 0, s>>>(img, wh, wv, lam, H, W, x0, ws.buf1, ws.st,
-                                                   ws.prm, ws.partials, ws.gaps,
-                                                   &ws.st->ticket_col);
-    tv_status st = check_cuda(cudaGetLastError(), "gap kernel launch");
+    tv_status st = check_cuda(launch_k(tv2d_gap_kernel, dim3(blocks), dim3(kGapThreads), 0, s, img,
+                                       wh, wv, lam, H, W, (const float *)x0,
+                                       (const float *)ws.buf1, ws.st, (const Tv2dParams *)ws.prm,
+                                       ws.partials, ws.gaps, &ws.st->ticket_col),
+                              "gap kernel launch");
     if (st == TV_OK) note_launch();
     return st;
 }
@@ -737,6 +739,7 @@ tv_status launch_gap(const float *img, const float *wh, const float *wv, float l
 __global__ void tv2d_final_copy(const Tv2dState *st, const float4 *buf1, float4 *x, long long n4,
                                 const float *buf1s, float *xs, long long n)
 {
+    pdl_enter();
     const int k = st->k;
     const bool finished = st->done || k >= st->max_iters;
     if (!finished || !(k & 1)) return;
@@ -833,6 +836,8 @@ tv_status tv2d_denoise(const float *d_img, int64_t H, int64_t W, const float *d_
     st = d_y0 ? check_cuda(cudaMemcpyAsync(ws.y, d_y0, npx, cudaMemcpyDeviceToDevice, s), "copy y0")
               : check_cuda(cudaMemsetAsync(ws.y, 0, npx, s), "zero y");
     if (st != TV_OK) return st;
+    // from here on each kernel may become resident while its predecessor finishes
+    PdlScope pdl(true);
     st = d_wh ? launch_init<true>(d_img, d_wh, lambda, H, W, d_x, ws, s)
               : launch_init<false>(d_img, d_wh, lambda, H, W, d_x, ws, s);
     if (st != TV_OK) return st;
@@ -847,11 +852,12 @@ tv_status tv2d_denoise(const float *d_img, int64_t H, int64_t W, const float *d_
     const long long N = H * W;
     const int copy_blocks = (int)std::min<long long>((N / 4 + 255) / 256 + 1, 4LL * sm_count_current());
     auto launch_copy = [&]() -> tv_status {
-        tv2d_final_copy<<<copy_blocks, 256, 0, s>>>(ws.st, reinterpret_cast<const float4 *>(ws.buf1),
-                                                    reinterpret_cast<float4 *>(d_x),
-                                                    aligned16(d_x) && aligned16(ws.buf1) ? N / 4 : 0,
-                                                    ws.buf1, d_x, N);
-        tv_status r = check_cuda(cudaGetLastError(), "result copy");
+        tv_status r = check_cuda(
+            launch_k(tv2d_final_copy, dim3(copy_blocks), dim3(256), 0, s, (const Tv2dState *)ws.st,
+                     reinterpret_cast<const float4 *>(ws.buf1), reinterpret_cast<float4 *>(d_x),
+                     aligned16(d_x) && aligned16(ws.buf1) ? N / 4 : 0, (const float *)ws.buf1,
+                     d_x, N),
+            "result copy");
         if (r == TV_OK) note_launch();
         return r;
     };

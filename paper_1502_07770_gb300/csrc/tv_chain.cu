@@ -62,6 +62,13 @@ static std::atomic<int> g_coop_split{1};
 int coop_split() { return g_coop_split.load(); }
 static std::atomic<int> g_thread_split{1};
 int thread_split() { return g_thread_split.load(); }
+
+// programmatic dependent launch: enabled by the ABI switch, active inside a PdlScope
+static std::atomic<int> g_pdl_enabled{1};
+static thread_local bool g_pdl_scope = false;
+bool pdl_on() { return g_pdl_scope; }
+PdlScope::PdlScope(bool on) : prev(g_pdl_scope) { g_pdl_scope = on && g_pdl_enabled.load() != 0; }
+PdlScope::~PdlScope() { g_pdl_scope = prev; }
 bool prof_on() { return g_prof_on; }
 
 void prof_mark(int kind, cudaStream_t s, bool start)
@@ -590,6 +597,17 @@ tv_status tv_set_coop_max_chains(int64_t max_chains)
         return TV_ERR_INVALID;
     }
     tvh::g_coop_max.store(max_chains == 0 ? kCoopMaxChainsDefault : max_chains);
+    return TV_OK;
+}
+
+tv_status tv_set_programmatic_launch(int on)
+{
+    clear_error();
+    if (on < 0 || on > 1) {
+        set_error("tv_set_programmatic_launch: 0 or 1");
+        return TV_ERR_INVALID;
+    }
+    tvh::g_pdl_enabled.store(on);
     return TV_OK;
 }
 

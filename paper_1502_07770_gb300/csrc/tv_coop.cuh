@@ -1047,6 +1047,7 @@ __global__ void __launch_bounds__(256) coop_pair_kernel(P p_in, float2 *rec_g, f
                                                         float2 *spill, WsHeader *hdr,
                                                         int smem_nodes)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     P p = p_in;
     if (!p.resolve()) return;
@@ -1095,6 +1096,7 @@ __global__ void coop_chain_kernel(P p_in, float2 *rec_g, float *crec_g,
                                                          float2 *spill, WsHeader *hdr,
                                                          int smem_nodes)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     P p = p_in;
     if (!p.resolve()) return;

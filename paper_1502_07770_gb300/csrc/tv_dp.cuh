@@ -257,6 +257,18 @@ __host__ __device__ __forceinline__ bool dp_step(DPState &d, const S &s, int cap
     return true;
 }
 
+// Programmatic dependent launch (griddepcontrol, sm_90 and later). A grid launched with
+// a programmatic dependency on the previous kernel of its stream is launched as that
+// kernel's blocks exit, before the kernel as a whole has completed; wait blocks until
+// the previous grid has completed and its memory is visible. For a grid launched
+// without the dependency it is a no-op. Called first thing by every kernel that may be
+// launched this way. (The kernels do not release their dependents early: blocks of the
+// next phase placed while this one still fills the SMs would be spread unevenly.)
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
 __device__ __forceinline__ float clip_to(float v, float lo, float hi)
 {
     return fminf(fmaxf(v, lo), hi);

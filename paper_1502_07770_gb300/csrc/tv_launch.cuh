@@ -43,6 +43,38 @@ tv_status launch_chains(const P &p, long long nchains, float2 *rec, float *crec,
     return st;
 }
 
+// Programmatic dependent launch for the kernels of one solve (tv_set_programmatic_launch,
+// on by default): inside a PdlScope(true) on the calling thread, launch_k launches with
+// the stream-serialization attribute, so that a kernel becomes resident while its
+// predecessor finishes (the kernels begin with tvk::pdl_enter()).
+bool pdl_on();
+struct PdlScope {
+    bool prev;
+    explicit PdlScope(bool on);
+    ~PdlScope();
+};
+
+template <class... KArgs, class... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args... args)
+{
+    if (!pdl_on()) {
+        kern<<<grid, block, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Warp-cooperative launch: one warp per chain, `wpb` warps per block. The records
 // of a chain stay in shared memory when max_len <= kCoopSmemNodes.
 constexpr int kCoopSmemNodes = 4096;
@@ -84,8 +116,9 @@ tv_status launch_coop(const P &p, long long nchains, int max_len, float2 *rec, f
     if (st != TV_OK) return st;
     const bool prof = prof_on();
     if (prof) prof_mark(kind, s, true);
-    kern<<<(unsigned)blocks, wpb * tvk::WARP, smem, s>>>(p, rec, crec, spill, hdr, smem_nodes);
-    st = check_cuda(cudaGetLastError(), "cooperative chain kernel launch");
+    st = check_cuda(launch_k(kern, dim3((unsigned)blocks), dim3(wpb * tvk::WARP), smem, s, p, rec,
+                             crec, spill, hdr, smem_nodes),
+                    "cooperative chain kernel launch");
     if (st == TV_OK) note_launch();
     if (prof) prof_mark(kind, s, false);
     return st;
