@@ -166,10 +166,79 @@ struct LagColsP {
     __device__ void finish_empty() const {}
 };
 
+// Both proximal steps of one iteration in one launch: they read the same ybar (or y)
+// and write separate iterates, so they are independent. Chains 0..H-1 are the rows,
+// H..H+W-1 the columns (one warp per chain, so each warp takes one branch); the two
+// latency-bound batches then share the GPU instead of running one after the other.
+// Overflow reserves: the rows' first, then the columns'.
+template <class PR, class PC>
+struct LagBothP {
+    static constexpr bool CREC = false;
+    static_assert(!PR::CREC && !PC::CREC, "no c records");
+    static constexpr bool UNIFORM_W = PR::UNIFORM_W && PC::UNIFORM_W;
+    using Raw = typename PR::Raw;
+    struct Acc {};
+    PR r;
+    PC c;
+
+    __device__ bool resolve() { return r.resolve() && c.resolve(); }
+    __device__ long long num_chains() const { return r.H + r.W; }
+    __device__ int max_len() const { return (int)(r.H > r.W ? r.H : r.W); }
+    __device__ bool chain(long long k, long long &start, int &n) const
+    {
+        return k < r.H ? r.chain(k, start, n) : c.chain(k - r.H, start, n);
+    }
+    __device__ void fetch(long long k, long long start, int n, int i, Raw &raw) const
+    {
+        if (k < r.H) {
+            r.fetch(k, start, n, i, raw);
+        } else {
+            typename PC::Raw q;
+            c.fetch(k - r.H, start, n, i, q);
+            raw = Raw{q.f, q.x, q.y, q.w};
+        }
+    }
+    __device__ void unary(long long k, long long start, int n, int i, const Raw &raw, float &cc,
+                          float &w, Acc &) const
+    {
+        if (k < r.H) {
+            typename PR::Acc a;
+            r.unary(k, start, n, i, raw, cc, w, a);
+        } else {
+            typename PC::Acc a;
+            c.unary(k - r.H, start, n, i, typename PC::Raw{raw.f, raw.x, raw.y, raw.w}, cc, w, a);
+        }
+    }
+    __device__ void emit(long long k, long long start, int i, float xv, float cc) const
+    {
+        if (k < r.H) r.emit(k, start, i, xv, cc);
+        else c.emit(k - r.H, start, i, xv, cc);
+    }
+    __device__ void unary_direct(int i, int n, long long k, long long start, float &cc,
+                                 float &w) const
+    {
+        if (k < r.H) r.unary_direct(i, n, k, start, cc, w);
+        else c.unary_direct(i, n, k - r.H, start, cc, w);
+    }
+    __device__ void emit_direct(int i, long long k, long long start, float xv, float cc) const
+    {
+        if (k < r.H) r.emit_direct(i, k, start, xv, cc);
+        else c.emit_direct(i, k - r.H, start, xv, cc);
+    }
+    __device__ long long spill_off(long long k, long long start) const
+    {
+        return k < r.H ? r.spill_off(k, start) : r.H * (2 * r.W + 2) + c.spill_off(k - r.H, start);
+    }
+    __device__ void acc_init(Acc &) const {}
+    __device__ void finish(Acc &, int) const {}
+    __device__ void finish_empty() const {}
+};
+
 // y_new = y + sigma (x_h - x_v); ybar = 2 y_new - y; y = y_new; xbar = (x_h + x_v) / 2.
 __global__ void lag_dual_update(long long N, const float *xh, const float *xv, float *y,
                                 float *ybar, float *xbar, float sigma)
 {
+    pdl_enter();
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
          q += (long long)gridDim.x * blockDim.x) {
         const float yo = y[q];
@@ -191,6 +260,7 @@ __global__ void __launch_bounds__(kLagThreads)
 {
     __shared__ double red[kLagThreads];
     __shared__ bool last;
+    pdl_enter();
     const long long N = H * W;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long dr = stride / W, dc = stride - dr * W;
@@ -284,36 +354,46 @@ LagWs carve_lag(void *base, long long H, long long W, int gap_blocks)
     o.ybar = cv.take<float>((size_t)N);
     o.xr = cv.take<float>((size_t)N);
     o.xc = cv.take<float>((size_t)N);
-    o.rec = cv.take<float2>((size_t)N);
-    o.spill = cv.take<float2>((size_t)std::max(H * (2 * W + 2), W * (2 * H + 2)));
+    // records of the row and column chains of one launch (at chain * max(H, W)) and
+    // their overflow reserves side by side
+    o.rec = cv.take<float2>((size_t)((H + W) * std::max(H, W)));
+    o.spill = cv.take<float2>((size_t)(H * (2 * W + 2) + W * (2 * H + 2)));
     o.bytes = align_up(cv.used, 256);
     return o;
 }
 
-template <int MODE>
-tv_status lag_rows(const float *f, const float *x, const float *y, const float *wh, float lam,
-                   long long H, long long W, float *xout, float inv_tau, float inv_a,
-                   const LagWs &ws, cudaStream_t s)
+template <int MODE, bool HW_, bool VW_>
+tv_status lag_both_t(const float *f, const float *xh, const float *xv, const float *y,
+                     const float *wh, const float *wv, float lam, long long H, long long W,
+                     float *xout_h, float *xout_v, float inv_tau, float inv_a, const LagWs &ws,
+                     cudaStream_t s)
 {
-    if (wh) {
-        LagRowsP<true, MODE> p{f, x, y, wh, xout, lam, H, W, inv_tau, inv_a};
-        return launch_coop(p, H, (int)W, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_ROW);
-    }
-    LagRowsP<false, MODE> p{f, x, y, wh, xout, lam, H, W, inv_tau, inv_a};
-    return launch_coop(p, H, (int)W, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_ROW);
+    LagBothP<LagRowsP<HW_, MODE>, LagColsP<VW_, MODE>> p{
+        {f, xh, y, wh, xout_h, lam, H, W, inv_tau, inv_a},
+        {f, xv, y, wv, xout_v, lam, H, W, inv_tau, inv_a}};
+    return launch_coop(p, H + W, (int)std::max(H, W), ws.rec, nullptr, ws.spill, ws.hdr, s,
+                       PK_ROW);
 }
 
+// The row and the column chains of one iteration (MODE 0: the proximal steps of x_h and
+// x_v; MODE 1: the two halves of D(y)) in one launch.
 template <int MODE>
-tv_status lag_cols(const float *f, const float *x, const float *y, const float *wv, float lam,
-                   long long H, long long W, float *xout, float inv_tau, float inv_a,
-                   const LagWs &ws, cudaStream_t s)
+tv_status lag_both(const float *f, const float *xh, const float *xv, const float *y,
+                   const float *wh, const float *wv, float lam, long long H, long long W,
+                   float *xout_h, float *xout_v, float inv_tau, float inv_a, const LagWs &ws,
+                   cudaStream_t s)
 {
-    if (wv) {
-        LagColsP<true, MODE> p{f, x, y, wv, xout, lam, H, W, inv_tau, inv_a};
-        return launch_coop(p, W, (int)H, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_COL);
-    }
-    LagColsP<false, MODE> p{f, x, y, wv, xout, lam, H, W, inv_tau, inv_a};
-    return launch_coop(p, W, (int)H, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_COL);
+    if (wh && wv)
+        return lag_both_t<MODE, true, true>(f, xh, xv, y, wh, wv, lam, H, W, xout_h, xout_v,
+                                            inv_tau, inv_a, ws, s);
+    if (wh)
+        return lag_both_t<MODE, true, false>(f, xh, xv, y, wh, wv, lam, H, W, xout_h, xout_v,
+                                             inv_tau, inv_a, ws, s);
+    if (wv)
+        return lag_both_t<MODE, false, true>(f, xh, xv, y, wh, wv, lam, H, W, xout_h, xout_v,
+                                             inv_tau, inv_a, ws, s);
+    return lag_both_t<MODE, false, false>(f, xh, xv, y, wh, wv, lam, H, W, xout_h, xout_v,
+                                          inv_tau, inv_a, ws, s);
 }
 
 int ew_blocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 8LL * sm_count_current()); }
@@ -383,29 +463,32 @@ tv_status tv2d_denoise_lagrangian(const float *d_img, int64_t H, int64_t W, cons
     double gap = NAN;
     int k = 1;
     bool done = false;
+    PdlScope pdl(true);  // each kernel may become resident while its predecessor finishes
     for (; k <= max_iters; ++k) {
         const double tau = (double)tau0 / k;
         const float inv_tau = (float)(1.0 / tau), inv_a = (float)(1.0 / (0.5 + 1.0 / tau));
         const float sigma = (float)(1.0 / (2.0 * tau));
-        if ((st = lag_rows<0>(d_img, ws.xh, ws.ybar, d_wh, lambda, H, W, ws.xh, inv_tau, inv_a, ws,
-                              s)) != TV_OK)
+        // the proximal steps of x_h (rows) and x_v (columns), in place, in one launch
+        if ((st = lag_both<0>(d_img, ws.xh, ws.xv, ws.ybar, d_wh, d_wv, lambda, H, W, ws.xh, ws.xv,
+                              inv_tau, inv_a, ws, s)) != TV_OK)
             return st;
-        if ((st = lag_cols<0>(d_img, ws.xv, ws.ybar, d_wv, lambda, H, W, ws.xv, inv_tau, inv_a, ws,
-                              s)) != TV_OK)
+        if ((st = check_cuda(launch_k(lag_dual_update, dim3(ew_blocks(N)), dim3(256), 0, s, N,
+                                      (const float *)ws.xh, (const float *)ws.xv, ws.y, ws.ybar,
+                                      d_x, sigma),
+                             "dual update")) != TV_OK)
             return st;
-        lag_dual_update<<<ew_blocks(N), 256, 0, s>>>(N, ws.xh, ws.xv, ws.y, ws.ybar, d_x, sigma);
-        if ((st = check_cuda(cudaGetLastError(), "dual update")) != TV_OK) return st;
         note_launch();
         if (k % check_every == 0 || k == max_iters) {
-            if ((st = lag_rows<1>(d_img, nullptr, ws.y, d_wh, lambda, H, W, ws.xr, 0.f, 0.f, ws,
-                                  s)) != TV_OK)
+            // the two halves of D(y) (rows into xr, columns into xc) in one launch
+            if ((st = lag_both<1>(d_img, nullptr, nullptr, ws.y, d_wh, d_wv, lambda, H, W, ws.xr,
+                                  ws.xc, 0.f, 0.f, ws, s)) != TV_OK)
                 return st;
-            if ((st = lag_cols<1>(d_img, nullptr, ws.y, d_wv, lambda, H, W, ws.xc, 0.f, 0.f, ws,
-                                  s)) != TV_OK)
+            if ((st = check_cuda(launch_k(lag_gap_kernel, dim3(gb), dim3(kLagThreads), 0, s, d_img,
+                                          d_wh, d_wv, lambda, H, W, (const float *)d_x,
+                                          (const float *)ws.xr, (const float *)ws.xc,
+                                          (const float *)ws.y, ws.partials, ws.ticket, ws.gap),
+                                 "gap")) != TV_OK)
                 return st;
-            lag_gap_kernel<<<gb, kLagThreads, 0, s>>>(d_img, d_wh, d_wv, lambda, H, W, d_x, ws.xr,
-                                                       ws.xc, ws.y, ws.partials, ws.ticket, ws.gap);
-            if ((st = check_cuda(cudaGetLastError(), "gap")) != TV_OK) return st;
             note_launch();
             st = check_cuda(cudaMemcpyAsync(&gap, ws.gap, sizeof(double), cudaMemcpyDeviceToHost, s),
                             "read gap");

@@ -93,10 +93,10 @@ tv_status launch_coop(const P &p, long long nchains, int max_len, float2 *rec, f
     if constexpr (tvk::has_unary_g<P>::value) {
         if (mode == 2) mode = 1;  // general chains: one warp per chain
     }
-    // few chains (at most 8 per SM): one chain per block, so that the block scheduler
+    // few chains (at most 16 per SM): one chain per block, so that the block scheduler
     // spreads the warps evenly over the SMs (4-warp blocks leave some SMs with 8 warps
     // and others with 4 when there are about 6.7 per SM)
-    if (nchains <= 8LL * sm_count_current()) wpb = mode == 2 ? 2 : 1;
+    if (nchains <= 16LL * sm_count_current()) wpb = mode == 2 ? 2 : 1;
     const bool pair = mode == 2 && wpb % 2 == 0;
     const int cpb = pair ? wpb / 2 : wpb;  // chains per block
     const long long blocks = (nchains + cpb - 1) / cpb;

@@ -52,3 +52,33 @@ def test_no_regulariser_is_the_identity():
                                                   check_every=1)
     np.testing.assert_allclose(x.cpu().numpy(), f, atol=1e-6)
     assert abs(gap) <= 1e-6
+
+
+@pytest.mark.parametrize("which", ["h", "v"])
+def test_weights_in_one_direction_only(which):
+    """Row and column chains run in one launch; here one of them has edge weights and the
+    other the uniform lambda."""
+    _, f = synth.shapes_image(72, 110, seed=12, n_shapes=25)
+    lam = 0.1
+    wh, wv = synth.edge_aware_weights(f, lam)
+    if which == "h":
+        wv = None
+    else:
+        wh = None
+    x, it, gap, ok = _lib.tv2d_denoise_lagrangian(_gpu(f), lam=lam, w_h=_gpu(wh), w_v=_gpu(wv),
+                                                  tau0=10.0, max_iters=4, tol=0.0, check_every=4)
+    xo, ito, tro, oko = oracle.tv2d_lagrangian(f, lam=lam, w_h=wh, w_v=wv, tau0=10.0, max_iters=4,
+                                               tol=0.0, check_every=4)
+    assert np.abs(x.cpu().numpy() - xo).max() <= TOL
+    assert abs(gap - tro[-1]) <= 1e-6 + 1e-3 * abs(tro[-1])
+
+
+def test_long_rows_keep_their_records_in_the_workspace():
+    """Rows of 5000 nodes: more than a warp keeps in shared memory, so the records of
+    every chain of the launch (40 rows and 5000 columns) live in the workspace."""
+    _, f = synth.shapes_image(40, 5000, seed=13, n_shapes=60)
+    x, it, gap, ok = _lib.tv2d_denoise_lagrangian(_gpu(f), lam=0.1, tau0=10.0, max_iters=2,
+                                                  tol=0.0, check_every=2)
+    xo, ito, tro, oko = oracle.tv2d_lagrangian(f, lam=0.1, tau0=10.0, max_iters=2, tol=0.0,
+                                               check_every=2)
+    assert np.abs(x.cpu().numpy() - xo).max() <= TOL
