@@ -110,8 +110,9 @@ __device__ __forceinline__ void pq_update(PqState &s, float a, float b, float al
     }
     const unsigned bge = __ballot_sync(FULL, valid && s.R >= wlo);
     const unsigned ble = __ballot_sync(FULL, valid && s.L <= whi);
-    const int ell = min(bge ? __ffs(bge) - 1 : WARP, s.size);
-    const int kl = ble ? 31 - __clz(ble) : -1;
+    // trailing zeros of an empty vote are 32 (ell = size); 31 - clz(0) = -1 (no kept point)
+    const int ell = min(__clz(__brev(bge)), s.size);
+    const int kl = 31 - __clz(ble);
     const float L0 = __shfl_sync(FULL, s.L, 0), lam0 = __shfl_sync(FULL, s.lam, 0);
     const float Le = __shfl_sync(FULL, s.L, ell & 31), Re = __shfl_sync(FULL, s.R, ell & 31),
                 lame = __shfl_sync(FULL, s.lam, ell & 31), Se = __shfl_sync(FULL, s.S, ell & 31);
@@ -225,8 +226,9 @@ __device__ __forceinline__ void pq_update_seg(PqState &s, float a, float b, floa
     }
     const unsigned bge = seg(__ballot_sync(FULL, valid && s.R >= wlo));
     const unsigned ble = seg(__ballot_sync(FULL, valid && s.L <= whi));
-    const int ell = min(bge ? __ffs(bge) - 1 : G, s.size);
-    const int kl = ble ? 31 - __clz(ble) : -1;
+    // trailing zeros of an empty vote are 32 (ell = size); 31 - clz(0) = -1 (no kept point)
+    const int ell = min(__clz(__brev(bge)), s.size);
+    const int kl = 31 - __clz(ble);
     const float L0 = __shfl_sync(FULL, s.L, 0, G), lam0 = __shfl_sync(FULL, s.lam, 0, G);
     const float Le = __shfl_sync(FULL, s.L, ell, G), Re = __shfl_sync(FULL, s.R, ell, G),
                 lame = __shfl_sync(FULL, s.lam, ell, G), Se = __shfl_sync(FULL, s.S, ell, G);
