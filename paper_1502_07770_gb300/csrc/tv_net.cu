@@ -517,18 +517,30 @@ __global__ void dual_head_grad(const float *o, int B, int H, int W, const float 
 }
 
 // Network input: channel 0 the image, channel 1 its lambda, 2..15 zero (BF16 NHWC).
-__global__ void pack_input(const float *f, int B, int H, int W, const float *lam,
-                           __nv_bfloat16 *x)
+// Image b of the batch is blockIdx.y. Each pixel's 16 channels (32 bytes: the image,
+// lambda, 14 zeros) go out as two 16-byte stores when x is 16-byte aligned.
+__global__ void pack_input(const float *f, int H, int W, const float *lam, __nv_bfloat16 *x,
+                           bool vec)
 {
-    const long long N = (long long)B * H * W;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(q / ((long long)H * W));
-        __nv_bfloat16 *dst = x + q * 16;
-        dst[0] = __float2bfloat16(f[q]);
-        dst[1] = __float2bfloat16(lam[b]);
+    const long long HW = (long long)H * W;
+    const int b = blockIdx.y;
+    const float *fb = f + (long long)b * HW;
+    __nv_bfloat16 *xb = x + (long long)b * HW * 16;
+    const __nv_bfloat16 lb = __float2bfloat16(lam[b]);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < HW; q += stride) {
+        const __nv_bfloat162 p01 = __halves2bfloat162(__float2bfloat16(fb[q]), lb);
+        if (vec) {
+            uint4 *d = reinterpret_cast<uint4 *>(xb + q * 16);
+            d[0] = make_uint4(*reinterpret_cast<const unsigned *>(&p01), 0u, 0u, 0u);
+            d[1] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            __nv_bfloat16 *dst = xb + q * 16;
+            dst[0] = p01.x;
+            dst[1] = p01.y;
 #pragma unroll
-        for (int c = 2; c < 16; ++c) dst[c] = __float2bfloat16(0.f);
+            for (int c = 2; c < 16; ++c) dst[c] = __float2bfloat16(0.f);
+        }
     }
 }
 
@@ -979,8 +991,11 @@ tv_status tv_net_pack_input(const float *d_f, int B, int H, int W, const float *
         return TV_ERR_INVALID;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    pack_input<<<ew_blocks((long long)B * H * W), 256, 0, s>>>(d_f, B, H, W, d_lam,
-                                                               static_cast<__nv_bfloat16 *>(d_x));
+    const long long HW = (long long)H * W;
+    const unsigned gx = (unsigned)std::max(1, ew_blocks(HW) / B);
+    pack_input<<<dim3(gx, (unsigned)B), 256, 0, s>>>(d_f, H, W, d_lam,
+                                                     static_cast<__nv_bfloat16 *>(d_x),
+                                                     ((uintptr_t)d_x & 15) == 0);
     tv_status st = check_cuda(cudaGetLastError(), "pack input");
     if (st == TV_OK) note_launch();
     return st;
