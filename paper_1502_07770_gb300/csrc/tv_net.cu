@@ -444,22 +444,42 @@ __global__ void __launch_bounds__(256)
     dual_head(const float *o, int B, int H, int W, const float *lam, const float *target, float *y,
               float *loss_part, float inv_count)
 {
-    const long long N = (long long)B * H * W;
+    const long long HW = (long long)H * W;
+    const long long N = (long long)B * HW;
+    const long long stride = (long long)gridDim.x * blockDim.x;
     float lsum = 0.f;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(q / ((long long)H * W));
-        const long long rem = q % ((long long)H * W);
-        const int r = (int)(rem / W);
-        const float L = lam[b];
-        auto pv = [&](long long qq, int rr) -> float {
-            return (rr >= 0 && rr < H - 1) ? L * tanhf(o[qq * 16]) : 0.f;
-        };
-        const float yv = pv(q - W, r - 1) - pv(q, r);
-        if (y) y[q] = yv;
-        if (target) {
-            const float e = yv - target[q];
-            lsum += e * e;
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < N) {
+        // image b, row r and column c of q, advanced along the grid-stride walk by the
+        // same decomposition of the stride (one carry per level)
+        int b = (int)(q / HW);
+        const long long rem = q - (long long)b * HW;
+        int r = (int)(rem / W), c = (int)(rem - (long long)r * W);
+        const int sb = (int)(stride / HW);
+        const long long srem = stride - (long long)sb * HW;
+        const int sr = (int)(srem / W), sc = (int)(srem - (long long)sr * W);
+        for (; q < N; q += stride) {
+            const float L = lam[b];
+            auto pv = [&](long long qq, int rr) -> float {
+                return (rr >= 0 && rr < H - 1) ? L * tanhf(o[qq * 16]) : 0.f;
+            };
+            const float yv = pv(q - W, r - 1) - pv(q, r);
+            if (y) y[q] = yv;
+            if (target) {
+                const float e = yv - target[q];
+                lsum += e * e;
+            }
+            c += sc;
+            r += sr;
+            b += sb;
+            if (c >= W) {
+                c -= W;
+                ++r;
+            }
+            if (r >= H) {
+                r -= H;
+                ++b;
+            }
         }
     }
     if (target && loss_part) {
