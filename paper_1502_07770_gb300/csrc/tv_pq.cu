@@ -167,8 +167,8 @@ __device__ __forceinline__ void pq_update(PqState &s, float a, float b, float al
 // The same update on a segment of G lanes (G = 16: two chain halves per warp, each
 // segment one half; sl the lane in the segment, seg_shift its first lane). Every lane
 // executes every shuffle; a segment whose half has no node at this step passes
-// active = false and keeps its state.
-template <int G>
+// active = false and keeps its state. ALWAYS: every segment updates (compile time).
+template <int G, bool ALWAYS = false>
 __device__ __forceinline__ void pq_update_seg(PqState &s, float a, float b, float al, float f,
                                               float wlo, float whi, int sl, int seg_shift,
                                               bool active, bool &ovf, float &lm, float &hp)
@@ -183,7 +183,7 @@ __device__ __forceinline__ void pq_update_seg(PqState &s, float a, float b, floa
                 pS = __shfl_sync(FULL, s.S, ins - 1, G);
     const float ul = __shfl_up_sync(FULL, s.lam, 1, G), uL = __shfl_up_sync(FULL, s.L, 1, G),
                 uR = __shfl_up_sync(FULL, s.R, 1, G), uS = __shfl_up_sync(FULL, s.S, 1, G);
-    if (active && !exists) {
+    if ((ALWAYS || active) && !exists) {
         if (s.size + 1 > G) ovf = true;
         float mval, Sn;
         if (ins == 0) {
@@ -208,7 +208,7 @@ __device__ __forceinline__ void pq_update_seg(PqState &s, float a, float b, floa
         valid = sl < s.size;
     }
     // ---- transformation (a): + a z - b - alpha left of f, + alpha right of it ----
-    if (active) {
+    if (ALWAYS || active) {
         const float lin = fmaf(a, s.lam, -b);
         const float dl = (sl <= ins) ? -al : al;
         const float dr = (sl < ins) ? -al : al;
@@ -254,13 +254,13 @@ __device__ __forceinline__ void pq_update_seg(PqState &s, float a, float b, floa
     else hp = cRk;
     const int k0 = ell + (jumpL ? 1 : 0), k1 = kl - (jumpR ? 1 : 0);
     const int K = k1 >= k0 ? k1 - k0 + 1 : 0;
-    if (active && K + 2 > G) ovf = true;
+    if ((ALWAYS || active) && K + 2 > G) ovf = true;
     const float lmR = jumpL ? fminf(Re, whi) : wlo;
     const float hpL = jumpR ? (both ? fminf(Re, whi) : fmaxf(Lk, wlo)) : whi;
     const int src = sl - 1 + k0;
     const float nl = __shfl_sync(FULL, s.lam, src, G), nL = __shfl_sync(FULL, s.L, src, G),
                 nR = __shfl_sync(FULL, s.R, src, G), nS = __shfl_sync(FULL, s.S, src, G);
-    if (active) {
+    if (ALWAYS || active) {
         if (sl == 0) {
             s.lam = lm;
             s.L = wlo;
@@ -579,7 +579,64 @@ __device__ float pq_root(const PqMsg &ML, const PqMsg &MR, float a, float b, flo
 // the whole warp finds the root (pq_root), then each segment clips its
 // half outwards. A half that outgrows 16 breakpoints sends the chain to the one-warp
 // solve from node 0 (32 breakpoints, then lane 0 from the workspace).
-__global__ void __launch_bounds__(kPqWarps * WARP) pq_halves_kernel(PqArgs p, WsHeader *hdr)
+// Up to 16 update steps of both halves (positions base..base+15; c16 of them exist).
+// ALWAYS: every step is an update in both halves. U: curvature 1, one alpha and one
+// weight for the whole chain, so only b and f are shuffled.
+template <bool ALWAYS, bool U>
+__device__ __forceinline__ void pq_half_steps(PqState &s, bool &ovf, float2 *rec, int base,
+                                              int c16, int cnt, int n, int seg, int sl,
+                                              int seg_shift, float av, float bv, float alv,
+                                              float fv, float wv, float alpha, float lam)
+{
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+        if (!ALWAYS && jj >= c16) break;  // c16 is the same in every lane
+        const float bi = __shfl_sync(FULL, bv, jj, 16), fi = __shfl_sync(FULL, fv, jj, 16);
+        float ai = 1.f, ali = alpha, wi = lam;
+        if constexpr (!U) {
+            ai = __shfl_sync(FULL, av, jj, 16);
+            ali = __shfl_sync(FULL, alv, jj, 16);
+            wi = __shfl_sync(FULL, wv, jj, 16);
+        }
+        const int q = base + jj;
+        const bool active = ALWAYS || q < cnt;
+        float lm, hp;
+        pq_update_seg<16, ALWAYS>(s, ai, bi, ali, fi, -wi, wi, sl, seg_shift, active, ovf, lm,
+                                  hp);
+        if (active && sl == 0) rec[seg == 0 ? q : n - 1 - q] = make_float2(lm, hp);
+    }
+}
+
+// This lane's node of block blk of its half (the inputs of a block are loaded one block
+// ahead): node j of the left half is j, of the right half n-1-j, whose edge towards the
+// root is the one before it.
+template <bool U>
+__device__ __forceinline__ void pq_half_load(const PqArgs &p, const float *a, const float *b,
+                                             const float *al, const float *f, const float *w,
+                                             int blk, int sl, int seg, int n, int cnt, float &av,
+                                             float &bv, float &alv, float &fv, float &wv)
+{
+    const int j_l = blk * 16 + sl;
+    const bool in = j_l < cnt;
+    const int i_l = in ? (seg == 0 ? j_l : n - 1 - j_l) : 0;
+    bv = in ? b[i_l] : 0.f;
+    fv = in ? f[i_l] : 0.f;
+    if constexpr (U) {
+        av = 1.f;
+        alv = p.alpha;
+        wv = p.lam;
+    } else {
+        const int e_l = seg == 0 ? i_l : i_l - 1;
+        av = (in && a) ? a[i_l] : 1.f;
+        alv = in ? (al ? al[i_l] : p.alpha) : 0.f;
+        wv = in ? (w ? w[e_l] * p.wscale : p.lam) : 0.f;
+    }
+}
+
+// Launched with kPqWarps warps per block and no launch bound (a bound capped the
+// kernel at 72 registers and spilled the update). U: see pq_half_steps.
+template <bool U>
+__global__ void pq_halves_kernel(PqArgs p, WsHeader *hdr)
 {
     __shared__ PqMsg msg[kPqWarps][2];
     const int lane = threadIdx.x & (WARP - 1);
@@ -602,26 +659,26 @@ __global__ void __launch_bounds__(kPqWarps * WARP) pq_halves_kernel(PqArgs p, Ws
     PqState s{0.f, 0.f, 0.f, 0.f, 0, 0.f, 0.f, 0.f};
     bool ovf = false;
     const int nblocks = (cmax + 15) / 16;
+    const int cnt_lo = min(mid, n - 1 - mid);  // the shorter half's update steps
+    float av = 1.f, bv = 0.f, alv = 0.f, fv = 0.f, wv = 0.f;
+    if (nblocks > 0) pq_half_load<U>(p, a, b, al, f, w, 0, sl, seg, n, cnt, av, bv, alv, fv, wv);
     for (int blk = 0; blk < nblocks && !ovf; ++blk) {
-        const int j_l = blk * 16 + sl;
-        const bool in = j_l < cnt;
-        const int i_l = in ? node_of(j_l) : 0;
-        const int e_l = seg == 0 ? i_l : i_l - 1;  // the edge towards the root
-        const float av = (in && a) ? a[i_l] : 1.f, bv = in ? b[i_l] : 0.f,
-                    alv = in ? (al ? al[i_l] : p.alpha) : 0.f, fv = in ? f[i_l] : 0.f,
-                    wv = in ? (w ? w[e_l] * p.wscale : p.lam) : 0.f;
-        const int c16 = min(16, cmax - blk * 16);
-        for (int jj = 0; jj < c16; ++jj) {
-            const float ai = __shfl_sync(FULL, av, jj, 16), bi = __shfl_sync(FULL, bv, jj, 16),
-                        ali = __shfl_sync(FULL, alv, jj, 16), fi = __shfl_sync(FULL, fv, jj, 16),
-                        wi = __shfl_sync(FULL, wv, jj, 16);
-            const int i = __shfl_sync(FULL, i_l, jj, 16);
-            const bool active = blk * 16 + jj < cnt;
-            float lm, hp;
-            pq_update_seg<16>(s, ai, bi, ali, fi, -wi, wi, sl, seg_shift, active, ovf, lm, hp);
-            if (active && sl == 0) rec[i] = make_float2(lm, hp);
-        }
+        float av2 = 1.f, bv2 = 0.f, alv2 = 0.f, fv2 = 0.f, wv2 = 0.f;
+        if (blk + 1 < nblocks)
+            pq_half_load<U>(p, a, b, al, f, w, blk + 1, sl, seg, n, cnt, av2, bv2, alv2, fv2, wv2);
+        const int base = blk * 16;
+        if (base + 16 <= cnt_lo)
+            pq_half_steps<true, U>(s, ovf, rec, base, 16, cnt, n, seg, sl, seg_shift, av, bv, alv,
+                                   fv, wv, p.alpha, p.lam);
+        else
+            pq_half_steps<false, U>(s, ovf, rec, base, min(16, cmax - base), cnt, n, seg, sl,
+                                    seg_shift, av, bv, alv, fv, wv, p.alpha, p.lam);
         ovf = __any_sync(FULL, ovf);
+        av = av2;
+        bv = bv2;
+        alv = alv2;
+        fv = fv2;
+        wv = wv2;
     }
     if (ovf) {
         // a half outgrew 16 breakpoints: the whole chain by the warp from node 0
@@ -665,7 +722,10 @@ void launch_pq(const PqArgs &p, long long nchains, long long max_len, WsHeader *
 {
     if (max_len >= 64) {
         const long long blocks = (nchains + kPqWarps - 1) / kPqWarps;
-        pq_halves_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
+        if (!p.a && !p.al && !p.w)
+            pq_halves_kernel<true><<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
+        else
+            pq_halves_kernel<false><<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
     } else {
         const long long blocks = (nchains + kPqWarps - 1) / kPqWarps;
         pq_chain_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
