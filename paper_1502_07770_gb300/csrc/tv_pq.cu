@@ -463,6 +463,7 @@ __device__ __forceinline__ bool pq_chain_of(const PqArgs &p, long long k, int la
 
 __global__ void __launch_bounds__(kPqWarps * WARP) pq_chain_kernel(PqArgs p, WsHeader *hdr)
 {
+    pdl_enter();
     const int lane = threadIdx.x & (WARP - 1);
     const long long k = (long long)blockIdx.x * kPqWarps + threadIdx.x / WARP;
     if (k >= p.nchains) return;
@@ -638,6 +639,7 @@ __device__ __forceinline__ void pq_half_load(const PqArgs &p, const float *a, co
 template <bool U>
 __global__ void pq_halves_kernel(PqArgs p, WsHeader *hdr)
 {
+    pdl_enter();
     __shared__ PqMsg msg[kPqWarps][2];
     const int lane = threadIdx.x & (WARP - 1);
     const int warp = threadIdx.x / WARP;
@@ -723,12 +725,14 @@ void launch_pq(const PqArgs &p, long long nchains, long long max_len, WsHeader *
     if (max_len >= 64) {
         const long long blocks = (nchains + kPqWarps - 1) / kPqWarps;
         if (!p.a && !p.al && !p.w)
-            pq_halves_kernel<true><<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
+            launch_k(pq_halves_kernel<true>, dim3((unsigned)blocks), dim3(kPqWarps * WARP), 0, s, p,
+                     hdr);
         else
-            pq_halves_kernel<false><<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
+            launch_k(pq_halves_kernel<false>, dim3((unsigned)blocks), dim3(kPqWarps * WARP), 0, s,
+                     p, hdr);
     } else {
         const long long blocks = (nchains + kPqWarps - 1) / kPqWarps;
-        pq_chain_kernel<<<(unsigned)blocks, kPqWarps * WARP, 0, s>>>(p, hdr);
+        launch_k(pq_chain_kernel, dim3((unsigned)blocks), dim3(kPqWarps * WARP), 0, s, p, hdr);
     }
 }
 
@@ -818,6 +822,7 @@ struct L1ColsP {
 
 __global__ void l1_xi(long long N, const float *x, const float *y, float tau, float *xi)
 {
+    pdl_enter();
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
          q += (long long)gridDim.x * blockDim.x)
         xi[q] = x[q] - tau * y[q];
@@ -826,6 +831,7 @@ __global__ void l1_xi(long long N, const float *x, const float *y, float tau, fl
 // xbar = 2 x_new - x; x = x_new
 __global__ void l1_relax(long long N, const float *xn, float *x, float *xbar)
 {
+    pdl_enter();
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N;
          q += (long long)gridDim.x * blockDim.x) {
         const float v = xn[q];
@@ -845,6 +851,7 @@ __global__ void __launch_bounds__(kL1Threads)
 {
     __shared__ double red[kL1Threads];
     __shared__ bool last;
+    pdl_enter();
     const long long N = H * W;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long dr = stride / W, dc = stride - dr * W;
@@ -1058,6 +1065,7 @@ tv_status tv2d_denoise_l1(const float *d_img, int64_t H, int64_t W, const float 
     double e_prev = NAN, e = NAN;
     int k = 0;
     bool done = false;
+    PdlScope pdl(true);  // each kernel may become resident while its predecessor finishes
     while (k < max_iters) {
         // dual step: column chains
         if (d_wv) {
@@ -1068,8 +1076,10 @@ tv_status tv2d_denoise_l1(const float *d_img, int64_t H, int64_t W, const float 
             st = launch_coop(p, W, (int)H, ws.rec, ws.crec, ws.spill, ws.hdr, s, PK_COL);
         }
         if (st != TV_OK) return st;
-        l1_xi<<<ew_blocks_pq(N), 256, 0, s>>>(N, d_x, ws.y, tau, ws.xi);
-        if ((st = check_cuda(cudaGetLastError(), "xi")) != TV_OK) return st;
+        if ((st = check_cuda(launch_k(l1_xi, dim3(ew_blocks_pq(N)), dim3(256), 0, s, N,
+                                      (const float *)d_x, (const float *)ws.y, tau, ws.xi),
+                             "xi")) != TV_OK)
+            return st;
         note_launch();
         // primal step: row chains with piecewise-quadratic unaries (scaled by tau)
         PqArgs p{nullptr, ws.xi, nullptr, d_img, d_wh, tau, tau * lambda, tau,
@@ -1080,14 +1090,18 @@ tv_status tv2d_denoise_l1(const float *d_img, int64_t H, int64_t W, const float 
         if ((st = check_cuda(cudaGetLastError(), "row chains")) != TV_OK) return st;
         note_launch();
         if (prof) prof_mark(PK_ROW, s, false);
-        l1_relax<<<ew_blocks_pq(N), 256, 0, s>>>(N, ws.xn, d_x, ws.xbar);
-        if ((st = check_cuda(cudaGetLastError(), "relax")) != TV_OK) return st;
+        if ((st = check_cuda(launch_k(l1_relax, dim3(ew_blocks_pq(N)), dim3(256), 0, s, N,
+                                      (const float *)ws.xn, d_x, ws.xbar),
+                             "relax")) != TV_OK)
+            return st;
         note_launch();
         ++k;
         if (k % check_every == 0 || k == max_iters) {
-            l1_energy_kernel<<<eb, kL1Threads, 0, s>>>(d_img, d_wh, d_wv, lambda, H, W, d_x,
-                                                       ws.partials, ws.ticket, ws.energy);
-            if ((st = check_cuda(cudaGetLastError(), "energy")) != TV_OK) return st;
+            if ((st = check_cuda(launch_k(l1_energy_kernel, dim3(eb), dim3(kL1Threads), 0, s, d_img,
+                                          d_wh, d_wv, lambda, H, W, (const float *)d_x, ws.partials,
+                                          ws.ticket, ws.energy),
+                                 "energy")) != TV_OK)
+                return st;
             note_launch();
             st = check_cuda(cudaMemcpyAsync(&e, ws.energy, sizeof(double), cudaMemcpyDeviceToHost, s),
                             "read energy");
