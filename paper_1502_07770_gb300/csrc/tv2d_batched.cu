@@ -468,8 +468,10 @@ struct BColsTP {
 };
 
 constexpr int kBGapThreads = 256;
+constexpr int kGapBatch = 4;  // pixels of a thread whose loads are in flight together
 
-__global__ void __launch_bounds__(kBGapThreads)
+// No launch bound: one capped the walk at 64 registers (kBGapThreads threads a block).
+__global__ void
     batched_gap_kernel(const BImg *imgs, BState *st, const GapTile *tiles, const Tv2dParams *prm,
                        double *partials, BCtl *ctl, cudaGraphConditionalHandle cond, int use_cond)
 {
@@ -488,29 +490,56 @@ __global__ void __launch_bounds__(kBGapThreads)
         const long long W = im->W, H = im->H;
         float part = 0.f;
         int cnt = 0;
-        // row and column advance incrementally along the block-stride walk
+        const float *__restrict__ f = im->f;
+        const float *__restrict__ wh = im->wh;
+        const float *__restrict__ wv = im->wv;
+        const float lam = im->lam;
+        // row and column advance incrementally along the block-stride walk; the loads of
+        // kGapBatch pixels are issued before any of them is used (memory-level
+        // parallelism), and the pixels are summed in walk order as before
         const long long stride = blockDim.x;
         const long long dr = stride / W, dc = stride - dr * W;
+        const long long end = t.first + t.count;
         long long q = t.first + threadIdx.x;
         long long r = q / W, c = q - r * W;
-#pragma unroll 4
-        for (; q < t.first + t.count; q += stride) {
-            const float xv = x1[q], fv = im->f[q];
-            const float z = xv + (xv - x0[q]) * inv_tau;
-            float v = 0.5f * (xv - fv) * (xv - fv) + 0.5f * (z - fv) * (z + fv);
-            if (c + 1 < W) v += (im->wh ? im->wh[r * (W - 1) + c] : im->lam) * fabsf(x1[q + 1] - xv);
-            if (r + 1 < H) v += (im->wv ? im->wv[q] : im->lam) * fabsf(x1[q + W] - xv);
-            part += v;
-            if (++cnt == 32) {
-                acc += (double)part;
-                part = 0.f;
-                cnt = 0;
+        for (; q < end; q += kGapBatch * stride) {
+            float xv[kGapBatch], fv[kGapBatch], xp[kGapBatch], xr[kGapBatch], xd[kGapBatch],
+                whv[kGapBatch], wvv[kGapBatch];
+            bool in[kGapBatch], hr[kGapBatch], hd[kGapBatch];
+            long long qj = q;
+#pragma unroll
+            for (int j = 0; j < kGapBatch; ++j) {
+                in[j] = qj < end;
+                hr[j] = in[j] && c + 1 < W;
+                hd[j] = in[j] && r + 1 < H;
+                xv[j] = in[j] ? x1[qj] : 0.f;
+                fv[j] = in[j] ? f[qj] : 0.f;
+                xp[j] = in[j] ? x0[qj] : 0.f;
+                xr[j] = hr[j] ? x1[qj + 1] : 0.f;
+                xd[j] = hd[j] ? x1[qj + W] : 0.f;
+                whv[j] = hr[j] ? (wh ? wh[r * (W - 1) + c] : lam) : 0.f;
+                wvv[j] = hd[j] ? (wv ? wv[qj] : lam) : 0.f;
+                qj += stride;
+                c += dc;
+                r += dr;
+                if (c >= W) {
+                    c -= W;
+                    ++r;
+                }
             }
-            c += dc;
-            r += dr;
-            if (c >= W) {
-                c -= W;
-                ++r;
+#pragma unroll
+            for (int j = 0; j < kGapBatch; ++j) {
+                if (!in[j]) continue;
+                const float z = xv[j] + (xv[j] - xp[j]) * inv_tau;
+                float v = 0.5f * (xv[j] - fv[j]) * (xv[j] - fv[j]) + 0.5f * (z - fv[j]) * (z + fv[j]);
+                if (hr[j]) v += whv[j] * fabsf(xr[j] - xv[j]);
+                if (hd[j]) v += wvv[j] * fabsf(xd[j] - xv[j]);
+                part += v;
+                if (++cnt == 32) {
+                    acc += (double)part;
+                    part = 0.f;
+                    cnt = 0;
+                }
             }
         }
         acc += (double)part;
