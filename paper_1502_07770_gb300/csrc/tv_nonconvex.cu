@@ -366,7 +366,9 @@ __device__ __forceinline__ void pair_bar(int id) { asm volatile("bar.sync %0, 64
 // message into the root; after a pair barrier both warps form M^_mid = f_mid + M_L + M_R
 // from the two messages and take the same x_mid in argmin M^_mid, then each clips its own
 // half outwards. Shared memory per warp: three message buffers of T points.
-__global__ void __launch_bounds__(kNcMaxWarps * WARP) nc_chain_kernel(NcArgs p, WsHeader *hdr)
+// At most kNcMaxWarps warps a block; no launch bound, which capped the kernel at 72
+// registers and spilled it.
+__global__ void nc_chain_kernel(NcArgs p, WsHeader *hdr)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & (WARP - 1);
