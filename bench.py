@@ -526,7 +526,7 @@ def main():
     pq_achieved = 12.0 * H * W / (pq_ms * 1e-3) / 1e9  # read xi, f; write x
     tv_l1 = {"ms": float(np.median(l1_ms)), "iterations": r1[1],
              "col_kernel_ms": l1c[0] / max(l1c[1], 1), "row_kernel_ms": pq_ms,
-             "row_roofline": {"bound": "hbm", "kernel": "pq_chain_kernel", "achieved": pq_achieved,
+             "row_roofline": {"bound": "hbm", "kernel": "pq_halves_kernel", "achieved": pq_achieved,
                               "peak": hbm, "unit": "GB/s", "frac": pq_achieved / hbm,
                               "traffic": recorded_traffic("pq_row"), "bytes_per_pixel": 12},
              "ms_per_iteration": float(np.median(l1_ms)) / L1_ITERS, "energy": r1[2],
