@@ -529,8 +529,9 @@ def set_thread_split(on: bool):
 
 
 def set_programmatic_launch(on: bool):
-    """Launch the 2D solver's kernels with a programmatic dependency on their
-    predecessor (the default) or in plain stream order; results are identical."""
+    """Launch the 2D solvers' kernels (ROF, Lagrangian split, TV-l1) with a programmatic
+    dependency on their predecessor (the default) or in plain stream order; results are
+    identical."""
     _check(load().tv_set_programmatic_launch(int(bool(on))))
 
 

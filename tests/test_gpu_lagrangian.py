@@ -82,3 +82,20 @@ def test_long_rows_keep_their_records_in_the_workspace():
     xo, ito, tro, oko = oracle.tv2d_lagrangian(f, lam=0.1, tau0=10.0, max_iters=2, tol=0.0,
                                                check_every=2)
     assert np.abs(x.cpu().numpy() - xo).max() <= TOL
+
+
+def test_programmatic_launch_gives_identical_results():
+    """Kernels launched with a programmatic dependency on their predecessor give
+    bitwise the same result as plain stream order."""
+    _, f = synth.shapes_image(120, 90, seed=14, n_shapes=30)
+    out = {}
+    try:
+        for on in (True, False):
+            _lib.set_programmatic_launch(on)
+            x, it, gap, ok = _lib.tv2d_denoise_lagrangian(_gpu(f), lam=0.1, tau0=10.0, max_iters=10,
+                                                          tol=0.0, check_every=5)
+            out[on] = (x.cpu().numpy(), it, gap)
+    finally:
+        _lib.set_programmatic_launch(True)
+    assert out[True][1] == out[False][1] and out[True][2] == out[False][2]
+    assert np.array_equal(out[True][0], out[False][0])
