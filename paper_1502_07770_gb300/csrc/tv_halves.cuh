@@ -56,14 +56,39 @@ __device__ __forceinline__ int half_node(int lane, int n, int j)
 // leave the chain are copied node by node.
 template <class P, int RING>
 __device__ __forceinline__ void half_fill(const P &p, HalfSmem<P, RING> *sm, int b, int chunk,
-                                          int lane, long long wc0, unsigned vmask, long long k,
-                                          long long start, int n, int cnt)
+                                          int lane, long long wc0, unsigned vmask, bool vw,
+                                          long long k, long long start, int n, int cnt)
 {
 #pragma unroll
     for (int a = 0; a < P::NIN; ++a) {
         const float *src = p.in_ptr(a);
         if (src == nullptr) continue;
         float *tile = sm->u.f.in[a][b];
+        if (!P::COLS && a == P::WI && vw) {
+            // edge weights, each lane for its own half: a left half's weight of step jj is
+            // node jj's (tile position jj); a right half's is node n-2-j's, so the chunk's
+            // eight lie in the 12-float window from n-12-chunk*CH, step jj at 10-jj
+            if (chunk * CH < cnt) {
+                const float *row = src + p.in_off(a, k, start);
+                const int lim = p.in_lim(a, n);
+                const bool lft = lane < HW;
+                const int w0 = lft ? chunk * CH : n - 12 - chunk * CH;
+#pragma unroll
+                for (int h = 0; h < 3; ++h) {
+                    if (lft && h == 2) break;
+                    const int lo = w0 + 4 * h;
+                    if (lo >= 0 && lo + 3 < lim && (((uintptr_t)(row + lo)) & 15) == 0) {
+                        cp_async16(&tile[lane * RP + 4 * h], row + lo);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (lo + e >= 0 && lo + e < lim)
+                                cp_async4(&tile[lane * RP + 4 * h + e], row + lo + e);
+                    }
+                }
+            }
+            continue;
+        }
         if (!P::COLS && ((vmask >> a) & 1u)) {
             if (chunk * CH < cnt) {
                 const float *row = src + p.in_off(a, k, start);
@@ -231,16 +256,18 @@ __global__ void __launch_bounds__(128) chain_halves_kernel(P p_in, float2 *rec, 
     // row inputs and outputs moved 16 bytes at a time by each lane for its own half
     // (edge weights excepted: a right half reads them one node off the 4-node grid)
     unsigned vmask = 0;
-    bool vout = false;
+    bool vout = false, vw = false;
     if constexpr (!P::COLS) {
 #pragma unroll
         for (int a = 0; a < P::NIN; ++a)
             if (a != P::WI && p.in_vec(a)) vmask |= 1u << a;
         vout = p.out_vec();
+        if constexpr (P::WI >= 0) vw = p.in_vec(P::WI);  // weights in per-lane windows
     }
-    // both staging layouts are shared across the warp's lanes: keep them warp-uniform
+    // the staging layouts are shared across the warp's lanes: keep them warp-uniform
     vmask = __reduce_and_sync(FULL, vmask);
     vout = __all_sync(FULL, vout);
+    vw = __all_sync(FULL, vw);
     sm->start[lane] = start;
     sm->n[lane] = n;
     sm->cnt[lane] = cnt;
@@ -263,11 +290,12 @@ __global__ void __launch_bounds__(128) chain_halves_kernel(P p_in, float2 *rec, 
     const int nchunks = (cmax + CH - 1) / CH;
 
     // ---------------- forward pass over each half ----------------
-    if (nchunks > 0) half_fill(p, sm, 0, 0, lane, wc0, vmask, k, start, n, cnt);
+    if (nchunks > 0) half_fill(p, sm, 0, 0, lane, wc0, vmask, vw, k, start, n, cnt);
     cp_async_commit();
     int b = 0;
     for (int ch = 0; ch < nchunks; ++ch) {
-        if (ch + 1 < nchunks) half_fill(p, sm, b ^ 1, ch + 1, lane, wc0, vmask, k, start, n, cnt);
+        if (ch + 1 < nchunks)
+            half_fill(p, sm, b ^ 1, ch + 1, lane, wc0, vmask, vw, k, start, n, cnt);
         cp_async_commit();
         cp_async_wait<1>();
         __syncwarp();
@@ -275,18 +303,26 @@ __global__ void __launch_bounds__(128) chain_halves_kernel(P p_in, float2 *rec, 
         for (int j4 = 0; j4 < CH; j4 += 4) {
             float4 q[P::NIN];
             const unsigned rv = left ? 0u : vmask;  // inputs whose steps run backwards in the tile
+            // a right half's windowed weights: steps j4..j4+3 at positions 10-j4 .. 7-j4
+            const bool rw = !left && vw;
+            float4 qw = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int a = 0; a < P::NIN; ++a)
-                q[a] = *reinterpret_cast<const float4 *>(
-                    &sm->u.f.in[a][b][lane * RP + (((rv >> a) & 1u) ? CH - 4 - j4 : j4)]);
+            for (int a = 0; a < P::NIN; ++a) {
+                const int pos = (a == P::WI && rw) ? CH - j4 : (((rv >> a) & 1u) ? CH - 4 - j4 : j4);
+                q[a] = *reinterpret_cast<const float4 *>(&sm->u.f.in[a][b][lane * RP + pos]);
+                if (a == P::WI && rw)
+                    qw = *reinterpret_cast<const float4 *>(&sm->u.f.in[a][b][lane * RP + CH - 4 - j4]);
+            }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = ch * CH + j4 + e;
                 if (j < cnt && alive) {
                     float v[P::NIN];
 #pragma unroll
-                    for (int a = 0; a < P::NIN; ++a)
-                        v[a] = ((rv >> a) & 1u) ? pick4(q[a], 3 - e) : pick4(q[a], e);
+                    for (int a = 0; a < P::NIN; ++a) {
+                        if (a == P::WI && rw) v[a] = e < 3 ? pick4(q[a], 2 - e) : qw.w;
+                        else v[a] = ((rv >> a) & 1u) ? pick4(q[a], 3 - e) : pick4(q[a], e);
+                    }
                     const int i = half_node(lane, n, j);
                     float c, w;
                     p.unary(v, 0.f, j, i, i + 2, k, c, w, acc);
