@@ -53,7 +53,9 @@ __device__ __forceinline__ int half_node(int lane, int n, int j)
 // copied by each lane for its own half: the chunk's CH nodes as CH/4 16-byte pieces, in
 // memory order. A left half's steps ascend with the nodes, so step jj of the chunk sits at
 // tile position jj; a right half's descend, so step jj sits at CH-1-jj. Pieces that would
-// leave the chain are copied node by node.
+// leave the chain are copied node by node. With `vw` the edge weights are copied per lane
+// too (see the weights branch). Otherwise an input is copied 4 bytes at a time, 8 lanes per
+// row, for every lane's row (k is this lane's chain, wc0 the warp's first).
 template <class P, int RING>
 __device__ __forceinline__ void half_fill(const P &p, HalfSmem<P, RING> *sm, int b, int chunk,
                                           int lane, long long wc0, unsigned vmask, bool vw,
@@ -132,8 +134,8 @@ __device__ __forceinline__ void half_fill(const P &p, HalfSmem<P, RING> *sm, int
                 if (j < sm->cnt[lt]) {
                     const int i = half_node(lt, sm->n[lt], j);
                     const int ii = (a == P::WI && lt >= HW) ? i - 1 : i;
-                    const long long k = wc0 + (lt & (HW - 1));
-                    cp_async4(&tile[lt * RP + jj], src + p.in_off(a, k, sm->start[lt]) + ii);
+                    const long long kt = wc0 + (lt & (HW - 1));  // the chain of row lt
+                    cp_async4(&tile[lt * RP + jj], src + p.in_off(a, kt, sm->start[lt]) + ii);
                 }
             }
         }
