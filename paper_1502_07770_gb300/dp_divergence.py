@@ -24,21 +24,24 @@ from . import synth
 f32 = np.float32
 
 
-def half_loops(c, lam):
+def half_loops(c, lam, records=None):
     """Iterations of (left scan, left re-walk, right scan, right re-walk) and the message
     size after every update of one half, whose nodes in walk order have unaries c.
-    Every node of a half has an edge of weight lam towards the root."""
-    lam = f32(lam)
+    ``lam`` is the weight of every node's edge towards the root, or a sequence of them.
+    With ``records`` (a list), the (lambda-, lambda+) of every node is appended to it."""
+    ws = np.broadcast_to(np.asarray(lam, dtype=np.float32), (len(c),))
     ring = {}
     out = []
     if len(c) == 0:
         return np.zeros((0, 5), dtype=np.int64)
-    c0 = f32(c[0])
+    c0, lam = f32(c[0]), f32(ws[0])
     fl, fs, bl, bs, wprev = c0 - lam, f32(0), c0 + lam, f32(-1), lam
+    if records is not None:
+        records.append((fl, bl))
     F, B = 0, 1
     ring[F], ring[B] = (fl, fs), (bl, bs)
     for i in range(1, len(c)):
-        ci, wi, abar = f32(c[i]), lam, f32(i + 1)
+        ci, wi, abar = f32(c[i]), f32(ws[i]), f32(i + 1)
         nwi = -wi
         vF = fl - ci - wprev
         al, av, asl, as_ = fl, vF, f32(1), f32(1) - abar
@@ -87,12 +90,32 @@ def half_loops(c, lam):
         if from_lm:
             bl2, bv, bsl = lm, nwi, lm_s + abar
         hp = f32(bl2 + (wi - bv) / bsl)
+        if records is not None:
+            records.append((lm, hp))
         nF = lastL
         nB = max(lastR - 1, nF) + 1
         ring[nF], ring[nB] = (lm, lm_s), (hp, -abar)
         F, B, fl, fs, bl, bs, wprev = nF, nB, lm, lm_s, hp, -abar, wi
         out.append((itL, wL, itR, wR, B - F + 1))
     return np.asarray(out, dtype=np.int64)
+
+
+def replay_chain(y, lam):
+    """The whole chain solved by the replayed update from node 0 (weight lam on every edge,
+    0 on the virtual edge after the last node) and the backward clips of Algorithm 2; used
+    to check the replay against an independent solver."""
+    n = len(y)
+    if n == 1:
+        return np.array([y[0]], dtype=np.float64)
+    w = np.full(n, lam, dtype=np.float32)
+    w[-1] = 0.0
+    rec = []
+    half_loops(np.asarray(y, np.float32), w, records=rec)
+    x = np.empty(n)
+    x[-1] = 0.5 * (float(rec[-1][0]) + float(rec[-1][1]))
+    for i in range(n - 2, -1, -1):
+        x[i] = min(max(x[i + 1], float(rec[i][0])), float(rec[i][1]))
+    return x
 
 
 def warp_stats(y, lam):
