@@ -38,6 +38,7 @@ LAM = 0.1
 TOL = 1e-4
 MAX_ITERS = 200
 CHAIN_B, CHAIN_N, CHAIN_LAM = 65536, 1024, 0.15
+CFG0_B, CFG0_N, CFG0_LAM = 512, 256, 0.2
 L2_FLUSH_BYTES = 256 << 20
 WORKLOAD = ("ROF denoise 1024x1024 (200 rectangles/disks, levels U[0,1], + N(0,0.1^2)), "
             "lambda 0.1, 4-connected, tau0=sigma0=1, to per-pixel gap 1e-4")
@@ -168,24 +169,71 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(f, seconds):
-    """The FP64 oracle (as it stands) on the host cores, on a bounded sample:
-    repeated full 1024x1024 denoises until `seconds` of wall time have passed."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _timed_runs(fn, seconds, min_runs=1):
+    """Runs fn() until `seconds` of wall time have passed (at least min_runs times);
+    returns (runs, elapsed seconds, last result)."""
+    runs, t0, r = 0, time.perf_counter(), None
+    while True:
+        r = fn()
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and runs >= min_runs:
+            return runs, el, r
+
+
+def cpu_baseline(f, seconds, chain_y, chain_lam):
+    """The FP64 oracle (as it stands) on the host cores, on bounded samples: repeated
+    full 1024x1024 denoises until `seconds` of wall time have passed, on all cores and on
+    one thread (the paper's single-core regime); and the batched chain prox (Gnode/s) on
+    a block of the benchmark's chains, on all cores and on one thread."""
     import oracle
     threads = os.cpu_count() or 1
     oracle.build()
-    runs, t0 = 0, time.perf_counter()
-    iters = None
-    while True:
-        _, iters, _, _ = oracle.tv2d_pd(f, lam=LAM, max_iters=MAX_ITERS, tol=TOL, nthreads=threads)
-        runs += 1
-        el = time.perf_counter() - t0
-        if el >= seconds and runs >= 2:
-            break
+
+    def denoise(nt):
+        return oracle.tv2d_pd(f, lam=LAM, max_iters=MAX_ITERS, tol=TOL, nthreads=nt)[1]
+    runs, el, iters = _timed_runs(lambda: denoise(threads), seconds, 2)
     ms = el / runs * 1e3
+    runs1, el1, _ = _timed_runs(lambda: denoise(1), seconds / 2, 1)
+    ms1 = el1 / runs1 * 1e3
+    nb, nn = chain_y.shape
+    flat = chain_y.reshape(-1)
+    offs = np.arange(nb + 1, dtype=np.int64) * nn
+
+    def chains(nt):
+        return oracle.chain_solve_batch(flat, offs, lam=chain_lam, nthreads=nt)
+    cr, cel, _ = _timed_runs(lambda: chains(threads), seconds / 4, 2)
+    cr1, cel1, _ = _timed_runs(lambda: chains(1), seconds / 4, 1)
     return {"value": ms, "unit": "ms", "cores": threads, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{runs} full 1024x1024 denoises ({iters} iterations each), FP64, "
-                      f"{threads} threads, {el:.1f} s"}
+                      f"{threads} threads, {el:.1f} s",
+            "single_thread": {"value": ms1, "unit": "ms", "cores": 1,
+                              "sample": f"{runs1} full denoises on one thread, {el1:.1f} s"},
+            "chain_prox": {"value": nb * nn * cr / cel / 1e9, "unit": "Gnode/s", "cores": threads,
+                           "single_thread": nb * nn * cr1 / cel1 / 1e9,
+                           "sample": f"{nb} chains x {nn} nodes of the chain-prox workload, "
+                                     f"lambda {chain_lam}, FP64; {cr} runs on {threads} threads "
+                                     f"({cel:.1f} s), {cr1} on one ({cel1:.1f} s)"}}
 
 
 def max_over_ranks(value, device, world):
@@ -224,6 +272,7 @@ def run_reference(args):
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": WORKLOAD, "iterations": iters},
            "cpu_baseline": {"value": ms, "unit": "ms", "cores": threads, "kind": "oracle",
+                            "cpu_model": cpu_model(),
                             "sample": f"{args.steps} full denoises, {threads} threads"},
            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -350,6 +399,30 @@ def main():
     chain_kernel_ms = kms / max(kn, 1)
     chain_achieved = 8.0 * nodes / (chain_kernel_ms * 1e-3) / 1e9
 
+    # ---------------- the 512 x 256 chain batch (launch-bound: 1 MB of traffic) ----------
+    y0c = torch.from_numpy(synth.chain_batch(CFG0_B, CFG0_N, seed0=0)).to(dev)
+    x0c = torch.empty_like(y0c)
+    ws0 = _lib.workspace(_lib.load().tv_chain_workspace_size(CFG0_B, CFG0_N), dev, "benchcfg0")
+    for _ in range(3):
+        _lib.chain_prox(y0c, lam=CFG0_LAM, out=x0c, ws=ws0)
+    cfg0_ms = []
+    for _ in range(max(10, args.steps // 2)):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _lib.chain_prox(y0c, lam=CFG0_LAM, out=x0c, ws=ws0)
+        b.record(stream)
+        b.synchronize()
+        cfg0_ms.append(a.elapsed_time(b))
+    c0ms = float(np.median(cfg0_ms))
+    cfg0 = {"value": CFG0_B * CFG0_N / (c0ms * 1e-3) / 1e9, "unit": "Gnode/s", "ms": c0ms,
+            "workload": f"{CFG0_B} chains x {CFG0_N} nodes (seeds 0..{CFG0_B - 1}), lambda "
+                        f"{CFG0_LAM}, piecewise-constant + N(0,0.1^2), L2 flushed",
+            "note": "1.05 MB of algorithmic traffic: bound by launch and the sequential "
+                    "256-node chains, not by HBM"}
+    del y0c, x0c
+
     # ---------------- chain-prox sweep: shapes and per-edge weights ----------------
     sweep = []
     for SB, SN in ((65536, 1024), (262144, 256), (16384, 4096)):
@@ -455,6 +528,10 @@ def main():
                                          outs=bouts)
     r = batched()
     b_iters = r[1]
+    # algorithmic bytes: per image and iteration 40 B a pixel (column phase: read x^k,
+    # x^{k-1}, y, w_v, write y; row phase: read f, x^k, y, w_h, write x^{k+1}); an image
+    # stops at its own iteration count
+    b_bytes = 40.0 * sum(h * w * int(k) for (h, w), k in zip(sizes, b_iters))
     batched_ms = []
     for _ in range(max(3, args.steps // 10)):
         flush.zero_()
@@ -599,11 +676,12 @@ def main():
     # ---------------- roofline of the dominant kernel of the step ----------------
     # algorithmic bytes: column (dual) phase reads x^k, x^{k-1}, y, f and writes y
     # (16 B/pixel); row (primal) phase reads f, x^k, y and writes x^{k+1} (16 B/pixel).
+    # The library times only the launches that did work: the phases of iterations
+    # launched after the stop flag was set return at once and are left out.
     npx = H * W
-    real = {"col": iters + 1, "row": iters}  # launches doing work per step; later ones return at once
     dom = max(("col", "row"), key=lambda k: prof[k][0])
     dom_ms_total, dom_launches = prof[dom]
-    dom_bytes = 16.0 * npx * real[dom] * args.steps
+    dom_bytes = 16.0 * npx * dom_launches
     dom_achieved = dom_bytes / (dom_ms_total * 1e-3) / 1e9
     traffic = recorded_traffic(f"tv2d_{dom}")
 
@@ -633,6 +711,7 @@ def main():
                      "avg_launch_ms": dom_ms_total / max(dom_launches, 1),
                      "note": "latency-bound: state of ~24 MB stays in L2; 1024 chains per phase"},
         "phase_ms_per_step": {k: prof[k][0] / args.steps for k in prof},
+        "phase_launches_per_step": {k: prof[k][1] / args.steps for k in prof},
         "chain_prox": {"value": nodes / (cms * 1e-3) / 1e9, "unit": "Gnode/s",
                        "workload": f"{CHAIN_B} chains x {CHAIN_N} nodes, lambda {CHAIN_LAM}, "
                                    "piecewise-constant + N(0,0.1^2), L2 flushed",
@@ -641,6 +720,7 @@ def main():
                                     "unit": "GB/s", "frac": chain_achieved / hbm,
                                     "traffic": recorded_traffic("chain"),
                                     "bytes_per_node": 8}},
+        "chain_prox_512x256": cfg0,
         "chain_prox_sweep": sweep,
         "general_chain": general,
         "diff_prox": {"value": DB * DN / (dms * 1e-3) / 1e9, "unit": "Gnode/s",
@@ -656,6 +736,12 @@ def main():
                     "graph_loop": int(_lib.load().tv2d_batched_last_mode()),
                     "sequential_ms": sms,
                     "speedup_vs_sequential": sms / bms,
+                    "roofline": {"bound": "hbm", "achieved": b_bytes / (bms * 1e-3) / 1e9,
+                                 "peak": hbm, "unit": "GB/s",
+                                 "frac": b_bytes / (bms * 1e-3) / 1e9 / hbm,
+                                 "bytes_per_pixel_iteration": 40,
+                                 "note": "whole solve (both phases, gap kernels, graph "
+                                         "loop) over the summed per-image iterations"},
                     "workload": "64 images, W ~ U{128..2048}, H ~ U{96..1536}, lambda ~ U[0.05,0.3], "
                                 "edge-aware weights lambda*exp(-|df|/0.2), to per-pixel gap 1e-4"},
         "lagrangian_split": lagrangian,
@@ -682,7 +768,7 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and world == 1:
-        result["cpu_baseline"] = cpu_baseline(f_np, args.cpu_seconds)
+        result["cpu_baseline"] = cpu_baseline(f_np, args.cpu_seconds, base[:64], CHAIN_LAM)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

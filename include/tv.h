@@ -94,8 +94,13 @@ size_t tv_chain_workspace_size(int64_t num_chains, int64_t max_len);
  *   d_offsets  num_chains+1 monotone int64 offsets on the DEVICE, or NULL: chain k
  *              then spans [k*max_len, (k+1)*max_len) (a uniform batch)
  *   max_len    upper bound on every chain length (the uniform length if d_offsets
- *              is NULL); a chain longer than this is skipped and flagged
- *   d_x        output, same layout as d_y; must not overlap d_y or d_w
+ *              is NULL), at most 2^24 (node counts enter the message slopes as exact
+ *              FP32 integers); a chain longer than this is skipped and flagged
+ *   d_x        output, same layout as d_y; must not overlap d_y or d_w. Without
+ *              offsets the host checks this (TV_ERR_INVALID); with offsets the host
+ *              rejects x == y or x == w, and the kernel rejects any other overlap of
+ *              the node ranges [off_0, off_num_chains) (no chain is solved, and
+ *              tv_workspace_status reports TV_ERR_INVALID)
  * Empty chains and chains of one node (x = y) are allowed. Weights must be >= 0.
  */
 tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
@@ -114,10 +119,16 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
  * batch: num_chains * max_len may be at most about 690 000 nodes (the records and
  * the reserve take about 24 bytes per node); larger batches are rejected with
  * TV_ERR_INVALID before any launch. The first call on a device looks up the
- * array's device address (make it before any stream capture). All calls share
- * the array: calls that overlap on the GPU race and must be ordered by the
- * caller. Device-side errors are not readable for this entry point (it has no
- * caller-visible workspace); malformed offsets skip the affected chains.
+ * array's device address (make it before any stream capture); the address belongs
+ * to the device's current CUDA context and is looked up again when that context
+ * changes (after cudaDeviceReset, say). All calls share the array: calls that
+ * overlap on the GPU race and must be ordered by the caller. Whatever the batch
+ * shape, this entry point runs the one-thread-per-chain kernel (tv_chain_solve
+ * picks one warp per chain for small batches and middle-rooted halves for long
+ * chains), so it can be slower than tv_chain_solve on the same batch. Device-side
+ * errors are not readable for this entry point (it has no caller-visible
+ * workspace): malformed offsets skip the affected chains, and CSR node ranges of x
+ * overlapping those of y or w skip the whole batch.
  */
 tv_status tv_chain_solve_noalloc(const float *d_y, const float *d_w, float lambda,
                                  const int64_t *d_offsets, int64_t num_chains, int64_t max_len,

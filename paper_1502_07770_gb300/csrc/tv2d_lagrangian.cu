@@ -415,7 +415,7 @@ tv_status tv2d_denoise_lagrangian(const float *d_img, int64_t H, int64_t W, cons
                                   tv_stream_t stream)
 {
     clear_error();
-    if (H < 1 || W < 1 || H > (1LL << 30) || W > (1LL << 30) || max_iters < 1 ||
+    if (H < 1 || W < 1 || H > (1LL << 24) || W > (1LL << 24) || max_iters < 1 ||
         check_every < 1 || !(tau0 > 0.f && tau0 < INFINITY)) {
         set_error("tv2d_denoise_lagrangian: need H, W >= 1, max_iters >= 1, check_every >= 1 "
                   "and a finite tau0 > 0");

@@ -91,6 +91,23 @@ void prof_mark(int kind, cudaStream_t s, bool start)
     }
 }
 
+size_t prof_pending(int kind)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    return g_prof_pending[kind].size();
+}
+
+void prof_drop_from(int kind, size_t first)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::vector<ProfPair> &v = g_prof_pending[kind];
+    while (v.size() > first) {
+        cudaEventSynchronize(v.back().b);
+        g_prof_free.push_back(v.back());
+        v.pop_back();
+    }
+}
+
 static void prof_collect(int kind)
 {
     for (ProfPair &pr : g_prof_pending[kind]) {
@@ -166,6 +183,23 @@ namespace {
 
 constexpr int kRing = 32;
 
+// CSR batches: the node range [offsets[0], offsets[num_chains]) of x must not overlap
+// that of y or of w (the host checks only x == y, since the offsets live on the device).
+// Read by every thread at kernel entry; an overlap flags ERR_BAD_CHAIN and skips the
+// whole launch.
+__device__ __forceinline__ bool csr_disjoint(const float *x, const float *y, const float *w,
+                                             long long off0, long long offn)
+{
+    if (offn <= off0) return true;
+    const size_t len = (size_t)(offn - off0) * sizeof(float);
+    auto apart = [&](const float *a) {
+        if (a == nullptr) return true;
+        const uintptr_t p = (uintptr_t)(x + off0), q = (uintptr_t)(a + off0);
+        return p + len <= q || q + len <= p;
+    };
+    return apart(y) && apart(w);
+}
+
 // Contiguous chains: chain k at [off_k, off_{k+1}) (or [k*len, (k+1)*len)).
 template <bool HAS_W>
 struct ChainRowsP {
@@ -185,10 +219,15 @@ struct ChainRowsP {
     float *x;
     bool vec;        // uniform chains, length % 4 == 0, 16-byte aligned arrays
     long long off0;  // offsets[0], so that reserve slices start at zero
+    int *status;     // workspace error word (CSR overlap check), or NULL
 
     __device__ bool resolve()
     {
         off0 = offsets ? (long long)offsets[0] : 0;
+        if (offsets && !csr_disjoint(x, y, w, off0, (long long)offsets[nchains])) {
+            if (status && threadIdx.x == 0) atomicOr(status, ERR_BAD_CHAIN);
+            return false;
+        }
         return true;
     }
     __device__ long long num_chains() const { return nchains; }
@@ -324,10 +363,15 @@ struct CoopRowsP {
     int maxlen;
     float *x;
     long long off0;
+    int *status;  // workspace error word (CSR overlap check), or NULL
 
     __device__ bool resolve()
     {
         off0 = offsets ? (long long)offsets[0] : 0;
+        if (offsets && !csr_disjoint(x, y, w, off0, (long long)offsets[nchains])) {
+            if (status && threadIdx.x == 0) atomicOr(status, ERR_BAD_CHAIN);
+            return false;
+        }
         return true;
     }
     __device__ long long num_chains() const { return nchains; }
@@ -669,8 +713,8 @@ tv_status tv_chain_solve_general(const float *d_a, const float *d_b, const float
                                  size_t workspace_bytes, tv_stream_t stream)
 {
     clear_error();
-    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 30)) {
-        set_error("tv_chain_solve_general: num_chains and max_len must be >= 0 (max_len <= 2^30)");
+    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 24)) {
+        set_error("tv_chain_solve_general: num_chains and max_len must be >= 0 (max_len <= 2^24)");
         return TV_ERR_INVALID;
     }
     if (num_chains == 0) return TV_OK;
@@ -714,8 +758,8 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
                          tv_stream_t stream)
 {
     clear_error();
-    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 30)) {
-        set_error("tv_chain_solve: num_chains and max_len must be >= 0 (max_len <= 2^30)");
+    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 24)) {
+        set_error("tv_chain_solve: num_chains and max_len must be >= 0 (max_len <= 2^24)");
         return TV_ERR_INVALID;
     }
     if (num_chains == 0) return TV_OK;
@@ -753,10 +797,12 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     if (st != TV_OK) return st;
     if (num_chains <= coop_max_chains()) {
         if (d_w) {
-            CoopRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x, 0};
+            CoopRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x, 0,
+                              &ws.hdr->status};
             return launch_coop(p, num_chains, (int)max_len, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_CHAIN);
         }
-        CoopRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x, 0};
+        CoopRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x, 0,
+                           &ws.hdr->status};
         return launch_coop(p, num_chains, (int)max_len, ws.rec, nullptr, ws.spill, ws.hdr, s, PK_CHAIN);
     }
     // chains of 64 nodes or more: two threads per chain (twice the warps, half the steps
@@ -764,12 +810,12 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     const bool halves = thread_split() != 0 && max_len >= kHalvesMinLen;
     if (d_w) {
         ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,
-                           vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0};
+                           vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0, &ws.hdr->status};
         if (halves) return launch_halves(p, num_chains, (int)max_len, ws.rec, ws.spill, ws.hdr, s);
         return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
     }
     ChainRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x,
-                        vec_ok(d_offsets, max_len, d_y, nullptr, d_x), 0};
+                        vec_ok(d_offsets, max_len, d_y, nullptr, d_x), 0, &ws.hdr->status};
     if (halves) return launch_halves(p, num_chains, (int)max_len, ws.rec, ws.spill, ws.hdr, s);
     return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
 }
@@ -786,7 +832,7 @@ tv_status tv_chain_solve_columns(const float *d_y, const float *d_w, float lambd
                                  size_t workspace_bytes, tv_stream_t stream)
 {
     clear_error();
-    if (H < 0 || W < 0 || ld < W || H > (1LL << 30)) {
+    if (H < 0 || W < 0 || ld < W || H > (1LL << 24)) {
         set_error("tv_chain_solve_columns: need H, W >= 0 and ld >= W");
         return TV_ERR_INVALID;
     }
@@ -864,8 +910,10 @@ tv_status tv_workspace_status(void *d_workspace, tv_stream_t stream, int *status
 // pass and the reserve for long message sequences) comes from this fixed array.
 //
 // The array lives in every GPU that loads the library, until the process exits.
-// Its device address is looked up once per device, on the first call made with
-// that device current; make that first call before any stream capture.
+// Its device address belongs to the CUDA context that is current when it is looked
+// up: the address is looked up on the first call made on a device (make that first
+// call before any stream capture) and again whenever that device's current context
+// has changed since (after cudaDeviceReset, say), keyed by the context's unique id.
 // Every call shares the array: calls that overlap on the GPU (different streams,
 // or different host threads, on the same device) race on it and must be ordered
 // by the caller. The header words are cleared on every call.
@@ -877,7 +925,31 @@ constexpr int kNoAllocMaxDevices = 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kNoAllocMaxDevices];
+struct NoAllocSlot {
+    void *ptr;
+    unsigned long long ctx;  // id of the context the address was looked up in
+};
+NoAllocSlot g_noalloc[kNoAllocMaxDevices];
+
+// Unique id of the current context (cuCtxGetId through the runtime's driver entry
+// point, so that the library needs no link to the driver library); false if there is
+// no current context or the driver has no such call.
+bool current_context_id(unsigned long long *id)
+{
+    typedef int (*CtxGetId)(void *, unsigned long long *);
+    static CtxGetId fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            (void)cudaGetLastError();
+            return (CtxGetId) nullptr;
+        }
+        return (CtxGetId)f;
+    }();
+    return fn != nullptr && fn(nullptr, id) == 0;
+}
 
 tv_status noalloc_scratch(void **out)
 {
@@ -889,13 +961,18 @@ tv_status noalloc_scratch(void **out)
         return TV_ERR_INVALID;
     }
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        st = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
-        if (st != TV_OK) return st;
-        g_noalloc_ptr[dev] = p;
+    unsigned long long ctx = 0;
+    if (g_noalloc[dev].ptr && current_context_id(&ctx) && ctx == g_noalloc[dev].ctx) {
+        *out = g_noalloc[dev].ptr;
+        return TV_OK;
     }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    st = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+    if (st != TV_OK) return st;
+    // without a context id the address is looked up again on every call
+    g_noalloc[dev].ptr = current_context_id(&ctx) ? p : nullptr;
+    g_noalloc[dev].ctx = ctx;
+    *out = p;
     return TV_OK;
 }
 
@@ -906,8 +983,8 @@ extern "C" tv_status tv_chain_solve_noalloc(const float *d_y, const float *d_w, 
                                             int64_t max_len, float *d_x, tv_stream_t stream)
 {
     clear_error();
-    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 30)) {
-        set_error("tv_chain_solve_noalloc: num_chains and max_len must be >= 0 (max_len <= 2^30)");
+    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 24)) {
+        set_error("tv_chain_solve_noalloc: num_chains and max_len must be >= 0 (max_len <= 2^24)");
         return TV_ERR_INVALID;
     }
     if (num_chains == 0) return TV_OK;
@@ -947,10 +1024,10 @@ extern "C" tv_status tv_chain_solve_noalloc(const float *d_y, const float *d_w, 
     if (st != TV_OK) return st;
     if (d_w) {
         ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,
-                           vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0};
+                           vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0, &ws.hdr->status};
         return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
     }
     ChainRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x,
-                        vec_ok(d_offsets, max_len, d_y, nullptr, d_x), 0};
+                        vec_ok(d_offsets, max_len, d_y, nullptr, d_x), 0, &ws.hdr->status};
     return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
 }

@@ -150,7 +150,7 @@ extern "C" tv_status tv_chain_solve_backward(const float *d_x, const float *d_gr
                                              tv_stream_t stream)
 {
     clear_error();
-    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 30)) {
+    if (num_chains < 0 || max_len < 0 || max_len > (1LL << 24)) {
         set_error("tv_chain_solve_backward: num_chains and max_len must be >= 0");
         return TV_ERR_INVALID;
     }

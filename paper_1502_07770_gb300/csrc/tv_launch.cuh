@@ -13,6 +13,11 @@ enum ProfKind { PK_CHAIN = 0, PK_COL = 1, PK_ROW = 2, PK_INIT = 3, PK_GRAD = 4, 
 void note_launch();
 bool prof_on();
 void prof_mark(int kind, cudaStream_t s, bool start);
+// Timed launches of `kind` recorded and not yet read, and the removal of those from
+// index `first` on (launches an entry point knows did no work, e.g. the phases of a
+// 2D solve launched after its stop flag was set, which return at once).
+size_t prof_pending(int kind);
+void prof_drop_from(int kind, size_t first);
 
 // Warps per block of a one-thread-per-chain launch: the spread of batch_shape for
 // small batches; for batches of at least two warps per SM, the largest block (up to

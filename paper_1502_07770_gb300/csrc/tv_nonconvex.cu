@@ -609,7 +609,7 @@ tv_status tv_chain_solve_nonconvex(const int64_t *d_uoff, const float *d_ulam,
 {
     clear_error();
     if (num_chains < 0 || max_len < 0 || num_nodes < 0 || max_breakpoints < 1 ||
-        max_breakpoints > 4096 || max_len > (1LL << 30)) {
+        max_breakpoints > 4096 || max_len > (1LL << 24)) {
         set_error("tv_chain_solve_nonconvex: need num_chains, max_len, num_nodes >= 0 and "
                   "1 <= max_breakpoints <= 4096");
         return TV_ERR_INVALID;

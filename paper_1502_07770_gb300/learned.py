@@ -279,19 +279,38 @@ def train(net, f, lam, target, epochs=10, batch=8, seed=0, log=None):
     return history
 
 
-def denoise_warm(net, f, lam: float, lam_t=None, tol=1e-4, max_iters=400, fallback_iters=None):
-    """Solve one (H, W) image from the network's warm start; if that does not reach
-    ``tol`` within ``fallback_iters`` (default ``max_iters``) or returns a non-finite
-    gap, solve again from y^0 = 0. ``lam_t``: the same lambda as a (1,) CUDA tensor
-    (made here if None). Returns (x, iterations incl. a failed attempt, gap,
-    converged, used_fallback)."""
+def denoise_warm(net, f, lam: float, lam_t=None, tol=1e-4, max_iters=400, first_check=6):
+    """Solve one (H, W) image from the network's warm start, with the plain method as
+    fallback and judge (y^0 = 0 is the method without the network).
+
+    First check, after ``first_check`` outer iterations (the solver's own first batch
+    of iterations, after which it reads the device state): a warm-started run that has
+    converged is returned. Otherwise its per-pixel gap is compared with the zero-init
+    curve at the same iteration, i.e. the gap the plain method reaches from y^0 = 0
+    after as many iterations on this image. A non-finite gap, or one above the plain
+    method's, sends the solve back to y^0 = 0 right there (the plain run is continued
+    to the tolerance); a warm start that is ahead is run to the tolerance. A bad network
+    thus costs at most two short runs of ``first_check`` iterations. ``lam_t``: the same
+    lambda as a (1,) CUDA tensor (made here if None).
+
+    Returns (x, outer iterations of every run, gap, converged, used_fallback)."""
     if lam_t is None:
         lam_t = torch.tensor([lam], dtype=torch.float32, device=f.device)
     y0 = net.predict_dual(f, lam_t)[0]
-    x, it, gap, ok = _lib.tv2d_denoise(f, lam=float(lam), y0=y0, tol=tol,
-                                       max_iters=fallback_iters or max_iters)
+    k1 = max(1, min(int(first_check), int(max_iters)))
+    x, it, gap, ok = _lib.tv2d_denoise(f, lam=float(lam), y0=y0, tol=tol, max_iters=k1)
     if ok and math.isfinite(gap):
         return x, it, gap, ok, False
+    if math.isfinite(gap):
+        # the zero-init curve at the first check
+        xz, itz, gz, okz = _lib.tv2d_denoise(f, lam=float(lam), tol=tol, max_iters=k1)
+        if okz:
+            return xz, it + itz, gz, okz, True
+        if gap <= gz:
+            x, it2, gap, ok = _lib.tv2d_denoise(f, lam=float(lam), y0=y0, tol=tol,
+                                                max_iters=max_iters)
+            return x, it + itz + it2, gap, ok, False
+        it += itz
     x, it2, gap, ok = _lib.tv2d_denoise(f, lam=float(lam), tol=tol, max_iters=max_iters)
     return x, it + it2, gap, ok, True
 

@@ -1,13 +1,13 @@
 """Small, fixed workloads for kernel profilers (one GPU, inputs resident).
 
-    python -m paper_1502_07770_gb300.profile_cases tv2d     [--reps R]   # 1024x1024 denoise, lambda 0.1
-    python -m paper_1502_07770_gb300.profile_cases chain    [--reps R] [--chains B] [--len N]
-    python -m paper_1502_07770_gb300.profile_cases backward [--reps R]   # 4096 x 1024 chain VJP
-    python -m paper_1502_07770_gb300.profile_cases net      [--reps R]   # warm-start inference 1024x1024
-    python -m paper_1502_07770_gb300.profile_cases train    [--reps R]   # one training step, 8 x 512x512
-    python -m paper_1502_07770_gb300.profile_cases batched  [--reps R]   # 16 uneven images, host-replayed loop
-    python -m paper_1502_07770_gb300.profile_cases l1       [--reps R]   # TV-l1 1024x1024, 10 iterations
-    python -m paper_1502_07770_gb300.profile_cases nonconvex [--reps R] [--chains B]  # B x 1482 x 126 cost volume
+    python profile_cases.py tv2d     [--reps R]   # 1024x1024 denoise, lambda 0.1
+    python profile_cases.py chain    [--reps R] [--chains B] [--len N]
+    python profile_cases.py backward [--reps R]   # 4096 x 1024 chain VJP
+    python profile_cases.py net      [--reps R]   # warm-start inference 1024x1024
+    python profile_cases.py train    [--reps R]   # one training step, 8 x 512x512
+    python profile_cases.py batched  [--reps R]   # 16 uneven images, host-replayed loop
+    python profile_cases.py l1       [--reps R]   # TV-l1 1024x1024, 10 iterations
+    python profile_cases.py nonconvex [--reps R] [--chains B]  # B x 1482 x 126 cost volume
 
 Each case runs its workload R times (after one untimed call) and prints one line. The
 batched case forbids the conditional-graph loop so that every kernel is an ordinary
@@ -16,11 +16,15 @@ launch that a profiler can replay.
 from __future__ import annotations
 
 import argparse
+import os
+import sys
 
 import numpy as np
 import torch
 
-from . import _lib, learned, synth
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+from paper_1502_07770_gb300 import _lib, learned, synth  # noqa: E402
 
 
 def main(argv=None):

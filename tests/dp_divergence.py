@@ -11,7 +11,7 @@ code) and counts, per node step, the iterations of each loop for every lane and 
 maximum over the warp. The ratio between the two is the SIMT divergence that bounds
 the thread kernel's instruction count.
 
-    python -m paper_1502_07770_gb300.dp_divergence [--chains 64] [--len 1024] [--lam 0.15]
+    python -m tests.dp_divergence [--chains 64] [--len 1024] [--lam 0.15]
 """
 from __future__ import annotations
 
@@ -19,7 +19,7 @@ import argparse
 
 import numpy as np
 
-from . import synth
+from paper_1502_07770_gb300 import synth
 
 f32 = np.float32
 

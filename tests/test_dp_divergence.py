@@ -3,7 +3,8 @@ the chain: its records and the backward clips of Algorithm 2 give the oracle's m
 import numpy as np
 
 import oracle
-from paper_1502_07770_gb300 import dp_divergence as dd, synth
+from paper_1502_07770_gb300 import synth
+from tests import dp_divergence as dd
 
 
 def test_replay_solves_the_chain():

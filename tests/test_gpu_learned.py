@@ -266,3 +266,28 @@ def test_training_reduces_iterations():
     summary, rows = learned.evaluate(net, range(20000, 20008), H=128, W=128, reps=1)
     assert summary["all_converged"]
     assert summary["iters_warm"] < summary["iters_zero"]
+
+
+def test_poor_network_falls_back_at_the_first_check():
+    """A deliberately poor network (random weights set on the host, the output layer
+    scaled so that every p_v = lambda * tanh(o) sits near +-lambda with a random sign)
+    is judged by the plain method after the first check: the solve returns to y^0 = 0
+    there and converges, at the cost of two short runs of first_check iterations, not
+    after max_iters."""
+    net = learned.WarmStartNet(DEV, seed=11)
+    g = torch.Generator().manual_seed(5)
+    with torch.no_grad():
+        w_last, b_last = net.layer_params()[-1]
+        w_last.copy_((torch.randn(w_last.shape, generator=g) * 5.0).to(DEV))
+        b_last.zero_()
+    net._refresh_bf16()
+    f = torch.from_numpy(synth.warm_start_sample(128, 128, 20001)[0]).to(DEV)
+    lam = 0.15
+    p = -torch.cumsum(net.predict_dual(f, lam)[0].double(), dim=0)
+    assert p.abs().mean().item() > 0.5 * lam  # the warm start is far from y = 0
+    _, it_zero, _, ok_zero = _lib.tv2d_denoise(f, lam=lam, tol=1e-4, max_iters=200)
+    x, it, gap, ok, fb = learned.denoise_warm(net, f, lam, tol=1e-4, max_iters=200,
+                                              first_check=3)
+    assert ok_zero and ok and fb
+    assert it <= 3 + 3 + it_zero
+    assert gap <= 1e-4

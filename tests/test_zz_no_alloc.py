@@ -1,4 +1,5 @@
-"""The allocation-free chain solve, called through the C ABI, against tv_chain_solve.
+"""The allocation-free chain solve, called through the C ABI, against tv_chain_solve
+and against the FP64 oracle.
 
 tv_chain_solve_noalloc serves callers that must not call cudaMalloc (for example
 code inside a framework that has reserved the GPU's memory for its own caching
@@ -12,6 +13,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1502_07770_gb300 import _lib, synth
 
 pytestmark = pytest.mark.gpu
@@ -53,6 +55,27 @@ def test_noalloc_matches_workspace_entry_point_twice():
     torch.cuda.synchronize()
     assert (a1 - b1).abs().max().item() <= TOL
     assert (a2 - b2).abs().max().item() <= TOL
+    # both calls element by element against the FP64 oracle
+    y1n = y1.cpu().numpy()
+    r1 = oracle.chain_solve_batch(y1n.ravel(), np.arange(513, dtype=np.int64) * 256, lam=0.2)
+    assert np.abs(a1.cpu().numpy().ravel() - r1).max() <= TOL
+    r2 = oracle.chain_solve_batch(y2n, off, w=w2n)
+    assert np.abs(a2.cpu().numpy() - r2).max() <= TOL
+
+
+def test_noalloc_near_its_scratch_limit_against_the_oracle():
+    # 640 chains of 1024 nodes: records and reserve take about 15.7 of the 16 MiB, so
+    # the records of the last warps sit at the far end of the fixed array
+    lib = _lib.load()
+    need = lib.tv_chain_workspace_size(640, 1024)
+    assert need <= 16 << 20
+    yn = synth.chain_batch(640, 1024, seed0=500)
+    y = torch.from_numpy(yn).to(DEV)
+    for _ in range(2):  # two calls in a row on the same scratch
+        x = _noalloc(y, lam=0.15)
+        torch.cuda.synchronize()
+        r = oracle.chain_solve_batch(yn.ravel(), np.arange(641, dtype=np.int64) * 1024, lam=0.15)
+        assert np.abs(x.cpu().numpy().ravel() - r).max() <= TOL
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
