@@ -522,10 +522,12 @@ def set_coop_split(mode: int):
     _check(load().tv_set_coop_split(int(mode)))
 
 
-def set_thread_split(on: bool):
-    """Middle-rooted chains (two threads per chain) in the one-thread-per-chain path of
-    ``chain_prox`` (True, the default) or one thread per chain from one end (False)."""
-    _check(load().tv_set_thread_split(1 if on else 0))
+def set_thread_split(mode: int):
+    """Kernel of the one-thread-per-chain path of ``chain_prox`` for chains of 64 nodes or
+    more: 2 (the default) middle-rooted chains, a thread per half, each lane updating its
+    message at its own pace with a fixed-shape step; 1 the same halves with the lanes'
+    updates in step; 0 one thread per chain from one end."""
+    _check(load().tv_set_thread_split(int(mode)))
 
 
 def set_programmatic_launch(on: bool):

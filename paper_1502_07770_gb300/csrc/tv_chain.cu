@@ -9,6 +9,7 @@
 #include <mutex>
 #include <vector>
 
+#include "tv_flat.cuh"
 #include "tv_halves.cuh"
 #include "tv_launch.cuh"
 
@@ -60,7 +61,7 @@ static std::atomic<long long> g_coop_max{kCoopMaxChainsDefault};
 long long coop_max_chains() { return g_coop_max.load(); }
 static std::atomic<int> g_coop_split{1};
 int coop_split() { return g_coop_split.load(); }
-static std::atomic<int> g_thread_split{1};
+static std::atomic<int> g_thread_split{2};
 int thread_split() { return g_thread_split.load(); }
 
 // programmatic dependent launch: enabled by the ABI switch, active inside a PdlScope
@@ -591,6 +592,29 @@ tv_status launch_halves(const ChainRowsP<HAS_W> &p, long long nchains, int max_l
     return st;
 }
 
+// chain_flat_kernel (tv_flat.cuh): one thread per chain half, fixed-shape update.
+template <bool HAS_W>
+tv_status launch_flat(const ChainRowsP<HAS_W> &p, long long nchains, int max_len, float2 *rec,
+                      float2 *spill, WsHeader *hdr, cudaStream_t s)
+{
+    const long long warps = (nchains + HW - 1) / HW;
+    const size_t per_warp = sizeof(FlatSmem<HAS_W ? 2 : 1>);
+    auto kern = chain_flat_kernel<ChainRowsP<HAS_W>>;
+    tv_status st = check_cuda(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * per_warp)),
+        "cudaFuncSetAttribute");
+    if (st != TV_OK) return st;
+    const Shape sh = chains_shape(warps, (const void *)kern, per_warp);
+    const bool prof = prof_on();
+    if (prof) prof_mark(PK_CHAIN, s, true);
+    kern<<<(unsigned)sh.blocks, sh.wpb * WARP, sh.wpb * per_warp, s>>>(p, rec, spill, hdr,
+                                                                       (max_len + 1) / 2);
+    st = check_cuda(cudaGetLastError(), "chain flat kernel launch");
+    if (st == TV_OK) note_launch();
+    if (prof) prof_mark(PK_CHAIN, s, false);
+    return st;
+}
+
 struct ChainWs {
     WsHeader *hdr;
     float2 *rec;
@@ -658,8 +682,8 @@ tv_status tv_set_programmatic_launch(int on)
 tv_status tv_set_thread_split(int on)
 {
     clear_error();
-    if (on < 0 || on > 1) {
-        set_error("tv_set_thread_split: 0 or 1");
+    if (on < 0 || on > 2) {
+        set_error("tv_set_thread_split: 0, 1 or 2");
         return TV_ERR_INVALID;
     }
     tvh::g_thread_split.store(on);
@@ -807,16 +831,19 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     }
     // chains of 64 nodes or more: two threads per chain (twice the warps, half the steps
     // each, and a 16-entry ring that keeps every warp of a full batch resident)
-    const bool halves = thread_split() != 0 && max_len >= kHalvesMinLen;
+    // mode 2 (default): the fixed-shape update; 1: the same halves with the scans in step
+    const int split = max_len >= kHalvesMinLen ? thread_split() : 0;
     if (d_w) {
         ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,
                            vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0, &ws.hdr->status};
-        if (halves) return launch_halves(p, num_chains, (int)max_len, ws.rec, ws.spill, ws.hdr, s);
+        if (split == 2) return launch_flat(p, num_chains, (int)max_len, ws.rec, ws.spill, ws.hdr, s);
+        if (split == 1) return launch_halves(p, num_chains, (int)max_len, ws.rec, ws.spill, ws.hdr, s);
         return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
     }
     ChainRowsP<false> p{d_y, nullptr, lambda, d_offsets, num_chains, (int)max_len, d_x,
                         vec_ok(d_offsets, max_len, d_y, nullptr, d_x), 0, &ws.hdr->status};
-    if (halves) return launch_halves(p, num_chains, (int)max_len, ws.rec, ws.spill, ws.hdr, s);
+    if (split == 2) return launch_flat(p, num_chains, (int)max_len, ws.rec, ws.spill, ws.hdr, s);
+    if (split == 1) return launch_halves(p, num_chains, (int)max_len, ws.rec, ws.spill, ws.hdr, s);
     return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);
 }
 

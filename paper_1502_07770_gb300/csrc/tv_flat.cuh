@@ -1,0 +1,412 @@
+// Batched row chains, one thread per chain half, with a message update of fixed shape.
+//
+// The update of Sec. 4.1 removes breakpoints from both ends of the message by scans whose
+// length depends on the data. Run by 32 lanes in step, every node costs the warp the
+// longest scan among its lanes. Here each lane instead runs its own node sequence at its
+// own pace ("flattened" loop): one iteration of the warp's loop is one fixed-shape attempt
+// at a node by every lane,
+//   - load the two entries after the first breakpoint and the two before the last one,
+//     compute the message values there (the forward recursion from the first breakpoint,
+//     the backward one from the last, Sec. 4.1), and decide which of the first three and
+//     the last three breakpoints fall below -w_i or above +w_i;
+//   - if neither side removes three or more, finish the node: place lambda^- and lambda^+
+//     on the segments found (Sec. 4.1, transformations (a) and (b)), push them, write the
+//     records (lambda^-_i, lambda^+_i) and go on to the next node;
+//   - otherwise remove two breakpoints from that side and retry the same node.
+// The two sides are evaluated independently: a breakpoint removed on the left has a value
+// below -w_i <= w_i and is never removed on the right; when the right side reaches the
+// breakpoints removed on the left, lambda^+ lies on the segment starting at lambda^-.
+// Where a probe reaches the far end of the message, the far end's exact value is used.
+//
+// Per lane the message is a linear array of S slots in shared memory (slot s of lane l at
+// row s + G, column l, 8 bytes: breakpoint lambda and stored slope s_p; the true slope is
+// s_p + abar), with G guard rows at each end for the probes. When a push would leave the
+// array the message is moved back to its middle. A message longer than S - 4 entries
+// sends the chain to the whole-chain path of the workspace.
+//
+// Inputs are staged by the whole warp: every T iterations the lanes' next steps are copied
+// into a per-lane ring of IR slots (4-byte asynchronous copies into [slot][lane], so that
+// the lanes' reads never share a bank), up to IR - T steps ahead of the slowest lane; a
+// lane that reaches the end of the staged range waits for the next copy round.
+//
+// Algorithm 2 roots chain k at node mid = n/2: lane l < 16 runs nodes 0..mid-1, lane l + 16
+// nodes n-1..mid+1; then the left lane solves the root from both messages and both lanes
+// clip their halves outwards, in step, from the records.
+#pragma once
+#include "tv_halves.cuh"
+
+namespace tvk {
+
+constexpr int FL_S = 32;   // message slots per lane
+constexpr int FL_G = 2;    // guard rows at each end
+constexpr int FL_IR = 32;  // staged steps per lane
+constexpr int FL_T = 8;    // loop iterations between copy rounds
+
+template <int NIN>
+struct alignas(16) FlatSmem {
+    union {
+        struct {
+            float2 msg[FL_S + 2 * FL_G][WARP];
+            float in[NIN][FL_IR][WARP];
+        } f;
+        struct {
+            float2 rec[2][CH][WARP];
+            float out[WARP * RP];
+        } b;
+    } u;
+};
+
+struct SlotStore {  // linear message array of one lane: entry j at row j (absolute rows)
+    unsigned base;  // shared address of row 0 of this lane
+    __device__ __forceinline__ float2 ld(int j) const
+    {
+        float2 e;
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(e.x), "=f"(e.y) : "r"(base + ((unsigned)j << 8)));
+        return e;
+    }
+};
+
+__device__ __forceinline__ float2 lds2(unsigned a)
+{
+    float2 e;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(e.x), "=f"(e.y) : "r"(a));
+    return e;
+}
+__device__ __forceinline__ void sts2(unsigned a, float x, float y)
+{
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(x), "f"(y) : "memory");
+}
+
+// L2 eviction priorities: the records, written forward and read back, are kept; the
+// streamed inputs and outputs go first.
+__device__ __forceinline__ unsigned long long l2_keep_policy()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ unsigned long long l2_stream_policy()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_keep(float2 *p, float a, float b, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;\n" ::"l"(p), "f"(a), "f"(b),
+                 "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4_hint(void *smem, const void *gmem, unsigned long long pol)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem),
+                 "l"(pol)
+                 : "memory");
+}
+// the 128-byte L2 line at p (128-byte aligned) is dropped without being written back
+__device__ __forceinline__ void l2_discard(const void *p)
+{
+    asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(p) : "memory");
+}
+
+// P: a row policy of tv_chain.cu (contiguous chains, CSR or uniform) with fields y, w, lam
+// and chain(); HAS_W = per-edge weights w.
+template <class P>
+__global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, float2 *spill,
+                                                         WsHeader *hdr, int halfmax)
+{
+    constexpr bool HAS_W = P::WI >= 0;
+    constexpr int NIN = HAS_W ? 2 : 1;
+    constexpr int S = FL_S, G = FL_G, IR = FL_IR, T = FL_T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P p = p_in;
+    if (!p.resolve()) return;
+    const int lane = threadIdx.x & (WARP - 1);
+    const int warp = threadIdx.x / WARP;
+    const int wpb = blockDim.x / WARP;
+    FlatSmem<NIN> *sm = reinterpret_cast<FlatSmem<NIN> *>(smem_raw) + warp;
+    const long long wg = (long long)blockIdx.x * wpb + warp;
+    const long long wc0 = wg * HW;
+    const long long k = wc0 + (lane & (HW - 1));
+    const bool left = lane < HW;
+    long long start = 0;
+    int n = 0;
+    if (k < p.num_chains()) {
+        if (!p.chain(k, start, n)) {
+            if (left) atomicOr(&hdr->status, ERR_BAD_CHAIN);
+            n = 0;
+        }
+    }
+    const int mid = n >> 1;
+    const int cnt = n == 0 ? 0 : (left ? mid : n - 1 - mid);  // steps of this half
+    const int cmax = __reduce_max_sync(FULL, cnt);
+    float2 *rec_w = rec + wg * (long long)halfmax * WARP;
+    const unsigned long long keep = l2_keep_policy(), stream = l2_stream_policy();
+
+    // ---------------- staging: step t of this half at in[a][t % IR][lane] ----------------
+    // left: node t (weight of edge t -> t+1); right: node n-1-t (weight of edge n-2-t -> n-1-t)
+    const float *ysrc = p.y + start + (left ? 0 : n - 1);
+    const float *wsrc = nullptr;
+    if constexpr (HAS_W) wsrc = p.w + start + (left ? 0 : n - 2);
+    const long long dir = left ? 1 : -1;
+    auto stage = [&](int t0, int t1) {  // steps [t0, t1), warp-uniform bounds
+        for (int t = t0; t < t1; ++t) {
+            if (t < cnt) {
+                cp_async4_hint(&sm->u.f.in[0][t & (IR - 1)][lane], ysrc + dir * t, stream);
+                if constexpr (HAS_W)
+                    cp_async4_hint(&sm->u.f.in[NIN - 1][t & (IR - 1)][lane], wsrc + dir * t, stream);
+            }
+        }
+        cp_async_commit();
+    };
+
+    // ---------------- message array ----------------
+    const unsigned msg0 = (unsigned)__cvta_generic_to_shared(&sm->u.f.msg[0][lane]);
+    auto slot = [&](int s) { return msg0 + ((unsigned)(s + G) << 8); };
+    const unsigned lo_lim = slot(1), hi_lim = slot(S - 2);
+
+    int hi = 0;      // steps < hi are staged and their copies complete
+    int issued = 0;  // steps < issued have copies issued
+    {
+        const int t1 = min(cmax, IR - T);
+        stage(0, t1);
+        issued = t1;
+        cp_async_wait<0>();
+        hi = issued;
+    }
+
+    unsigned PF = 0, PB = 0;          // shared addresses of the first and last breakpoint
+    float fl = 0.f, fs = 0.f, bl = 0.f;  // first breakpoint (lambda, stored slope), last lambda
+    float uF = 0.f, uB = 0.f;         // message values at the first / last breakpoint
+    float ab = 1.f, wprev = 0.f;
+    bool fresh = true;                // the current node has not been started
+    bool alive = true;
+    int j = 0;
+    bool fw = cnt > 0;
+    if (fw) {  // leaf node: m^(z) = z - c has slope 1, lambda^-+ = c -+ w
+        const float c = sm->u.f.in[0][0][lane];
+        const float w0 = HAS_W ? sm->u.f.in[NIN - 1][0][lane] : p.lam;
+        PF = slot(S / 2 - 1);
+        PB = PF + 256;
+        fl = c - w0;
+        fs = 0.f;
+        bl = c + w0;
+        sts2(PF, fl, 0.f);
+        sts2(PB, bl, -1.f);
+        st_keep(rec_w + lane, fl, bl, keep);
+        wprev = w0;
+        ab = 2.f;
+        j = 1;
+        fw = j < cnt;
+    }
+
+    // ---------------- forward pass, each lane at its own pace ----------------
+    for (int it = 0;; ++it) {
+        if ((it & (T - 1)) == 0) {
+            const int jmin = __reduce_min_sync(FULL, fw ? j : 0x7fffffff);
+            if (jmin == 0x7fffffff) break;
+            cp_async_wait<0>();
+            hi = issued;
+            const int t1 = min(cmax, jmin + IR - T);
+            if (t1 > issued) {
+                stage(issued, t1);
+                issued = t1;
+            }
+        }
+        if (!(fw && j < hi)) continue;
+        const int sl = j & (IR - 1);
+        const float c = sm->u.f.in[0][sl][lane];
+        const float w = HAS_W ? sm->u.f.in[NIN - 1][sl][lane] : p.lam;
+        const float nw = -w;
+        if (fresh) {
+            uF = fl - c - wprev;
+            uB = bl - c + wprev;
+        }
+        const unsigned d = PB - PF;  // (entries - 1) * 256
+        const bool m2 = d >= 256u, m3 = d >= 512u;
+        const float2 e1 = lds2(PF + 256), e2 = lds2(PF + 512);
+        const float2 g1 = lds2(PB - 256), g2 = lds2(PB - 512);
+        const float sl1 = fs + ab, sl2 = e1.y + ab;
+        const float r1 = g1.y + ab, r2 = g2.y + ab;
+        float u1 = fmaf(sl1, e1.x - fl, uF);
+        float u2 = fmaf(sl2, e2.x - e1.x, u1);
+        float v1 = fmaf(-r1, bl - g1.x, uB);
+        float v2 = fmaf(-r2, g1.x - g2.x, v1);
+        if (d == 256u) {  // two entries: the other end is the probe
+            u1 = uB;
+            v1 = uF;
+        }
+        if (d == 512u) {
+            u2 = uB;
+            v2 = uF;
+        }
+        const bool p0 = uF < nw, p1 = p0 && m2 && u1 < nw, p2 = p1 && m3 && u2 < nw;
+        const bool q0 = uB > w, q1 = q0 && m2 && v1 > w, q2 = q1 && m3 && v2 > w;
+        if (p2 || q2) {
+            // three or more removals on a side: remove two there and retry the node
+            if (p2) {
+                PF += 512;
+                fl = e2.x;
+                fs = e2.y;
+                uF = (d == 512u) ? uB : u2;
+            } else {
+                PB -= 512;
+                bl = g2.x;
+                uB = (d == 512u) ? uF : v2;
+            }
+            fresh = false;
+            continue;
+        }
+        // lambda^- on the segment right of the last breakpoint removed on the left (or the
+        // left end piece, slope 1); it keeps that segment's stored slope
+        const float al = p1 ? e1.x : fl;
+        const float av = p1 ? u1 : uF;
+        const float asl = p1 ? sl2 : (p0 ? sl1 : 1.f);
+        const float as = p1 ? e1.y : (p0 ? fs : 1.f - ab);
+        const float lm = al + slope_div(nw - av, asl);
+        const unsigned nPF = p1 ? PF + 256 : (p0 ? PF : PF - 256);
+        // lambda^+ on the segment left of the last breakpoint removed on the right (or the
+        // right end piece), or on lambda^-'s segment when the right side reached it
+        const unsigned kPB = q1 ? PB - 512 : (q0 ? PB - 256 : PB);  // last kept on the right
+        const bool flm = kPB <= nPF;
+        const float ar = flm ? lm : (q1 ? g1.x : bl);
+        const float avr = flm ? nw : (q1 ? v1 : uB);
+        const float asr = flm ? as + ab : (q1 ? r2 : (q0 ? r1 : 1.f));
+        const float hp = ar + slope_div(w - avr, asr);
+        const unsigned nPB = (flm ? nPF : kPB) + 256;
+        sts2(nPF, lm, as);
+        sts2(nPB, hp, -ab);
+        st_keep(rec_w + (long long)j * WARP + lane, lm, hp, keep);
+        PF = nPF;
+        PB = nPB;
+        fl = lm;
+        fs = as;
+        bl = hp;
+        wprev = w;
+        ab += 1.f;
+        fresh = true;
+        ++j;
+        fw = j < cnt;
+        if (PF < lo_lim || PB > hi_lim) {
+            // move the message back to the middle of the array
+            const int mm = (int)((PB - PF) >> 8) + 1;
+            if (mm > S - 4) {
+                alive = false;
+                fw = false;
+            } else {
+                const unsigned dst = slot((S - mm) >> 1);
+                if (dst < PF) {
+                    for (int q = 0; q < mm; ++q) {
+                        const float2 e = lds2(PF + ((unsigned)q << 8));
+                        sts2(dst + ((unsigned)q << 8), e.x, e.y);
+                    }
+                } else {
+                    for (int q = mm - 1; q >= 0; --q) {
+                        const float2 e = lds2(PF + ((unsigned)q << 8));
+                        sts2(dst + ((unsigned)q << 8), e.x, e.y);
+                    }
+                }
+                PB = dst + (PB - PF);
+                PF = dst;
+            }
+        }
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+
+    // ---------------- root ----------------
+    const SlotStore SS{msg0};
+    const int F = (int)((PF - msg0) >> 8), B = (int)((PB - msg0) >> 8);
+    const int FR = __shfl_down_sync(FULL, F, HW), BR = __shfl_down_sync(FULL, B, HW);
+    const float wR = __shfl_down_sync(FULL, wprev, HW);
+    const int cntR = __shfl_down_sync(FULL, cnt, HW);
+    const bool aliveR = __shfl_down_sync(FULL, (int)alive, HW) != 0;
+    const bool ok = __shfl_sync(FULL, (int)(alive && aliveR), lane & (HW - 1)) != 0;
+    float xroot = 0.f;
+    if (left && n > 0 && ok) {
+        float c_root, w_unused;
+        p.unary_direct(mid, n, k, start, c_root, w_unused);
+        const SlotStore SR{msg0 + HW * 8};  // lane + 16's array
+        xroot = half_root(SS, cnt > 0 ? F : 0, cnt > 0 ? B : -1, (float)cnt, wprev, SR,
+                          cntR > 0 ? FR : 0, cntR > 0 ? BR : -1, (float)cntR, wR, c_root,
+                          2 * S + 4);
+        p.emit_direct(mid, k, start, xroot, c_root);
+    }
+    xroot = __shfl_sync(FULL, xroot, lane & (HW - 1));
+    __syncwarp();
+
+    // ---------------- backward pass, outwards from the root, in step ----------------
+    const int cnt_eff = ok ? cnt : 0;
+    float xv = xroot;
+    const bool vout = p.out_vec();
+    float *dst = p.x + start;
+    auto load_recs = [&](int buf, int ch) {
+#pragma unroll 4
+        for (int u = 0; u < CH; ++u) {
+            const int jj = ch * CH + u;
+            if (jj < cnt_eff) cp_async8(&sm->u.b.rec[buf][u][lane], rec_w + (long long)jj * WARP + lane);
+        }
+    };
+    const int nchunks = (cmax + CH - 1) / CH;
+    int b = 0;
+    if (nchunks > 0) load_recs(0, nchunks - 1);
+    cp_async_commit();
+    for (int ch = nchunks - 1; ch >= 0; --ch) {
+        if (ch > 0) load_recs(b ^ 1, ch - 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp();
+        // this chunk's records are in shared memory: drop their L2 lines (two per step)
+        if (lane < 2 * CH) {
+            const int jj = ch * CH + (lane >> 1);
+            if (jj < cmax) l2_discard(rec_w + (long long)jj * WARP + (lane & 1) * HW);
+        }
+        if (vout) {
+#pragma unroll
+            for (int g = CH / 4 - 1; g >= 0; --g) {
+                float xs[4];
+#pragma unroll
+                for (int e = 3; e >= 0; --e) {
+                    const int jj = 4 * g + e;
+                    xs[e] = 0.f;
+                    if (ch * CH + jj < cnt_eff) {
+                        const float2 r = sm->u.b.rec[b][jj][lane];
+                        xv = clip_to(xv, r.x, r.y);
+                        xs[e] = xv;
+                    }
+                }
+                const int j0 = ch * CH + 4 * g;
+                const int lo = left ? j0 : n - 4 - j0;
+                if (j0 + 3 < cnt_eff) {
+                    *reinterpret_cast<float4 *>(dst + lo) = left ? make_float4(xs[0], xs[1], xs[2], xs[3])
+                                                                 : make_float4(xs[3], xs[2], xs[1], xs[0]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (j0 + e < cnt_eff) dst[left ? lo + e : lo + 3 - e] = xs[e];
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int jj = CH - 1; jj >= 0; --jj) {
+                const int t = ch * CH + jj;
+                if (t < cnt_eff) {
+                    const float2 r = sm->u.b.rec[b][jj][lane];
+                    xv = clip_to(xv, r.x, r.y);
+                    dst[left ? t : n - 1 - t] = xv;
+                }
+            }
+        }
+        __syncwarp();
+        b ^= 1;
+    }
+    cp_async_wait<0>();
+    if (left && n > 0 && !ok) {
+        atomicAdd(&hdr->overflowed, 1ull);
+        half_fallback(p, k, start, n, spill + p.spill_off(k, start), rec_w + lane,
+                      (float *)nullptr);
+    }
+}
+
+}  // namespace tvk

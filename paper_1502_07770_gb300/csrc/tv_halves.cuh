@@ -184,11 +184,12 @@ __device__ void half_fallback(const P &p, long long k, long long start, int n, f
 
 // Root of z - c + m_L(z) + m_R(z): each message is -w left of its first breakpoint,
 // +w right of its last, with slope s_p + abar right of breakpoint p (abar = the half's
-// node count); an empty half contributes 0.
-template <int RING>
-__device__ __forceinline__ float half_root(const RingStore<RING> &SL, int FL, int BL, float aL,
-                                           float wL, const RingStore<RING> &SR, int FR, int BR,
-                                           float aR, float wR, float c)
+// node count); an empty half contributes 0. St: a store with ld(index) (ring or linear);
+// max_steps bounds the walk (both messages hold at most max_steps - 4 breakpoints).
+template <class St>
+__device__ __forceinline__ float half_root(const St &SL, int FL, int BL, float aL, float wL,
+                                           const St &SR, int FR, int BR, float aR, float wR,
+                                           float c, int max_steps)
 {
     const bool hasL = BL >= FL, hasR = BR >= FR;
     if (!hasL) wL = 0.f;
@@ -200,7 +201,7 @@ __device__ __forceinline__ float half_root(const RingStore<RING> &SL, int FL, in
     if (!(zc < INFINITY)) return c;  // no message at all
     float hc = zc - c - wL - wR;      // h at the first breakpoint (slope 1 to its left)
     float slope = 1.f;                // slope of h on the segment ending at zc
-    for (int it = 0; it < 2 * RING + 4; ++it) {
+    for (int it = 0; it < max_steps; ++it) {
         if (hc >= 0.f) return zc - hc / slope;
         // pass the breakpoint(s) at zc; the slopes right of it come from the last
         // breakpoint passed in each half
@@ -356,7 +357,8 @@ __global__ void __launch_bounds__(128) chain_halves_kernel(P p_in, float2 *rec, 
         if constexpr (P::CREC) c_root = p.c_direct(mid, k, start);
         const RingStore<RING> SR{S.base + HW * 8};  // lane + 16's ring
         xroot = half_root(S, cnt > 0 ? d.F : 0, cnt > 0 ? d.B : -1, (float)cnt, d.w_prev, SR,
-                          cntR > 0 ? FR : 0, cntR > 0 ? BR : -1, (float)cntR, wR, c_root);
+                          cntR > 0 ? FR : 0, cntR > 0 ? BR : -1, (float)cntR, wR, c_root,
+                          2 * RING + 4);
         p.emit_direct(mid, k, start, xroot, c_root);
     }
     xroot = __shfl_sync(FULL, xroot, lane & (HW - 1));

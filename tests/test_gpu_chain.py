@@ -168,16 +168,16 @@ def test_middle_rooted_chains(split):
         _lib.set_coop_split(1)
 
 
-@pytest.fixture(params=[1, 0], ids=["middle-rooted", "one-end"])
+@pytest.fixture(params=[2, 1, 0], ids=["fixed-shape", "middle-rooted", "one-end"])
 def thread_path(request):
     """Every batch on the one-thread-per-chain kernels: chains of 64 nodes or more rooted
-    at their middle node with a thread per half (1, the default), or one thread from one
-    end (0)."""
+    at their middle node with a thread per half, each lane at its own pace (2, the
+    default) or with the lanes' updates in step (1), or one thread from one end (0)."""
     _lib.set_coop_max_chains(1)
-    _lib.set_thread_split(bool(request.param))
+    _lib.set_thread_split(request.param)
     yield
     _lib.set_coop_max_chains(0)
-    _lib.set_thread_split(True)
+    _lib.set_thread_split(2)
 
 
 def test_thread_kernel_rows_columns_weights(thread_path):
