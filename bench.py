@@ -87,7 +87,8 @@ def peaks():
 # shared headers): a change to any of them voids that kernel's recorded traffic
 KERNEL_SOURCES = {
     "tv2d": ["tv2d.cu", "tv2d_common.cuh", "tv_coop.cuh", "tv_dp.cuh", "tv_launch.cuh", "tv_host.h"],
-    "chain": ["tv_chain.cu", "tv_halves.cuh", "tv_coop.cuh", "tv_dp.cuh", "tv_launch.cuh", "tv_host.h"],
+    "chain": ["tv_chain.cu", "tv_flat.cuh", "tv_halves.cuh", "tv_coop.cuh", "tv_dp.cuh", "tv_launch.cuh",
+              "tv_host.h"],
     "pq": ["tv_pq.cu", "tv_coop.cuh", "tv_dp.cuh", "tv_launch.cuh", "tv_host.h"],
 }
 

@@ -569,6 +569,7 @@ tv_status launch_batch(const P &p, long long nchains, float2 *rec, float *crec, 
 constexpr int kRingHalf = 16;
 
 constexpr int kHalvesMinLen = 64;
+constexpr int kFlatMinLenW = 512;
 
 template <bool HAS_W>
 tv_status launch_halves(const ChainRowsP<HAS_W> &p, long long nchains, int max_len, float2 *rec,
@@ -831,8 +832,11 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     }
     // chains of 64 nodes or more: two threads per chain (twice the warps, half the steps
     // each, and a 16-entry ring that keeps every warp of a full batch resident)
-    // mode 2 (default): the fixed-shape update; 1: the same halves with the scans in step
-    const int split = max_len >= kHalvesMinLen ? thread_split() : 0;
+    // mode 2 (default): the fixed-shape update, except per-edge weights on chains shorter
+    // than kFlatMinLenW nodes, where the halves with the scans in step (mode 1) measured
+    // faster (the flat kernel stages every weight with its own 4-byte copy)
+    int split = max_len >= kHalvesMinLen ? thread_split() : 0;
+    if (split == 2 && d_w && max_len < kFlatMinLenW) split = 1;
     if (d_w) {
         ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,
                            vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0, &ws.hdr->status};

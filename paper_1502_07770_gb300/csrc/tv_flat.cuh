@@ -3,8 +3,8 @@
 // The update of Sec. 4.1 removes breakpoints from both ends of the message by scans whose
 // length depends on the data. Run by 32 lanes in step, every node costs the warp the
 // longest scan among its lanes. Here each lane instead runs its own node sequence at its
-// own pace ("flattened" loop): one iteration of the warp's loop is one fixed-shape attempt
-// at a node by every lane,
+// own pace: one iteration of the warp's loop is one fixed-shape, branch-free attempt at a
+// node by every lane,
 //   - load the two entries after the first breakpoint and the two before the last one,
 //     compute the message values there (the forward recursion from the first breakpoint,
 //     the backward one from the last, Sec. 4.1), and decide which of the first three and
@@ -13,25 +13,29 @@
 //     on the segments found (Sec. 4.1, transformations (a) and (b)), push them, write the
 //     records (lambda^-_i, lambda^+_i) and go on to the next node;
 //   - otherwise remove two breakpoints from that side and retry the same node.
-// The two sides are evaluated independently: a breakpoint removed on the left has a value
-// below -w_i <= w_i and is never removed on the right; when the right side reaches the
-// breakpoints removed on the left, lambda^+ lies on the segment starting at lambda^-.
-// Where a probe reaches the far end of the message, the far end's exact value is used.
+// The state is updated by selects and the three stores are predicated, so the lanes of a
+// warp never take different paths through the loop body. The two sides are evaluated
+// independently: a breakpoint removed on the left has a value below -w_i <= w_i and is
+// never removed on the right; when the right side reaches the breakpoints removed on the
+// left, lambda^+ lies on the segment starting at lambda^-. Where a probe reaches the far
+// end of the message, the far end's exact value is used.
 //
 // Per lane the message is a linear array of S slots in shared memory (slot s of lane l at
 // row s + G, column l, 8 bytes: breakpoint lambda and stored slope s_p; the true slope is
 // s_p + abar), with G guard rows at each end for the probes. When a push would leave the
-// array the message is moved back to its middle. A message longer than S - 4 entries
-// sends the chain to the whole-chain path of the workspace.
+// array the message is moved back to its middle (a warp vote keeps that rare copy off the
+// common path). A message longer than S - 4 entries sends the chain to the whole-chain
+// path of the workspace.
 //
-// Inputs are staged by the whole warp: every T iterations the lanes' next steps are copied
-// into a per-lane ring of IR slots (4-byte asynchronous copies into [slot][lane], so that
-// the lanes' reads never share a bank), up to IR - T steps ahead of the slowest lane; a
-// lane that reaches the end of the staged range waits for the next copy round.
+// Inputs are staged by the whole warp: between rounds of T iterations the lanes' next steps
+// are copied into a per-lane ring of IR slots (4-byte asynchronous copies into
+// [slot][lane], so that the lanes' reads never share a bank), up to IR - T steps ahead of
+// the slowest lane; a lane that reaches the end of the staged range waits for the next
+// round.
 //
 // Algorithm 2 roots chain k at node mid = n/2: lane l < 16 runs nodes 0..mid-1, lane l + 16
-// nodes n-1..mid+1; then the left lane solves the root from both messages and both lanes
-// clip their halves outwards, in step, from the records.
+// nodes n-1..mid+1; then the left lane solves the root from both messages (flat_root) and
+// both lanes clip their halves outwards, in step, from the records.
 #pragma once
 #include "tv_halves.cuh"
 
@@ -56,65 +60,80 @@ struct alignas(16) FlatSmem {
     } u;
 };
 
-struct SlotStore {  // linear message array of one lane: entry j at row j (absolute rows)
-    unsigned base;  // shared address of row 0 of this lane
-    __device__ __forceinline__ float2 ld(int j) const
-    {
-        float2 e;
-        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(e.x), "=f"(e.y) : "r"(base + ((unsigned)j << 8)));
-        return e;
-    }
-};
-
 __device__ __forceinline__ float2 lds2(unsigned a)
 {
     float2 e;
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(e.x), "=f"(e.y) : "r"(a));
     return e;
 }
+__device__ __forceinline__ float lds1(unsigned a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts2_if(bool p, unsigned a, float x, float y)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %3, 0;\n @q st.shared.v2.f32 [%0], {%1, %2};\n}\n" ::"r"(a),
+                 "f"(x), "f"(y), "r"((unsigned)p)
+                 : "memory");
+}
+__device__ __forceinline__ void stg2_if(bool p, float2 *g, float x, float y)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %3, 0;\n @q st.global.v2.f32 [%0], {%1, %2};\n}\n" ::"l"(g),
+                 "f"(x), "f"(y), "r"((unsigned)p)
+                 : "memory");
+}
 __device__ __forceinline__ void sts2(unsigned a, float x, float y)
 {
     asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(x), "f"(y) : "memory");
 }
 
-// L2 eviction priorities: the records, written forward and read back, are kept; the
-// streamed inputs and outputs go first.
-__device__ __forceinline__ unsigned long long l2_keep_policy()
+// Root of h(z) = z - c + m_L(z) + m_R(z) (Algorithm 2 rooted at the middle node): each half's
+// message is -w left of its first breakpoint and +w right of its last, with slope s_p + a
+// right of breakpoint p (a = the half's node count); h has slope 1 left of all breakpoints.
+// The two breakpoint sequences (rows FL..BL of the array at baseL, FR..BR at baseR; an empty
+// half has B < F and w = 0) are walked in increasing order, h is accumulated segment by
+// segment, and the root is placed on the segment where h reaches 0.
+__device__ __forceinline__ float flat_root(unsigned baseL, int FL, int BL, float aL, float wL,
+                                           unsigned baseR, int FR, int BR, float aR, float wR,
+                                           float c)
 {
-    unsigned long long pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ unsigned long long l2_stream_policy()
-{
-    unsigned long long pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ void st_keep(float2 *p, float a, float b, unsigned long long pol)
-{
-    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;\n" ::"l"(p), "f"(a), "f"(b),
-                 "l"(pol)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async4_hint(void *smem, const void *gmem, unsigned long long pol)
-{
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem),
-                 "l"(pol)
-                 : "memory");
-}
-// the 128-byte L2 line at p (128-byte aligned) is dropped without being written back
-__device__ __forceinline__ void l2_discard(const void *p)
-{
-    asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(p) : "memory");
+    auto lam = [](unsigned base, int r) { return lds2(base + ((unsigned)r << 8)); };
+    int iL = FL, iR = FR;
+    float zL = iL <= BL ? lam(baseL, iL).x : INFINITY;
+    float zR = iR <= BR ? lam(baseR, iR).x : INFINITY;
+    float z = fminf(zL, zR);
+    if (!(z < INFINITY)) return c;  // no message: z = c
+    float h = z - c - (BL >= FL ? wL : 0.f) - (BR >= FR ? wR : 0.f);
+    float gL = 0.f, gR = 0.f;  // slope of each message right of the breakpoints passed
+    const int steps = (BL - FL + 1 > 0 ? BL - FL + 1 : 0) + (BR - FR + 1 > 0 ? BR - FR + 1 : 0);
+    for (int it = 0; it <= steps; ++it) {
+        const float sl = 1.f + gL + gR;
+        if (h >= 0.f) return z - h / sl;
+        if (iL <= BL && zL == z) {
+            gL = lam(baseL, iL).y + aL;
+            ++iL;
+            zL = iL <= BL ? lam(baseL, iL).x : INFINITY;
+        }
+        if (iR <= BR && zR == z) {
+            gR = lam(baseR, iR).y + aR;
+            ++iR;
+            zR = iR <= BR ? lam(baseR, iR).x : INFINITY;
+        }
+        const float s2 = 1.f + gL + gR;
+        const float zn = fminf(zL, zR);
+        if (!(zn < INFINITY)) return z - h / s2;
+        h = fmaf(s2, zn - z, h);
+        z = zn;
+    }
+    return z - h / (1.f + gL + gR);
 }
 
 // P: a row policy of tv_chain.cu (contiguous chains, CSR or uniform) with fields y, w, lam
 // and chain(); HAS_W = per-edge weights w.
 template <class P>
-__global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, float2 *spill,
-                                                         WsHeader *hdr, int halfmax)
+__global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *hdr, int halfmax)
 {
     constexpr bool HAS_W = P::WI >= 0;
     constexpr int NIN = HAS_W ? 2 : 1;
@@ -142,7 +161,6 @@ __global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, fl
     const int cnt = n == 0 ? 0 : (left ? mid : n - 1 - mid);  // steps of this half
     const int cmax = __reduce_max_sync(FULL, cnt);
     float2 *rec_w = rec + wg * (long long)halfmax * WARP;
-    const unsigned long long keep = l2_keep_policy(), stream = l2_stream_policy();
 
     // ---------------- staging: step t of this half at in[a][t % IR][lane] ----------------
     // left: node t (weight of edge t -> t+1); right: node n-1-t (weight of edge n-2-t -> n-1-t)
@@ -153,9 +171,9 @@ __global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, fl
     auto stage = [&](int t0, int t1) {  // steps [t0, t1), warp-uniform bounds
         for (int t = t0; t < t1; ++t) {
             if (t < cnt) {
-                cp_async4_hint(&sm->u.f.in[0][t & (IR - 1)][lane], ysrc + dir * t, stream);
+                cp_async4(&sm->u.f.in[0][t & (IR - 1)][lane], ysrc + dir * t);
                 if constexpr (HAS_W)
-                    cp_async4_hint(&sm->u.f.in[NIN - 1][t & (IR - 1)][lane], wsrc + dir * t, stream);
+                    cp_async4(&sm->u.f.in[NIN - 1][t & (IR - 1)][lane], wsrc + dir * t);
             }
         }
         cp_async_commit();
@@ -165,6 +183,7 @@ __global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, fl
     const unsigned msg0 = (unsigned)__cvta_generic_to_shared(&sm->u.f.msg[0][lane]);
     auto slot = [&](int s) { return msg0 + ((unsigned)(s + G) << 8); };
     const unsigned lo_lim = slot(1), hi_lim = slot(S - 2);
+    const unsigned in0 = (unsigned)__cvta_generic_to_shared(&sm->u.f.in[0][0][lane]);
 
     int hi = 0;      // steps < hi are staged and their copies complete
     int issued = 0;  // steps < issued have copies issued
@@ -176,7 +195,7 @@ __global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, fl
         hi = issued;
     }
 
-    unsigned PF = 0, PB = 0;          // shared addresses of the first and last breakpoint
+    unsigned PF = slot(S / 2 - 1), PB = slot(S / 2);  // shared addresses of the first and last breakpoint
     float fl = 0.f, fs = 0.f, bl = 0.f;  // first breakpoint (lambda, stored slope), last lambda
     float uF = 0.f, uB = 0.f;         // message values at the first / last breakpoint
     float ab = 1.f, wprev = 0.f;
@@ -194,7 +213,7 @@ __global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, fl
         bl = c + w0;
         sts2(PF, fl, 0.f);
         sts2(PB, bl, -1.f);
-        st_keep(rec_w + lane, fl, bl, keep);
+        rec_w[lane] = make_float2(fl, bl);
         wprev = w0;
         ab = 2.f;
         j = 1;
@@ -202,113 +221,103 @@ __global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, fl
     }
 
     // ---------------- forward pass, each lane at its own pace ----------------
-    for (int it = 0;; ++it) {
-        if ((it & (T - 1)) == 0) {
-            const int jmin = __reduce_min_sync(FULL, fw ? j : 0x7fffffff);
-            if (jmin == 0x7fffffff) break;
-            cp_async_wait<0>();
-            hi = issued;
+    // Rounds of T loop iterations; between rounds the warp refills the staging rings. In an
+    // iteration a lane with a staged node either finishes it or removes two breakpoints.
+    for (;;) {
+        __syncwarp();
+        const int jmin = __reduce_min_sync(FULL, fw ? j : 0x7fffffff);
+        if (jmin == 0x7fffffff) break;
+        cp_async_wait<0>();
+        hi = issued;
+        {
             const int t1 = min(cmax, jmin + IR - T);
             if (t1 > issued) {
                 stage(issued, t1);
                 issued = t1;
             }
         }
-        if (!(fw && j < hi)) continue;
-        const int sl = j & (IR - 1);
-        const float c = sm->u.f.in[0][sl][lane];
-        const float w = HAS_W ? sm->u.f.in[NIN - 1][sl][lane] : p.lam;
-        const float nw = -w;
-        if (fresh) {
-            uF = fl - c - wprev;
-            uB = bl - c + wprev;
-        }
-        const unsigned d = PB - PF;  // (entries - 1) * 256
-        const bool m2 = d >= 256u, m3 = d >= 512u;
-        const float2 e1 = lds2(PF + 256), e2 = lds2(PF + 512);
-        const float2 g1 = lds2(PB - 256), g2 = lds2(PB - 512);
-        const float sl1 = fs + ab, sl2 = e1.y + ab;
-        const float r1 = g1.y + ab, r2 = g2.y + ab;
-        float u1 = fmaf(sl1, e1.x - fl, uF);
-        float u2 = fmaf(sl2, e2.x - e1.x, u1);
-        float v1 = fmaf(-r1, bl - g1.x, uB);
-        float v2 = fmaf(-r2, g1.x - g2.x, v1);
-        if (d == 256u) {  // two entries: the other end is the probe
-            u1 = uB;
-            v1 = uF;
-        }
-        if (d == 512u) {
-            u2 = uB;
-            v2 = uF;
-        }
-        const bool p0 = uF < nw, p1 = p0 && m2 && u1 < nw, p2 = p1 && m3 && u2 < nw;
-        const bool q0 = uB > w, q1 = q0 && m2 && v1 > w, q2 = q1 && m3 && v2 > w;
-        if (p2 || q2) {
-            // three or more removals on a side: remove two there and retry the node
-            if (p2) {
-                PF += 512;
-                fl = e2.x;
-                fs = e2.y;
-                uF = (d == 512u) ? uB : u2;
-            } else {
-                PB -= 512;
-                bl = g2.x;
-                uB = (d == 512u) ? uF : v2;
-            }
-            fresh = false;
-            continue;
-        }
-        // lambda^- on the segment right of the last breakpoint removed on the left (or the
-        // left end piece, slope 1); it keeps that segment's stored slope
-        const float al = p1 ? e1.x : fl;
-        const float av = p1 ? u1 : uF;
-        const float asl = p1 ? sl2 : (p0 ? sl1 : 1.f);
-        const float as = p1 ? e1.y : (p0 ? fs : 1.f - ab);
-        const float lm = al + slope_div(nw - av, asl);
-        const unsigned nPF = p1 ? PF + 256 : (p0 ? PF : PF - 256);
-        // lambda^+ on the segment left of the last breakpoint removed on the right (or the
-        // right end piece), or on lambda^-'s segment when the right side reached it
-        const unsigned kPB = q1 ? PB - 512 : (q0 ? PB - 256 : PB);  // last kept on the right
-        const bool flm = kPB <= nPF;
-        const float ar = flm ? lm : (q1 ? g1.x : bl);
-        const float avr = flm ? nw : (q1 ? v1 : uB);
-        const float asr = flm ? as + ab : (q1 ? r2 : (q0 ? r1 : 1.f));
-        const float hp = ar + slope_div(w - avr, asr);
-        const unsigned nPB = (flm ? nPF : kPB) + 256;
-        sts2(nPF, lm, as);
-        sts2(nPB, hp, -ab);
-        st_keep(rec_w + (long long)j * WARP + lane, lm, hp, keep);
-        PF = nPF;
-        PB = nPB;
-        fl = lm;
-        fs = as;
-        bl = hp;
-        wprev = w;
-        ab += 1.f;
-        fresh = true;
-        ++j;
-        fw = j < cnt;
-        if (PF < lo_lim || PB > hi_lim) {
-            // move the message back to the middle of the array
-            const int mm = (int)((PB - PF) >> 8) + 1;
-            if (mm > S - 4) {
-                alive = false;
-                fw = false;
-            } else {
-                const unsigned dst = slot((S - mm) >> 1);
-                if (dst < PF) {
-                    for (int q = 0; q < mm; ++q) {
-                        const float2 e = lds2(PF + ((unsigned)q << 8));
-                        sts2(dst + ((unsigned)q << 8), e.x, e.y);
-                    }
-                } else {
-                    for (int q = mm - 1; q >= 0; --q) {
-                        const float2 e = lds2(PF + ((unsigned)q << 8));
-                        sts2(dst + ((unsigned)q << 8), e.x, e.y);
+#pragma unroll 1
+        for (int it = 0; it < T; ++it) {
+            const bool act = fw && j < hi;
+            const unsigned ia = in0 + ((unsigned)(j & (IR - 1)) << 7);
+            const float c = lds1(ia);
+            const float w = HAS_W ? lds1(ia + IR * 128) : p.lam;
+            const float nw = -w;
+            const float uF0 = fresh ? fl - c - wprev : uF;
+            const float uB0 = fresh ? bl - c + wprev : uB;
+            const unsigned d = PB - PF;  // (entries - 1) * 256
+            const bool m2 = d >= 256u, m3 = d >= 512u, d2 = d == 256u, d3 = d == 512u;
+            const float2 e1 = lds2(PF + 256), e2 = lds2(PF + 512);
+            const float2 g1 = lds2(PB - 256), g2 = lds2(PB - 512);
+            const float sl1 = fs + ab, sl2 = e1.y + ab;
+            const float r1 = g1.y + ab, r2 = g2.y + ab;
+            float u1 = fmaf(sl1, e1.x - fl, uF0);
+            float u2 = fmaf(sl2, e2.x - e1.x, u1);
+            float v1 = fmaf(-r1, bl - g1.x, uB0);
+            float v2 = fmaf(-r2, g1.x - g2.x, v1);
+            u1 = d2 ? uB0 : u1;
+            v1 = d2 ? uF0 : v1;
+            u2 = d3 ? uB0 : u2;
+            v2 = d3 ? uF0 : v2;
+            const bool p0 = uF0 < nw, p1 = p0 && m2 && u1 < nw, p2 = p1 && m3 && u2 < nw;
+            const bool q0 = uB0 > w, q1 = q0 && m2 && v1 > w, q2 = q1 && m3 && v2 > w;
+            // lambda^- / lambda^+ as if the node finishes now
+            const float al = p1 ? e1.x : fl;
+            const float av = p1 ? u1 : uF0;
+            const float asl = p1 ? sl2 : (p0 ? sl1 : 1.f);
+            const float as = p1 ? e1.y : (p0 ? fs : 1.f - ab);
+            const float lm = al + slope_div(nw - av, asl);
+            const unsigned nPF = p1 ? PF + 256 : (p0 ? PF : PF - 256);
+            const unsigned kPB = q1 ? PB - 512 : (q0 ? PB - 256 : PB);
+            const bool flm = kPB <= nPF;
+            const float ar = flm ? lm : (q1 ? g1.x : bl);
+            const float avr = flm ? nw : (q1 ? v1 : uB0);
+            const float asr = flm ? as + ab : (q1 ? r2 : (q0 ? r1 : 1.f));
+            const float hp = ar + slope_div(w - avr, asr);
+            const unsigned nPB = (flm ? nPF : kPB) + 256;
+            const bool done = act && !p2 && !q2;  // the node finishes
+            const bool cL = act && p2;            // remove two on the left and retry
+            const bool cR = act && !p2 && q2;     // remove two on the right and retry
+            sts2_if(done, nPF, lm, as);
+            sts2_if(done, nPB, hp, -ab);
+            stg2_if(done, rec_w + (long long)j * WARP + lane, lm, hp);
+            PF = done ? nPF : (cL ? PF + 512 : PF);
+            PB = done ? nPB : (cR ? PB - 512 : PB);
+            fl = done ? lm : (cL ? e2.x : fl);
+            fs = done ? as : (cL ? e2.y : fs);
+            bl = done ? hp : (cR ? g2.x : bl);
+            uF = cL ? (d3 ? uB0 : u2) : uF0;
+            uB = cR ? (d3 ? uF0 : v2) : uB0;
+            fresh = done || (fresh && !act);
+            wprev = done ? w : wprev;
+            ab = done ? ab + 1.f : ab;
+            j = done ? j + 1 : j;
+            fw = done ? j < cnt : fw;
+            const bool rc = done && (PF < lo_lim || PB > hi_lim);
+            if (__any_sync(FULL, rc)) {
+                if (rc) {
+                    // move the message back to the middle of the array
+                    const int mm = (int)((PB - PF) >> 8) + 1;
+                    if (mm > S - 4) {
+                        alive = false;
+                        fw = false;
+                    } else {
+                        const unsigned dst = slot((S - mm) >> 1);
+                        if (dst < PF) {
+                            for (int q = 0; q < mm; ++q) {
+                                const float2 e = lds2(PF + ((unsigned)q << 8));
+                                sts2(dst + ((unsigned)q << 8), e.x, e.y);
+                            }
+                        } else {
+                            for (int q = mm - 1; q >= 0; --q) {
+                                const float2 e = lds2(PF + ((unsigned)q << 8));
+                                sts2(dst + ((unsigned)q << 8), e.x, e.y);
+                            }
+                        }
+                        PB = dst + (PB - PF);
+                        PF = dst;
                     }
                 }
-                PB = dst + (PB - PF);
-                PF = dst;
             }
         }
     }
@@ -316,7 +325,6 @@ __global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, fl
     __syncwarp();
 
     // ---------------- root ----------------
-    const SlotStore SS{msg0};
     const int F = (int)((PF - msg0) >> 8), B = (int)((PB - msg0) >> 8);
     const int FR = __shfl_down_sync(FULL, F, HW), BR = __shfl_down_sync(FULL, B, HW);
     const float wR = __shfl_down_sync(FULL, wprev, HW);
@@ -327,10 +335,9 @@ __global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, fl
     if (left && n > 0 && ok) {
         float c_root, w_unused;
         p.unary_direct(mid, n, k, start, c_root, w_unused);
-        const SlotStore SR{msg0 + HW * 8};  // lane + 16's array
-        xroot = half_root(SS, cnt > 0 ? F : 0, cnt > 0 ? B : -1, (float)cnt, wprev, SR,
-                          cntR > 0 ? FR : 0, cntR > 0 ? BR : -1, (float)cntR, wR, c_root,
-                          2 * S + 4);
+        xroot = flat_root(msg0, cnt > 0 ? F : 0, cnt > 0 ? B : -1, (float)cnt, wprev,
+                          msg0 + HW * 8, cntR > 0 ? FR : 0, cntR > 0 ? BR : -1, (float)cntR, wR,
+                          c_root);  // lane + 16's array is 16 columns along
         p.emit_direct(mid, k, start, xroot, c_root);
     }
     xroot = __shfl_sync(FULL, xroot, lane & (HW - 1));
@@ -357,11 +364,6 @@ __global__ void __launch_bounds__(128) chain_flat_kernel(P p_in, float2 *rec, fl
         cp_async_commit();
         cp_async_wait<1>();
         __syncwarp();
-        // this chunk's records are in shared memory: drop their L2 lines (two per step)
-        if (lane < 2 * CH) {
-            const int jj = ch * CH + (lane >> 1);
-            if (jj < cmax) l2_discard(rec_w + (long long)jj * WARP + (lane & 1) * HW);
-        }
         if (vout) {
 #pragma unroll
             for (int g = CH / 4 - 1; g >= 0; --g) {
