@@ -769,7 +769,7 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and world == 1:
-        result["cpu_baseline"] = cpu_baseline(f_np, args.cpu_seconds, base[:64], CHAIN_LAM)
+        result["cpu_baseline"] = cpu_baseline(f_np, args.cpu_seconds, np.tile(base, (8, 1)), CHAIN_LAM)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -456,6 +456,16 @@ tv_status tv_net_pack_input(const float *d_f, int B, int H, int W, const float *
  * d_target: *d_loss = mean (y - target)^2 if d_loss (block partials in the workspace,
  * summed in a fixed order) and, if d_grad_o, its gradient with respect to o (BF16, 16
  * channels, channels 1..15 zero). d_ws may be NULL when d_loss is. */
+/* Inference-only form of the first layer, on the CUDA cores. The network's input has two
+ * non-zero channels (the image and its lambda, 2..15 zero), so the first layer needs no
+ * packed input: tv_net_first_layer reads the FP32 images d_f (B x H x W) and d_lam, rounds
+ * both to BF16 as tv_net_pack_input would, and writes the ReLU'd 32-channel BF16
+ * activation (16-byte aligned) of the 16 -> 32 layer with weights d_w ([32][3][3][16]
+ * BF16; input channels 2..15 are not read) and bias d_bias (may be NULL). It equals
+ * tv_net_pack_input followed by tv_net_conv3x3 up to the order of FP32 sums. */
+tv_status tv_net_first_layer(const float *d_f, int B, int H, int W, const float *d_lam,
+                             const void *d_w, const float *d_bias, void *d_act_out,
+                             tv_stream_t stream);
 tv_status tv_net_dual_head(const float *d_o, int B, int H, int W, const float *d_lam,
                            const float *d_target, float *d_y, float *d_loss, void *d_grad_o,
                            void *d_ws, size_t ws_bytes, tv_stream_t stream);

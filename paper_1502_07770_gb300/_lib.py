@@ -97,6 +97,8 @@ SIGNATURES = {
                                          _p]),
     "tv_net_dual_head": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _p, _p,
                                         _p, _p, _p, _sz, _p]),
+    "tv_net_first_layer": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _p,
+                                          _p, _p, _p]),
     "tv_net_cast_bf16": (ctypes.c_int, [_p, _i64, _p, _p]),
     "tv_net_adam": (ctypes.c_int, [_p, _p, _p, _p, _i64, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, ctypes.c_int, _p, _p]),

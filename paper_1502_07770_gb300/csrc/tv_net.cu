@@ -895,6 +895,93 @@ __global__ void cast_bf16(const float *a, long long n, __nv_bfloat16 *out)
         out[i] = __float2bfloat16(a[i]);
 }
 
+
+// ---------------------------------------------------------------- inference --
+// The first layer of the network specialised for inference, on the CUDA cores.
+constexpr int FT = 16;  // 16 x 16 output pixels per block, 256 threads
+
+// Layer 1: the packed input has two non-zero channels, the image and lambda, both rounded
+// to BF16 and zero outside the image, so
+//     out[co] = bias[co] + sum over the taps inside the image of w[co][tap][0] f + w[co][tap][1] lambda,
+// then ReLU and BF16 (32 channels). The products of BF16 values are exact in FP32 and are
+// summed in FP32, as on the tensor cores (in another order); no packed input is written.
+// 128 threads per 16 x 16 tile, two pixels (rows ty and ty + 8) per thread, so that each
+// weight read from shared memory serves both.
+__device__ __forceinline__ void store_act32(__nv_bfloat16 *dst, const float (&acc)[32])
+{
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        unsigned u[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(acc[q * 8 + 2 * e], 0.f),
+                                                           fmaxf(acc[q * 8 + 2 * e + 1], 0.f));
+            u[e] = *reinterpret_cast<const unsigned *>(&h);
+        }
+        d[q] = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+}
+
+__global__ void __launch_bounds__(128)
+    first_layer(const float *f, int H, int W, const float *lam, const __nv_bfloat16 *Wt,
+                const float *bias, __nv_bfloat16 *act)
+{
+    __shared__ __align__(16) float wsm[9][2][32];  // [tap][image, lambda][co]
+    __shared__ __align__(16) float bsm[32];
+    __shared__ float patch[FT + 2][FT + 2];
+    const int b = blockIdx.z;
+    const int x0 = blockIdx.x * FT, y0 = blockIdx.y * FT;
+    for (int t = threadIdx.x; t < 9 * 2 * 32; t += blockDim.x) {
+        const int co = t & 31, ch = (t >> 5) & 1, tap = t >> 6;
+        wsm[tap][ch][co] = __bfloat162float(Wt[(co * 9 + tap) * 16 + ch]);
+    }
+    if (threadIdx.x < 32) bsm[threadIdx.x] = bias ? bias[threadIdx.x] : 0.f;
+    const float *fb = f + (long long)b * H * W;
+    for (int t = threadIdx.x; t < (FT + 2) * (FT + 2); t += blockDim.x) {
+        const int py = t / (FT + 2), px = t % (FT + 2);
+        const int gy = y0 + py - 1, gx = x0 + px - 1;
+        float v = 0.f;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            v = __bfloat162float(__float2bfloat16(fb[(long long)gy * W + gx]));
+        patch[py][px] = v;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / FT, tx = threadIdx.x % FT;  // rows ty and ty + 8
+    const int x = x0 + tx, ya = y0 + ty, yb = ya + 8;
+    if (x >= W || ya >= H) return;
+    const float lb = __bfloat162float(__float2bfloat16(lam[b]));
+    float acc0[32], acc1[32];
+#pragma unroll
+    for (int co = 0; co < 32; ++co) acc0[co] = acc1[co] = bsm[co];
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+        const int gx = x + kx - 1;
+        const bool inx = gx >= 0 && gx < W;
+        const int ga = ya + ky - 1, gb = yb + ky - 1;
+        const float va = patch[ty + ky][tx + kx], vb = patch[ty + 8 + ky][tx + kx];
+        const float la = (inx && ga >= 0 && ga < H) ? lb : 0.f;
+        const float lbb = (inx && gb >= 0 && gb < H) ? lb : 0.f;
+        const float4 *w0 = reinterpret_cast<const float4 *>(&wsm[tap][0][0]);
+        const float4 *w1 = reinterpret_cast<const float4 *>(&wsm[tap][1][0]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 a = w0[q], c = w1[q];
+            acc0[4 * q + 0] = fmaf(a.x, va, fmaf(c.x, la, acc0[4 * q + 0]));
+            acc0[4 * q + 1] = fmaf(a.y, va, fmaf(c.y, la, acc0[4 * q + 1]));
+            acc0[4 * q + 2] = fmaf(a.z, va, fmaf(c.z, la, acc0[4 * q + 2]));
+            acc0[4 * q + 3] = fmaf(a.w, va, fmaf(c.w, la, acc0[4 * q + 3]));
+            acc1[4 * q + 0] = fmaf(a.x, vb, fmaf(c.x, lbb, acc1[4 * q + 0]));
+            acc1[4 * q + 1] = fmaf(a.y, vb, fmaf(c.y, lbb, acc1[4 * q + 1]));
+            acc1[4 * q + 2] = fmaf(a.z, vb, fmaf(c.z, lbb, acc1[4 * q + 2]));
+            acc1[4 * q + 3] = fmaf(a.w, vb, fmaf(c.w, lbb, acc1[4 * q + 3]));
+        }
+    }
+    store_act32(act + (((long long)b * H + ya) * W + x) * 32, acc0);
+    if (yb < H) store_act32(act + (((long long)b * H + yb) * W + x) * 32, acc1);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1017,6 +1104,25 @@ tv_status tv_net_pack_input(const float *d_f, int B, int H, int W, const float *
                                                      static_cast<__nv_bfloat16 *>(d_x),
                                                      ((uintptr_t)d_x & 15) == 0);
     tv_status st = check_cuda(cudaGetLastError(), "pack input");
+    if (st == TV_OK) note_launch();
+    return st;
+}
+
+tv_status tv_net_first_layer(const float *d_f, int B, int H, int W, const float *d_lam,
+                             const void *d_w, const float *d_bias, void *d_act_out,
+                             tv_stream_t stream)
+{
+    clear_error();
+    if (!d_f || !d_lam || !d_w || !d_act_out || !valid_shape(B, H, W) || !aligned16(d_act_out)) {
+        set_error("tv_net_first_layer: need f, lam, w and a 16-byte aligned output, "
+                  "1 <= B <= 65535, H, W >= 1");
+        return TV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const dim3 grid((W + FT - 1) / FT, (H + FT - 1) / FT, B);
+    first_layer<<<grid, 128, 0, s>>>(d_f, H, W, d_lam, static_cast<const __nv_bfloat16 *>(d_w),
+                                     d_bias, static_cast<__nv_bfloat16 *>(d_act_out));
+    tv_status st = check_cuda(cudaGetLastError(), "first layer");
     if (st == TV_OK) note_launch();
     return st;
 }

@@ -162,7 +162,35 @@ class WarmStartNet:
     def predict_dual(self, f, lam):
         """Warm start y^0 (B, H, W) for images f (B, H, W) with per-image lambdas
         ``lam`` (a float, a sequence or a (B,) float32 CUDA tensor). The result lives in
-        a buffer of the network that the next call overwrites."""
+        a buffer of the network that the next call overwrites.
+
+        Inference takes the specialised first layer (two non-zero input channels, no
+        packed input); the other layers and the head are the general kernels.
+        ``predict_dual_layers`` computes the same through the kernels of training."""
+        f, lam = self._inputs(f, lam)
+        B, H, W = f.shape
+        bufs = self._buffers(B, H, W, train=False)
+        s = _lib._stream(self.device)
+        lib = self.lib
+        w0, b0 = self.offsets[0]
+        _lib._check(lib.tv_net_first_layer(_vp(f), B, H, W, _vp(lam), _vp(self.params_bf16, w0),
+                                           _vp(self.params, b0), _vp(bufs["acts"][0]), s))
+        x = bufs["acts"][0]
+        for li in range(1, len(LAYERS)):
+            (cin, cout, relu), (w_off, b_off) = LAYERS[li], self.offsets[li]
+            last = li == len(LAYERS) - 1
+            _lib._check(lib.tv_net_conv3x3(_vp(x), B, H, W, cin, _vp(self.params_bf16, w_off),
+                                           _vp(self.params, b_off), cout, int(relu),
+                                           _vp(bufs["o"]) if last else None,
+                                           None if last else _vp(bufs["acts"][li]), s))
+            x = None if last else bufs["acts"][li]
+        _lib._check(lib.tv_net_dual_head(_vp(bufs["o"]), B, H, W, _vp(lam), None, _vp(bufs["y"]),
+                                         None, None, None, 0, s))
+        return bufs["y"]
+
+    def predict_dual_layers(self, f, lam):
+        """predict_dual through the general kernels (packed input, four convolutions,
+        the head): the reference the specialised inference path is checked against."""
         f, lam = self._inputs(f, lam)
         B, H, W = f.shape
         bufs = self._buffers(B, H, W, train=False)

@@ -291,3 +291,22 @@ def test_poor_network_falls_back_at_the_first_check():
     assert ok_zero and ok and fb
     assert it <= 3 + 3 + it_zero
     assert gap <= 1e-4
+
+
+@pytest.mark.parametrize("shape", [(1, 96, 80), (2, 37, 53), (1, 512, 512), (3, 17, 16)])
+def test_inference_layers_match_the_general_path(shape):
+    """The inference path (first layer from the image and lambda directly) against the
+    general kernels (packed input, four convolutions, head) on the stored network:
+    equal up to the order of FP32 sums, which can move a BF16 activation by one ulp (the
+    bound is the one the smoke check holds the network's output to against FP64)."""
+    net = learned.load_weights(DEV)
+    B, H, W = shape
+    f = torch.from_numpy(np.stack([synth.warm_start_sample(H, W, 700 + i)[0] for i in range(B)])).to(DEV)
+    lam = torch.tensor([0.08 + 0.05 * i for i in range(B)], dtype=torch.float32, device=DEV)
+    y_fast = net.predict_dual(f, lam).clone()
+    y_ref = net.predict_dual_layers(f, lam).clone()
+    err = (y_fast - y_ref).abs().max().item()
+    assert err <= 1e-2 * lam.max().item(), err
+    # feasibility of the fast path's dual: |p_v| <= lambda on every vertical edge
+    p = -torch.cumsum(y_fast.double(), dim=1)
+    assert (p.abs() <= lam.double().view(B, 1, 1) + 1e-6).all()
