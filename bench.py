@@ -760,9 +760,11 @@ def main():
                                     "peak": bf16_peak[0], "unit": "TFLOP/s",
                                     "frac": net_flop / (net_ms * 1e-3) / 1e12 / bf16_peak[0],
                                     "peak_kind": bf16_peak[1],
-                                    "note": "mma.sync m16n8k16 BF16; FLOP count includes the "
-                                            "zero-padded input channels and the 15 unused "
-                                            "output channels"},
+                                    "note": "first layer on the CUDA cores (two non-zero input "
+                                            "channels), the other three on tcgen05 fed by TMA in "
+                                            "the channel-group layout; FLOP count of the dense "
+                                            "16->32->32->32->16 network, including the zero-padded "
+                                            "input channels and the 15 unused output channels"},
             "workload": "held-out seeds 20000.. at 512x512, lambda ~ U[0.05,0.3]; network "
                         "trained on 2000 images (seeds 10000..11999) by the library's kernels",
         },

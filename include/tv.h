@@ -427,6 +427,28 @@ tv_status tv_set_programmatic_launch(int on);
  * 128 x 32 x 16 and the forward pass of the network is faster on mma.sync (0.38 against
  * 0.53 ms at 1024 x 1024). The backward kernels always use mma.sync. */
 tv_status tv_net_set_tensor_path(int mode);
+/* Mode 2: the same tcgen05 GEMM per 128-pixel row tile, fed by TMA and run by warp roles
+ * over vertical strips: a block walks runs of consecutive rows of one 128-pixel column, so
+ * that each input row is loaded once per run (into a ring of six row slots) instead of
+ * once per output row that reads it; one warp loads, one issues the MMAs into one of four
+ * TMEM accumulators, four read the accumulators back, add the bias, apply the ReLU and
+ * store. Measured at 1024 x 1024: 32 -> 32 channels 47 us against 66 us on mma.sync.
+ * Every mbarrier wait of modes 1 and 2 gives up after a bounded number of polls (the tile
+ * is then not written); tv_net_tensor_timeouts() returns how many waits gave up since the
+ * library was loaded (-1 if the count cannot be read). */
+int64_t tv_net_tensor_timeouts(void);
+
+/* Inference layout ("grouped"): a C-channel BF16 activation stored as
+ * [image][row][C/8 channel groups][pixel][8 channels], so that one group of one image row
+ * is a contiguous run of W x 16 bytes (NHWC keeps a pixel's C channels together instead).
+ * tv_net_conv3x3_grouped is tv_net_conv3x3 on this layout: x and act_out are grouped,
+ * pre_out (FP32, may be NULL) stays NHWC. It always runs the tcgen05 kernel of mode 2 (a
+ * row's TMA boxes are then 2048- and 32-byte runs instead of 130 16-byte pieces), whatever
+ * the mode set by tv_net_set_tensor_path, and counts its timed-out waits in
+ * tv_net_tensor_timeouts(). The same argument rules and errors as tv_net_conv3x3 apply. */
+tv_status tv_net_conv3x3_grouped(const void *d_x, int B, int H, int W, int cin, const void *d_w,
+                                 const float *d_bias, int cout, int relu, float *d_pre_out,
+                                 void *d_act_out, tv_stream_t stream);
 
 /* y = conv(x) + bias (bias may be NULL), optionally ReLU'd into act_out (BF16, may be
  * NULL); pre_out (FP32, may be NULL) receives the value before the ReLU; at least one of
@@ -462,9 +484,10 @@ tv_status tv_net_pack_input(const float *d_f, int B, int H, int W, const float *
  * both to BF16 as tv_net_pack_input would, and writes the ReLU'd 32-channel BF16
  * activation (16-byte aligned) of the 16 -> 32 layer with weights d_w ([32][3][3][16]
  * BF16; input channels 2..15 are not read) and bias d_bias (may be NULL). It equals
- * tv_net_pack_input followed by tv_net_conv3x3 up to the order of FP32 sums. */
+ * tv_net_pack_input followed by tv_net_conv3x3 up to the order of FP32 sums. With
+ * grouped != 0 the activation is written in the grouped layout (above) instead of NHWC. */
 tv_status tv_net_first_layer(const float *d_f, int B, int H, int W, const float *d_lam,
-                             const void *d_w, const float *d_bias, void *d_act_out,
+                             const void *d_w, const float *d_bias, void *d_act_out, int grouped,
                              tv_stream_t stream);
 tv_status tv_net_dual_head(const float *d_o, int B, int H, int W, const float *d_lam,
                            const float *d_target, float *d_y, float *d_loss, void *d_grad_o,

@@ -84,6 +84,7 @@ SIGNATURES = {
     "tv_set_thread_split": (ctypes.c_int, [ctypes.c_int]),
     "tv_set_programmatic_launch": (ctypes.c_int, [ctypes.c_int]),
     "tv_net_set_tensor_path": (ctypes.c_int, [ctypes.c_int]),
+    "tv_net_tensor_timeouts": (_i64, []),
     "tv_net_conv3x3": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       _p, _p, ctypes.c_int, ctypes.c_int, _p, _p, _p]),
     "tv_net_conv3x3_backward_data": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -98,7 +99,10 @@ SIGNATURES = {
     "tv_net_dual_head": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _p, _p,
                                         _p, _p, _p, _sz, _p]),
     "tv_net_first_layer": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _p,
-                                          _p, _p, _p]),
+                                          _p, _p, ctypes.c_int, _p]),
+    "tv_net_conv3x3_grouped": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, _p, _p, ctypes.c_int, ctypes.c_int,
+                                              _p, _p, _p]),
     "tv_net_cast_bf16": (ctypes.c_int, [_p, _i64, _p, _p]),
     "tv_net_adam": (ctypes.c_int, [_p, _p, _p, _p, _i64, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, ctypes.c_int, _p, _p]),
@@ -540,8 +544,9 @@ def set_programmatic_launch(on: bool):
 
 
 def set_net_tensor_path(mode: int):
-    """Forward convolutions of the warm-start network on mma.sync (0, the default) or on
-    tcgen05 with TMEM accumulators (1)."""
+    """Forward convolutions of the warm-start network (NHWC) on mma.sync (0), on tcgen05
+    with TMEM accumulators (1), or on tcgen05 fed by TMA with warp roles over row strips
+    (2). Inference in the channel-group layout always takes the kernel of mode 2."""
     _check(load().tv_net_set_tensor_path(int(mode)))
 
 

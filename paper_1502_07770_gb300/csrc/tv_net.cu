@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -846,6 +847,479 @@ __global__ void __launch_bounds__(NTHR)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem) : "memory");
 }
 
+// ---------------------- forward on tcgen05, fed by TMA, with warp roles (tensor path 2) --
+// The same GEMM per tile as conv3x3_tc (M = 128 pixels of one image row, N = COUT,
+// K = 9 * CIN as nine shifted views of three input rows), organised as a pipeline of warp
+// roles over vertical strips. The tiles are grouped in chunks of up to L consecutive rows
+// of one 128-pixel column of one image; a block takes chunks blockIdx.x, + gridDim.x, ..
+// and walks each top-down, so that a chunk of n tiles loads its n + 2 input rows once
+// each, into a ring of TW_NR row slots:
+//   warp 0 (one lane): TMA loads of the next input row (zero-filled outside the image)
+//     into the next slot once that slot is free, completing on the slot's "full" mbarrier;
+//   warp 2 (one lane, also the TMEM owner): for the next tile waits for its three rows
+//     and a free accumulator, issues the tile's 9 * CIN / 16 MMAs into one of TW_NA TMEM
+//     accumulators of COUT columns, and commits them to the accumulator's "full" mbarrier
+//     and to the "empty" mbarrier of the tile's top row, which no later tile of the chunk
+//     reads (after the chunk's last tile, also of its last two rows);
+//   warps 3-6: wait for a full accumulator, read their 32 TMEM lanes (warp w reads lanes
+//     32 (w mod 4) ..), free the accumulator, add the bias, ReLU and store.
+// A row slot holds, per 8-channel group, pixels x0 - 1 .. x0 + 128 at 16 bytes each (2080
+// bytes at a group stride of TW_GS = 2176): the operand of tap (dy, dx) and K step k starts
+// at group 2k of the slot of row dy, pixel dx, with the next 8 channels one group along
+// (leading byte offset) and the next 8 pixels 128 bytes on.
+// GROUPED selects the activation layout of x and act_out.
+//  * NHWC: one box per group and row, 130 separate 16-byte pieces (one per pixel), which
+//    the TMA unit moves one by one.
+//  * [image][row][group][pixel][8 channels]: one group of one row is a contiguous run, seen
+//    by the tensor map as 8-byte elements; per group and row two 1-D boxes, 128 pixels
+//    (2048 bytes, the largest box: 256 elements) from pixel x0 - 1 and the last 2 pixels
+//    (32 bytes) right behind them (both start on 128-byte boundaries).
+// Every wait gives up after kTcSpin polls (counted in g_tc_timeouts; the tile is then not
+// written) and the other roles stop at their next wait.
+constexpr int TW_NR = 6;            // row slots
+constexpr int TW_NA = 4;            // TMEM accumulators
+constexpr int TW_THREADS = 224;     // warp 0 loads, warp 2 issues the MMAs, warps 3-6 epilogue
+constexpr int TW_GS = 2176;         // bytes per 8-channel group in a row slot
+constexpr int TW_ROWB = TC_P * 16;  // bytes of one group's row that the loads deliver
+
+template <int CIN, int COUT>
+constexpr size_t conv_tw_smem()
+{
+    // alignment slack, row slots, weights, 2 (TW_NR + TW_NA) mbarriers, TMEM address and
+    // flag, bias
+    return 1024 + (size_t)TW_NR * (CIN / 8) * TW_GS + (size_t)9 * COUT * CIN * 2 +
+           8 * 2 * (TW_NR + TW_NA) + 16 + 4 * COUT;
+}
+
+// Wait for the phase of parity `parity` of the mbarrier at `bar`; false (and *bad set) after
+// kTcSpin polls or once another role has set *bad.
+__device__ __forceinline__ bool tw_wait(unsigned bar, unsigned parity, volatile int *bad)
+{
+    for (unsigned it = 0; it < kTcSpin; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 1023u) == 1023u && *bad) return false;
+    }
+    if (atomicExch((int *)bad, 1) == 0) atomicAdd(&g_tc_timeouts, 1u);
+    return false;
+}
+
+// Chunk c: rows y0 .. y0 + n - 1 of the pixel column starting at x0 of image b.
+struct TwChunk {
+    int b, x0, y0, n;
+};
+__device__ __forceinline__ TwChunk tw_chunk(long long c, int cpc, int L, int tiles_x, int H)
+{
+    const long long col = c / cpc;
+    TwChunk r;
+    r.b = (int)(col / tiles_x);
+    r.x0 = (int)(col % tiles_x) * TC_M;
+    r.y0 = (int)(c % cpc) * L;
+    r.n = min(L, H - r.y0);
+    return r;
+}
+
+template <int CIN, int COUT, bool GROUPED>
+__global__ void __launch_bounds__(TW_THREADS, 3)
+    conv3x3_tw(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_tail,
+               int B, int H, int W, int L, const __nv_bfloat16 *Wt, const float *bias, int relu,
+               float *pre_out, __nv_bfloat16 *act_out)
+{
+    constexpr int KG = CIN / 8;
+    constexpr int SLOT = KG * TW_GS;
+    constexpr unsigned RBYTES = KG * TW_ROWB;
+    extern __shared__ __align__(1024) unsigned char smem_tw[];
+    unsigned char *base = smem_tw + ((1024u - (smem_u32(smem_tw) & 1023u)) & 1023u);
+    unsigned char *bbuf = base + TW_NR * SLOT;
+    unsigned char *barp = bbuf + 9 * COUT * CIN * 2;
+    unsigned *tslot = reinterpret_cast<unsigned *>(barp + 8 * 2 * (TW_NR + TW_NA));
+    volatile int *bad = reinterpret_cast<volatile int *>(tslot + 1);
+    float *bias_s = reinterpret_cast<float *>(tslot + 4);
+    const unsigned a_s = smem_u32(base), b_s = smem_u32(bbuf), bar0 = smem_u32(barp);
+    // mbarriers: full[r], empty[r] of the row slots, then full[t], empty[t] of the accumulators
+    auto r_full = [&](int r) { return bar0 + 8u * r; };
+    auto r_empty = [&](int r) { return bar0 + 8u * (TW_NR + r); };
+    auto c_full = [&](int t) { return bar0 + 8u * (2 * TW_NR + t); };
+    auto c_empty = [&](int t) { return bar0 + 8u * (2 * TW_NR + TW_NA + t); };
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = (W + TC_M - 1) / TC_M;
+    const int cpc = (H + L - 1) / L;  // chunks per column
+    const long long nchunks = (long long)B * tiles_x * cpc;
+
+    // weights: [tap][group][co][8 channels]
+    for (int t = tid; t < 9 * KG * COUT; t += TW_THREADS) {
+        const int co = t % COUT, g = (t / COUT) % KG, tap = t / (COUT * KG);
+        *reinterpret_cast<uint4 *>(bbuf + ((tap * KG + g) * COUT + co) * 16) =
+            *reinterpret_cast<const uint4 *>(Wt + ((long long)co * 9 + tap) * CIN + g * 8);
+    }
+    if (tid < COUT) bias_s[tid] = bias ? bias[tid] : 0.f;
+    if (tid == 0) {
+        for (int q = 0; q < TW_NR; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(r_full(q)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(r_empty(q)) : "memory");
+        }
+        for (int q = 0; q < TW_NA; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(c_full(q)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(c_empty(q)) : "memory");
+        }
+        *bad = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(tslot)),
+                     "n"(TW_NA * COUT)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // weights for the MMAs
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long q = 0;  // rows issued by this block
+            int sl = 0;       // its slot (q mod TW_NR) and the parity of that slot's fill
+            unsigned lp = 0;
+            bool ok = true;
+            for (long long c = blockIdx.x; c < nchunks && ok; c += gridDim.x) {
+                const TwChunk ch = tw_chunk(c, cpc, L, tiles_x, H);
+                for (int r = 0; r < ch.n + 2; ++r) {
+                    if (!tw_wait(r_empty(sl), lp ^ 1u, bad)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(r_full(sl)),
+                                 "r"(RBYTES)
+                                 : "memory");
+                    const int y = ch.y0 - 1 + r;
+                    const unsigned d0 = a_s + sl * SLOT;
+#pragma unroll
+                    for (int g = 0; g < KG; ++g) {
+                        if constexpr (GROUPED) {
+                            // 8-byte elements: pixel p of a row starts at element 2 p
+                            asm volatile(
+                                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(d0 + g * TW_GS),
+                                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(2 * (ch.x0 - 1)), "r"(g), "r"(y),
+                                "r"(ch.b), "r"(r_full(sl))
+                                : "memory");
+                            asm volatile(
+                                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(d0 + g * TW_GS + 2048),
+                                "l"(reinterpret_cast<uint64_t>(&tmap_tail)), "r"(2 * (ch.x0 + 127)), "r"(g),
+                                "r"(y), "r"(ch.b), "r"(r_full(sl))
+                                : "memory");
+                        } else {
+                            asm volatile(
+                                "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(d0 + g * TW_GS),
+                                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(g), "r"(ch.x0 - 1),
+                                "r"(y), "r"(ch.b), "r"(r_full(sl))
+                                : "memory");
+                        }
+                    }
+                    ++q;
+                    if (++sl == TW_NR) {
+                        sl = 0;
+                        lp ^= 1u;
+                    }
+                }
+            }
+            // after a wait gave up: let the copies of every slot's last load land before the
+            // block exits (the phase of that load completes once its bytes arrive)
+            if (*bad) {
+                for (int sl = 0; sl < TW_NR && sl < q; ++sl) {
+                    const long long last = sl + ((q - 1 - sl) / TW_NR) * TW_NR;
+                    const unsigned par = (unsigned)(last / TW_NR) & 1u;
+                    for (unsigned it = 0; it < kTcSpin; ++it) {
+                        unsigned done;
+                        asm volatile(
+                            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                            " selp.u32 %0, 1, 0, p;\n}\n"
+                            : "=r"(done)
+                            : "r"(r_full(sl)), "r"(par)
+                            : "memory");
+                        if (done) break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 2) {
+        if (lane == 0) {
+            // The issuing lane runs alone, so its per-tile scalar work is on the critical
+            // path: slots and parities advance as counters, and every MMA's descriptors are
+            // a base descriptor plus a compile-time offset (start address >> 4 lives in the
+            // low 14 bits, and shared addresses stay below 256 KB, so the add cannot carry).
+            constexpr uint32_t idesc = tc_idesc(TC_M, COUT);
+            const uint64_t a0d = tc_desc(a_s, TW_GS, 128), b0d = tc_desc(b_s, COUT * 16, 128);
+            int s0 = 0;         // slot of the tile's top row and the parity of its fill
+            unsigned p0 = 0;
+            int t = 0;          // accumulator and the parity of its use
+            unsigned tpar = 0;
+            int i = 0;          // tiles issued by this block
+            bool ok = true;
+            for (long long c = blockIdx.x; c < nchunks && ok; c += gridDim.x) {
+                const TwChunk ch = tw_chunk(c, cpc, L, tiles_x, H);
+                int s1 = 0, s2 = 0;
+                unsigned p1 = 0, p2 = 0;
+                for (int j = 0; j < ch.n; ++j, ++i) {
+                    s1 = s0 + 1;
+                    p1 = p0;
+                    if (s1 == TW_NR) {
+                        s1 = 0;
+                        p1 ^= 1u;
+                    }
+                    s2 = s1 + 1;
+                    p2 = p1;
+                    if (s2 == TW_NR) {
+                        s2 = 0;
+                        p2 ^= 1u;
+                    }
+                    ok = tw_wait(r_full(s0), p0, bad) && tw_wait(r_full(s1), p1, bad) &&
+                         tw_wait(r_full(s2), p2, bad) && tw_wait(c_empty(t), tpar ^ 1u, bad);
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const unsigned acc_addr = tmem + (unsigned)(t * COUT);
+                    const uint64_t dr[3] = {a0d + (uint64_t)(s0 * (SLOT >> 4)), a0d + (uint64_t)(s1 * (SLOT >> 4)),
+                                            a0d + (uint64_t)(s2 * (SLOT >> 4))};
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int dyi = tap / 3, dxi = tap % 3;
+#pragma unroll
+                        for (int ks = 0; ks < KG / 2; ++ks) {
+                            const uint64_t ad = dr[dyi] + (uint64_t)((2 * ks * TW_GS + dxi * 16) >> 4);
+                            const uint64_t bd = b0d + (uint64_t)((tap * KG + 2 * ks) * COUT);
+                            const unsigned acc = (tap | ks) ? 1u : 0u;
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_addr),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                : "memory");
+                        }
+                    }
+                    // the top row is free once these MMAs complete; after the chunk's last
+                    // tile its last two rows are too
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                            r_empty(s0))
+                        : "memory");
+                    if (j == ch.n - 1) {
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                r_empty(s1))
+                            : "memory");
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                r_empty(s2))
+                            : "memory");
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(c_full(t))
+                        : "memory");
+                    s0 = s1;
+                    p0 = p1;
+                    if (++t == TW_NA) {
+                        t = 0;
+                        tpar ^= 1u;
+                    }
+                }
+                // the next chunk's top row follows this chunk's last two rows
+                s0 = s2 + 1;
+                p0 = p2;
+                if (s0 == TW_NR) {
+                    s0 = 0;
+                    p0 ^= 1u;
+                }
+            }
+            // the last tile's MMAs complete before the accumulators are released
+            if (i > 0) (void)tw_wait(c_full((i - 1) % TW_NA), (unsigned)((i - 1) / TW_NA) & 1u, bad);
+        }
+    } else if (warp >= 3) {
+        const int lg = warp & 3;  // TMEM lanes 32 lg .. 32 lg + 31 (pixels of the tile)
+        int t = 0;  // accumulator and the parity of its use
+        unsigned tpar = 0;
+        bool ok = true;
+        for (long long ck = blockIdx.x; ck < nchunks && ok; ck += gridDim.x) {
+            const TwChunk ch = tw_chunk(ck, cpc, L, tiles_x, H);
+            for (int j = 0; j < ch.n; ++j) {
+                int got = 1;
+                if (lane == 0) got = tw_wait(c_full(t), tpar, bad) ? 1 : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                float v[COUT];
+                tc_ld<COUT>(tmem + (unsigned)(t * COUT) + ((unsigned)(lg * 32) << 16), v);
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(c_empty(t)) : "memory");
+                if (++t == TW_NA) {
+                    t = 0;
+                    tpar ^= 1u;
+                }
+                const long long row = (long long)ch.b * H + ch.y0 + j;
+                const int x = ch.x0 + lg * 32 + lane;
+                if (x < W) {
+                    const long long pbase = (row * W + x) * COUT;
+#pragma unroll
+                    for (int c = 0; c < COUT; c += 8) {
+                        float q[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) q[e] = v[c + e] + bias_s[c + e];
+                        if (pre_out) {
+                            *reinterpret_cast<float4 *>(pre_out + pbase + c) = make_float4(q[0], q[1], q[2], q[3]);
+                            *reinterpret_cast<float4 *>(pre_out + pbase + c + 4) = make_float4(q[4], q[5], q[6], q[7]);
+                        }
+                        if (act_out) {
+                            unsigned u[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float a0 = q[2 * e], a1 = q[2 * e + 1];
+                                if (relu) {
+                                    a0 = fmaxf(a0, 0.f);
+                                    a1 = fmaxf(a1, 0.f);
+                                }
+                                const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+                                u[e] = *reinterpret_cast<const unsigned *>(&h);
+                            }
+                            // NHWC, or grouped: [image][row][8-channel group][pixel][8]
+                            const long long o = GROUPED ? ((row * (COUT / 8) + c / 8) * W + x) * 8 : pbase + c;
+                            *reinterpret_cast<uint4 *>(act_out + o) = make_uint4(u[0], u[1], u[2], u[3]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TW_NA * COUT)
+                     : "memory");
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver library)
+typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TmapEncodeFn tmap_encoder()
+{
+    static TmapEncodeFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            (void)cudaGetLastError();
+            return (TmapEncodeFn) nullptr;
+        }
+        return (TmapEncodeFn)f;
+    }();
+    return fn;
+}
+
+template <int CIN, int COUT, bool GROUPED>
+tv_status launch_conv_tw(const __nv_bfloat16 *X, int B, int H, int W, const __nv_bfloat16 *Wt,
+                         const float *bias, int relu, float *pre_out, __nv_bfloat16 *act_out,
+                         cudaStream_t s)
+{
+    TmapEncodeFn enc = tmap_encoder();
+    if (!enc) {
+        set_error("tv_net_conv3x3: cuTensorMapEncodeTiled is not available from the driver");
+        return TV_ERR_CUDA;
+    }
+    // NHWC: the activation as a 5-D BF16 tensor, 8 channels x CIN/8 groups x W x H x B, one
+    // box per group and row (8 x 1 x 130 pixels x 1 x 1). Grouped: a 4-D tensor of 8-byte
+    // elements, 2 W x CIN/8 groups x H x B, boxes of 256 and of 4 elements of one row.
+    CUtensorMap tmap, tmap_tail;
+    const cuuint64_t KG = CIN / 8;
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r0, r1 = CUDA_SUCCESS;
+    if (GROUPED) {
+        const cuuint64_t dims[4] = {2 * (cuuint64_t)W, KG, (cuuint64_t)H, (cuuint64_t)B};
+        const cuuint64_t strides[3] = {(cuuint64_t)W * 16, (cuuint64_t)W * CIN * 2,
+                                       (cuuint64_t)H * W * CIN * 2};
+        const cuuint32_t box[4] = {256, 1, 1, 1}, box_tail[4] = {4, 1, 1, 1};
+        r0 = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<__nv_bfloat16 *>(X), dims, strides, box,
+                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        r1 = enc(&tmap_tail, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<__nv_bfloat16 *>(X), dims, strides,
+                 box_tail, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[5] = {8, KG, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+        const cuuint64_t strides[4] = {16, 16 * KG, (cuuint64_t)W * CIN * 2, (cuuint64_t)H * W * CIN * 2};
+        const cuuint32_t box[5] = {8, 1, (cuuint32_t)TC_P, 1, 1};
+        r0 = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(X), dims, strides, box,
+                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        tmap_tail = tmap;  // not read
+    }
+    if (r0 != CUDA_SUCCESS || r1 != CUDA_SUCCESS) {
+        set_error("tv_net_conv3x3: cuTensorMapEncodeTiled rejected the activation layout");
+        return TV_ERR_INVALID;
+    }
+    auto kern = conv3x3_tw<CIN, COUT, GROUPED>;
+    constexpr size_t smem = conv_tw_smem<CIN, COUT>();
+    static bool attr = false;
+    if (!attr) {
+        tv_status st0 = check_cuda(
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "cudaFuncSetAttribute");
+        if (st0 != TV_OK) return st0;
+        st0 = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              (int)cudaSharedmemCarveoutMaxShared),
+                         "cudaFuncSetAttribute");
+        if (st0 != TV_OK) return st0;
+        attr = true;
+    }
+    // resident blocks per SM from registers, shared memory and TMEM columns (the occupancy
+    // query reports one block for a kernel that allocates TMEM, whatever it allocates)
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncAttributes fa;
+        int dev = 0, smem_sm = 0, regs_sm = 0;
+        tv_status st0 = check_cuda(cudaFuncGetAttributes(&fa, kern), "cudaFuncGetAttributes");
+        if (st0 == TV_OK) st0 = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+        if (st0 == TV_OK)
+            st0 = check_cuda(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev),
+                             "cudaDeviceGetAttribute");
+        if (st0 == TV_OK)
+            st0 = check_cuda(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev),
+                             "cudaDeviceGetAttribute");
+        if (st0 != TV_OK) return st0;
+        const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp
+        const int by_regs = regs_sm / (warp_regs * (TW_THREADS / 32));
+        const int by_smem = smem_sm / (int)(smem + 1024);         // 1 KB reserved per block
+        per_sm = std::max(1, std::min(std::min(by_regs, by_smem), 512 / (TW_NA * COUT)));
+    }
+    // chunks of L rows: about one per block, each loading L + 2 input rows for L tiles
+    const long long cols = (long long)B * ((W + TC_M - 1) / TC_M);
+    const long long slots = (long long)per_sm * sm_count_current();
+    const long long L = std::max(1LL, std::min<long long>(H, (cols * H + slots - 1) / slots));
+    const long long nchunks = cols * ((H + L - 1) / L);
+    const long long blocks = std::min(nchunks, slots);
+    kern<<<(unsigned)blocks, TW_THREADS, smem, s>>>(tmap, tmap_tail, B, H, W, (int)L, Wt, bias, relu,
+                                                     pre_out, act_out);
+    tv_status st = check_cuda(cudaGetLastError(), "conv launch");
+    if (st == TV_OK) note_launch();
+    return st;
+}
+
 static std::atomic<int> g_net_tc{0};  // mma.sync by default: faster for N = 16/32 (see tv.h)
 
 template <int CIN, int COUT>
@@ -923,9 +1397,25 @@ __device__ __forceinline__ void store_act32(__nv_bfloat16 *dst, const float (&ac
     }
 }
 
+// the same, into the grouped layout: group q of this pixel at dst + q * W * 8
+__device__ __forceinline__ void store_act32_grouped(__nv_bfloat16 *dst, int W, const float (&acc)[32])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        unsigned u[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(acc[q * 8 + 2 * e], 0.f),
+                                                           fmaxf(acc[q * 8 + 2 * e + 1], 0.f));
+            u[e] = *reinterpret_cast<const unsigned *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(dst + (long long)q * W * 8) = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+}
+
 __global__ void __launch_bounds__(128)
     first_layer(const float *f, int H, int W, const float *lam, const __nv_bfloat16 *Wt,
-                const float *bias, __nv_bfloat16 *act)
+                const float *bias, __nv_bfloat16 *act, bool grouped)
 {
     __shared__ __align__(16) float wsm[9][2][32];  // [tap][image, lambda][co]
     __shared__ __align__(16) float bsm[32];
@@ -978,19 +1468,34 @@ __global__ void __launch_bounds__(128)
             acc1[4 * q + 3] = fmaf(a.w, vb, fmaf(c.w, lbb, acc1[4 * q + 3]));
         }
     }
-    store_act32(act + (((long long)b * H + ya) * W + x) * 32, acc0);
-    if (yb < H) store_act32(act + (((long long)b * H + yb) * W + x) * 32, acc1);
+    if (grouped) {
+        store_act32_grouped(act + ((long long)b * H + ya) * 4 * W * 8 + (long long)x * 8, W, acc0);
+        if (yb < H) store_act32_grouped(act + ((long long)b * H + yb) * 4 * W * 8 + (long long)x * 8, W, acc1);
+    } else {
+        store_act32(act + (((long long)b * H + ya) * W + x) * 32, acc0);
+        if (yb < H) store_act32(act + (((long long)b * H + yb) * W + x) * 32, acc1);
+    }
 }
 
 }  // namespace
 
 extern "C" {
 
+int64_t tv_net_tensor_timeouts(void)
+{
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_timeouts, sizeof(v)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return -1;
+    }
+    return (int64_t)v;
+}
+
 tv_status tv_net_set_tensor_path(int mode)
 {
     clear_error();
-    if (mode < 0 || mode > 1) {
-        set_error("tv_net_set_tensor_path: 0 (mma.sync) or 1 (tcgen05)");
+    if (mode < 0 || mode > 2) {
+        set_error("tv_net_set_tensor_path: 0 (mma.sync), 1 (tcgen05) or 2 (tcgen05 fed by TMA, warp roles)");
         return TV_ERR_INVALID;
     }
     g_net_tc.store(mode);
@@ -1016,7 +1521,13 @@ tv_status tv_net_conv3x3(const void *d_x, int B, int H, int W, int cin, const vo
     auto X = static_cast<const __nv_bfloat16 *>(d_x);
     auto Wt = static_cast<const __nv_bfloat16 *>(d_w);
     auto A = static_cast<__nv_bfloat16 *>(d_act_out);
-    if (g_net_tc.load() != 0) {
+    if (g_net_tc.load() == 2) {
+        if (cin == 16 && cout == 32) return launch_conv_tw<16, 32, false>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+        if (cin == 32 && cout == 32) return launch_conv_tw<32, 32, false>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+        if (cin == 32 && cout == 16) return launch_conv_tw<32, 16, false>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+        return launch_conv_tw<16, 16, false>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+    }
+    if (g_net_tc.load() == 1) {
         if (cin == 16 && cout == 32) return launch_conv_tc<16, 32>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
         if (cin == 32 && cout == 32) return launch_conv_tc<32, 32>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
         if (cin == 32 && cout == 16) return launch_conv_tc<32, 16>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
@@ -1026,6 +1537,31 @@ tv_status tv_net_conv3x3(const void *d_x, int B, int H, int W, int cin, const vo
     if (cin == 32 && cout == 32) return launch_conv<32, 32, 0>(X, B, H, W, Wt, d_bias, relu, nullptr, d_pre_out, A, s);
     if (cin == 32 && cout == 16) return launch_conv<32, 16, 0>(X, B, H, W, Wt, d_bias, relu, nullptr, d_pre_out, A, s);
     return launch_conv<16, 16, 0>(X, B, H, W, Wt, d_bias, relu, nullptr, d_pre_out, A, s);
+}
+
+tv_status tv_net_conv3x3_grouped(const void *d_x, int B, int H, int W, int cin, const void *d_w,
+                                 const float *d_bias, int cout, int relu, float *d_pre_out,
+                                 void *d_act_out, tv_stream_t stream)
+{
+    clear_error();
+    if (!d_x || !d_w || (!d_act_out && !d_pre_out) || !valid_shape(B, H, W) ||
+        !valid_channels(cin, cout)) {
+        set_error("tv_net_conv3x3_grouped: need x, w, an output, 1 <= B <= 65535, H, W >= 1 and "
+                  "channels in {16, 32}");
+        return TV_ERR_INVALID;
+    }
+    if (!aligned16(d_x) || !aligned16(d_w) || !aligned16(d_act_out) || !aligned16(d_pre_out)) {
+        set_error("tv_net_conv3x3_grouped: x, w and outputs must be 16-byte aligned");
+        return TV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto X = static_cast<const __nv_bfloat16 *>(d_x);
+    auto Wt = static_cast<const __nv_bfloat16 *>(d_w);
+    auto A = static_cast<__nv_bfloat16 *>(d_act_out);
+    if (cin == 16 && cout == 32) return launch_conv_tw<16, 32, true>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+    if (cin == 32 && cout == 32) return launch_conv_tw<32, 32, true>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+    if (cin == 32 && cout == 16) return launch_conv_tw<32, 16, true>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+    return launch_conv_tw<16, 16, true>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
 }
 
 tv_status tv_net_conv3x3_backward_data(const void *d_dy, int B, int H, int W, int cout,
@@ -1109,7 +1645,7 @@ tv_status tv_net_pack_input(const float *d_f, int B, int H, int W, const float *
 }
 
 tv_status tv_net_first_layer(const float *d_f, int B, int H, int W, const float *d_lam,
-                             const void *d_w, const float *d_bias, void *d_act_out,
+                             const void *d_w, const float *d_bias, void *d_act_out, int grouped,
                              tv_stream_t stream)
 {
     clear_error();
@@ -1121,7 +1657,7 @@ tv_status tv_net_first_layer(const float *d_f, int B, int H, int W, const float 
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 grid((W + FT - 1) / FT, (H + FT - 1) / FT, B);
     first_layer<<<grid, 128, 0, s>>>(d_f, H, W, d_lam, static_cast<const __nv_bfloat16 *>(d_w),
-                                     d_bias, static_cast<__nv_bfloat16 *>(d_act_out));
+                                     d_bias, static_cast<__nv_bfloat16 *>(d_act_out), grouped != 0);
     tv_status st = check_cuda(cudaGetLastError(), "first layer");
     if (st == TV_OK) note_launch();
     return st;

@@ -78,6 +78,8 @@ class WarmStartNet:
         self.v = torch.zeros_like(self.grad)
         self.step = 0
         self.meta = {}
+        # inference activations in the channel-group layout on the TMA-fed tcgen05 kernel
+        self.grouped_inference = True
         self._flip = torch.empty(32 * 9 * 32, dtype=torch.bfloat16, device=self.device)
         self._bufs = {}
         self._refresh_bf16()
@@ -159,30 +161,35 @@ class WarmStartNet:
                                            _lib._ptr(act), s))
             x = act
 
-    def predict_dual(self, f, lam):
+    def predict_dual(self, f, lam, grouped=None):
         """Warm start y^0 (B, H, W) for images f (B, H, W) with per-image lambdas
         ``lam`` (a float, a sequence or a (B,) float32 CUDA tensor). The result lives in
         a buffer of the network that the next call overwrites.
 
         Inference takes the specialised first layer (two non-zero input channels, no
-        packed input); the other layers and the head are the general kernels.
+        packed input); the other layers and the head are the general kernels. With
+        ``grouped`` (default ``self.grouped_inference``) the activations are kept in the
+        channel-group layout and the convolutions run on tcgen05 fed by TMA.
         ``predict_dual_layers`` computes the same through the kernels of training."""
         f, lam = self._inputs(f, lam)
         B, H, W = f.shape
         bufs = self._buffers(B, H, W, train=False)
         s = _lib._stream(self.device)
         lib = self.lib
+        grouped = self.grouped_inference if grouped is None else bool(grouped)
+        conv = lib.tv_net_conv3x3_grouped if grouped else lib.tv_net_conv3x3
         w0, b0 = self.offsets[0]
         _lib._check(lib.tv_net_first_layer(_vp(f), B, H, W, _vp(lam), _vp(self.params_bf16, w0),
-                                           _vp(self.params, b0), _vp(bufs["acts"][0]), s))
+                                           _vp(self.params, b0), _vp(bufs["acts"][0]),
+                                           int(grouped), s))
         x = bufs["acts"][0]
         for li in range(1, len(LAYERS)):
             (cin, cout, relu), (w_off, b_off) = LAYERS[li], self.offsets[li]
             last = li == len(LAYERS) - 1
-            _lib._check(lib.tv_net_conv3x3(_vp(x), B, H, W, cin, _vp(self.params_bf16, w_off),
-                                           _vp(self.params, b_off), cout, int(relu),
-                                           _vp(bufs["o"]) if last else None,
-                                           None if last else _vp(bufs["acts"][li]), s))
+            _lib._check(conv(_vp(x), B, H, W, cin, _vp(self.params_bf16, w_off),
+                             _vp(self.params, b_off), cout, int(relu),
+                             _vp(bufs["o"]) if last else None,
+                             None if last else _vp(bufs["acts"][li]), s))
             x = None if last else bufs["acts"][li]
         _lib._check(lib.tv_net_dual_head(_vp(bufs["o"]), B, H, W, _vp(lam), None, _vp(bufs["y"]),
                                          None, None, None, 0, s))

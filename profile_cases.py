@@ -3,7 +3,7 @@
     python profile_cases.py tv2d     [--reps R]   # 1024x1024 denoise, lambda 0.1
     python profile_cases.py chain    [--reps R] [--chains B] [--len N]
     python profile_cases.py backward [--reps R]   # 4096 x 1024 chain VJP
-    python profile_cases.py net      [--reps R]   # warm-start inference 1024x1024
+    python profile_cases.py net      [--reps R] [--grouped]  # warm-start inference 1024x1024
     python profile_cases.py train    [--reps R]   # one training step, 8 x 512x512
     python profile_cases.py batched  [--reps R]   # 16 uneven images, host-replayed loop
     python profile_cases.py l1       [--reps R]   # TV-l1 1024x1024, 10 iterations
@@ -34,6 +34,8 @@ def main(argv=None):
     ap.add_argument("--chains", type=int, default=None,
                     help="chains (chain case, default 32768) or rows (nonconvex, default 1000)")
     ap.add_argument("--len", type=int, default=1024)
+    ap.add_argument("--grouped", action="store_true",
+                    help="net case: activations in the channel-group layout")
     a = ap.parse_args(argv)
     dev = torch.device("cuda:0")
     if a.case == "tv2d":
@@ -53,7 +55,7 @@ def main(argv=None):
         net = learned.load_weights(dev)
         if a.case == "net":
             f = torch.from_numpy(synth.shapes_image(1024, 1024, seed=0)[1]).to(dev)
-            run = lambda: net.predict_dual(f, 0.1)
+            run = lambda: net.predict_dual(f, 0.1, grouped=a.grouped)
         else:
             fs, lams, ys = learned.make_dataset(range(10000, 10008), H=512, W=512, device=dev,
                                                 tol=1e-4, max_iters=50)

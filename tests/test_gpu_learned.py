@@ -70,8 +70,10 @@ def test_conv_forward(cin, cout):
 @pytest.mark.parametrize("cin,cout", PAIRS)
 @pytest.mark.parametrize("shape", [(2, 13, 37), (1, 7, 300), (3, 2, 128)])
 def test_conv_forward_tensor_paths(cin, cout, shape):
-    """The tcgen05 forward (128-pixel row tiles, TMEM accumulators) and the mma.sync
-    forward against the FP64 reference, on rows of one, several and partial tiles."""
+    """The two tcgen05 forwards (128-pixel row tiles, TMEM accumulators; the second fed
+    by TMA with warp roles) and the mma.sync forward against the FP64 reference, on rows
+    of one, several and partial tiles, images shorter than the three staged rows, and
+    batches of images (TMA zero-fills outside each image)."""
     lib = _lib.load()
     b_, h_, w_ = shape
     x = _bf16((b_, h_, w_, cin), 11)
@@ -81,7 +83,8 @@ def test_conv_forward_tensor_paths(cin, cout, shape):
     tol = 2e-5 * max(1.0, np.abs(want).max())
     outs = []
     try:
-        for mode in (1, 0):
+        t0 = lib.tv_net_tensor_timeouts()
+        for mode in (2, 1, 0):
             _lib.set_net_tensor_path(mode)
             pre = torch.full((b_, h_, w_, cout), float("nan"), device=DEV)
             act = torch.empty(b_, h_, w_, cout, dtype=torch.bfloat16, device=DEV)
@@ -91,9 +94,49 @@ def test_conv_forward_tensor_paths(cin, cout, shape):
             np.testing.assert_allclose(got, want, rtol=0, atol=tol)
             _bf16_close(_np(act), np.maximum(want, 0.0), atol=1e-4)
             outs.append(got)
+        assert lib.tv_net_tensor_timeouts() == t0
     finally:
         _lib.set_net_tensor_path(0)
-    np.testing.assert_allclose(outs[0], outs[1], rtol=0, atol=tol)
+    for o in outs[:-1]:
+        np.testing.assert_allclose(o, outs[-1], rtol=0, atol=tol)
+
+
+def _grouped(x):
+    """NHWC (B, H, W, C) -> the channel-group layout (B, H, C/8, W, 8)."""
+    b_, h_, w_, c = x.shape
+    return x.reshape(b_, h_, w_, c // 8, 8).permute(0, 1, 3, 2, 4).contiguous()
+
+
+def _ungrouped(x):
+    b_, h_, g, w_, _ = x.shape
+    return x.permute(0, 1, 3, 2, 4).reshape(b_, h_, w_, g * 8)
+
+
+@pytest.mark.parametrize("cin,cout", PAIRS)
+@pytest.mark.parametrize("shape", [(2, 13, 37), (1, 7, 300), (3, 2, 128), (1, 1, 1)])
+def test_conv_forward_grouped_layout(cin, cout, shape):
+    """The convolution on the channel-group layout (TMA boxes of whole row runs)
+    against the FP64 reference: FP32 pre-activation (NHWC) and the BF16 activation
+    (grouped), with and without bias and ReLU, and no timed-out wait."""
+    lib = _lib.load()
+    b_, h_, w_ = shape
+    x = _bf16((b_, h_, w_, cin), 21)
+    w = _bf16((cout, 3, 3, cin), 22, scale=0.2)
+    b = torch.randn(cout, generator=torch.Generator().manual_seed(23)).to(DEV)
+    xg = _grouped(x)
+    t0 = lib.tv_net_tensor_timeouts()
+    for bias, relu in ((b, 1), (None, 0)):
+        want = ref.conv3x3(_np(x), _np(w), None if bias is None else
+                           bias.cpu().numpy().astype(np.float64)).numpy()
+        tol = 2e-5 * max(1.0, np.abs(want).max())
+        pre = torch.full((b_, h_, w_, cout), float("nan"), device=DEV)
+        act = torch.full((b_, h_, cout // 8, w_, 8), float("nan"), dtype=torch.bfloat16, device=DEV)
+        _lib._check(lib.tv_net_conv3x3_grouped(_vp(xg), b_, h_, w_, cin, _vp(w),
+                                               None if bias is None else _vp(bias), cout, relu,
+                                               _vp(pre), _vp(act), _stream()))
+        np.testing.assert_allclose(pre.cpu().numpy(), want, rtol=0, atol=tol)
+        _bf16_close(_np(_ungrouped(act)), np.maximum(want, 0.0) if relu else want, atol=1e-4)
+    assert lib.tv_net_tensor_timeouts() == t0
 
 
 @pytest.mark.parametrize("cin,cout", PAIRS)
@@ -293,17 +336,19 @@ def test_poor_network_falls_back_at_the_first_check():
     assert gap <= 1e-4
 
 
+@pytest.mark.parametrize("grouped", [False, True])
 @pytest.mark.parametrize("shape", [(1, 96, 80), (2, 37, 53), (1, 512, 512), (3, 17, 16)])
-def test_inference_layers_match_the_general_path(shape):
-    """The inference path (first layer from the image and lambda directly) against the
-    general kernels (packed input, four convolutions, head) on the stored network:
-    equal up to the order of FP32 sums, which can move a BF16 activation by one ulp (the
-    bound is the one the smoke check holds the network's output to against FP64)."""
+def test_inference_layers_match_the_general_path(shape, grouped):
+    """The inference path (first layer from the image and lambda directly; NHWC or the
+    channel-group layout) against the general kernels (packed input, four convolutions,
+    head) on the stored network: equal up to the order of FP32 sums, which can move a
+    BF16 activation by one ulp (the bound is the one the smoke check holds the network's
+    output to against FP64)."""
     net = learned.load_weights(DEV)
     B, H, W = shape
     f = torch.from_numpy(np.stack([synth.warm_start_sample(H, W, 700 + i)[0] for i in range(B)])).to(DEV)
     lam = torch.tensor([0.08 + 0.05 * i for i in range(B)], dtype=torch.float32, device=DEV)
-    y_fast = net.predict_dual(f, lam).clone()
+    y_fast = net.predict_dual(f, lam, grouped=grouped).clone()
     y_ref = net.predict_dual_layers(f, lam).clone()
     err = (y_fast - y_ref).abs().max().item()
     assert err <= 1e-2 * lam.max().item(), err
