@@ -485,10 +485,22 @@ tv_status tv_net_pack_input(const float *d_f, int B, int H, int W, const float *
  * activation (16-byte aligned) of the 16 -> 32 layer with weights d_w ([32][3][3][16]
  * BF16; input channels 2..15 are not read) and bias d_bias (may be NULL). It equals
  * tv_net_pack_input followed by tv_net_conv3x3 up to the order of FP32 sums. With
- * grouped != 0 the activation is written in the grouped layout (above) instead of NHWC. */
+ * grouped != 0 the activation is written in the grouped layout (above) instead of NHWC,
+ * and the layer runs on tcgen05 (the kernel of tv_net_conv3x3_grouped, whose loading warp
+ * builds each BF16 input row from f and lambda in shared memory); with grouped == 0 on the
+ * CUDA cores. */
 tv_status tv_net_first_layer(const float *d_f, int B, int H, int W, const float *d_lam,
                              const void *d_w, const float *d_bias, void *d_act_out, int grouped,
                              tv_stream_t stream);
+/* The network's last layer fused with its head, for inference: the cin -> 16 convolution
+ * of the grouped activation d_x (weights d_w [16][3][3][cin] BF16, bias d_bias, may be
+ * NULL) whose epilogue keeps only channel 0, o, and writes d_p = lambda tanh(o) on the
+ * vertical edges (rows 0 .. H-2; 0 on each image's last row; B x H x W FP32), followed by
+ * d_y = D_v^T p (y[r] = p[r-1] - p[r]), which equals tv_net_dual_head on that o. cin is 16
+ * or 32; x and w 16-byte aligned; timed-out waits count in tv_net_tensor_timeouts(). */
+tv_status tv_net_conv3x3_dual_head(const void *d_x, int B, int H, int W, int cin, const void *d_w,
+                                   const float *d_bias, const float *d_lam, float *d_p, float *d_y,
+                                   tv_stream_t stream);
 tv_status tv_net_dual_head(const float *d_o, int B, int H, int W, const float *d_lam,
                            const float *d_target, float *d_y, float *d_loss, void *d_grad_o,
                            void *d_ws, size_t ws_bytes, tv_stream_t stream);

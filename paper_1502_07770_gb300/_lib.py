@@ -100,6 +100,8 @@ SIGNATURES = {
                                         _p, _p, _p, _sz, _p]),
     "tv_net_first_layer": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _p,
                                           _p, _p, ctypes.c_int, _p]),
+    "tv_net_conv3x3_dual_head": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, _p, _p, _p, _p, _p, _p]),
     "tv_net_conv3x3_grouped": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, _p, _p, ctypes.c_int, ctypes.c_int,
                                               _p, _p, _p]),

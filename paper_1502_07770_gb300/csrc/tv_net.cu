@@ -14,6 +14,7 @@
 // fragments are read with ldmatrix from rows padded by 16 bytes (conflict-free).
 #include <atomic>
 #include <cstdint>
+#include <cstring>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -497,6 +498,17 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// y = D_v^T p for p already on the vertical edges (0 on each image's last row):
+// y[r] = p[r-1] - p[r], p[-1] = 0.
+__global__ void __launch_bounds__(256) head_from_p(const float *p, long long n, int H, int W, float *y)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)((q / W) % H);
+        y[q] = (r > 0 ? p[q - W] : 0.f) - p[q];
+    }
+}
+
 // *loss = sum of n block partials, in a fixed order (one block).
 __global__ void __launch_bounds__(256) sum_partials(const float *part, int n, float *loss)
 {
@@ -848,47 +860,70 @@ __global__ void __launch_bounds__(NTHR)
 }
 
 // ---------------------- forward on tcgen05, fed by TMA, with warp roles (tensor path 2) --
-// The same GEMM per tile as conv3x3_tc (M = 128 pixels of one image row, N = COUT,
-// K = 9 * CIN as nine shifted views of three input rows), organised as a pipeline of warp
-// roles over vertical strips. The tiles are grouped in chunks of up to L consecutive rows
-// of one 128-pixel column of one image; a block takes chunks blockIdx.x, + gridDim.x, ..
-// and walks each top-down, so that a chunk of n tiles loads its n + 2 input rows once
-// each, into a ring of TW_NR row slots:
+// The convolution as one GEMM per input row rather than per output row. Output row y is
+// the sum over dy of input row y - 1 + dy times the weights W(dy, .); equivalently input
+// row r feeds output rows r + 1, r and r - 1 through W(0, .), W(1, .) and W(2, .). So for
+// each input row, shift dx and K step, one MMA with A = the row's 128 pixels from
+// x0 - 1 + dx (M = 128, K = 16) and B = [W(0, dx) | W(1, dx) | W(2, dx)] (N = 3 COUT)
+// adds into the TMEM accumulators of those three output rows at once, which lie side by
+// side: output row o (counted along the block's rows) owns accumulator block
+// TW_R - 1 - (o mod TW_R) of COUT columns, so the blocks of o + 1, o, o - 1 are
+// consecutive. Where they wrap around the ring the MMA is split in two. 9 CIN / 16 MMAs
+// of N = COUT per output row become 3 CIN / 16 (a little more at the wraps) of N = 3 COUT;
+// a tcgen05 MMA of M = 128 and K = 16 costs nearly the same for N = 16 .. 96, so the
+// count of MMAs is what sets the time. The MMAs always accumulate: the blocks start at
+// zero and the epilogue zeroes each one after reading it.
+// The tiles are grouped in chunks of up to L consecutive rows of one 128-pixel column of
+// one image; a block takes chunks blockIdx.x, + gridDim.x, .. and walks each top-down, so
+// that a chunk of n output rows reads its n + 2 input rows once each, through a ring of
+// TW_NR row slots. Warp roles:
 //   warp 0 (one lane): TMA loads of the next input row (zero-filled outside the image)
-//     into the next slot once that slot is free, completing on the slot's "full" mbarrier;
-//   warp 2 (one lane, also the TMEM owner): for the next tile waits for its three rows
-//     and a free accumulator, issues the tile's 9 * CIN / 16 MMAs into one of TW_NA TMEM
-//     accumulators of COUT columns, and commits them to the accumulator's "full" mbarrier
-//     and to the "empty" mbarrier of the tile's top row, which no later tile of the chunk
-//     reads (after the chunk's last tile, also of its last two rows);
-//   warps 3-6: wait for a full accumulator, read their 32 TMEM lanes (warp w reads lanes
-//     32 (w mod 4) ..), free the accumulator, add the bias, ReLU and store.
+//     into the next slot once that slot is free, completing on the slot's "full" mbarrier
+//     (for the image input, warps 0 and 1 build alternate rows with plain loads instead);
+//   warp 2 (one lane, also the TMEM owner): for the next input row waits for its slot and,
+//     if it opens an output row, for that row's accumulator block to be free; issues the
+//     row's MMAs; commits them to the slot's "empty" mbarrier and, once an output row has
+//     had its last input row, to that block's "full" mbarrier;
+//   warps 3-6: wait for a full block, read their 32 TMEM lanes (warp w reads lanes
+//     32 (w mod 4) ..), zero them, free the block, add the bias, ReLU and store.
 // A row slot holds, per 8-channel group, pixels x0 - 1 .. x0 + 128 at 16 bytes each (2080
-// bytes at a group stride of TW_GS = 2176): the operand of tap (dy, dx) and K step k starts
-// at group 2k of the slot of row dy, pixel dx, with the next 8 channels one group along
-// (leading byte offset) and the next 8 pixels 128 bytes on.
-// GROUPED selects the activation layout of x and act_out.
-//  * NHWC: one box per group and row, 130 separate 16-byte pieces (one per pixel), which
-//    the TMA unit moves one by one.
-//  * [image][row][group][pixel][8 channels]: one group of one row is a contiguous run, seen
-//    by the tensor map as 8-byte elements; per group and row two 1-D boxes, 128 pixels
-//    (2048 bytes, the largest box: 256 elements) from pixel x0 - 1 and the last 2 pixels
-//    (32 bytes) right behind them (both start on 128-byte boundaries).
+// bytes at a group stride of TW_GS = 2176): the A operand of shift dx and K step k starts
+// at group 2k, pixel dx, with the next 8 channels one group along (leading byte offset)
+// and the next 8 pixels 128 bytes on. The weights are stored [dx][group][dy][co][8], so
+// that the B rows (dy, co) of one shift and group are consecutive.
+// IO selects where the input rows come from and where the result goes:
+//  * TW_NHWC: x and act_out NHWC; one box per group and row, 130 separate 16-byte pieces
+//    (one per pixel), which the TMA unit moves one by one.
+//  * TW_GROUPED: x and act_out [image][row][group][pixel][8 channels]; one group of one row
+//    is a contiguous run, seen by the tensor map as 8-byte elements; per group and row two
+//    1-D boxes, 128 pixels (2048 bytes, the largest box: 256 elements) from pixel x0 - 1
+//    and the last 2 pixels (32 bytes) right behind them (both start on 128-byte
+//    boundaries).
+//  * TW_IMAGE (the network's first layer, CIN = 16): the input is the FP32 image and its
+//    lambda, channels 0 and 1, rounded to BF16 by the loading warp, which writes them into
+//    group 0 of the slot (channels 2..15 stay zero); act_out grouped.
+//  * TW_HEAD (the last layer, COUT = 16): x grouped; the epilogue keeps only channel 0, o,
+//    and writes p = lambda tanh(o) on the vertical edges (rows 0 .. H - 2, 0 on the last
+//    row) for the dual head.
 // Every wait gives up after kTcSpin polls (counted in g_tc_timeouts; the tile is then not
 // written) and the other roles stop at their next wait.
-constexpr int TW_NR = 6;            // row slots
-constexpr int TW_NA = 4;            // TMEM accumulators
+constexpr int TW_NHWC = 0, TW_GROUPED = 1, TW_IMAGE = 2, TW_HEAD = 3;
+// Row slots: the image rows come from plain loads, whose latency a deeper ring hides; the
+// TMA rows need fewer, and a smaller ring lets three blocks share an SM.
+__host__ __device__ constexpr int tw_nr(int io) { return io == TW_IMAGE ? 8 : 4; }
+// TMEM accumulator blocks: 128 columns per block either way, so that three blocks fit
+__host__ __device__ constexpr int tw_r(int cout) { return 128 / cout; }
 constexpr int TW_THREADS = 224;     // warp 0 loads, warp 2 issues the MMAs, warps 3-6 epilogue
 constexpr int TW_GS = 2176;         // bytes per 8-channel group in a row slot
 constexpr int TW_ROWB = TC_P * 16;  // bytes of one group's row that the loads deliver
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, int IO>
 constexpr size_t conv_tw_smem()
 {
-    // alignment slack, row slots, weights, 2 (TW_NR + TW_NA) mbarriers, TMEM address and
+    // alignment slack, row slots, weights, 2 (NR + R) + 1 mbarriers, TMEM address and
     // flag, bias
-    return 1024 + (size_t)TW_NR * (CIN / 8) * TW_GS + (size_t)9 * COUT * CIN * 2 +
-           8 * 2 * (TW_NR + TW_NA) + 16 + 4 * COUT;
+    return 1024 + (size_t)tw_nr(IO) * (CIN / 8) * TW_GS + (size_t)9 * COUT * CIN * 2 +
+           8 * (2 * (tw_nr(IO) + tw_r(COUT)) + 1) + 16 + 4 * COUT;
 }
 
 // Wait for the phase of parity `parity` of the mbarrier at `bar`; false (and *bad set) after
@@ -910,6 +945,27 @@ __device__ __forceinline__ bool tw_wait(unsigned bar, unsigned parity, volatile 
     return false;
 }
 
+// Zero N (16 or 32) TMEM columns of the calling warp's 32 lanes from taddr.
+template <int N>
+__device__ __forceinline__ void tc_st_zero(unsigned taddr)
+{
+    static_assert(N == 16 || N == 32, "tcgen05.st of 16 or 32 columns");
+    const unsigned z = 0;
+    if constexpr (N == 32) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+            "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(taddr),
+            "r"(z)
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(
+                taddr),
+            "r"(z)
+            : "memory");
+    }
+}
+
 // Chunk c: rows y0 .. y0 + n - 1 of the pixel column starting at x0 of image b.
 struct TwChunk {
     int b, x0, y0, n;
@@ -925,38 +981,82 @@ __device__ __forceinline__ TwChunk tw_chunk(long long c, int cpc, int L, int til
     return r;
 }
 
-template <int CIN, int COUT, bool GROUPED>
+// Walks the input rows of a block's chunks in load order (n + 2 rows per chunk).
+struct TwRows {
+    long long c, nchunks;
+    int r, cpc, L, tiles_x, H;
+    TwChunk ch;
+    __device__ __forceinline__ bool valid() const { return c < nchunks; }
+    __device__ __forceinline__ void start(long long c0, long long nc, int cpc_, int L_, int tx_, int H_)
+    {
+        c = c0;
+        nchunks = nc;
+        cpc = cpc_;
+        L = L_;
+        tiles_x = tx_;
+        H = H_;
+        r = 0;
+        if (c < nchunks) ch = tw_chunk(c, cpc, L, tiles_x, H);
+    }
+    __device__ __forceinline__ void next(long long stride)
+    {
+        if (++r == ch.n + 2) {
+            r = 0;
+            c += stride;
+            if (c < nchunks) ch = tw_chunk(c, cpc, L, tiles_x, H);
+        }
+    }
+};
+
+// accumulator block of output row o (counted along the block's rows) in a ring of R
+template <int R>
+__device__ __forceinline__ int tw_block(unsigned o)
+{
+    return R - 1 - (int)(o % R);
+}
+
+template <int CIN, int COUT, int IO>
 __global__ void __launch_bounds__(TW_THREADS, 3)
     conv3x3_tw(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_tail,
                int B, int H, int W, int L, const __nv_bfloat16 *Wt, const float *bias, int relu,
-               float *pre_out, __nv_bfloat16 *act_out)
+               float *pre_out, __nv_bfloat16 *act_out, const float *img, const float *lam, float *p_out)
 {
+    static_assert(IO != TW_IMAGE || CIN == 16, "the image input has 16 (2 non-zero) channels");
+    static_assert(IO != TW_HEAD || COUT == 16, "the head reads a 16-channel output");
+    constexpr int TW_NR = tw_nr(IO), TW_R = tw_r(COUT);
+    constexpr bool GROUPED_OUT = IO == TW_GROUPED || IO == TW_IMAGE;
     constexpr int KG = CIN / 8;
     constexpr int SLOT = KG * TW_GS;
     constexpr unsigned RBYTES = KG * TW_ROWB;
+    constexpr int NCOL = TW_R * COUT;  // TMEM columns (128)
     extern __shared__ __align__(1024) unsigned char smem_tw[];
     unsigned char *base = smem_tw + ((1024u - (smem_u32(smem_tw) & 1023u)) & 1023u);
     unsigned char *bbuf = base + TW_NR * SLOT;
     unsigned char *barp = bbuf + 9 * COUT * CIN * 2;
-    unsigned *tslot = reinterpret_cast<unsigned *>(barp + 8 * 2 * (TW_NR + TW_NA));
+    unsigned *tslot = reinterpret_cast<unsigned *>(barp + 8 * (2 * (TW_NR + TW_R) + 1));
     volatile int *bad = reinterpret_cast<volatile int *>(tslot + 1);
     float *bias_s = reinterpret_cast<float *>(tslot + 4);
     const unsigned a_s = smem_u32(base), b_s = smem_u32(bbuf), bar0 = smem_u32(barp);
-    // mbarriers: full[r], empty[r] of the row slots, then full[t], empty[t] of the accumulators
-    auto r_full = [&](int r) { return bar0 + 8u * r; };
-    auto r_empty = [&](int r) { return bar0 + 8u * (TW_NR + r); };
-    auto c_full = [&](int t) { return bar0 + 8u * (2 * TW_NR + t); };
-    auto c_empty = [&](int t) { return bar0 + 8u * (2 * TW_NR + TW_NA + t); };
+    // mbarriers: full[s], empty[s] of the row slots, full[k], empty[k] of the blocks, and
+    // one that the MMA lane's last commit completes
+    auto r_full = [&](int s) { return bar0 + 8u * s; };
+    auto r_empty = [&](int s) { return bar0 + 8u * (TW_NR + s); };
+    auto c_full = [&](int k) { return bar0 + 8u * (2 * TW_NR + k); };
+    auto c_empty = [&](int k) { return bar0 + 8u * (2 * TW_NR + TW_R + k); };
+    const unsigned mma_done = bar0 + 8u * (2 * TW_NR + 2 * TW_R);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = (W + TC_M - 1) / TC_M;
     const int cpc = (H + L - 1) / L;  // chunks per column
     const long long nchunks = (long long)B * tiles_x * cpc;
 
-    // weights: [tap][group][co][8 channels]
+    if (IO == TW_IMAGE)  // channels 2..15 of the image rows stay zero
+        for (int t = tid; t < TW_NR * SLOT / 16; t += TW_THREADS)
+            reinterpret_cast<uint4 *>(base)[t] = make_uint4(0u, 0u, 0u, 0u);
+    // weights: [dx][group][dy][co][8 channels]
     for (int t = tid; t < 9 * KG * COUT; t += TW_THREADS) {
-        const int co = t % COUT, g = (t / COUT) % KG, tap = t / (COUT * KG);
-        *reinterpret_cast<uint4 *>(bbuf + ((tap * KG + g) * COUT + co) * 16) =
-            *reinterpret_cast<const uint4 *>(Wt + ((long long)co * 9 + tap) * CIN + g * 8);
+        const int co = t % COUT, dy = (t / COUT) % 3, g = (t / (3 * COUT)) % KG, dx = t / (3 * COUT * KG);
+        *reinterpret_cast<uint4 *>(bbuf + (size_t)t * 16) =
+            *reinterpret_cast<const uint4 *>(Wt + ((long long)co * 9 + dy * 3 + dx) * CIN + g * 8);
     }
     if (tid < COUT) bias_s[tid] = bias ? bias[tid] : 0.f;
     if (tid == 0) {
@@ -964,17 +1064,18 @@ __global__ void __launch_bounds__(TW_THREADS, 3)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(r_full(q)) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(r_empty(q)) : "memory");
         }
-        for (int q = 0; q < TW_NA; ++q) {
+        for (int q = 0; q < TW_R; ++q) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(c_full(q)) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(c_empty(q)) : "memory");
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mma_done) : "memory");
         *bad = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(tslot)),
-                     "n"(TW_NA * COUT)
+                     "n"(NCOL)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -983,8 +1084,77 @@ __global__ void __launch_bounds__(TW_THREADS, 3)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const unsigned tmem = *tslot;
+    if (warp >= 3) {  // every accumulator block starts at zero
+        const unsigned lanes = (unsigned)((warp & 3) * 32) << 16;
+#pragma unroll
+        for (int c = 0; c < NCOL; c += COUT) tc_st_zero<COUT>(tmem + lanes + (unsigned)c);
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
-    if (warp == 0) {
+    if (IO == TW_IMAGE && warp < 2) {
+        // warps 0 and 1 build alternate rows (load-order rows q = warp, warp + 2, ..): pixel
+        // x0 - 1 + px of row y becomes (bf16 f, bf16 lambda, 0, ..); each warp loads its
+        // next row into registers before it waits for a slot and stores the current one
+        TwRows it;
+        it.start(blockIdx.x, nchunks, cpc, L, tiles_x, H);
+        if (warp == 1) it.next(gridDim.x);
+        float cur[5], nxt[5];
+        unsigned cmask = 0u, nmask = 0u;
+        float clam = 0.f, nlam = 0.f;
+        auto load_row = [&](const TwRows &rw, float (&v)[5], unsigned &mask, float &lv) {
+            const int y = rw.ch.y0 - 1 + rw.r;
+            const float *src = img + ((long long)rw.ch.b * H + (y < 0 ? 0 : y)) * W;
+            lv = lam[rw.ch.b];
+            mask = 0u;
+#pragma unroll
+            for (int kk = 0; kk < 5; ++kk) {
+                const int x = rw.ch.x0 - 1 + lane + 32 * kk;
+                const bool in = lane + 32 * kk < TC_P && y >= 0 && y < H && x >= 0 && x < W;
+                v[kk] = in ? src[x] : 0.f;
+                mask |= in ? 1u << kk : 0u;
+            }
+        };
+        if (it.valid()) load_row(it, cur, cmask, clam);
+        bool ok = true;
+        for (unsigned q = (unsigned)warp; it.valid() && ok; q += 2u) {
+            TwRows nx = it;
+            nx.next(gridDim.x);
+            nx.next(gridDim.x);
+            if (nx.valid()) load_row(nx, nxt, nmask, nlam);
+            const int sl = (int)(q % TW_NR);
+            int got = 1;
+            if (lane == 0) got = tw_wait(r_empty(sl), ((q / TW_NR) & 1u) ^ 1u, bad) ? 1 : 0;
+            if (!__shfl_sync(0xffffffffu, got, 0)) {
+                ok = false;
+                break;
+            }
+            unsigned char *dst = base + sl * SLOT;
+#pragma unroll
+            for (int kk = 0; kk < 5; ++kk) {
+                const int px = lane + 32 * kk;
+                if (px < TC_P) {
+                    unsigned v = 0u;
+                    if (cmask >> kk & 1u) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(cur[kk], clam);
+                        v = *reinterpret_cast<const unsigned *>(&h);
+                    }
+                    *reinterpret_cast<unsigned *>(dst + px * 16) = v;
+                }
+            }
+            // the generic-proxy writes become visible to the MMAs (async proxy)
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(r_full(sl)) : "memory");
+            it = nx;
+#pragma unroll
+            for (int kk = 0; kk < 5; ++kk) cur[kk] = nxt[kk];
+            cmask = nmask;
+            clam = nlam;
+        }
+    } else if (warp == 0) {
         if (lane == 0) {
             long long q = 0;  // rows issued by this block
             int sl = 0;       // its slot (q mod TW_NR) and the parity of that slot's fill
@@ -1004,7 +1174,7 @@ __global__ void __launch_bounds__(TW_THREADS, 3)
                     const unsigned d0 = a_s + sl * SLOT;
 #pragma unroll
                     for (int g = 0; g < KG; ++g) {
-                        if constexpr (GROUPED) {
+                        if constexpr (IO != TW_NHWC) {
                             // 8-byte elements: pixel p of a row starts at element 2 p
                             asm volatile(
                                 "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
@@ -1037,8 +1207,8 @@ __global__ void __launch_bounds__(TW_THREADS, 3)
             // after a wait gave up: let the copies of every slot's last load land before the
             // block exits (the phase of that load completes once its bytes arrive)
             if (*bad) {
-                for (int sl = 0; sl < TW_NR && sl < q; ++sl) {
-                    const long long last = sl + ((q - 1 - sl) / TW_NR) * TW_NR;
+                for (int s = 0; s < TW_NR && s < q; ++s) {
+                    const long long last = s + ((q - 1 - s) / TW_NR) * TW_NR;
                     const unsigned par = (unsigned)(last / TW_NR) & 1u;
                     for (unsigned it = 0; it < kTcSpin; ++it) {
                         unsigned done;
@@ -1046,7 +1216,7 @@ __global__ void __launch_bounds__(TW_THREADS, 3)
                             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                             " selp.u32 %0, 1, 0, p;\n}\n"
                             : "=r"(done)
-                            : "r"(r_full(sl)), "r"(par)
+                            : "r"(r_full(s)), "r"(par)
                             : "memory");
                         if (done) break;
                     }
@@ -1055,104 +1225,97 @@ __global__ void __launch_bounds__(TW_THREADS, 3)
         }
     } else if (warp == 2) {
         if (lane == 0) {
-            // The issuing lane runs alone, so its per-tile scalar work is on the critical
-            // path: slots and parities advance as counters, and every MMA's descriptors are
-            // a base descriptor plus a compile-time offset (start address >> 4 lives in the
-            // low 14 bits, and shared addresses stay below 256 KB, so the add cannot carry).
-            constexpr uint32_t idesc = tc_idesc(TC_M, COUT);
-            const uint64_t a0d = tc_desc(a_s, TW_GS, 128), b0d = tc_desc(b_s, COUT * 16, 128);
-            int s0 = 0;         // slot of the tile's top row and the parity of its fill
-            unsigned p0 = 0;
-            int t = 0;          // accumulator and the parity of its use
-            unsigned tpar = 0;
-            int i = 0;          // tiles issued by this block
+            // The issuing lane runs alone, so its scalar work is on the critical path: slots,
+            // blocks and parities advance as counters, and each descriptor is a base
+            // descriptor plus an offset (the start address >> 4 lives in the low 14 bits and
+            // shared addresses stay below 256 KB, so the add cannot carry out of it).
+            constexpr uint32_t idesc0 = tc_idesc(TC_M, 16) & ~(0x3Fu << 17);  // N set per MMA
+            const uint64_t a0d = tc_desc(a_s, TW_GS, 128), b0d = tc_desc(b_s, 3 * COUT * 16, 128);
+            int sl = 0;       // slot of the next input row and the parity of its fill
+            unsigned sp = 0;
+            unsigned o0 = 0;  // output rows of the finished chunks
             bool ok = true;
             for (long long c = blockIdx.x; c < nchunks && ok; c += gridDim.x) {
                 const TwChunk ch = tw_chunk(c, cpc, L, tiles_x, H);
-                int s1 = 0, s2 = 0;
-                unsigned p1 = 0, p2 = 0;
-                for (int j = 0; j < ch.n; ++j, ++i) {
-                    s1 = s0 + 1;
-                    p1 = p0;
-                    if (s1 == TW_NR) {
-                        s1 = 0;
-                        p1 ^= 1u;
+                for (int i = 0; i < ch.n + 2; ++i) {
+                    // input row i of the chunk feeds its output rows i - dy, dy = dlo .. dhi
+                    ok = tw_wait(r_full(sl), sp, bad);
+                    if (ok && i < ch.n) {  // opens output row i: its block must be free
+                        const unsigned o = o0 + (unsigned)i;
+                        ok = tw_wait(c_empty(tw_block<TW_R>(o)), ((o / TW_R) & 1u) ^ 1u, bad);
                     }
-                    s2 = s1 + 1;
-                    p2 = p1;
-                    if (s2 == TW_NR) {
-                        s2 = 0;
-                        p2 ^= 1u;
-                    }
-                    ok = tw_wait(r_full(s0), p0, bad) && tw_wait(r_full(s1), p1, bad) &&
-                         tw_wait(r_full(s2), p2, bad) && tw_wait(c_empty(t), tpar ^ 1u, bad);
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const unsigned acc_addr = tmem + (unsigned)(t * COUT);
-                    const uint64_t dr[3] = {a0d + (uint64_t)(s0 * (SLOT >> 4)), a0d + (uint64_t)(s1 * (SLOT >> 4)),
-                                            a0d + (uint64_t)(s2 * (SLOT >> 4))};
+                    const int dlo = max(0, i - (ch.n - 1)), dhi = min(2, i);
+                    const int nb = dhi - dlo + 1;
+                    const int k0 = tw_block<TW_R>(o0 + (unsigned)(i - dlo));  // block of the lowest column
+                    const int m = min(nb, TW_R - k0);                    // blocks before the wrap
+                    const unsigned acc1 = tmem + (unsigned)(k0 * COUT), acc2 = tmem;
+                    const uint32_t id1 = idesc0 | ((uint32_t)(m * COUT) >> 3) << 17;
+                    const uint32_t id2 = idesc0 | ((uint32_t)((nb - m) * COUT) >> 3) << 17;
+                    const uint64_t ar = a0d + (uint64_t)(sl * (SLOT >> 4));
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int dyi = tap / 3, dxi = tap % 3;
+                    for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
                         for (int ks = 0; ks < KG / 2; ++ks) {
-                            const uint64_t ad = dr[dyi] + (uint64_t)((2 * ks * TW_GS + dxi * 16) >> 4);
-                            const uint64_t bd = b0d + (uint64_t)((tap * KG + 2 * ks) * COUT);
-                            const unsigned acc = (tap | ks) ? 1u : 0u;
+                            const uint64_t ad = ar + (uint64_t)((2 * ks * TW_GS + dx * 16) >> 4);
+                            // B rows (dy, co) of this shift and K step, from dy = dlo
+                            const uint64_t bd = b0d + (uint64_t)(((dx * KG + 2 * ks) * 3 + dlo) * COUT);
                             asm volatile(
-                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_addr),
-                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                "{\n .reg .pred p;\n setp.eq.u32 p, 1, 1;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc1),
+                                "l"(ad), "l"(bd), "r"(id1)
                                 : "memory");
+                            if (m < nb)
+                                asm volatile(
+                                    "{\n .reg .pred p;\n setp.eq.u32 p, 1, 1;\n"
+                                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc2),
+                                    "l"(ad), "l"(bd + (uint64_t)(m * COUT)), "r"(id2)
+                                    : "memory");
                         }
                     }
-                    // the top row is free once these MMAs complete; after the chunk's last
-                    // tile its last two rows are too
                     asm volatile(
                         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                            r_empty(s0))
+                            r_empty(sl))
                         : "memory");
-                    if (j == ch.n - 1) {
+                    if (i >= 2)  // output row i - 2 has had its last input row
                         asm volatile(
                             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                                r_empty(s1))
+                                c_full(tw_block<TW_R>(o0 + (unsigned)(i - 2))))
                             : "memory");
-                        asm volatile(
-                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                                r_empty(s2))
-                            : "memory");
-                    }
-                    asm volatile(
-                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(c_full(t))
-                        : "memory");
-                    s0 = s1;
-                    p0 = p1;
-                    if (++t == TW_NA) {
-                        t = 0;
-                        tpar ^= 1u;
+                    if (++sl == TW_NR) {
+                        sl = 0;
+                        sp ^= 1u;
                     }
                 }
-                // the next chunk's top row follows this chunk's last two rows
-                s0 = s2 + 1;
-                p0 = p2;
-                if (s0 == TW_NR) {
-                    s0 = 0;
-                    p0 ^= 1u;
-                }
+                o0 += (unsigned)ch.n;
             }
-            // the last tile's MMAs complete before the accumulators are released
-            if (i > 0) (void)tw_wait(c_full((i - 1) % TW_NA), (unsigned)((i - 1) / TW_NA) & 1u, bad);
+            // every MMA issued completes before the accumulators are released
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mma_done)
+                : "memory");
+            for (unsigned it = 0; it < kTcSpin; ++it) {
+                unsigned done;
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                    " selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(done)
+                    : "r"(mma_done), "r"(0u)
+                    : "memory");
+                if (done) break;
+            }
         }
     } else if (warp >= 3) {
         const int lg = warp & 3;  // TMEM lanes 32 lg .. 32 lg + 31 (pixels of the tile)
-        int t = 0;  // accumulator and the parity of its use
-        unsigned tpar = 0;
+        const unsigned lanes = (unsigned)(lg * 32) << 16;
+        unsigned o = 0;
         bool ok = true;
         for (long long ck = blockIdx.x; ck < nchunks && ok; ck += gridDim.x) {
             const TwChunk ch = tw_chunk(ck, cpc, L, tiles_x, H);
-            for (int j = 0; j < ch.n; ++j) {
+            for (int j = 0; j < ch.n; ++j, ++o) {
+                const int k = tw_block<TW_R>(o);
                 int got = 1;
-                if (lane == 0) got = tw_wait(c_full(t), tpar, bad) ? 1 : 0;
+                if (lane == 0) got = tw_wait(c_full(k), (o / TW_R) & 1u, bad) ? 1 : 0;
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
                     ok = false;
@@ -1160,17 +1323,18 @@ __global__ void __launch_bounds__(TW_THREADS, 3)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 float v[COUT];
-                tc_ld<COUT>(tmem + (unsigned)(t * COUT) + ((unsigned)(lg * 32) << 16), v);
+                const unsigned ta = tmem + lanes + (unsigned)(k * COUT);
+                tc_ld<COUT>(ta, v);
+                tc_st_zero<COUT>(ta);
+                asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                 __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(c_empty(t)) : "memory");
-                if (++t == TW_NA) {
-                    t = 0;
-                    tpar ^= 1u;
-                }
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(c_empty(k)) : "memory");
                 const long long row = (long long)ch.b * H + ch.y0 + j;
                 const int x = ch.x0 + lg * 32 + lane;
-                if (x < W) {
+                if (IO == TW_HEAD && x < W) {
+                    p_out[row * W + x] = ch.y0 + j < H - 1 ? lam[ch.b] * tanhf(v[0] + bias_s[0]) : 0.f;
+                } else if (x < W) {
                     const long long pbase = (row * W + x) * COUT;
 #pragma unroll
                     for (int c = 0; c < COUT; c += 8) {
@@ -1194,8 +1358,8 @@ __global__ void __launch_bounds__(TW_THREADS, 3)
                                 u[e] = *reinterpret_cast<const unsigned *>(&h);
                             }
                             // NHWC, or grouped: [image][row][8-channel group][pixel][8]
-                            const long long o = GROUPED ? ((row * (COUT / 8) + c / 8) * W + x) * 8 : pbase + c;
-                            *reinterpret_cast<uint4 *>(act_out + o) = make_uint4(u[0], u[1], u[2], u[3]);
+                            const long long o8 = GROUPED_OUT ? ((row * (COUT / 8) + c / 8) * W + x) * 8 : pbase + c;
+                            *reinterpret_cast<uint4 *>(act_out + o8) = make_uint4(u[0], u[1], u[2], u[3]);
                         }
                     }
                 }
@@ -1206,8 +1370,7 @@ __global__ void __launch_bounds__(TW_THREADS, 3)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (warp == 2)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TW_NA * COUT)
-                     : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(NCOL) : "memory");
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver library)
@@ -1232,10 +1395,11 @@ TmapEncodeFn tmap_encoder()
     return fn;
 }
 
-template <int CIN, int COUT, bool GROUPED>
+template <int CIN, int COUT, int IO>
 tv_status launch_conv_tw(const __nv_bfloat16 *X, int B, int H, int W, const __nv_bfloat16 *Wt,
                          const float *bias, int relu, float *pre_out, __nv_bfloat16 *act_out,
-                         cudaStream_t s)
+                         cudaStream_t s, const float *img = nullptr, const float *lam = nullptr,
+                         float *p_out = nullptr)
 {
     TmapEncodeFn enc = tmap_encoder();
     if (!enc) {
@@ -1248,8 +1412,11 @@ tv_status launch_conv_tw(const __nv_bfloat16 *X, int B, int H, int W, const __nv
     CUtensorMap tmap, tmap_tail;
     const cuuint64_t KG = CIN / 8;
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    CUresult r0, r1 = CUDA_SUCCESS;
-    if (GROUPED) {
+    CUresult r0 = CUDA_SUCCESS, r1 = CUDA_SUCCESS;
+    if (IO == TW_IMAGE) {
+        memset(&tmap, 0, sizeof(tmap));  // not read: the rows come from the image
+        tmap_tail = tmap;
+    } else if (IO != TW_NHWC) {
         const cuuint64_t dims[4] = {2 * (cuuint64_t)W, KG, (cuuint64_t)H, (cuuint64_t)B};
         const cuuint64_t strides[3] = {(cuuint64_t)W * 16, (cuuint64_t)W * CIN * 2,
                                        (cuuint64_t)H * W * CIN * 2};
@@ -1273,8 +1440,8 @@ tv_status launch_conv_tw(const __nv_bfloat16 *X, int B, int H, int W, const __nv
         set_error("tv_net_conv3x3: cuTensorMapEncodeTiled rejected the activation layout");
         return TV_ERR_INVALID;
     }
-    auto kern = conv3x3_tw<CIN, COUT, GROUPED>;
-    constexpr size_t smem = conv_tw_smem<CIN, COUT>();
+    auto kern = conv3x3_tw<CIN, COUT, IO>;
+    constexpr size_t smem = conv_tw_smem<CIN, COUT, IO>();
     static bool attr = false;
     if (!attr) {
         tv_status st0 = check_cuda(
@@ -1305,7 +1472,7 @@ tv_status launch_conv_tw(const __nv_bfloat16 *X, int B, int H, int W, const __nv
         const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp
         const int by_regs = regs_sm / (warp_regs * (TW_THREADS / 32));
         const int by_smem = smem_sm / (int)(smem + 1024);         // 1 KB reserved per block
-        per_sm = std::max(1, std::min(std::min(by_regs, by_smem), 512 / (TW_NA * COUT)));
+        per_sm = std::max(1, std::min(std::min(by_regs, by_smem), 512 / (tw_r(COUT) * COUT)));
     }
     // chunks of L rows: about one per block, each loading L + 2 input rows for L tiles
     const long long cols = (long long)B * ((W + TC_M - 1) / TC_M);
@@ -1314,7 +1481,7 @@ tv_status launch_conv_tw(const __nv_bfloat16 *X, int B, int H, int W, const __nv
     const long long nchunks = cols * ((H + L - 1) / L);
     const long long blocks = std::min(nchunks, slots);
     kern<<<(unsigned)blocks, TW_THREADS, smem, s>>>(tmap, tmap_tail, B, H, W, (int)L, Wt, bias, relu,
-                                                     pre_out, act_out);
+                                                     pre_out, act_out, img, lam, p_out);
     tv_status st = check_cuda(cudaGetLastError(), "conv launch");
     if (st == TV_OK) note_launch();
     return st;
@@ -1522,10 +1689,10 @@ tv_status tv_net_conv3x3(const void *d_x, int B, int H, int W, int cin, const vo
     auto Wt = static_cast<const __nv_bfloat16 *>(d_w);
     auto A = static_cast<__nv_bfloat16 *>(d_act_out);
     if (g_net_tc.load() == 2) {
-        if (cin == 16 && cout == 32) return launch_conv_tw<16, 32, false>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
-        if (cin == 32 && cout == 32) return launch_conv_tw<32, 32, false>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
-        if (cin == 32 && cout == 16) return launch_conv_tw<32, 16, false>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
-        return launch_conv_tw<16, 16, false>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+        if (cin == 16 && cout == 32) return launch_conv_tw<16, 32, TW_NHWC>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+        if (cin == 32 && cout == 32) return launch_conv_tw<32, 32, TW_NHWC>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+        if (cin == 32 && cout == 16) return launch_conv_tw<32, 16, TW_NHWC>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+        return launch_conv_tw<16, 16, TW_NHWC>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
     }
     if (g_net_tc.load() == 1) {
         if (cin == 16 && cout == 32) return launch_conv_tc<16, 32>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
@@ -1558,10 +1725,10 @@ tv_status tv_net_conv3x3_grouped(const void *d_x, int B, int H, int W, int cin, 
     auto X = static_cast<const __nv_bfloat16 *>(d_x);
     auto Wt = static_cast<const __nv_bfloat16 *>(d_w);
     auto A = static_cast<__nv_bfloat16 *>(d_act_out);
-    if (cin == 16 && cout == 32) return launch_conv_tw<16, 32, true>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
-    if (cin == 32 && cout == 32) return launch_conv_tw<32, 32, true>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
-    if (cin == 32 && cout == 16) return launch_conv_tw<32, 16, true>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
-    return launch_conv_tw<16, 16, true>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+    if (cin == 16 && cout == 32) return launch_conv_tw<16, 32, TW_GROUPED>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+    if (cin == 32 && cout == 32) return launch_conv_tw<32, 32, TW_GROUPED>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+    if (cin == 32 && cout == 16) return launch_conv_tw<32, 16, TW_GROUPED>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
+    return launch_conv_tw<16, 16, TW_GROUPED>(X, B, H, W, Wt, d_bias, relu, d_pre_out, A, s);
 }
 
 tv_status tv_net_conv3x3_backward_data(const void *d_dy, int B, int H, int W, int cout,
@@ -1655,10 +1822,43 @@ tv_status tv_net_first_layer(const float *d_f, int B, int H, int W, const float 
         return TV_ERR_INVALID;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    if (grouped)  // on tcgen05: the image rows built in shared memory, 3 MMAs per row
+        return launch_conv_tw<16, 32, TW_IMAGE>(nullptr, B, H, W, static_cast<const __nv_bfloat16 *>(d_w),
+                                                d_bias, 1, nullptr, static_cast<__nv_bfloat16 *>(d_act_out),
+                                                s, d_f, d_lam);
     const dim3 grid((W + FT - 1) / FT, (H + FT - 1) / FT, B);
     first_layer<<<grid, 128, 0, s>>>(d_f, H, W, d_lam, static_cast<const __nv_bfloat16 *>(d_w),
-                                     d_bias, static_cast<__nv_bfloat16 *>(d_act_out), grouped != 0);
+                                     d_bias, static_cast<__nv_bfloat16 *>(d_act_out), false);
     tv_status st = check_cuda(cudaGetLastError(), "first layer");
+    if (st == TV_OK) note_launch();
+    return st;
+}
+
+tv_status tv_net_conv3x3_dual_head(const void *d_x, int B, int H, int W, int cin, const void *d_w,
+                                   const float *d_bias, const float *d_lam, float *d_p, float *d_y,
+                                   tv_stream_t stream)
+{
+    clear_error();
+    if (!d_x || !d_w || !d_lam || !d_p || !d_y || !valid_shape(B, H, W) || !(cin == 16 || cin == 32)) {
+        set_error("tv_net_conv3x3_dual_head: need x, w, lam, p and y, 1 <= B <= 65535, H, W >= 1 "
+                  "and cin in {16, 32}");
+        return TV_ERR_INVALID;
+    }
+    if (!aligned16(d_x) || !aligned16(d_w)) {
+        set_error("tv_net_conv3x3_dual_head: x and w must be 16-byte aligned");
+        return TV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto X = static_cast<const __nv_bfloat16 *>(d_x);
+    auto Wt = static_cast<const __nv_bfloat16 *>(d_w);
+    tv_status st = cin == 32 ? launch_conv_tw<32, 16, TW_HEAD>(X, B, H, W, Wt, d_bias, 0, nullptr, nullptr, s,
+                                                              nullptr, d_lam, d_p)
+                             : launch_conv_tw<16, 16, TW_HEAD>(X, B, H, W, Wt, d_bias, 0, nullptr, nullptr, s,
+                                                              nullptr, d_lam, d_p);
+    if (st != TV_OK) return st;
+    const long long n = (long long)B * H * W;
+    head_from_p<<<ew_blocks(n), 256, 0, s>>>(d_p, n, H, W, d_y);
+    st = check_cuda(cudaGetLastError(), "dual head");
     if (st == TV_OK) note_launch();
     return st;
 }

@@ -169,7 +169,8 @@ class WarmStartNet:
         Inference takes the specialised first layer (two non-zero input channels, no
         packed input); the other layers and the head are the general kernels. With
         ``grouped`` (default ``self.grouped_inference``) the activations are kept in the
-        channel-group layout and the convolutions run on tcgen05 fed by TMA.
+        channel-group layout, every layer runs on tcgen05 (the first from the image rows,
+        the others fed by TMA) and the last layer's epilogue applies the head.
         ``predict_dual_layers`` computes the same through the kernels of training."""
         f, lam = self._inputs(f, lam)
         B, H, W = f.shape
@@ -186,6 +187,11 @@ class WarmStartNet:
         for li in range(1, len(LAYERS)):
             (cin, cout, relu), (w_off, b_off) = LAYERS[li], self.offsets[li]
             last = li == len(LAYERS) - 1
+            if last and grouped:  # epilogue keeps channel 0 and applies the head
+                _lib._check(lib.tv_net_conv3x3_dual_head(
+                    _vp(x), B, H, W, cin, _vp(self.params_bf16, w_off), _vp(self.params, b_off),
+                    _vp(lam), _vp(bufs["o"]), _vp(bufs["y"]), s))
+                return bufs["y"]
             _lib._check(conv(_vp(x), B, H, W, cin, _vp(self.params_bf16, w_off),
                              _vp(self.params, b_off), cout, int(relu),
                              _vp(bufs["o"]) if last else None,

@@ -139,6 +139,56 @@ def test_conv_forward_grouped_layout(cin, cout, shape):
     assert lib.tv_net_tensor_timeouts() == t0
 
 
+@pytest.mark.parametrize("shape", [(2, 13, 37), (1, 7, 300), (3, 2, 128), (1, 1, 1)])
+def test_first_layer_from_the_image(shape):
+    """The first layer on tcgen05 with the image rows built in shared memory (f and its
+    lambda rounded to BF16, channels 2..15 zero) against the FP64 reference on the packed
+    input; the activation comes out in the channel-group layout."""
+    lib = _lib.load()
+    b_, h_, w_ = shape
+    f = torch.rand(b_, h_, w_, generator=torch.Generator().manual_seed(31)).to(DEV)
+    lam = torch.tensor([0.05 + 0.1 * i for i in range(b_)], dtype=torch.float32, device=DEV)
+    w = _bf16((32, 3, 3, 16), 32, scale=0.3)
+    bias = torch.randn(32, generator=torch.Generator().manual_seed(33)).to(DEV)
+    act = torch.full((b_, h_, 4, w_, 8), float("nan"), dtype=torch.bfloat16, device=DEV)
+    t0 = lib.tv_net_tensor_timeouts()
+    _lib._check(lib.tv_net_first_layer(_vp(f), b_, h_, w_, _vp(lam), _vp(w), _vp(bias), _vp(act), 1,
+                                       _stream()))
+    x = ref.pack_input(_np(f.to(torch.bfloat16)), lam.to(torch.bfloat16).float().cpu().numpy())
+    want = ref.conv3x3(x, _np(w), bias.cpu().numpy().astype(np.float64)).numpy()
+    _bf16_close(_np(_ungrouped(act)), np.maximum(want, 0.0), atol=1e-4)
+    assert lib.tv_net_tensor_timeouts() == t0
+
+
+@pytest.mark.parametrize("cin", [32, 16])
+@pytest.mark.parametrize("shape", [(2, 13, 37), (1, 7, 300), (3, 2, 128), (1, 1, 1)])
+def test_last_layer_fused_with_the_dual_head(cin, shape):
+    """The last convolution (cin -> 16, grouped input) whose epilogue keeps channel 0 and
+    writes p = lambda tanh(o) on the vertical edges, then y = D_v^T p, against the FP64
+    reference convolution followed by the reference head."""
+    lib = _lib.load()
+    b_, h_, w_ = shape
+    x = _bf16((b_, h_, w_, cin), 41)
+    w = _bf16((16, 3, 3, cin), 42, scale=0.2)
+    bias = torch.randn(16, generator=torch.Generator().manual_seed(43)).to(DEV)
+    lam = torch.tensor([0.1 + 0.07 * i for i in range(b_)], dtype=torch.float32, device=DEV)
+    p = torch.full((b_, h_, w_), float("nan"), device=DEV)
+    y = torch.full((b_, h_, w_), float("nan"), device=DEV)
+    t0 = lib.tv_net_tensor_timeouts()
+    _lib._check(lib.tv_net_conv3x3_dual_head(_vp(_grouped(x)), b_, h_, w_, cin, _vp(w), _vp(bias),
+                                             _vp(lam), _vp(p), _vp(y), _stream()))
+    o = ref.conv3x3(_np(x), _np(w), bias.cpu().numpy().astype(np.float64))[..., 0]
+    lam64 = lam.cpu().numpy().astype(np.float64)
+    want_y = ref.dual_head(o, lam64).numpy()
+    # |d tanh| <= 1: an FP32-sum difference in o moves y by at most lambda times as much
+    tol = 2e-5 * max(1.0, float(o.abs().max())) * float(lam64.max()) * 2 + 1e-6
+    np.testing.assert_allclose(y.cpu().numpy(), want_y, rtol=0, atol=tol)
+    want_p = lam64[:, None, None] * np.tanh(o.numpy())
+    want_p[:, -1] = 0.0
+    np.testing.assert_allclose(p.cpu().numpy(), want_p, rtol=0, atol=tol)
+    assert lib.tv_net_tensor_timeouts() == t0
+
+
 @pytest.mark.parametrize("cin,cout", PAIRS)
 def test_conv_backward_data_and_weight(cin, cout):
     lib = _lib.load()
