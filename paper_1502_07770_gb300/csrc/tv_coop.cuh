@@ -604,6 +604,61 @@ __device__ __forceinline__ float clip_suffix16(float lo, float hi, float x_next,
     return clip_to(x_next, lo, hi);
 }
 
+// Ring form of coop_update for a 16-lane half (TV-l2): the message's breakpoints sit at
+// ring positions 0 .. size-1 counted from lane `head` (lane (head + t) mod 16 holds
+// position t). Removing breakpoints at either end and adding lambda^-, lambda^+ moves no
+// data: lambda^- lies on the piece right of the last breakpoint removed on the left, so
+// that lane turns into it (with none removed, the lane before the head takes the
+// closed-form crossing on the flat left end); the lane after the last kept breakpoint
+// turns into lambda^+, the crossing on its predecessor's piece, which every lane passes
+// to its successor by one fixed-offset shuffle; and head moves. The numbers of
+// breakpoints removed on the left and kept through the right are population counts of
+// one vote each (m^_i increases along the ring). The lanes that turn into lambda^- and
+// lambda^+ store the step's record. The arithmetic is coop_update's, operation for
+// operation, so the results are the same; what is gone are the shuffles that shifted
+// the state by a vote-dependent offset. (Computing the predecessor's crossing in the
+// successor lane from its shuffled state, to take that one shuffle off the path, was
+// slower: the three extra shuffles per step cost more than the latency they hide.)
+template <bool ALWAYS>
+__device__ __forceinline__ void coop_ring_update(float &lam, float &V, float &T, int &head,
+                                                 int &size, float &w_prev, float ci, float wi,
+                                                 int sl, unsigned seg_mask, bool active,
+                                                 bool &ovf, float2 *rec)
+{
+    const int idx = (sl - head) & (SEG - 1);
+    const bool valid = idx < size;
+    const float S = T + 1.f;
+    const float v = lam + V - ci;
+    const float lam_n = __shfl_sync(FULL, lam, (sl + 1) & (SEG - 1), SEG);
+    const float rS = __fdividef(1.f, S);
+    float candL = fmaxf(fmaf(-wi - v, rS, lam), lam);
+    float candR = fmaxf(fmaf(wi - v, rS, lam), lam);
+    if (idx != size - 1) {
+        candL = fminf(candL, lam_n);
+        candR = fminf(candR, lam_n);
+    }
+    const float candR_prev = __shfl_sync(FULL, candR, (sl - 1) & (SEG - 1), SEG);
+    const int ell = __popc(__ballot_sync(FULL, valid && v < -wi) & seg_mask);
+    const int nle = __popc(__ballot_sync(FULL, valid && v <= wi) & seg_mask);
+    const int keep_last = max(nle - 1, ell - 1);
+    const int K = keep_last - ell + 1;
+    ovf = ovf || ((ALWAYS || active) && K + 2 > SEG);
+    if (ALWAYS || active) {
+        const bool is_lm = idx == ((ell - 1) & (SEG - 1));
+        const bool is_hp = idx == ((keep_last + 1) & (SEG - 1));
+        const float lm = ell == 0 ? ci - wi + w_prev : candL;
+        const float hp = keep_last < 0 ? ci + wi + w_prev : candR_prev;
+        if (is_lm) rec->x = lm;
+        if (is_hp) rec->y = hp;
+        lam = is_lm ? lm : (is_hp ? hp : lam);
+        V = is_lm ? -wi : (is_hp ? wi : v);
+        T = is_lm ? (ell == 0 ? 1.f : S) : (is_hp ? 0.f : S);
+        head = (head + ell - 1) & (SEG - 1);
+        size = K + 2;
+        w_prev = wi;
+    }
+}
+
 // Policies whose edge weights are one value for the whole chain (a scaled lambda) say
 // so with `static constexpr bool UNIFORM_W = true`: the halves then take each step's
 // weight from their own lane instead of a shuffle.
@@ -618,16 +673,23 @@ template <bool FB, bool UW, class P>
 __device__ __forceinline__ void coop_halves_block(
     const P &p, typename P::Acc &acc, long long k, long long start, int n, int base, int cntw,
     int half, int sl, int seg_shift, float cv, float wv, float wsel,
-    const typename P::Raw &raw_next, float2 *rec_b, float &lam, float &V, float &T, int &size,
-    float &w_prev, float &c_s, bool &ovf)
+    const typename P::Raw &raw_next, float2 *rec_b, float &lam, float &V, float &T, int &head,
+    int &size, float &w_prev, float &c_s, bool &ovf)
 {
+    // the block's c_i (and w_i) broadcast up front, off the steps' critical path
+    float cis[SEG], wis[SEG];
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) {
+        cis[j] = __shfl_sync(FULL, cv, j, SEG);
+        if constexpr (!UW) wis[j] = __shfl_sync(FULL, wsel, j, SEG);
+    }
 #pragma unroll
     for (int j = 0; j < SEG; ++j) {
         const int qq = base + j;
-        const float ci = __shfl_sync(FULL, cv, j, SEG);
+        const float ci = cis[j];
         float wi = wv;
         if constexpr (!UW) {
-            wi = __shfl_sync(FULL, wsel, j, SEG);
+            wi = wis[j];
             if (j == SEG - 1) {
                 // the right half's last step takes the weight staged with the next block
                 float c2, w2;
@@ -642,10 +704,8 @@ __device__ __forceinline__ void coop_halves_block(
         if constexpr (!FB) {
             if (half == 0 && qq == cntw - 1) c_s = ci;
         }
-        float lmv, hpv;
-        coop_update<SEG, FB>(lam, V, T, size, w_prev, ci, wi, sl, seg_shift, stepping, ovf,
-                             lmv, hpv);
-        if (stepping && sl == 0) rec_b[j] = make_float2(lmv, hpv);
+        coop_ring_update<FB>(lam, V, T, head, size, w_prev, ci, wi, sl, 0xFFFFu << seg_shift,
+                             stepping, ovf, rec_b + j);
     }
 }
 
@@ -674,7 +734,7 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
     // Message state of this half; the empty message (size 0, w_prev = 0) makes
     // the first update produce m_{0,1} = clip(z - c_0, -w_0, w_0) exactly.
     float lam = 0.f, V = 0.f, T = 0.f, w_prev = 0.f, c_s = 0.f;
-    int size = 0;
+    int size = 0, head = 0;  // the message in ring order from lane `head` of the half
     bool ok = true, ovf = false;
     typename P::Raw raw, raw_next{};
     fetch_at(sl, raw);
@@ -706,12 +766,12 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
         if (ok) {
             if (base + SEG < cnt_lo)
                 coop_halves_block<true, UW>(p, acc, k, start, n, base, cntw, half, sl, seg_shift,
-                                            cv, wv, wsel, raw_next, rec_b, lam, V, T, size, w_prev,
-                                            c_s, ovf);
+                                            cv, wv, wsel, raw_next, rec_b, lam, V, T, head, size,
+                                            w_prev, c_s, ovf);
             else
                 coop_halves_block<false, UW>(p, acc, k, start, n, base, cntw, half, sl, seg_shift,
-                                             cv, wv, wsel, raw_next, rec_b, lam, V, T, size, w_prev,
-                                             c_s, ovf);
+                                             cv, wv, wsel, raw_next, rec_b, lam, V, T, head, size,
+                                             w_prev, c_s, ovf);
             ok = !__any_sync(FULL, ovf);
         }
         raw = raw_next;
@@ -725,8 +785,11 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
         return;
     }
     PairMsg &mine = xc.m[half];
-    mine.lam[sl] = lam;
-    mine.val[sl] = V;
+    const int pos = (sl - head) & (SEG - 1);  // back to ascending order from entry 0
+    if (pos < size) {
+        mine.lam[pos] = lam;
+        mine.val[pos] = V;
+    }
     if (sl == 0) mine.size = size;
     __syncwarp();
     const float cs_all = __shfl_sync(FULL, c_s, 0);
