@@ -605,38 +605,36 @@ __device__ __forceinline__ float clip_suffix16(float lo, float hi, float x_next,
 }
 
 // Ring form of coop_update for a 16-lane half (TV-l2): the message's breakpoints sit at
-// ring positions 0 .. size-1 counted from lane `head` (lane (head + t) mod 16 holds
-// position t). Removing breakpoints at either end and adding lambda^-, lambda^+ moves no
-// data: lambda^- lies on the piece right of the last breakpoint removed on the left, so
-// that lane turns into it (with none removed, the lane before the head takes the
+// ring positions 0 .. size-1 counted from a head lane, and each lane carries its own
+// position `idx`. Removing breakpoints at either end and adding lambda^-, lambda^+ moves
+// no data: lambda^- lies on the piece right of the last breakpoint removed on the left,
+// so that lane turns into it (with none removed, the lane before the head takes the
 // closed-form crossing on the flat left end); the lane after the last kept breakpoint
 // turns into lambda^+, the crossing on its predecessor's piece, which every lane passes
-// to its successor by one fixed-offset shuffle; and head moves. The numbers of
-// breakpoints removed on the left and kept through the right are population counts of
-// one vote each (m^_i increases along the ring). The lanes that turn into lambda^- and
-// lambda^+ store the step's record. The arithmetic is coop_update's, operation for
-// operation, so the results are the same; what is gone are the shuffles that shifted
-// the state by a vote-dependent offset. (Computing the predecessor's crossing in the
-// successor lane from its shuffled state, to take that one shuffle off the path, was
+// to its successor by one fixed-offset shuffle; and the positions shift by ell - 1. The
+// numbers of breakpoints removed on the left and kept through the right are population
+// counts of one vote each (m^_i increases along the ring). The lanes that turn into
+// lambda^- and lambda^+ store the step's record. The crossings are Sec. 4.1's formula,
+// lambda_k + (+-w - v_k) / S_k, kept from falling below lambda_k; the bound at the next
+// breakpoint is not applied, since the crossing that is used lies before it
+// (v_{k+1} is beyond +-w). What is gone against coop_update are the shuffles that
+// shifted the state by a vote-dependent offset. (Computing the predecessor's crossing in
+// the successor lane from its shuffled state, to take that one shuffle off the path, was
 // slower: the three extra shuffles per step cost more than the latency they hide.)
 template <bool ALWAYS>
-__device__ __forceinline__ void coop_ring_update(float &lam, float &V, float &T, int &head,
+__device__ __forceinline__ void coop_ring_update(float &lam, float &V, float &T, int &idx,
                                                  int &size, float &w_prev, float ci, float wi,
                                                  int sl, unsigned seg_mask, bool active,
                                                  bool &ovf, float2 *rec)
 {
-    const int idx = (sl - head) & (SEG - 1);
     const bool valid = idx < size;
     const float S = T + 1.f;
     const float v = lam + V - ci;
-    const float lam_n = __shfl_sync(FULL, lam, (sl + 1) & (SEG - 1), SEG);
+    // crossings of this lane's piece with -w and +w (not below its breakpoint; the one
+    // that is used lies on the piece, before the next breakpoint, as v increases)
     const float rS = __fdividef(1.f, S);
-    float candL = fmaxf(fmaf(-wi - v, rS, lam), lam);
-    float candR = fmaxf(fmaf(wi - v, rS, lam), lam);
-    if (idx != size - 1) {
-        candL = fminf(candL, lam_n);
-        candR = fminf(candR, lam_n);
-    }
+    const float candL = fmaxf(fmaf(-wi - v, rS, lam), lam);
+    const float candR = fmaxf(fmaf(wi - v, rS, lam), lam);
     const float candR_prev = __shfl_sync(FULL, candR, (sl - 1) & (SEG - 1), SEG);
     const int ell = __popc(__ballot_sync(FULL, valid && v < -wi) & seg_mask);
     const int nle = __popc(__ballot_sync(FULL, valid && v <= wi) & seg_mask);
@@ -653,7 +651,7 @@ __device__ __forceinline__ void coop_ring_update(float &lam, float &V, float &T,
         lam = is_lm ? lm : (is_hp ? hp : lam);
         V = is_lm ? -wi : (is_hp ? wi : v);
         T = is_lm ? (ell == 0 ? 1.f : S) : (is_hp ? 0.f : S);
-        head = (head + ell - 1) & (SEG - 1);
+        idx = (idx - ell + 1) & (SEG - 1);
         size = K + 2;
         w_prev = wi;
     }
@@ -673,7 +671,7 @@ template <bool FB, bool UW, class P>
 __device__ __forceinline__ void coop_halves_block(
     const P &p, typename P::Acc &acc, long long k, long long start, int n, int base, int cntw,
     int half, int sl, int seg_shift, float cv, float wv, float wsel,
-    const typename P::Raw &raw_next, float2 *rec_b, float &lam, float &V, float &T, int &head,
+    const typename P::Raw &raw_next, float2 *rec_b, float &lam, float &V, float &T, int &idx,
     int &size, float &w_prev, float &c_s, bool &ovf)
 {
     // the block's c_i (and w_i) broadcast up front, off the steps' critical path
@@ -704,7 +702,7 @@ __device__ __forceinline__ void coop_halves_block(
         if constexpr (!FB) {
             if (half == 0 && qq == cntw - 1) c_s = ci;
         }
-        coop_ring_update<FB>(lam, V, T, head, size, w_prev, ci, wi, sl, 0xFFFFu << seg_shift,
+        coop_ring_update<FB>(lam, V, T, idx, size, w_prev, ci, wi, sl, 0xFFFFu << seg_shift,
                              stepping, ovf, rec_b + j);
     }
 }
@@ -734,7 +732,7 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
     // Message state of this half; the empty message (size 0, w_prev = 0) makes
     // the first update produce m_{0,1} = clip(z - c_0, -w_0, w_0) exactly.
     float lam = 0.f, V = 0.f, T = 0.f, w_prev = 0.f, c_s = 0.f;
-    int size = 0, head = 0;  // the message in ring order from lane `head` of the half
+    int size = 0, idx = sl;  // the message in ring order; idx: this lane's ring position
     bool ok = true, ovf = false;
     typename P::Raw raw, raw_next{};
     fetch_at(sl, raw);
@@ -766,11 +764,11 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
         if (ok) {
             if (base + SEG < cnt_lo)
                 coop_halves_block<true, UW>(p, acc, k, start, n, base, cntw, half, sl, seg_shift,
-                                            cv, wv, wsel, raw_next, rec_b, lam, V, T, head, size,
+                                            cv, wv, wsel, raw_next, rec_b, lam, V, T, idx, size,
                                             w_prev, c_s, ovf);
             else
                 coop_halves_block<false, UW>(p, acc, k, start, n, base, cntw, half, sl, seg_shift,
-                                             cv, wv, wsel, raw_next, rec_b, lam, V, T, head, size,
+                                             cv, wv, wsel, raw_next, rec_b, lam, V, T, idx, size,
                                              w_prev, c_s, ovf);
             ok = !__any_sync(FULL, ovf);
         }
@@ -785,10 +783,9 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
         return;
     }
     PairMsg &mine = xc.m[half];
-    const int pos = (sl - head) & (SEG - 1);  // back to ascending order from entry 0
-    if (pos < size) {
-        mine.lam[pos] = lam;
-        mine.val[pos] = V;
+    if (idx < size) {  // back to ascending order from entry 0
+        mine.lam[idx] = lam;
+        mine.val[idx] = V;
     }
     if (sl == 0) mine.size = size;
     __syncwarp();
