@@ -500,12 +500,18 @@ __global__ void __launch_bounds__(256)
 
 // y = D_v^T p for p already on the vertical edges (0 on each image's last row):
 // y[r] = p[r-1] - p[r], p[-1] = 0.
-__global__ void __launch_bounds__(256) head_from_p(const float *p, long long n, int H, int W, float *y)
+// Blocks along x cover a row's columns; blocks along y walk the B*H rows.
+__global__ void __launch_bounds__(256) head_from_p(const float *p, long long rows, int H, int W, float *y)
 {
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)((q / W) % H);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    int r = (int)(blockIdx.y % (unsigned)H);  // row within its image
+    const int dr = (int)(gridDim.y % (unsigned)H);
+    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
+        const long long q = row * W + x;
         y[q] = (r > 0 ? p[q - W] : 0.f) - p[q];
+        r += dr;
+        if (r >= H) r -= H;
     }
 }
 
@@ -1856,8 +1862,9 @@ tv_status tv_net_conv3x3_dual_head(const void *d_x, int B, int H, int W, int cin
                              : launch_conv_tw<16, 16, TW_HEAD>(X, B, H, W, Wt, d_bias, 0, nullptr, nullptr, s,
                                                               nullptr, d_lam, d_p);
     if (st != TV_OK) return st;
-    const long long n = (long long)B * H * W;
-    head_from_p<<<ew_blocks(n), 256, 0, s>>>(d_p, n, H, W, d_y);
+    const long long rows = (long long)B * H;
+    const dim3 hg((unsigned)((W + 255) / 256), (unsigned)std::min<long long>(rows, 65535));
+    head_from_p<<<hg, 256, 0, s>>>(d_p, rows, H, W, d_y);
     st = check_cuda(cudaGetLastError(), "dual head");
     if (st == TV_OK) note_launch();
     return st;
