@@ -638,21 +638,24 @@ __device__ __forceinline__ void coop_ring_update(float &lam, float &V, float &T,
     const float candR_prev = __shfl_sync(FULL, candR, (sl - 1) & (SEG - 1), SEG);
     const int ell = __popc(__ballot_sync(FULL, valid && v < -wi) & seg_mask);
     const int nle = __popc(__ballot_sync(FULL, valid && v <= wi) & seg_mask);
-    const int keep_last = max(nle - 1, ell - 1);
-    const int K = keep_last - ell + 1;
-    ovf = ovf || ((ALWAYS || active) && K + 2 > SEG);
+    // lambda^+ takes ring position max(nle, ell) (one past the last kept breakpoint), and
+    // the new message holds the kept ones between lambda^- and lambda^+
+    const int hpos = max(nle, ell);
+    const int nsize = hpos - ell + 2;
+    ovf = ovf || ((ALWAYS || active) && nsize > SEG);
     if (ALWAYS || active) {
-        const bool is_lm = idx == ((ell - 1) & (SEG - 1));
-        const bool is_hp = idx == ((keep_last + 1) & (SEG - 1));
+        const int lpos = ell - 1;
+        const bool is_lm = idx == (lpos & (SEG - 1));
+        const bool is_hp = idx == (hpos & (SEG - 1));
         const float lm = ell == 0 ? ci - wi + w_prev : candL;
-        const float hp = keep_last < 0 ? ci + wi + w_prev : candR_prev;
+        const float hp = hpos == 0 ? ci + wi + w_prev : candR_prev;
         if (is_lm) rec->x = lm;
         if (is_hp) rec->y = hp;
         lam = is_lm ? lm : (is_hp ? hp : lam);
         V = is_lm ? -wi : (is_hp ? wi : v);
         T = is_lm ? (ell == 0 ? 1.f : S) : (is_hp ? 0.f : S);
-        idx = (idx - ell + 1) & (SEG - 1);
-        size = K + 2;
+        idx = (idx - lpos) & (SEG - 1);
+        size = nsize;
         w_prev = wi;
     }
 }
