@@ -660,6 +660,36 @@ __device__ __forceinline__ void coop_ring_update(float &lam, float &V, float &T,
     }
 }
 
+// clip_suffix16's composition for two segments at once (their rounds interleaved, since
+// neither waits for x_next): lane j of each gets the clips of lanes j..15 composed.
+__device__ __forceinline__ void clip_compose16_pair(float &lo0, float &hi0, bool inb0, float &lo1,
+                                                    float &hi1, bool inb1, int sl)
+{
+    if (!inb0) {
+        lo0 = -INFINITY;
+        hi0 = INFINITY;
+    }
+    if (!inb1) {
+        lo1 = -INFINITY;
+        hi1 = INFINITY;
+    }
+#pragma unroll
+    for (int o = 1; o < SEG; o <<= 1) {
+        const float a = __shfl_down_sync(FULL, lo0, o, SEG);
+        const float b = __shfl_down_sync(FULL, hi0, o, SEG);
+        const float c = __shfl_down_sync(FULL, lo1, o, SEG);
+        const float d = __shfl_down_sync(FULL, hi1, o, SEG);
+        if (sl + o < SEG) {
+            const float nlo0 = clip_to(a, lo0, hi0), nhi0 = clip_to(b, lo0, hi0);
+            const float nlo1 = clip_to(c, lo1, hi1), nhi1 = clip_to(d, lo1, hi1);
+            lo0 = nlo0;
+            hi0 = nhi0;
+            lo1 = nlo1;
+            hi1 = nhi1;
+        }
+    }
+}
+
 // Policies whose edge weights are one value for the whole chain (a scaled lambda) say
 // so with `static constexpr bool UNIFORM_W = true`: the halves then take each step's
 // weight from their own lane instead of a shuffle.
@@ -806,10 +836,7 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
     const int nbl_l = (s + SEG - 1) / SEG;
     const int nbl_r = (n - 1 - s + SEG - 1) / SEG;
     const int nbb = nbl_l > nbl_r ? nbl_l : nbl_r;
-    float x_next = xs;
-    for (int t = 0; t < nbb; ++t) {
-        int i;
-        bool inb;
+    auto seg_node = [&](int t, int &i, bool &inb) {
         if (half == 0) {
             const int blk = nbl_l - 1 - t;
             i = blk * SEG + sl;
@@ -818,19 +845,42 @@ __device__ void coop_solve_chain_halves(const P &p, typename P::Acc &acc, long l
             i = s + 1 + t * SEG + (SEG - 1 - sl);
             inb = t < nbl_r && i < n;
         }
-        float lo = -INFINITY, hi = INFINITY;
+    };
+    auto load_rec = [&](int i, bool inb, float &lo, float &hi) {
+        lo = -INFINITY;
+        hi = INFINITY;
         if (inb) {
             const float2 r = recp[half == 0 ? i : n + s - i];  // right half: mirrored slots
             lo = r.x;
             hi = r.y;
         }
-        const float xv = clip_suffix16(lo, hi, x_next, sl, inb);
+    };
+    auto finish = [&](int i, bool inb, float xv) {
         if (inb) {
             float cc = 0.f;
             if constexpr (P::CREC) cc = crecp[i];
             p.emit(k, start, i, xv, cc);
         }
-        x_next = __shfl_sync(FULL, xv, 0, SEG);
+    };
+    // two segments per round: their compositions do not wait for x_next, only the final
+    // clips do
+    float x_next = xs;
+    for (int t = 0; t < nbb; t += 2) {
+        int i0, i1;
+        bool in0, in1;
+        seg_node(t, i0, in0);
+        seg_node(t + 1, i1, in1);
+        if (t + 1 >= nbb) in1 = false;
+        float lo0, hi0, lo1, hi1;
+        load_rec(i0, in0, lo0, hi0);
+        load_rec(i1, in1, lo1, hi1);
+        clip_compose16_pair(lo0, hi0, in0, lo1, hi1, in1, sl);
+        const float x0 = clip_to(x_next, lo0, hi0);
+        finish(i0, in0, x0);
+        x_next = __shfl_sync(FULL, x0, 0, SEG);
+        const float x1 = clip_to(x_next, lo1, hi1);
+        finish(i1, in1, x1);
+        x_next = __shfl_sync(FULL, x1, 0, SEG);
     }
 }
 
