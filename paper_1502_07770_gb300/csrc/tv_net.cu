@@ -915,9 +915,9 @@ __global__ void __launch_bounds__(NTHR)
 // written) and the other roles stop at their next wait.
 constexpr int TW_NHWC = 0, TW_GROUPED = 1, TW_IMAGE = 2, TW_HEAD = 3;
 // Row slots: the image rows come from plain loads, whose latency a deeper ring hides; the
-// TMA rows need fewer, and a smaller ring lets three blocks share an SM.
+// TMA rows need fewer, and a smaller ring lets four blocks share an SM.
 __host__ __device__ constexpr int tw_nr(int io) { return io == TW_IMAGE ? 8 : 4; }
-// TMEM accumulator blocks: 128 columns per block either way, so that three blocks fit
+// TMEM accumulator blocks: 128 columns per block either way, so that four blocks fit
 __host__ __device__ constexpr int tw_r(int cout) { return 128 / cout; }
 constexpr int TW_THREADS = 224;     // warp 0 loads, warp 2 issues the MMAs, warps 3-6 epilogue
 constexpr int TW_GS = 2176;         // bytes per 8-channel group in a row slot
@@ -1022,7 +1022,7 @@ __device__ __forceinline__ int tw_block(unsigned o)
 }
 
 template <int CIN, int COUT, int IO>
-__global__ void __launch_bounds__(TW_THREADS, 3)
+__global__ void __launch_bounds__(TW_THREADS, 4)
     conv3x3_tw(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_tail,
                int B, int H, int W, int L, const __nv_bfloat16 *Wt, const float *bias, int relu,
                float *pre_out, __nv_bfloat16 *act_out, const float *img, const float *lam, float *p_out)
