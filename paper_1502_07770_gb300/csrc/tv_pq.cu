@@ -164,119 +164,92 @@ __device__ __forceinline__ void pq_update(PqState &s, float a, float b, float al
     s.wlo_p = wlo;
 }
 
-// The same update on a segment of G lanes (G = 16: two chain halves per warp, each
-// segment one half; sl the lane in the segment, seg_shift its first lane). Every lane
-// executes every shuffle; a segment whose half has no node at this step passes
-// active = false and keeps its state. ALWAYS: every segment updates (compile time).
-template <int G, bool ALWAYS = false>
-__device__ __forceinline__ void pq_update_seg(PqState &s, float a, float b, float al, float f,
-                                              float wlo, float whi, int sl, int seg_shift,
-                                              bool active, bool &ovf, float &lm, float &hp)
+// pq_update for a 16-lane half (two chain halves per warp), in ring form: the breakpoints
+// sit at ring positions 0 .. size-1 counted from a head lane, each lane carrying its
+// position idx. Inserting f
+// at position ins moves the entries at positions ins.. up by one (one fixed-offset
+// shuffle per field: every lane reads its ring predecessor, which for the new entry is
+// also the entry the message's value at f is read from). Removing entries at either end
+// moves nothing: lambda^- and lambda^+ take the lanes of the entries they replace (the
+// last one removed on the left, the first one removed on the right, or the entry at a
+// jump itself), and the positions shift. The counts that place them are population
+// counts of votes (limits increase along the ring): entries with R < w^-, with L <= w^+,
+// and the jumps from those with L < w^- and with R <= w^+. The lanes that take lambda^-
+// and lambda^+ store the step's record. The arithmetic is pq_update's.
+struct PqRing {
+    float lam, L, R, S;  // this lane's entry (ring position idx)
+    int idx, size;
+    float wlo_p;         // the message's value left of its first breakpoint
+};
+
+template <bool ALWAYS>
+__device__ __forceinline__ void pq_ring_update(PqRing &s, float a, float b, float al, float f,
+                                               float wlo, float whi, int sl, unsigned seg_mask,
+                                               bool active, bool &ovf, float2 *rec)
 {
-    auto seg = [&](unsigned bal) { return (bal >> seg_shift) & ((1u << G) - 1u); };
-    bool valid = sl < s.size;
-    // ---- insert f (unless a breakpoint is already there) ----
-    const int ins = __popc(seg(__ballot_sync(FULL, valid && s.lam < f)));
-    const float lam_at = __shfl_sync(FULL, s.lam, ins, G);
-    const bool exists = ins < s.size && lam_at == f;
-    const float pl = __shfl_sync(FULL, s.lam, ins - 1, G), pR = __shfl_sync(FULL, s.R, ins - 1, G),
-                pS = __shfl_sync(FULL, s.S, ins - 1, G);
-    const float ul = __shfl_up_sync(FULL, s.lam, 1, G), uL = __shfl_up_sync(FULL, s.L, 1, G),
-                uR = __shfl_up_sync(FULL, s.R, 1, G), uS = __shfl_up_sync(FULL, s.S, 1, G);
-    if ((ALWAYS || active) && !exists) {
-        if (s.size + 1 > G) ovf = true;
-        float mval, Sn;
-        if (ins == 0) {
-            mval = s.size > 0 ? s.wlo_p : 0.f;  // the message's flat left end (0 before node 0)
-            Sn = 0.f;
-        } else {
-            mval = fmaf(pS, f - pl, pR);
-            Sn = pS;
-        }
-        if (sl == ins) {
-            s.lam = f;
-            s.L = mval;
-            s.R = mval;
-            s.S = Sn;
-        } else if (sl > ins) {
-            s.lam = ul;
-            s.L = uL;
-            s.R = uR;
-            s.S = uS;
-        }
-        s.size += 1;
-        valid = sl < s.size;
-    }
-    // ---- transformation (a): + a z - b - alpha left of f, + alpha right of it ----
+    constexpr int G = 16;
+    const int prv = (sl - 1) & (G - 1), nxt = (sl + 1) & (G - 1);
+    bool valid = s.idx < s.size;
+    // ---- insert f (unless an entry is already there) ----
+    const int ins = __popc(__ballot_sync(FULL, valid && s.lam < f) & seg_mask);
+    const bool fresh = (__ballot_sync(FULL, valid && s.lam == f) & seg_mask) == 0u;
+    const float ul = __shfl_sync(FULL, s.lam, prv, G), uL = __shfl_sync(FULL, s.L, prv, G),
+                uR = __shfl_sync(FULL, s.R, prv, G), uS = __shfl_sync(FULL, s.S, prv, G);
     if (ALWAYS || active) {
+        if (fresh && s.size + 1 > G) ovf = true;
+        const bool at = fresh && s.idx == ins;
+        const bool up = fresh && s.idx > ins && s.idx <= s.size;
+        const float mval = ins == 0 ? (s.size > 0 ? s.wlo_p : 0.f) : fmaf(uS, f - ul, uR);
+        const float Sn = ins == 0 ? 0.f : uS;
+        s.lam = at ? f : (up ? ul : s.lam);
+        s.L = at ? mval : (up ? uL : s.L);
+        s.R = at ? mval : (up ? uR : s.R);
+        s.S = at ? Sn : (up ? uS : s.S);
+        s.size += fresh ? 1 : 0;
+        // ---- transformation (a): + a z - b - alpha left of f, + alpha right of it ----
         const float lin = fmaf(a, s.lam, -b);
-        const float dl = (sl <= ins) ? -al : al;
-        const float dr = (sl < ins) ? -al : al;
-        s.L += lin + dl;
-        s.R += lin + dr;
+        s.L += lin + (s.idx <= ins ? -al : al);
+        s.R += lin + (s.idx < ins ? -al : al);
         s.S += a;
     }
-    const float lam_n = __shfl_down_sync(FULL, s.lam, 1, G);
-    const bool last = sl == s.size - 1;
+    valid = s.idx < s.size;
+    const float lam_n = __shfl_sync(FULL, s.lam, nxt, G), R_n = __shfl_sync(FULL, s.R, nxt, G);
+    const bool last = s.idx == s.size - 1;
     float cL = fmaxf(s.lam + __fdividef(wlo - s.R, s.S), s.lam);
     float cR = fmaxf(s.lam + __fdividef(whi - s.R, s.S), s.lam);
     if (!last) {
         cL = fminf(cL, lam_n);
         cR = fminf(cR, lam_n);
     }
-    const unsigned bge = seg(__ballot_sync(FULL, valid && s.R >= wlo));
-    const unsigned ble = seg(__ballot_sync(FULL, valid && s.L <= whi));
-    // trailing zeros of an empty vote are 32 (ell = size); 31 - clz(0) = -1 (no kept point)
-    const int ell = min(__clz(__brev(bge)), s.size);
-    const int kl = 31 - __clz(ble);
-    const float L0 = __shfl_sync(FULL, s.L, 0, G), lam0 = __shfl_sync(FULL, s.lam, 0, G);
-    const float Le = __shfl_sync(FULL, s.L, ell, G), Re = __shfl_sync(FULL, s.R, ell, G),
-                lame = __shfl_sync(FULL, s.lam, ell, G), Se = __shfl_sync(FULL, s.S, ell, G);
-    const float cLm = __shfl_sync(FULL, cL, ell - 1, G), Sm = __shfl_sync(FULL, s.S, ell - 1, G);
-    const float Lk = __shfl_sync(FULL, s.L, kl, G), Rk = __shfl_sync(FULL, s.R, kl, G),
-                lamk = __shfl_sync(FULL, s.lam, kl, G), cRk = __shfl_sync(FULL, cR, kl, G);
-    const bool jumpL = ell < s.size && Le < wlo;
-    const bool jumpR = kl >= 0 && Rk > whi;
+    const float cR_prev = __shfl_sync(FULL, cR, prv, G);
+    const int head = (sl - s.idx) & (G - 1);
+    const float lam0 = __shfl_sync(FULL, s.lam, head, G), L0 = __shfl_sync(FULL, s.L, head, G);
+    const int ell = __popc(__ballot_sync(FULL, valid && s.R < wlo) & seg_mask);
+    const int kl = __popc(__ballot_sync(FULL, valid && s.L <= whi) & seg_mask) - 1;
+    const bool jumpL = __popc(__ballot_sync(FULL, valid && s.L < wlo) & seg_mask) > ell;
+    const bool jumpR = __popc(__ballot_sync(FULL, valid && s.R <= whi) & seg_mask) <= kl;
     const bool both = jumpL && jumpR && ell == kl;
-    float Sl;
-    if (jumpL) {
-        lm = lame;
-        Sl = Se;
-    } else if (ell == 0) {
-        lm = fminf(lam0 + (wlo - L0) / a, lam0);  // on the left end piece (slope a)
-        Sl = a;
-    } else {
-        lm = cLm;
-        Sl = Sm;
-    }
-    if (jumpR) hp = lamk;
-    else if (kl < 0) hp = fminf(lam0 + (whi - L0) / a, lam0);
-    else hp = cRk;
     const int k0 = ell + (jumpL ? 1 : 0), k1 = kl - (jumpR ? 1 : 0);
     const int K = k1 >= k0 ? k1 - k0 + 1 : 0;
     if ((ALWAYS || active) && K + 2 > G) ovf = true;
-    const float lmR = jumpL ? fminf(Re, whi) : wlo;
-    const float hpL = jumpR ? (both ? fminf(Re, whi) : fmaxf(Lk, wlo)) : whi;
-    const int src = sl - 1 + k0;
-    const float nl = __shfl_sync(FULL, s.lam, src, G), nL = __shfl_sync(FULL, s.L, src, G),
-                nR = __shfl_sync(FULL, s.R, src, G), nS = __shfl_sync(FULL, s.S, src, G);
     if (ALWAYS || active) {
-        if (sl == 0) {
-            s.lam = lm;
-            s.L = wlo;
-            s.R = lmR;
-            s.S = both ? 0.f : Sl;
-        } else if (sl == K + 1) {
-            s.lam = hp;
-            s.L = hpL;
-            s.R = whi;
-            s.S = 0.f;
-        } else {
-            s.lam = nl;
-            s.L = nL;
-            s.R = nR;
-            s.S = nS;
-        }
+        const int p_lm = (jumpL && !both) ? ell : ell - 1;  // ring position of lambda^-
+        const int p_hp = jumpR ? kl : kl + 1;               // of lambda^+
+        const bool is_lm = s.idx == (p_lm & (G - 1)), is_hp = s.idx == (p_hp & (G - 1));
+        const float lm_end = fminf(lam0 + (wlo - L0) / a, lam0);  // on the left end piece
+        const float hp_end = fminf(lam0 + (whi - L0) / a, lam0);
+        const float lmv = both ? lam_n : (jumpL ? s.lam : (ell == 0 ? lm_end : cL));
+        const float lmR = both ? fminf(R_n, whi) : (jumpL ? fminf(s.R, whi) : wlo);
+        const float lmS = both ? 0.f : (jumpL ? s.S : (ell == 0 ? a : s.S));
+        const float hpv = jumpR ? s.lam : (kl < 0 ? hp_end : cR_prev);
+        const float hpL = both ? fminf(s.R, whi) : (jumpR ? fmaxf(s.L, wlo) : whi);
+        if (is_lm) rec->x = lmv;
+        if (is_hp) rec->y = hpv;
+        s.lam = is_lm ? lmv : (is_hp ? hpv : s.lam);
+        s.L = is_lm ? wlo : (is_hp ? hpL : s.L);
+        s.R = is_lm ? lmR : (is_hp ? whi : s.R);
+        s.S = is_lm ? lmS : (is_hp ? 0.f : s.S);
+        s.idx = (s.idx - p_lm) & (G - 1);
         s.size = K + 2;
         s.wlo_p = wlo;
     }
@@ -574,7 +547,7 @@ __device__ float pq_root(const PqMsg &ML, const PqMsg &MR, float a, float b, flo
 }
 
 // ----------------------------------------------------- middle-rooted halves --
-// One warp per chain, rooted at node mid = n/2: lanes 0-15 run pq_update_seg<16> over
+// One warp per chain, rooted at node mid = n/2: lanes 0-15 run pq_ring_update over
 // nodes 0..mid-1, lanes 16-31 over nodes n-1..mid+1, both in the same instructions;
 // the two messages into the root (at most 16 breakpoints each) go to shared memory and
 // the whole warp finds the root (pq_root), then each segment clips its
@@ -584,7 +557,7 @@ __device__ float pq_root(const PqMsg &ML, const PqMsg &MR, float a, float b, flo
 // ALWAYS: every step is an update in both halves. U: curvature 1, one alpha and one
 // weight for the whole chain, so only b and f are shuffled.
 template <bool ALWAYS, bool U>
-__device__ __forceinline__ void pq_half_steps(PqState &s, bool &ovf, float2 *rec, int base,
+__device__ __forceinline__ void pq_half_steps(PqRing &s, bool &ovf, float2 *rec, int base,
                                               int c16, int cnt, int n, int seg, int sl,
                                               int seg_shift, float av, float bv, float alv,
                                               float fv, float wv, float alpha, float lam)
@@ -601,10 +574,8 @@ __device__ __forceinline__ void pq_half_steps(PqState &s, bool &ovf, float2 *rec
         }
         const int q = base + jj;
         const bool active = ALWAYS || q < cnt;
-        float lm, hp;
-        pq_update_seg<16, ALWAYS>(s, ai, bi, ali, fi, -wi, wi, sl, seg_shift, active, ovf, lm,
-                                  hp);
-        if (active && sl == 0) rec[seg == 0 ? q : n - 1 - q] = make_float2(lm, hp);
+        pq_ring_update<ALWAYS>(s, ai, bi, ali, fi, -wi, wi, sl, 0xFFFFu << seg_shift, active, ovf,
+                               rec + (seg == 0 ? q : n - 1 - q));
     }
 }
 
@@ -658,7 +629,7 @@ __global__ void pq_halves_kernel(PqArgs p, WsHeader *hdr)
     const float *b = p.b + start, *f = p.f + start;
     const float *al = p.al ? p.al + start : nullptr;
     const float *w = p.w ? p.w + (p.w_stride > 0 ? k * p.w_stride : start) : nullptr;
-    PqState s{0.f, 0.f, 0.f, 0.f, 0, 0.f, 0.f, 0.f};
+    PqRing s{0.f, 0.f, 0.f, 0.f, sl, 0, 0.f};  // the message in ring order from lane 0
     bool ovf = false;
     const int nblocks = (cmax + 15) / 16;
     const int cnt_lo = min(mid, n - 1 - mid);  // the shorter half's update steps
@@ -688,10 +659,12 @@ __global__ void pq_halves_kernel(PqArgs p, WsHeader *hdr)
         return;
     }
     PqMsg &mine = msg[warp][seg];
-    mine.lam[sl] = s.lam;
-    mine.L[sl] = s.L;
-    mine.R[sl] = s.R;
-    mine.S[sl] = s.S;
+    if (s.idx < s.size) {  // back to ascending order from entry 0
+        mine.lam[s.idx] = s.lam;
+        mine.L[s.idx] = s.L;
+        mine.R[s.idx] = s.R;
+        mine.S[s.idx] = s.S;
+    }
     if (sl == 0) {
         mine.size = cnt > 0 ? s.size : 0;
         mine.ovf = 0;
