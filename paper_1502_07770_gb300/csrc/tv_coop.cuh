@@ -690,6 +690,44 @@ __device__ __forceinline__ void clip_compose16_pair(float &lo0, float &hi0, bool
     }
 }
 
+// coop_ring_update for the general unary a_i z^2 / 2 - b_i z and slopes [w^-_i, w^+_i]
+// (coop_update_g's arithmetic in the ring form; wl_prev is w^-_{i-1}).
+template <bool ALWAYS>
+__device__ __forceinline__ void coop_ring_update_g(float &lam, float &V, float &T, int &idx,
+                                                   int &size, float &wl_prev, float ai, float bi,
+                                                   float wl, float wh, int sl, unsigned seg_mask,
+                                                   bool active, bool &ovf, float2 *rec)
+{
+    const bool valid = idx < size;
+    const float S = T + ai;
+    const float v = fmaf(ai, lam, V) - bi;
+    const float rS = __fdividef(1.f, S);
+    const float candL = fmaxf(fmaf(wl - v, rS, lam), lam);
+    const float candR = fmaxf(fmaf(wh - v, rS, lam), lam);
+    const float candR_prev = __shfl_sync(FULL, candR, (sl - 1) & (SEG - 1), SEG);
+    const int ell = __popc(__ballot_sync(FULL, valid && v < wl) & seg_mask);
+    const int nle = __popc(__ballot_sync(FULL, valid && v <= wh) & seg_mask);
+    const int hpos = max(nle, ell);
+    const int nsize = hpos - ell + 2;
+    ovf = ovf || ((ALWAYS || active) && nsize > SEG);
+    if (ALWAYS || active) {
+        const int lpos = ell - 1;
+        const bool is_lm = idx == (lpos & (SEG - 1));
+        const bool is_hp = idx == (hpos & (SEG - 1));
+        // on the flat left end m^_i = w^-_{i-1} + a_i z - b_i
+        const float lm = ell == 0 ? (bi + wl - wl_prev) / ai : candL;
+        const float hp = hpos == 0 ? (bi + wh - wl_prev) / ai : candR_prev;
+        if (is_lm) rec->x = lm;
+        if (is_hp) rec->y = hp;
+        lam = is_lm ? lm : (is_hp ? hp : lam);
+        V = is_lm ? wl : (is_hp ? wh : v);
+        T = is_lm ? (ell == 0 ? ai : S) : (is_hp ? 0.f : S);
+        idx = (idx - lpos) & (SEG - 1);
+        size = nsize;
+        wl_prev = wl;
+    }
+}
+
 // Policies whose edge weights are one value for the whole chain (a scaled lambda) say
 // so with `static constexpr bool UNIFORM_W = true`: the halves then take each step's
 // weight from their own lane instead of a shuffle.
@@ -1062,7 +1100,7 @@ __device__ void coop_solve_chain_halves_general(const P &p, typename P::Acc &acc
         p.fetch(k, start, n, q < cntw ? node(q) : n, r);
     };
     float lam = 0.f, V = 0.f, T = 0.f, wl_prev = 0.f, a_s = 1.f, b_s = 0.f;
-    int size = 0;
+    int size = 0, idx = sl;  // the message in ring order; idx: this lane's ring position
     bool ok = true, ovf = false;
     typename P::Raw raw, raw_next{};
     fetch_at(sl, raw);
@@ -1103,10 +1141,8 @@ __device__ void coop_solve_chain_halves_general(const P &p, typename P::Acc &acc
                     a_s = ai;
                     b_s = bi;
                 }
-                float lmv, hpv;
-                coop_update_g<SEG>(lam, V, T, size, wl_prev, ai, bi, wl, wh, sl, seg_shift,
-                                   stepping, ovf, lmv, hpv);
-                if (stepping && sl == 0) recp[node(qq)] = make_float2(lmv, hpv);
+                coop_ring_update_g<false>(lam, V, T, idx, size, wl_prev, ai, bi, wl, wh, sl,
+                                          0xFFFFu << seg_shift, stepping, ovf, recp + node(qq));
             }
             ok = !__any_sync(FULL, ovf);
         }
@@ -1119,8 +1155,10 @@ __device__ void coop_solve_chain_halves_general(const P &p, typename P::Acc &acc
         return;
     }
     PairMsg &mine = xc.m[half];
-    mine.lam[sl] = lam;
-    mine.val[sl] = V;
+    if (idx < size) {  // back to ascending order from entry 0
+        mine.lam[idx] = lam;
+        mine.val[idx] = V;
+    }
     if (sl == 0) mine.size = size;
     __syncwarp();
     const float as_all = __shfl_sync(FULL, a_s, 0), bs_all = __shfl_sync(FULL, b_s, 0);
