@@ -569,7 +569,7 @@ tv_status launch_batch(const P &p, long long nchains, float2 *rec, float *crec, 
 constexpr int kRingHalf = 16;
 
 constexpr int kHalvesMinLen = 64;
-constexpr int kFlatMinLenW = 512;
+constexpr int kFlatMinLenW = 1024;
 
 template <bool HAS_W>
 tv_status launch_halves(const ChainRowsP<HAS_W> &p, long long nchains, int max_len, float2 *rec,
