@@ -257,6 +257,31 @@ def test_thread_kernel_closed_forms(thread_path):
         assert pins.kkt_residual(yk[k], 0.15, x[k]) < 2e-3
 
 
+def test_halves_at_full_ring_capacity():
+    """Chains whose half messages peak at exactly 16 breakpoints, all the lanes of a
+    16-lane half (a 28-node steep ramp with heavy weights, at the start of the chain or,
+    mirrored, at its end): the ring of each half wraps all the way round without falling
+    back to the whole warp. Against the oracle."""
+    n = 80
+    ys, ws = [], []
+    for k in range(16):
+        base = np.concatenate([(-np.arange(28) / 40.0),
+                               np.random.default_rng(k).uniform(0, 1, n - 28)])
+        w = np.concatenate([np.full(28, 2.5), np.full(n - 28, 0.05)])
+        if k % 2:  # mirrored: the ramp in the right half (edge i of the mirror is n-2-i)
+            base = base[::-1].copy()
+            w = np.concatenate([w[:n - 1][::-1], [0.0]])
+        ys.append(base)
+        ws.append(w)
+    y = np.stack(ys).astype(np.float32)
+    w = np.stack(ws).astype(np.float32)
+    ws_ = _lib.workspace(_lib.load().tv_chain_workspace_size(16, n), DEV, "full-ring")
+    x = _lib.chain_prox(_gpu(y), _gpu(w), ws=ws_).cpu().numpy()
+    assert _lib.workspace_status(ws_)[1] == 0
+    xr = oracle.chain_solve_batch(y.ravel(), np.arange(17) * n, w=w.ravel()).reshape(y.shape)
+    assert np.abs(x - xr).max() <= TOL
+
+
 def test_half_overflow_falls_back_to_the_whole_warp():
     """A chain whose left half needs ~22 breakpoints: more than a 16-lane half holds, fewer
     than the 32 lanes of the whole warp, which solves it without the lane-0 path."""

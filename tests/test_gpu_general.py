@@ -80,3 +80,31 @@ def test_general_overflow_path():
     xr = oracle.chain_solve_general(a.ravel(), b.ravel(), wlo.ravel(), whi.ravel(),
                                     np.arange(B + 1) * n).reshape(B, n)
     assert np.abs(x - xr).max() <= TOL
+
+
+def test_general_halves_at_full_ring_capacity():
+    """Half messages that peak at exactly 16 breakpoints (a 28-node steep ramp with heavy
+    slopes, at either end) through the general chain halves, with a = 1 and
+    [w-, w+] = [-w, w]: against the general oracle and against the TV-l2 oracle, which
+    this case reduces to."""
+    n = 80
+    ys, wv = [], []
+    for k in range(16):
+        base = np.concatenate([(-np.arange(28) / 40.0),
+                               np.random.default_rng(40 + k).uniform(0, 1, n - 28)])
+        w = np.concatenate([np.full(28, 2.5), np.full(n - 28, 0.05)])
+        if k % 2:
+            base = base[::-1].copy()
+            w = np.concatenate([w[:n - 1][::-1], [0.0]])
+        ys.append(base)
+        wv.append(w)
+    b = np.concatenate(ys).astype(np.float32)
+    w = np.concatenate(wv).astype(np.float32)
+    a = np.ones_like(b)
+    off = (np.arange(17) * n).astype(np.int64)
+    x = _lib.chain_prox_general(_gpu(b), _gpu(-w), _gpu(w), a=_gpu(a),
+                                offsets=torch.from_numpy(off).to(DEV), max_len=n).cpu().numpy()
+    xg = oracle.chain_solve_general(a, b, -w, w, off)
+    xt = oracle.chain_solve_batch(b, off, w=w)
+    assert np.abs(x - xg).max() <= TOL
+    assert np.abs(xg - xt).max() <= 1e-9
