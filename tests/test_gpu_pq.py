@@ -80,3 +80,33 @@ def test_overflow_path():
     xr = oracle.chain_solve_pq(np.ones(4 * n), b.ravel(), np.full(4 * n, 0.01), f.ravel(),
                                np.full(4 * n, n / 16.0), np.arange(5) * n)
     assert np.abs(x.ravel() - xr).max() <= TOL
+
+
+def test_pq_halves_at_full_ring_capacity():
+    """Piecewise-quadratic chains whose half messages peak at exactly 16 entries (a
+    24-node ramp of b and f with heavy weights, at either end of a 64-node chain; every
+    node inserts its own f): the ring of each half wraps all the way round. Against the
+    oracle."""
+    n = 64
+    bs, fs, ws = [], [], []
+    for k in range(16):
+        rng = np.random.default_rng(60 + k)
+        b = np.concatenate([-np.arange(24) / 10.0, rng.uniform(0, 1, n - 24)])
+        f = np.concatenate([np.arange(24) / 10.0, rng.uniform(0, 1, n - 24)])
+        w = np.concatenate([np.full(24, 5.0), np.full(n - 24, 0.05)])
+        if k % 2:  # mirrored: the ramp in the right half
+            b, f = b[::-1].copy(), f[::-1].copy()
+            w = np.concatenate([w[:n - 1][::-1], [0.0]])
+        bs.append(b)
+        fs.append(f)
+        ws.append(w)
+    b = np.concatenate(bs).astype(np.float32)
+    f = np.concatenate(fs).astype(np.float32)
+    w = np.concatenate(ws).astype(np.float32)
+    a = np.ones_like(b)
+    al = np.full_like(b, 0.05)
+    off = (np.arange(17) * n).astype(np.int64)
+    x = _lib.chain_prox_pq(_gpu(b), _gpu(f), alpha=_gpu(al), w=_gpu(w),
+                           offsets=torch.from_numpy(off).to(DEV), max_len=n).cpu().numpy()
+    xr = oracle.chain_solve_pq(a, b, al, f, w, off)
+    assert np.abs(x - xr).max() <= TOL
