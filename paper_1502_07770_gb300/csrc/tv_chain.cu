@@ -600,7 +600,9 @@ tv_status launch_flat(const ChainRowsP<HAS_W> &p, long long nchains, int max_len
 {
     const long long warps = (nchains + HW - 1) / HW;
     const size_t per_warp = sizeof(FlatSmem<HAS_W ? 2 : 1>);
-    auto kern = chain_flat_kernel<ChainRowsP<HAS_W>>;
+    auto kern = chain_flat_kernel<ChainRowsP<HAS_W>, false>;
+    if constexpr (!HAS_W)
+        if (p.vec) kern = chain_flat_kernel<ChainRowsP<HAS_W>, true>;
     tv_status st = check_cuda(
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * per_warp)),
         "cudaFuncSetAttribute");

@@ -28,10 +28,14 @@
 // path of the workspace.
 //
 // Inputs are staged by the whole warp: between rounds of T iterations the lanes' next steps
-// are copied into a per-lane ring of IR slots (4-byte asynchronous copies into
-// [slot][lane], so that the lanes' reads never share a bank), up to IR - T steps ahead of
-// the slowest lane; a lane that reaches the end of the staged range waits for the next
-// round.
+// are copied into a per-lane ring of IR slots, up to IR - T steps ahead of the slowest lane;
+// a lane that reaches the end of the staged range waits for the next round. In general the
+// copies are 4-byte ones into [slot][lane] (the lanes' reads never share a bank); for
+// uniform chains whose length is a multiple of 4 (VEC) each lane copies 4 steps of its half
+// with one 16-byte copy into [slot / 4][lane][4]. Every lane reads a different chain, so a
+// copy instruction touches 32 sectors either way, and the 16-byte form needs a quarter of
+// the instructions and of the L1 wavefronts per node (a right half's 4 steps lie in memory
+// in reverse, read back with the element index flipped).
 //
 // Algorithm 2 roots chain k at node mid = n/2: lane l < 16 runs nodes 0..mid-1, lane l + 16
 // nodes n-1..mid+1; then the left lane solves the root from both messages (flat_root) and
@@ -131,11 +135,13 @@ __device__ __forceinline__ float flat_root(unsigned baseL, int FL, int BL, float
 }
 
 // P: a row policy of tv_chain.cu (contiguous chains, CSR or uniform) with fields y, w, lam
-// and chain(); HAS_W = per-edge weights w.
-template <class P>
+// and chain(); HAS_W = per-edge weights w. VEC: 16-byte staging (uniform chains, length a
+// multiple of 4, y 16-byte aligned; no per-edge weights).
+template <class P, bool VEC>
 __global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *hdr, int halfmax)
 {
     constexpr bool HAS_W = P::WI >= 0;
+    static_assert(!(VEC && HAS_W), "16-byte staging is for uniform weights only");
     constexpr int NIN = HAS_W ? 2 : 1;
     constexpr int S = FL_S, G = FL_G, IR = FL_IR, T = FL_T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -168,27 +174,46 @@ __global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *
     const float *wsrc = nullptr;
     if constexpr (HAS_W) wsrc = p.w + start + (left ? 0 : n - 2);
     const long long dir = left ? 1 : -1;
+    // VEC: steps 4q..4q+3 at in[0][4 (q % (IR/4)) ...] as [slot/4][lane][4]; a right half's
+    // chunk is nodes n-4-4q..n-1-4q in memory order (step 4q+e at element 3-e)
+    float *const in4 = &sm->u.f.in[0][0][0] + 4 * lane;
     auto stage = [&](int t0, int t1) {  // steps [t0, t1), warp-uniform bounds
-        for (int t = t0; t < t1; ++t) {
-            if (t < cnt) {
-                cp_async4(&sm->u.f.in[0][t & (IR - 1)][lane], ysrc + dir * t);
-                if constexpr (HAS_W)
-                    cp_async4(&sm->u.f.in[NIN - 1][t & (IR - 1)][lane], wsrc + dir * t);
+        if constexpr (VEC) {
+            for (int t = t0; t < t1; t += 4)
+                if (t < cnt)
+                    cp_async16(in4 + ((t >> 2) & (IR / 4 - 1)) * (4 * WARP), left ? ysrc + t : ysrc - t - 3);
+        } else {
+            for (int t = t0; t < t1; ++t) {
+                if (t < cnt) {
+                    cp_async4(&sm->u.f.in[0][t & (IR - 1)][lane], ysrc + dir * t);
+                    if constexpr (HAS_W)
+                        cp_async4(&sm->u.f.in[NIN - 1][t & (IR - 1)][lane], wsrc + dir * t);
+                }
             }
         }
         cp_async_commit();
     };
+    // staged ranges end on 4-step boundaries for VEC (the chunk past a half's end stays in
+    // its chain: node mid + 2 at most on the left, mid - 2 at least on the right)
+    const int cmaxs = VEC ? (cmax + 3) & ~3 : cmax;
+    auto stage_end = [&](int t) { return VEC ? t & ~3 : t; };
 
     // ---------------- message array ----------------
     const unsigned msg0 = (unsigned)__cvta_generic_to_shared(&sm->u.f.msg[0][lane]);
     auto slot = [&](int s) { return msg0 + ((unsigned)(s + G) << 8); };
     const unsigned lo_lim = slot(1), hi_lim = slot(S - 2);
-    const unsigned in0 = (unsigned)__cvta_generic_to_shared(&sm->u.f.in[0][0][lane]);
+    const unsigned in0 = VEC ? (unsigned)__cvta_generic_to_shared(in4)
+                             : (unsigned)__cvta_generic_to_shared(&sm->u.f.in[0][0][lane]);
+    const unsigned flip = VEC && !left ? 3u : 0u;
+    auto in_addr = [&](int t) {
+        return VEC ? in0 + (((unsigned)(t >> 2) & (IR / 4 - 1)) << 9) + ((((unsigned)t & 3u) ^ flip) << 2)
+                   : in0 + ((unsigned)(t & (IR - 1)) << 7);
+    };
 
     int hi = 0;      // steps < hi are staged and their copies complete
     int issued = 0;  // steps < issued have copies issued
     {
-        const int t1 = min(cmax, IR - T);
+        const int t1 = min(cmaxs, IR - T);
         stage(0, t1);
         issued = t1;
         cp_async_wait<0>();
@@ -204,7 +229,7 @@ __global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *
     int j = 0;
     bool fw = cnt > 0;
     if (fw) {  // leaf node: m^(z) = z - c has slope 1, lambda^-+ = c -+ w
-        const float c = sm->u.f.in[0][0][lane];
+        const float c = lds1(in_addr(0));
         const float w0 = HAS_W ? sm->u.f.in[NIN - 1][0][lane] : p.lam;
         PF = slot(S / 2 - 1);
         PB = PF + 256;
@@ -230,7 +255,7 @@ __global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *
         cp_async_wait<0>();
         hi = issued;
         {
-            const int t1 = min(cmax, jmin + IR - T);
+            const int t1 = min(cmaxs, stage_end(jmin + IR - T));
             if (t1 > issued) {
                 stage(issued, t1);
                 issued = t1;
@@ -239,7 +264,7 @@ __global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *
 #pragma unroll 1
         for (int it = 0; it < T; ++it) {
             const bool act = fw && j < hi;
-            const unsigned ia = in0 + ((unsigned)(j & (IR - 1)) << 7);
+            const unsigned ia = in_addr(j);
             const float c = lds1(ia);
             const float w = HAS_W ? lds1(ia + IR * 128) : p.lam;
             const float nw = -w;

@@ -215,6 +215,14 @@ def test_thread_kernel_ragged_long_and_overflow(thread_path):
     assert _lib.workspace_status(ws)[1] >= 20
     xr = oracle.chain_solve_batch(yy.ravel(), np.arange(65) * n, w=ww.ravel()).reshape(yy.shape)
     assert np.abs(x - xr).max() <= TOL
+    # one weight for every edge on aligned rows (staged 16 bytes at a time): every chain
+    # is the ramp, and every one overflows
+    yr = np.tile((-np.arange(n) / n).astype(np.float32), (32, 1))
+    ws2 = _lib.workspace(_lib.load().tv_chain_workspace_size(32, n), DEV, "overflow-thread-vec")
+    x = _lib.chain_prox(_gpu(yr), lam=n / 16.0, ws=ws2).cpu().numpy()
+    assert _lib.workspace_status(ws2)[1] >= 1
+    xr = oracle.chain_solve_batch(yr.ravel(), np.arange(33) * n, lam=n / 16.0).reshape(yr.shape)
+    assert np.abs(x - xr).max() <= TOL
 
 
 def test_thread_kernel_aligned_rows_stay_in_bounds(thread_path):
