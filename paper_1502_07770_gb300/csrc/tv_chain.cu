@@ -600,9 +600,7 @@ tv_status launch_flat(const ChainRowsP<HAS_W> &p, long long nchains, int max_len
 {
     const long long warps = (nchains + HW - 1) / HW;
     const size_t per_warp = sizeof(FlatSmem<HAS_W ? 2 : 1>);
-    auto kern = chain_flat_kernel<ChainRowsP<HAS_W>, false>;
-    if constexpr (!HAS_W)
-        if (p.vec) kern = chain_flat_kernel<ChainRowsP<HAS_W>, true>;
+    auto kern = p.vec ? chain_flat_kernel<ChainRowsP<HAS_W>, true> : chain_flat_kernel<ChainRowsP<HAS_W>, false>;
     tv_status st = check_cuda(
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * per_warp)),
         "cudaFuncSetAttribute");
@@ -835,13 +833,15 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     // chains of 64 nodes or more: two threads per chain (twice the warps, half the steps
     // each, and a 16-entry ring that keeps every warp of a full batch resident)
     // mode 2 (default): the fixed-shape update, except per-edge weights on chains shorter
-    // than kFlatMinLenW nodes, where the halves with the scans in step (mode 1) measured
-    // faster (the flat kernel stages every weight with its own 4-byte copy)
+    // than kFlatMinLenW nodes that are not staged 16 bytes at a time, where the halves with
+    // the scans in step (mode 1) measured faster (the flat kernel then stages every weight
+    // with its own 4-byte copy)
     int split = max_len >= kHalvesMinLen ? thread_split() : 0;
-    if (split == 2 && d_w && max_len < kFlatMinLenW) split = 1;
+    const bool vec_w = vec_ok(d_offsets, max_len, d_y, d_w, d_x);
+    if (split == 2 && d_w && max_len < kFlatMinLenW && !vec_w) split = 1;
     if (d_w) {
         ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,
-                           vec_ok(d_offsets, max_len, d_y, d_w, d_x), 0, &ws.hdr->status};
+                           vec_w, 0, &ws.hdr->status};
         if (split == 2) return launch_flat(p, num_chains, (int)max_len, ws.rec, ws.spill, ws.hdr, s);
         if (split == 1) return launch_halves(p, num_chains, (int)max_len, ws.rec, ws.spill, ws.hdr, s);
         return launch_batch(p, num_chains, ws.rec, nullptr, ws.spill, ws.hdr, s);

@@ -35,7 +35,10 @@
 // with one 16-byte copy into [slot / 4][lane][4]. Every lane reads a different chain, so a
 // copy instruction touches 32 sectors either way, and the 16-byte form needs a quarter of
 // the instructions and of the L1 wavefronts per node (a right half's 4 steps lie in memory
-// in reverse, read back with the element index flipped).
+// in reverse, read back with the element index flipped). Per-edge weights go the same way:
+// a right half's step s takes edge n-2-s, which sits where step s+1's node does, so its
+// lanes read the weight one staged step further on (and run a step behind the staged
+// range).
 //
 // Algorithm 2 roots chain k at node mid = n/2: lane l < 16 runs nodes 0..mid-1, lane l + 16
 // nodes n-1..mid+1; then the left lane solves the root from both messages (flat_root) and
@@ -136,12 +139,11 @@ __device__ __forceinline__ float flat_root(unsigned baseL, int FL, int BL, float
 
 // P: a row policy of tv_chain.cu (contiguous chains, CSR or uniform) with fields y, w, lam
 // and chain(); HAS_W = per-edge weights w. VEC: 16-byte staging (uniform chains, length a
-// multiple of 4, y 16-byte aligned; no per-edge weights).
+// multiple of 4, y and w 16-byte aligned).
 template <class P, bool VEC>
 __global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *hdr, int halfmax)
 {
     constexpr bool HAS_W = P::WI >= 0;
-    static_assert(!(VEC && HAS_W), "16-byte staging is for uniform weights only");
     constexpr int NIN = HAS_W ? 2 : 1;
     constexpr int S = FL_S, G = FL_G, IR = FL_IR, T = FL_T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -174,14 +176,22 @@ __global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *
     const float *wsrc = nullptr;
     if constexpr (HAS_W) wsrc = p.w + start + (left ? 0 : n - 2);
     const long long dir = left ? 1 : -1;
-    // VEC: steps 4q..4q+3 at in[0][4 (q % (IR/4)) ...] as [slot/4][lane][4]; a right half's
-    // chunk is nodes n-4-4q..n-1-4q in memory order (step 4q+e at element 3-e)
+    // VEC: steps 4q..4q+3 at in[a][4 (q % (IR/4)) ...] as [slot/4][lane][4]; a right half's
+    // chunk is nodes n-4-4q..n-1-4q in memory order (step 4q+e at element 3-e). A right
+    // half's weights are read one step further on (edge n-2-s at step s+1's place), so its
+    // chunks run to step cnt: nodes from mid-3 >= 0 (n = 4: the chunk of step 0 only).
     float *const in4 = &sm->u.f.in[0][0][0] + 4 * lane;
+    const int wlag = VEC && HAS_W && !left ? 1 : 0;
+    const int cnt_st = cnt > 0 ? cnt + wlag : 0;  // staged steps (none for an empty half)
     auto stage = [&](int t0, int t1) {  // steps [t0, t1), warp-uniform bounds
         if constexpr (VEC) {
             for (int t = t0; t < t1; t += 4)
-                if (t < cnt)
-                    cp_async16(in4 + ((t >> 2) & (IR / 4 - 1)) * (4 * WARP), left ? ysrc + t : ysrc - t - 3);
+                if (t < cnt_st) {
+                    const int o = ((t >> 2) & (IR / 4 - 1)) * (4 * WARP);
+                    cp_async16(in4 + o, left ? ysrc + t : ysrc - t - 3);
+                    if constexpr (HAS_W)
+                        cp_async16(in4 + IR * WARP + o, left ? wsrc + t : wsrc - t - 2);
+                }
         } else {
             for (int t = t0; t < t1; ++t) {
                 if (t < cnt) {
@@ -195,7 +205,7 @@ __global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *
     };
     // staged ranges end on 4-step boundaries for VEC (the chunk past a half's end stays in
     // its chain: node mid + 2 at most on the left, mid - 2 at least on the right)
-    const int cmaxs = VEC ? (cmax + 3) & ~3 : cmax;
+    const int cmaxs = VEC ? (cmax + (HAS_W ? 4 : 3)) & ~3 : cmax;
     auto stage_end = [&](int t) { return VEC ? t & ~3 : t; };
 
     // ---------------- message array ----------------
@@ -230,7 +240,7 @@ __global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *
     bool fw = cnt > 0;
     if (fw) {  // leaf node: m^(z) = z - c has slope 1, lambda^-+ = c -+ w
         const float c = lds1(in_addr(0));
-        const float w0 = HAS_W ? sm->u.f.in[NIN - 1][0][lane] : p.lam;
+        const float w0 = HAS_W ? lds1(in_addr(wlag) + IR * 128) : p.lam;
         PF = slot(S / 2 - 1);
         PB = PF + 256;
         fl = c - w0;
@@ -263,10 +273,10 @@ __global__ void chain_flat_kernel(P p_in, float2 *rec, float2 *spill, WsHeader *
         }
 #pragma unroll 1
         for (int it = 0; it < T; ++it) {
-            const bool act = fw && j < hi;
+            const bool act = fw && j + wlag < hi;
             const unsigned ia = in_addr(j);
             const float c = lds1(ia);
-            const float w = HAS_W ? lds1(ia + IR * 128) : p.lam;
+            const float w = HAS_W ? lds1((VEC ? in_addr(j + wlag) : ia) + IR * 128) : p.lam;
             const float nw = -w;
             const float uF0 = fresh ? fl - c - wprev : uF;
             const float uB0 = fresh ? bl - c + wprev : uB;
