@@ -402,8 +402,10 @@ tv_status tv_set_coop_split(int mode);
  * solution up to FP32 rounding. Read when a batched solve is planned. */
 tv_status tv_set_thread_split(int on);
 /* Whether tv2d_denoise, tv2d_denoise_lagrangian and tv2d_denoise_l1 launch the kernels
- * of their iterations with a programmatic dependency on the previous kernel of the
- * stream: 1 (the default) lets each kernel
+ * of their iterations, and the network's tensor-core convolutions and dual head
+ * (tv_net_conv3x3 on tensor path 2, tv_net_conv3x3_grouped, tv_net_first_layer with
+ * grouped output, tv_net_conv3x3_dual_head), with a programmatic dependency on the
+ * previous kernel of the stream: 1 (the default) lets each kernel
  * become resident while its predecessor finishes, and the kernel waits in hardware for
  * that predecessor's completion and memory before it reads anything; 0 launches them
  * in plain stream order. The results are identical either way; only the gaps between

@@ -503,6 +503,7 @@ __global__ void __launch_bounds__(256)
 // Blocks along x cover a row's columns; blocks along y walk the B*H rows.
 __global__ void __launch_bounds__(256) head_from_p(const float *p, long long rows, int H, int W, float *y)
 {
+    pdl_enter();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= W) return;
     int r = (int)(blockIdx.y % (unsigned)H);  // row within its image
@@ -1058,13 +1059,6 @@ __global__ void __launch_bounds__(TW_THREADS, 4)
     if (IO == TW_IMAGE)  // channels 2..15 of the image rows stay zero
         for (int t = tid; t < TW_NR * SLOT / 16; t += TW_THREADS)
             reinterpret_cast<uint4 *>(base)[t] = make_uint4(0u, 0u, 0u, 0u);
-    // weights: [dx][group][dy][co][8 channels]
-    for (int t = tid; t < 9 * KG * COUT; t += TW_THREADS) {
-        const int co = t % COUT, dy = (t / COUT) % 3, g = (t / (3 * COUT)) % KG, dx = t / (3 * COUT * KG);
-        *reinterpret_cast<uint4 *>(bbuf + (size_t)t * 16) =
-            *reinterpret_cast<const uint4 *>(Wt + ((long long)co * 9 + dy * 3 + dx) * CIN + g * 8);
-    }
-    if (tid < COUT) bias_s[tid] = bias ? bias[tid] : 0.f;
     if (tid == 0) {
         for (int q = 0; q < TW_NR; ++q) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(r_full(q)) : "memory");
@@ -1085,6 +1079,17 @@ __global__ void __launch_bounds__(TW_THREADS, 4)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
+    // Everything above is on chip. Launched with a programmatic dependency, the block got
+    // here while the previous kernel of the stream finished; every global read (weights
+    // included) comes after that kernel's completion.
+    pdl_enter();
+    // weights: [dx][group][dy][co][8 channels]
+    for (int t = tid; t < 9 * KG * COUT; t += TW_THREADS) {
+        const int co = t % COUT, dy = (t / COUT) % 3, g = (t / (3 * COUT)) % KG, dx = t / (3 * COUT * KG);
+        *reinterpret_cast<uint4 *>(bbuf + (size_t)t * 16) =
+            *reinterpret_cast<const uint4 *>(Wt + ((long long)co * 9 + dy * 3 + dx) * CIN + g * 8);
+    }
+    if (tid < COUT) bias_s[tid] = bias ? bias[tid] : 0.f;
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // weights for the MMAs
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -1486,9 +1491,13 @@ tv_status launch_conv_tw(const __nv_bfloat16 *X, int B, int H, int W, const __nv
     const long long L = std::max(1LL, std::min<long long>(H, (cols * H + slots - 1) / slots));
     const long long nchunks = cols * ((H + L - 1) / L);
     const long long blocks = std::min(nchunks, slots);
-    kern<<<(unsigned)blocks, TW_THREADS, smem, s>>>(tmap, tmap_tail, B, H, W, (int)L, Wt, bias, relu,
-                                                     pre_out, act_out, img, lam, p_out);
-    tv_status st = check_cuda(cudaGetLastError(), "conv launch");
+    // with a programmatic dependency on the previous kernel (tv_set_programmatic_launch):
+    // the block set-up above the kernel's pdl_enter overlaps that kernel's end
+    PdlScope pdl(true);
+    tv_status st = check_cuda(launch_k(kern, dim3((unsigned)blocks), dim3(TW_THREADS), smem, s, tmap,
+                                       tmap_tail, B, H, W, (int)L, Wt, bias, relu, pre_out, act_out,
+                                       img, lam, p_out),
+                              "conv launch");
     if (st == TV_OK) note_launch();
     return st;
 }
@@ -1864,8 +1873,11 @@ tv_status tv_net_conv3x3_dual_head(const void *d_x, int B, int H, int W, int cin
     if (st != TV_OK) return st;
     const long long rows = (long long)B * H;
     const dim3 hg((unsigned)((W + 255) / 256), (unsigned)std::min<long long>(rows, 65535));
-    head_from_p<<<hg, 256, 0, s>>>(d_p, rows, H, W, d_y);
-    st = check_cuda(cudaGetLastError(), "dual head");
+    {
+        PdlScope pdl(true);
+        st = check_cuda(launch_k(head_from_p, hg, dim3(256), 0, s, (const float *)d_p, rows, H, W, d_y),
+                        "dual head");
+    }
     if (st == TV_OK) note_launch();
     return st;
 }
