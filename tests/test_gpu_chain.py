@@ -143,6 +143,25 @@ def test_bench_size_sampled():
     assert torch.equal(xv[0], xv[-1])
 
 
+@pytest.mark.parametrize("B,n", [(65536, 1024), (262144, 256), (16384, 4096)])
+def test_sweep_sizes_per_edge_sampled(B, n):
+    """The benchmark's per-edge sweep batches (256 distinct chains of the chain workload,
+    edge weights U[0.05, 0.3], tiled to B chains; 16-byte staged rows on the default
+    path): sampled chains against the oracle, mean preservation on every chain."""
+    base = synth.chain_batch(256, n, seed0=2000)
+    wrow = np.random.default_rng(3).uniform(0.05, 0.3, size=(256, n)).astype(np.float32)
+    yg = _gpu(base).repeat(B // 256, 1)
+    wg = _gpu(wrow).repeat(B // 256, 1)
+    x = _lib.chain_prox(yg, wg)
+    sample = np.sort(np.random.default_rng(1).choice(B, size=48, replace=False))
+    xs = x[torch.from_numpy(sample).to(DEV)].cpu().numpy()
+    xr = oracle.chain_solve_batch(base[sample % 256].ravel(), np.arange(len(sample) + 1) * n,
+                                  w=wrow[sample % 256].ravel())
+    assert np.abs(xs.ravel() - xr).max() <= TOL
+    d = (x.double().sum(1) - yg.double().sum(1)).abs().max().item()
+    assert d < 5e-3
+
+
 @pytest.mark.parametrize("split", [0, 1, 2])
 def test_middle_rooted_chains(split):
     """Chains solved by one warp from one end (0), rooted at their middle node with the
