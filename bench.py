@@ -760,9 +760,11 @@ def main():
                                     "peak": bf16_peak[0], "unit": "TFLOP/s",
                                     "frac": net_flop / (net_ms * 1e-3) / 1e12 / bf16_peak[0],
                                     "peak_kind": bf16_peak[1],
-                                    "note": "first layer on the CUDA cores (two non-zero input "
-                                            "channels), the other three on tcgen05 fed by TMA in "
-                                            "the channel-group layout; FLOP count of the dense "
+                                    "note": "every layer on tcgen05 (the first from the image "
+                                            "rows built by two loader warps, the others fed by TMA "
+                                            "in the channel-group layout, the head in the last "
+                                            "layer's epilogue), launched with a programmatic "
+                                            "dependency; FLOP count of the dense "
                                             "16->32->32->32->16 network, including the zero-padded "
                                             "input channels and the 15 unused output channels"},
             "workload": "held-out seeds 20000.. at 512x512, lambda ~ U[0.05,0.3]; network "
