@@ -383,7 +383,11 @@ tv_status tv_set_batched_graph(int on);
 /*
  * Tuning knobs set by the autotuner (the paper has no counterpart): warps per block
  * of the batched phase kernels (1, 2, 4 or 8), and the largest chain batch solved
- * with one warp per chain instead of one thread per chain (0 restores the default).
+ * with one warp per chain instead of one thread per chain. 0 restores the defaults:
+ * 4096 chains, and 2048 for tv_chain_solve batches of uniform rows of at least 64
+ * nodes, a multiple of 4, with 16-byte aligned arrays (the one-thread-per-half kernel
+ * stages those 16 bytes at a time and is the faster one from about 2048 chains on).
+ * A value set here applies to every batch.
  */
 tv_status tv_set_batched_warps(int warps_per_block);
 tv_status tv_set_coop_max_chains(int64_t max_chains);

@@ -58,7 +58,9 @@ static long long g_prof_n[PK_N];
 void note_launch() { g_launches.fetch_add(1); }
 
 static std::atomic<long long> g_coop_max{kCoopMaxChainsDefault};
+static std::atomic<bool> g_coop_auto{true};
 long long coop_max_chains() { return g_coop_max.load(); }
+bool coop_max_auto() { return g_coop_auto.load(); }
 static std::atomic<int> g_coop_split{1};
 int coop_split() { return g_coop_split.load(); }
 static std::atomic<int> g_thread_split{2};
@@ -666,6 +668,7 @@ tv_status tv_set_coop_max_chains(int64_t max_chains)
         return TV_ERR_INVALID;
     }
     tvh::g_coop_max.store(max_chains == 0 ? kCoopMaxChainsDefault : max_chains);
+    tvh::g_coop_auto.store(max_chains == 0);
     return TV_OK;
 }
 
@@ -820,7 +823,12 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     cudaStream_t s = (cudaStream_t)stream;
     tv_status st = check_cuda(cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), s), "memset header");
     if (st != TV_OK) return st;
-    if (num_chains <= coop_max_chains()) {
+    const bool vec_w = vec_ok(d_offsets, max_len, d_y, d_w, d_x);
+    // by default, batches the fixed-shape thread kernel stages 16 bytes at a time leave
+    // the warp-per-chain kernel at a smaller batch size
+    const bool vec_flat = vec_w && max_len >= kHalvesMinLen && thread_split() == 2;
+    const long long coop_max = coop_max_auto() && vec_flat ? kCoopMaxChainsVec : coop_max_chains();
+    if (num_chains <= coop_max) {
         if (d_w) {
             CoopRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x, 0,
                               &ws.hdr->status};
@@ -837,7 +845,6 @@ tv_status tv_chain_solve(const float *d_y, const float *d_w, float lambda,
     // the scans in step (mode 1) measured faster (the flat kernel then stages every weight
     // with its own 4-byte copy)
     int split = max_len >= kHalvesMinLen ? thread_split() : 0;
-    const bool vec_w = vec_ok(d_offsets, max_len, d_y, d_w, d_x);
     if (split == 2 && d_w && max_len < kFlatMinLenW && !vec_w) split = 1;
     if (d_w) {
         ChainRowsP<true> p{d_y, d_w, 0.f, d_offsets, num_chains, (int)max_len, d_x,

@@ -133,6 +133,11 @@ tv_status launch_coop(const P &p, long long nchains, int max_len, float2 *rec, f
 // chain is then latency-bound, and a warp shortens its critical path); larger
 // batches run one thread per chain.
 constexpr long long kCoopMaxChainsDefault = 4096;
+// The same for tv_chain_solve batches that the fixed-shape thread kernel stages 16 bytes
+// at a time (uniform rows of >= 64 nodes, a multiple of 4, 16-byte aligned arrays):
+// measured crossover near 2048 chains at 256 and 1024 nodes.
+constexpr long long kCoopMaxChainsVec = 2048;
 long long coop_max_chains();  // tunable, see tv_set_coop_max_chains
+bool coop_max_auto();         // no value set (the defaults above apply)
 
 }  // namespace tvh

@@ -162,6 +162,21 @@ def test_sweep_sizes_per_edge_sampled(B, n):
     assert d < 5e-3
 
 
+@pytest.mark.parametrize("nc", [2048, 2049, 3000, 4096])
+def test_default_path_around_the_warp_kernel_threshold(nc):
+    """Batches of 16-byte aligned rows leave the warp-per-chain kernel above 2048 chains
+    by default (and other batches above 4096): both sides of that threshold, a ragged
+    last warp included, against the oracle on every chain."""
+    n = 128
+    y = synth.chain_batch(nc, n, seed0=300)
+    w = np.random.default_rng(nc).uniform(0.05, 0.3, size=y.shape).astype(np.float32)
+    off = np.arange(nc + 1) * n
+    x = _rows(y, lam=0.2)
+    assert np.abs(x.ravel() - oracle.chain_solve_batch(y.ravel(), off, lam=0.2)).max() <= TOL
+    x = _rows(y, w=w)
+    assert np.abs(x.ravel() - oracle.chain_solve_batch(y.ravel(), off, w=w.ravel())).max() <= TOL
+
+
 @pytest.mark.parametrize("split", [0, 1, 2])
 def test_middle_rooted_chains(split):
     """Chains solved by one warp from one end (0), rooted at their middle node with the
