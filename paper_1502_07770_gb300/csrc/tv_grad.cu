@@ -16,7 +16,9 @@
 // One warp per chain, 32 nodes per step: a forward segmented scan of (sum, count)
 // with a carry across steps yields each segment's mean at its last node; a reverse
 // segmented scan spreads it over the segment. The chain's g and the means stay in
-// shared memory when the chain fits, so each node is read and written once.
+// shared memory when the chain fits, so each node is read and written once. The loads
+// of kGradUnroll steps are issued together before their scans run one after another:
+// with one step's loads in flight per warp, the kernel was bound by memory latency.
 #include <cuda_runtime.h>
 
 #include "tv_launch.cuh"
@@ -28,6 +30,7 @@ namespace {
 
 constexpr int kGradWarps = 4;
 constexpr int kGradSmemNodes = 4096;  // g and segment means of one chain: 8 bytes per node
+constexpr int kGradUnroll = 4;        // steps whose loads are in flight together
 
 struct GradArgs {
     const float *x, *g;
@@ -69,75 +72,108 @@ __global__ void __launch_bounds__(kGradWarps * WARP) chain_vjp_kernel(GradArgs a
     const int nblk = (n + WARP - 1) / WARP;
 
     // ---- forward: segmented (sum, count); the mean lands on each segment's last node
+    constexpr int U = kGradUnroll;
     float carry_s = 0.f;
     int carry_c = 0;  // open segment entering this block
-    for (int b = 0; b < nblk; ++b) {
-        const int i = b * WARP + lane;
-        const bool in = i < n;
-        const float xi = in ? x[i] : 0.f;
-        const float xprev = (in && i > 0) ? x[i - 1] : 0.f;
-        const float xnext = (i + 1 < n) ? x[i + 1] : 0.f;
-        const bool head = in && (i == 0 || xi != xprev);
-        const bool tail = in && (i == n - 1 || xi != xnext);
-        float s = in ? g[i] : 0.f;
-        int c = in ? 1 : 0;
-        bool f = head;  // a segment starts within [block start, lane]
+    for (int b0 = 0; b0 < nblk; b0 += U) {
+        float xv[U], xp[U], xn[U], gv[U];
 #pragma unroll
-        for (int o = 1; o < WARP; o <<= 1) {
-            const float s2 = __shfl_up_sync(FULL, s, o);
-            const int c2 = __shfl_up_sync(FULL, c, o);
-            const bool f2 = __shfl_up_sync(FULL, (int)f, o);
-            if (lane >= o && !f) {
-                s += s2;
-                c += c2;
-                f = f2;
+        for (int q = 0; q < U; ++q) {
+            const int i = (b0 + q) * WARP + lane;
+            const bool in = i < n;
+            xv[q] = in ? x[i] : 0.f;
+            xp[q] = (in && i > 0) ? x[i - 1] : 0.f;
+            xn[q] = (i + 1 < n) ? x[i + 1] : 0.f;
+            gv[q] = in ? g[i] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int b = b0 + q;
+            if (b >= nblk) break;  // the same for every lane
+            const int i = b * WARP + lane;
+            const bool in = i < n;
+            const float xi = xv[q];
+            const float xprev = xp[q];
+            const float xnext = xn[q];
+            const bool head = in && (i == 0 || xi != xprev);
+            const bool tail = in && (i == n - 1 || xi != xnext);
+            float s = gv[q];
+            int c = in ? 1 : 0;
+            bool f = head;  // a segment starts within [block start, lane]
+    #pragma unroll
+            for (int o = 1; o < WARP; o <<= 1) {
+                const float s2 = __shfl_up_sync(FULL, s, o);
+                const int c2 = __shfl_up_sync(FULL, c, o);
+                const bool f2 = __shfl_up_sync(FULL, (int)f, o);
+                if (lane >= o && !f) {
+                    s += s2;
+                    c += c2;
+                    f = f2;
+                }
             }
-        }
-        if (!f) {
-            s += carry_s;
-            c += carry_c;
-        }
-        if (tail) mean[i] = s / (float)c;
-        carry_s = __shfl_sync(FULL, s, WARP - 1);
-        carry_c = __shfl_sync(FULL, c, WARP - 1);
-        // a segment that ended on the block's last node does not carry on
-        const bool last_tail = __shfl_sync(FULL, (int)tail, WARP - 1);
-        if (last_tail) {
-            carry_s = 0.f;
-            carry_c = 0;
+            if (!f) {
+                s += carry_s;
+                c += carry_c;
+            }
+            if (tail) mean[i] = s / (float)c;
+            carry_s = __shfl_sync(FULL, s, WARP - 1);
+            carry_c = __shfl_sync(FULL, c, WARP - 1);
+            // a segment that ended on the block's last node does not carry on
+            const bool last_tail = __shfl_sync(FULL, (int)tail, WARP - 1);
+            if (last_tail) {
+                carry_s = 0.f;
+                carry_c = 0;
+            }
         }
     }
     __syncwarp();
     // ---- backward: every node takes the mean stored at its segment's last node
+    // (a batch's tail means are read before any of its outputs is written: for a chain
+    // longer than the shared-memory records the means live in grad_y itself, each at its
+    // segment's last node, inside the step that owns that node)
     float carry_m = 0.f;
-    for (int b = nblk - 1; b >= 0; --b) {
-        const int i = b * WARP + lane;
-        const bool in = i < n;
-        const float xi = in ? x[i] : 0.f;
-        const float xnext = (i + 1 < n) ? x[i + 1] : 0.f;
-        const bool tail = in && (i == n - 1 || xi != xnext);
-        float m = tail ? mean[i] : 0.f;
-        bool f = tail;  // a segment ends within [lane, block end]
+    for (int b0 = nblk - 1; b0 >= 0; b0 -= U) {
+        float xv[U], xn[U], mv[U];
 #pragma unroll
-        for (int o = 1; o < WARP; o <<= 1) {
-            const float m2 = __shfl_down_sync(FULL, m, o);
-            const bool f2 = __shfl_down_sync(FULL, (int)f, o);
-            if (lane + o < WARP && !f) {
-                m = m2;
-                f = f2;
+        for (int q = 0; q < U; ++q) {
+            const int i = (b0 - q) * WARP + lane;
+            const bool in = b0 - q >= 0 && i < n;
+            xv[q] = in ? x[i] : 0.f;
+            xn[q] = (in && i + 1 < n) ? x[i + 1] : 0.f;
+            mv[q] = (in && (i == n - 1 || xv[q] != xn[q])) ? mean[i] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int b = b0 - q;
+            if (b < 0) break;  // the same for every lane
+            const int i = b * WARP + lane;
+            const bool in = i < n;
+            const float xi = xv[q];
+            const float xnext = xn[q];
+            const bool tail = in && (i == n - 1 || xi != xnext);
+            float m = mv[q];
+            bool f = tail;  // a segment ends within [lane, block end]
+    #pragma unroll
+            for (int o = 1; o < WARP; o <<= 1) {
+                const float m2 = __shfl_down_sync(FULL, m, o);
+                const bool f2 = __shfl_down_sync(FULL, (int)f, o);
+                if (lane + o < WARP && !f) {
+                    m = m2;
+                    f = f2;
+                }
             }
+            if (!f) m = carry_m;
+            const float mn = __shfl_down_sync(FULL, m, 1);
+            const float mright = (lane == WARP - 1) ? carry_m : mn;  // mean of node i+1
+            __syncwarp();
+            if (in) {
+                gy[i] = m;
+                // jump edge i -> i+1: sign * (mean left - mean right); fused edges: 0
+                if (a.gw && i + 1 < n)
+                    a.gw[start + i] = tail ? ((xnext > xi ? 1.f : -1.f) * (m - mright)) : 0.f;
+            }
+            carry_m = __shfl_sync(FULL, m, 0);
         }
-        if (!f) m = carry_m;
-        const float mn = __shfl_down_sync(FULL, m, 1);
-        const float mright = (lane == WARP - 1) ? carry_m : mn;  // mean of node i+1
-        __syncwarp();
-        if (in) {
-            gy[i] = m;
-            // jump edge i -> i+1: sign * (mean left - mean right); fused edges: 0
-            if (a.gw && i + 1 < n)
-                a.gw[start + i] = tail ? ((xnext > xi ? 1.f : -1.f) * (m - mright)) : 0.f;
-        }
-        carry_m = __shfl_sync(FULL, m, 0);
     }
 }
 

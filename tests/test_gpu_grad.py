@@ -118,6 +118,29 @@ def test_ragged_offsets_backward():
                                                                     fuse_tol=0.0), atol=1e-6)
 
 
+def test_long_chains_backward():
+    """A batch with chains longer than the shared-memory records (4096 nodes): every
+    chain's segment means then live in grad_y itself. Lengths around the 32-node step and
+    the 128-node batch of steps; dL/dy and dL/dw against the oracle's VJP on the GPU's
+    own segments."""
+    lengths = [5000, 4097, 129, 128, 127, 33, 1, 0, 4100, 97]
+    yv, off = synth.ragged_chain_batch(lengths, seed0=21)
+    rng = np.random.default_rng(4)
+    g = rng.normal(size=yv.shape).astype(np.float32)
+    w = rng.uniform(0.05, 0.3, size=yv.shape).astype(np.float32)
+    offd = _gpu(off)
+    x = _lib.chain_prox(_gpu(yv), _gpu(w), offsets=offd, max_len=max(lengths))
+    gy, gw = _lib.chain_prox_backward(x, _gpu(g), offsets=offd, max_len=max(lengths), with_w=True)
+    x_np, gy_np, gw_np = x.cpu().numpy(), gy.cpu().numpy(), gw.cpu().numpy()
+    for k in range(len(lengths)):
+        a, b = off[k], off[k + 1]
+        if b > a:
+            go, gwo = oracle.chain_vjp(x_np[a:b].astype(np.float64), g[a:b], fuse_tol=0.0,
+                                       with_w=True)
+            np.testing.assert_allclose(gy_np[a:b], go, atol=1e-5)
+            np.testing.assert_allclose(gw_np[a:b - 1], gwo, atol=1e-5)
+
+
 def test_autograd_function():
     y = torch.from_numpy(synth.chain_batch(16, 200, seed0=3)).to(DEV).requires_grad_(True)
     w = torch.full((16, 200), 0.1, device=DEV, requires_grad=True)
