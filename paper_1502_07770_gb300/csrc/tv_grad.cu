@@ -98,23 +98,18 @@ __global__ void __launch_bounds__(kGradWarps * WARP) chain_vjp_kernel(GradArgs a
             const bool head = in && (i == 0 || xi != xprev);
             const bool tail = in && (i == n - 1 || xi != xnext);
             float s = gv[q];
-            int c = in ? 1 : 0;
-            bool f = head;  // a segment starts within [block start, lane]
-    #pragma unroll
+            // the segment of node i starts at lane hs of this step (-1: before it); the
+            // sum over [max(hs, 0), lane] by the doubling scan, taking a partial sum only
+            // from a lane inside the segment; the count from the lane index
+            const unsigned hm = __ballot_sync(FULL, head) & (0xffffffffu >> (WARP - 1 - lane));
+            const int hs = hm ? WARP - 1 - __clz(hm) : -1;
+#pragma unroll
             for (int o = 1; o < WARP; o <<= 1) {
                 const float s2 = __shfl_up_sync(FULL, s, o);
-                const int c2 = __shfl_up_sync(FULL, c, o);
-                const bool f2 = __shfl_up_sync(FULL, (int)f, o);
-                if (lane >= o && !f) {
-                    s += s2;
-                    c += c2;
-                    f = f2;
-                }
+                if (lane - o >= (hs < 0 ? 0 : hs)) s += s2;
             }
-            if (!f) {
-                s += carry_s;
-                c += carry_c;
-            }
+            int c = hs < 0 ? lane + 1 + carry_c : lane - hs + 1;
+            if (hs < 0) s += carry_s;
             if (tail) mean[i] = s / (float)c;
             carry_s = __shfl_sync(FULL, s, WARP - 1);
             carry_c = __shfl_sync(FULL, c, WARP - 1);
@@ -151,18 +146,12 @@ __global__ void __launch_bounds__(kGradWarps * WARP) chain_vjp_kernel(GradArgs a
             const float xi = xv[q];
             const float xnext = xn[q];
             const bool tail = in && (i == n - 1 || xi != xnext);
-            float m = mv[q];
-            bool f = tail;  // a segment ends within [lane, block end]
-    #pragma unroll
-            for (int o = 1; o < WARP; o <<= 1) {
-                const float m2 = __shfl_down_sync(FULL, m, o);
-                const bool f2 = __shfl_down_sync(FULL, (int)f, o);
-                if (lane + o < WARP && !f) {
-                    m = m2;
-                    f = f2;
-                }
-            }
-            if (!f) m = carry_m;
+            // the mean sits at the segment's last node: lane te of this step, or (no tail
+            // at or after this lane) a later step, whose mean is the carry
+            const unsigned tm = __ballot_sync(FULL, tail) & (0xffffffffu << lane);
+            const int te = tm ? __ffs(tm) - 1 : lane;
+            float m = __shfl_sync(FULL, mv[q], te);
+            if (!tm) m = carry_m;
             const float mn = __shfl_down_sync(FULL, m, 1);
             const float mright = (lane == WARP - 1) ? carry_m : mn;  // mean of node i+1
             __syncwarp();
